@@ -1,0 +1,178 @@
+/*
+ * simrank.h - C ABI of libsimrank, incremental all-pairs SimRank on one GB300.
+ *
+ * Method: Yu, Lin, Zhang, McCann, "Dynamical SimRank Search on Time-Varying
+ * Networks".  SimRank here is Li et al.'s model (§3.1, Eq. 1):
+ *     S = C Q S Q^T + (1 - C) I,
+ * with Q the backward transition matrix, [Q]_{a,b} = 1/in-degree(a) when there
+ * is an edge b -> a.  An edge (i, j) means i -> j.  After an edge update the
+ * change of S solves a low-rank Sylvester equation (Thm 2, Eq. 13-14) whose
+ * K-truncated series is sum_k xi_k eta_k^T + eta_k xi_k^T (Eq. 16a, Alg 1).
+ *
+ * Conventions shared by every entry point:
+ *  - The caller owns every buffer it passes; the library copies what it needs
+ *    and never keeps a caller pointer after a call returns.
+ *  - Host pointers are plain CPU memory (pinned or not) unless an argument
+ *    says "device".  Device pointers are CUDA global memory on the current
+ *    device of the calling thread.
+ *  - Every call is ordered on the handle's CUDA stream (simrank_config.cuda_stream,
+ *    NULL = the legacy default stream).  A call that returns data in host
+ *    memory synchronises that stream before it returns.
+ *  - No C++ exception crosses this ABI.  Errors are reported by the status code;
+ *    simrank_last_error() gives a one-line message.  A call that fails
+ *    validation leaves the handle unchanged (all-or-nothing).
+ *  - A handle is not thread-safe: one thread at a time per handle.
+ *  - Node ids are int32 in [0, n_cur).  New nodes are named by the caller as
+ *    the next ids n_cur, n_cur + 1, ... (§6 Remark); they must be contiguous
+ *    and stay below n_capacity.
+ */
+#ifndef SIMRANK_H
+#define SIMRANK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SIMRANK_ABI_VERSION 1
+
+typedef struct simrank_ctx* simrank_t;
+
+typedef enum simrank_status {
+  SR_OK = 0,
+  SR_ERR_ARG = 1,            /* bad argument, bad id, non-contiguous new ids, bad config */
+  SR_ERR_EDGE_EXISTS = 2,    /* insertion of an existing edge, a self-loop, or a duplicate */
+  SR_ERR_EDGE_MISSING = 3,   /* deletion of an absent edge */
+  SR_ERR_CAPACITY = 4,       /* more nodes than n_capacity */
+  SR_ERR_OOM = 5,            /* device or host allocation failed */
+  SR_ERR_CUDA = 6,           /* a CUDA runtime call or kernel launch failed */
+  SR_ERR_TIMEOUT = 7,        /* a bounded device wait ran out (status word set by a kernel) */
+  SR_ERR_NOT_CONVERGED = 8,  /* batch initialisation did not reach init_tol in init_max_sweeps */
+  SR_ERR_UNSUPPORTED = 9     /* valid request that this build does not implement */
+} simrank_status;
+
+/* One edge update.  op = +1 inserts (src -> dst), op = -1 deletes it.
+ * weight is ignored by apply_updates (updates are on unweighted graphs, §3.1). */
+typedef struct simrank_update {
+  int32_t src;
+  int32_t dst;
+  int32_t op;
+  float weight;
+} simrank_update;
+
+/* Storage / apply modes. */
+enum { SR_MODE_DENSE = 0,        /* dense n_cap x n_cap S resident in HBM */
+       SR_MODE_COLUMN = 1 };     /* no dense S: columns on demand (§7, O(Kn + m) memory) */
+enum { SR_APPLY_UNIT = 0,        /* each update in order, one rank-one update each (Alg 1/2) */
+       SR_APPLY_SINK_BLOCKS = 1, /* net update + similar-sink blocks, sequentially (§8, Alg 6, Table 2) */
+       SR_APPLY_ONE_SHOT = 2 };  /* whole batch as one rank-2r update (proof of Thm 2, Eq. 23-28) */
+enum { SR_SUPDATE_FUSED = 0,     /* one read-modify-write pass of S per update: S += Xi H^T + H Xi^T */
+       SR_SUPDATE_PLAIN = 1 };   /* K+1 passes, one rank-2 term xi_k eta_k^T + eta_k xi_k^T each (Alg 1 as printed) */
+
+typedef struct simrank_config {
+  double C;               /* damping factor, 0 < C < 1 (Eq. 1) */
+  int32_t K;              /* iterations of the xi/eta recurrence (Eq. 16a); terms k = 0..K; 0 <= K <= 1023 */
+  int32_t s_precision;    /* 32: S stored in FP32; 64: S stored in FP64.  Vectors are FP64 in both. */
+  int32_t mode;           /* SR_MODE_DENSE or SR_MODE_COLUMN */
+  int32_t n_capacity;     /* maximum number of nodes, including nodes added later; >= n at init */
+  int32_t aff;            /* 1: skip S tiles outside the affected area of Thm 4; 0: touch every tile */
+  int32_t apply;          /* SR_APPLY_* */
+  int32_t s_update;       /* SR_SUPDATE_* */
+  int32_t tc;             /* one-shot batch form: 0 = CUDA-core FFMA update, 1 = tensor cores (3xTF32 split) */
+  int32_t init_max_sweeps;/* cap on Jacobi sweeps of Eq. 1 at init / re-anchor */
+  double init_tol;        /* init stops when a sweep changes S by less than this (max-abs) */
+  int32_t profile;        /* 1: time every S-update launch with CUDA events (simrank_get_profile) */
+  int32_t reserved0;
+  int64_t timeout_iters;  /* bound on any device spin-wait (0 = library default) */
+  void* cuda_stream;      /* cudaStream_t for all work of this handle; NULL = default stream */
+  int32_t reserved[8];
+} simrank_config;
+
+/* Fills *cfg with defaults: C = 0.6, K = 15, s_precision = 32, dense, aff = 1,
+ * unit apply, fused update, init_tol = 1e-12 (FP64) / 1e-7 (FP32). */
+simrank_status simrank_default_config(simrank_config* cfg);
+
+/* Creates a handle for the graph (src[e] -> dst[e]), e < m, on n nodes.
+ * Host pointers.  weight (nullable) gives per-edge weights w_e > 0 for the
+ * weighted Q (row a normalised by its total in-weight); NULL means 1/in-degree.
+ * S0 (nullable, host, n x n row-major, FP32 or FP64 per cfg->s_precision) is the
+ * old SimRank matrix; NULL computes it by Jacobi sweeps of Eq. 1 on the GPU
+ * until the max-abs change is below cfg->init_tol.  Self-loops and duplicate
+ * edges return SR_ERR_EDGE_EXISTS.  Nodes n..n_capacity-1 are pre-allocated as
+ * isolated nodes (S_xx = 1 - C, a valid fixed point) and become nodes when
+ * an update names them.  On success *out owns device memory until simrank_destroy. */
+simrank_status simrank_init(const simrank_config* cfg, int32_t n, int64_t m,
+                            const int32_t* src, const int32_t* dst, const float* weight,
+                            const void* S0, simrank_t* out);
+
+/* Applies count updates (host array) and brings S to the new graph
+ * (Alg 1 / Alg 2 per update, §6 new-node cases C1-C3 through pre-allocated
+ * isolated nodes, §8 batches).  All updates are validated first, in order;
+ * if any is invalid nothing is applied.  Asynchronous on the handle's stream:
+ * the host returns once the work is queued. */
+simrank_status simrank_apply_updates(simrank_t h, const simrank_update* u, int64_t count);
+
+/* Copies columns cols[0..ncols) of the current S (n_cur rows each) to out,
+ * column-major: out[c * n_cur + a] = S[a, cols[c]].  out is device memory if
+ * out_on_device != 0, else host memory (the call then synchronises).  out_fp64
+ * selects double (1) or float (0) output.  In SR_MODE_COLUMN the columns are
+ * computed from the graph history (Procedure 1 + Eq. 70-71). */
+simrank_status simrank_columns(simrank_t h, const int32_t* cols, int32_t ncols, void* out,
+                               int32_t out_on_device, int32_t out_fp64);
+
+/* Current number of nodes n_cur (<= n_capacity). */
+int32_t simrank_num_nodes(simrank_t h);
+
+/* Message of the last failed call on h (or of the last failed simrank_init when
+ * h is NULL).  The string lives until the next call on h. */
+const char* simrank_last_error(simrank_t h);
+
+/* Waits for all work queued on the handle's stream; returns SR_ERR_CUDA with a
+ * message if a kernel failed, SR_ERR_TIMEOUT if a bounded wait ran out. */
+simrank_status simrank_sync(simrank_t h);
+
+/* Releases all memory of h.  NULL is ignored. */
+void simrank_destroy(simrank_t h);
+
+/* Cumulative counters since init (synchronises). */
+typedef struct simrank_stats {
+  int64_t updates;          /* updates accepted by apply_updates */
+  int64_t rank_one_updates; /* rank-one (sink-block / unit) updates run on the GPU */
+  int64_t tiles_total;      /* 128 x 128 S tiles that an unpruned update would touch */
+  int64_t tiles_touched;    /* S tiles actually read and written */
+  int64_t s_bytes;          /* algorithmic bytes of S read + written by S-update launches */
+  int64_t panel_bytes;      /* algorithmic bytes of xi/eta panels read by S-update launches */
+  int64_t s_update_launches;
+  int64_t kernel_launches;  /* all libsimrank kernel launches on the handle's stream */
+  double s_update_ms;       /* summed CUDA-event time of S-update launches (profile = 1 only) */
+  double init_residual;     /* max-abs change of the last Jacobi sweep at init / re-anchor */
+  int32_t init_sweeps;
+  int32_t reserved[7];
+} simrank_stats;
+simrank_status simrank_get_stats(simrank_t h, simrank_stats* out);
+
+/* Re-anchors S to the fixed point of Eq. 1 on the current graph by up to
+ * `sweeps` Jacobi sweeps started from the current S (drift correction after
+ * long FP32 update streams).  *max_change (nullable) receives the max-abs
+ * change of the last sweep.  Synchronises. */
+simrank_status simrank_reanchor(simrank_t h, int32_t sweeps, double* max_change);
+
+/* Host-only planning of one batch (no GPU work, usable without a device):
+ * net update by edge counts, split by sign, similar-sink partition (§8,
+ * Alg 6), deletion blocks by ascending sink, then for each sink ascending its
+ * old-source sub-block followed by its new-source sub-block.  n_old is |V|
+ * before the batch.  Writes up to max_blocks blocks: block b covers
+ * sources block_src[block_off[b] .. block_off[b+1]) into sink block_sink[b]
+ * with block_op[b] = +1/-1.  *nblocks receives the number of blocks;
+ * block_off needs max_blocks + 1 entries and block_src `count` entries.
+ * Returns SR_ERR_ARG for a net count outside {-1, 0, +1}. */
+simrank_status simrank_plan_batch(const simrank_update* u, int64_t count, int32_t n_old,
+                                  int32_t max_blocks, int32_t* nblocks, int32_t* block_sink,
+                                  int32_t* block_op, int64_t* block_off, int32_t* block_src);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SIMRANK_H */

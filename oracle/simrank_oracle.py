@@ -51,6 +51,13 @@ def transition_matrix(n, src, dst, weight=None, sparse=False):
     return Q.tocsr() if sparse else Q.toarray()
 
 
+def _row(Q, j):
+    """Row j of a dense or SciPy-sparse matrix as a dense 1-D array."""
+    if sp.issparse(Q):
+        return np.asarray(Q[j, :].toarray()).ravel()
+    return np.asarray(Q[j, :]).ravel()
+
+
 def in_degrees(n, dst):
     """In-degree vector d (Table 1)."""
     return np.bincount(np.asarray(dst, np.int64), minlength=n).astype(np.int64)
@@ -154,7 +161,7 @@ def rank_one_factors(Q, d, j, sources, op):
         eI[i] += 1.0
     ej = np.zeros(n)
     ej[j] = 1.0
-    qj = np.asarray(Q[j, :]).ravel()
+    qj = _row(Q, j)
     if op == INSERT:
         if d == 0:
             return ej.copy(), eI / delta
@@ -638,7 +645,7 @@ def one_shot_batch(n_final, src_old, dst_old, src_new, dst_new, S, C, K):
 # Column-wise update (Alg 7, Inc-SR-All-P)
 # ----------------------------------------------------------------------------
 
-def inc_sr_all_p(n, src, dst, S_col_x, x, updates, C, K):
+def inc_sr_all_p(n, src, dst, S_col_x, x, updates, C, K, K_old=None):
     """Alg 7 (Inc-SR-All-P): column x of S updated through a list of unit
     updates between existing or new nodes, using O(Kn + m) memory.
 
@@ -650,7 +657,10 @@ def inc_sr_all_p(n, src, dst, S_col_x, x, updates, C, K):
     (j gains the in-neighbour i); deletions of existing edges are handled
     like C0 with Thm 9's u, v, gamma (the algorithm prints only insertions).
     New nodes take the next free id, as the caller names them.
+    ``K_old`` (default K, as in Alg 7) is the truncation of PartialSim for
+    the old columns; a large K_old gives the converged old columns.
     """
+    K_old = K if K_old is None else K_old
     edges = set(zip(np.asarray(src).tolist(), np.asarray(dst).tolist()))
     n_cur = n
     col = np.array(S_col_x, np.float64).copy()
@@ -662,13 +672,13 @@ def inc_sr_all_p(n, src, dst, S_col_x, x, updates, C, K):
     for i, j, op in updates:
         i, j, op = int(i), int(j), int(op)
         s_arr, d_arr = arrays()
-        Q = transition_matrix(n_cur, s_arr, d_arr)
+        Q = transition_matrix(n_cur, s_arr, d_arr, sparse=True)
         i_in, j_in = i < n_cur, j < n_cur
         if i_in and j_in and x >= n_cur:
             pass  # column x is not a node yet: nothing to update
         elif i_in and j_in:
-            Si = partial_sim(Q, i, K, C)
-            Sj = partial_sim(Q, j, K, C)
+            Si = partial_sim(Q, i, K_old, C)
+            Sj = partial_sim(Q, j, K_old, C)
             d = int(in_degrees(n_cur, d_arr)[j])
             w = Q @ Si
             u, v = rank_one_factors(Q, d, j, [i], op)
@@ -685,7 +695,7 @@ def inc_sr_all_p(n, src, dst, S_col_x, x, updates, C, K):
                 n_acc = xi[x] * eta + n_acc
             col = col + m_acc + n_acc
         elif i_in and not j_in:  # C1
-            Si = partial_sim(Q, i, K, C)
+            Si = partial_sim(Q, i, K_old, C)
             y = C * (Q @ Si)
             if x == j:
                 col = np.concatenate([y, [C * Si[i] + 1.0 - C]])
@@ -700,12 +710,12 @@ def inc_sr_all_p(n, src, dst, S_col_x, x, updates, C, K):
             elif x >= n_cur:
                 col = np.concatenate([col, [0.0]])
             else:
-                Sj = partial_sim(Q, j, K, C)
+                Sj = partial_sim(Q, j, K_old, C)
                 d = int(in_degrees(n_cur, d_arr)[j])
                 ej = np.zeros(n_cur)
                 ej[j] = 1.0
                 z = ((Sj[j] - (1.0 - C) ** 2) / (2.0 * C * (d + 1)) + (1.0 - C) / C) * ej - Sj / C
-                qj = Q[j, :]
+                qj = _row(Q, j)
                 xi = ej.copy()
                 eta = z.copy()
                 m_acc = z[x] * ej

@@ -1,0 +1,811 @@
+// C ABI of libsimrank and its host engine: validation, graph bookkeeping
+// (mirrored CSR/CSC with per-row slack, exact integer patches), batch
+// planning (§8 net update and similar-sink partition), and the stream-ordered
+// launch sequence of each rank-one update.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <unordered_map>
+#include <unordered_set>
+#include <utility>
+#include <vector>
+
+#include "sr_internal.h"
+
+using namespace sr;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct simrank_ctx {
+  simrank_config cfg{};
+  cudaStream_t st = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  int n_cur = 0, n_cap = 0, n_pad = 0, nT_cap = 0, K1 = 0;
+  int64_t ld = 0;
+  bool weighted = false;
+  // host mirror of the graph
+  HostAdj hin, hout;
+  std::unordered_set<uint64_t> edges;
+  // device graph
+  DevAdj din, dout;
+  float* d_in_w = nullptr;
+  double* d_wsum = nullptr;
+  // dense S and panels
+  void* S = nullptr;
+  double* P64 = nullptr;
+  float* P32 = nullptr;
+  uint64_t* mXi = nullptr;
+  uint64_t* mEta = nullptr;
+  uint32_t* tiles = nullptr;
+  int* ntiles = nullptr;
+  double* sI = nullptr;
+  double* sJ = nullptr;
+  double* scal = nullptr;
+  int64_t* counters = nullptr;
+  unsigned long long* diffbits = nullptr;
+  // per-call staging
+  int32_t* d_srcs = nullptr;
+  int64_t srcs_cap = 0;
+  PatchOp* d_ops = nullptr;
+  int64_t ops_cap = 0;
+  int32_t* d_cols = nullptr;
+  int64_t cols_cap = 0;
+  // profiling
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+  size_t events_used = 0;
+  double prof_ms = 0.0;
+  int64_t prof_launches = 0;
+  int64_t launches = 0;  // every kernel launch of this handle
+  // stats
+  simrank_stats stats{};
+  std::string err;
+};
+
+namespace {
+
+simrank_status fail(simrank_ctx* h, simrank_status s, const std::string& msg) {
+  if (h)
+    h->err = msg;
+  else
+    g_init_error = msg;
+  return s;
+}
+
+#define CUDA_TRY(h, call)                                                                  \
+  do {                                                                                     \
+    cudaError_t e__ = (call);                                                              \
+    if (e__ != cudaSuccess)                                                                \
+      return fail((h), e__ == cudaErrorMemoryAllocation ? SR_ERR_OOM : SR_ERR_CUDA,        \
+                  std::string(#call) + ": " + cudaGetErrorString(e__));                    \
+  } while (0)
+
+#define LAUNCH_CHECK(h)                                                                    \
+  do {                                                                                     \
+    cudaError_t e__ = cudaGetLastError();                                                  \
+    if (e__ != cudaSuccess)                                                                \
+      return fail((h), SR_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e__)); \
+  } while (0)
+
+inline uint64_t ekey(int32_t s, int32_t d) { return ((uint64_t)(uint32_t)s << 32) | (uint32_t)d; }
+
+inline int elem_bytes(const simrank_ctx* h) { return h->cfg.s_precision == 64 ? 8 : 4; }
+
+template <typename T>
+cudaError_t dev_alloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T));
+}
+
+// Builds adjacency lists (rows indexed by `key`, entries `val`) with per-row slack.
+void build_adj(HostAdj& A, int n_rows, const std::vector<std::vector<int32_t>>& rows) {
+  A.start.assign(n_rows, 0);
+  A.len.assign(n_rows, 0);
+  A.cap.assign(n_rows, 0);
+  int64_t used = 0;
+  for (int a = 0; a < n_rows; ++a) {
+    const int len = (int)rows[a].size();
+    const int cap = len + std::max(4, len / 4);
+    A.start[a] = used;
+    A.len[a] = len;
+    A.cap[a] = cap;
+    used += cap;
+  }
+  A.pool.assign((size_t)(used + used / 4 + 65536), 0);
+  for (int a = 0; a < n_rows; ++a)
+    std::copy(rows[a].begin(), rows[a].end(), A.pool.begin() + A.start[a]);
+  A.used = used;
+}
+
+// Appends `v` to row r of the mirror, recording the device patch ops.
+void adj_append(HostAdj& A, int r, int32_t v, std::vector<PatchOp>& ops, bool is_in) {
+  if (A.len[r] == A.cap[r]) {
+    const int new_cap = 2 * A.len[r] + 4;
+    const int64_t ns = A.used;
+    if ((int64_t)A.pool.size() < ns + new_cap) A.pool.resize((size_t)(2 * (ns + new_cap)), 0);
+    std::copy(A.pool.begin() + A.start[r], A.pool.begin() + A.start[r] + A.len[r],
+              A.pool.begin() + ns);
+    ops.push_back({is_in ? PK_IN_COPY : PK_OUT_COPY, A.len[r], ns, A.start[r]});
+    ops.push_back({is_in ? PK_IN_START : PK_OUT_START, 0, (int64_t)r, ns});
+    A.start[r] = ns;
+    A.cap[r] = new_cap;
+    A.used += new_cap;
+  }
+  const int64_t pos = A.start[r] + A.len[r];
+  A.pool[pos] = v;
+  A.len[r] += 1;
+  ops.push_back({is_in ? PK_IN_COL : PK_OUT_COL, v, pos, 0});
+  ops.push_back({is_in ? PK_IN_LEN : PK_OUT_LEN, A.len[r], (int64_t)r, 0});
+}
+
+// Removes `v` from row r (swap with the last entry), recording the patch ops.
+void adj_remove(HostAdj& A, int r, int32_t v, std::vector<PatchOp>& ops, bool is_in) {
+  const int64_t s = A.start[r];
+  const int len = A.len[r];
+  int p = -1;
+  for (int e = 0; e < len; ++e)
+    if (A.pool[s + e] == v) {
+      p = e;
+      break;
+    }
+  if (p < 0) return;  // validated earlier; cannot happen
+  const int last = len - 1;
+  if (p != last) {
+    A.pool[s + p] = A.pool[s + last];
+    ops.push_back({is_in ? PK_IN_COL : PK_OUT_COL, A.pool[s + p], s + p, 0});
+  }
+  A.len[r] = last;
+  ops.push_back({is_in ? PK_IN_LEN : PK_OUT_LEN, last, (int64_t)r, 0});
+}
+
+// ---------------------------------------------------------------------------
+// Batch planning (§8): net update, sign split, similar-sink partition.
+// ---------------------------------------------------------------------------
+struct Block {
+  int32_t sink;
+  int32_t op;
+  std::vector<int32_t> srcs;
+};
+
+simrank_status plan_blocks(const simrank_update* u, int64_t count, int32_t n_old,
+                           std::vector<Block>& out, std::string& msg) {
+  std::unordered_map<uint64_t, int> cnt;
+  std::vector<uint64_t> order;
+  cnt.reserve((size_t)count * 2);
+  for (int64_t t = 0; t < count; ++t) {
+    const uint64_t k = ekey(u[t].src, u[t].dst);
+    auto it = cnt.find(k);
+    if (it == cnt.end()) {
+      cnt.emplace(k, 0);
+      order.push_back(k);
+    }
+    cnt[k] += (u[t].op > 0) ? 1 : -1;
+  }
+  std::map<int32_t, std::vector<int32_t>> plus, minus;
+  for (uint64_t k : order) {
+    const int c = cnt[k];
+    const int32_t s = (int32_t)(k >> 32), d = (int32_t)(k & 0xffffffffu);
+    if (c == 1)
+      plus[d].push_back(s);
+    else if (c == -1)
+      minus[d].push_back(s);
+    else if (c != 0) {
+      msg = "net count " + std::to_string(c) + " for edge (" + std::to_string(s) + "," +
+            std::to_string(d) + ")";
+      return SR_ERR_ARG;
+    }
+  }
+  out.clear();
+  for (auto& kv : minus) {
+    std::vector<int32_t> s = kv.second;
+    std::sort(s.begin(), s.end());
+    out.push_back({kv.first, -1, s});
+  }
+  // Insertion sub-blocks: per sink (ascending) the sources in the old V, then
+  // the new ones.  A sub-block is split again by the node set at the time it
+  // runs (sources that an earlier sub-block of this batch created come first),
+  // so every block is one of the cases C0..C3 of §8 when it is applied.
+  std::unordered_set<int32_t> created;
+  auto exists = [&](int32_t x) { return x < n_old || created.count(x) != 0; };
+  for (auto& kv : plus) {
+    std::vector<int32_t> olds, news;
+    for (int32_t s : kv.second) (s < n_old ? olds : news).push_back(s);
+    std::sort(olds.begin(), olds.end());
+    std::sort(news.begin(), news.end());
+    for (const std::vector<int32_t>* sub : {&olds, &news}) {
+      if (sub->empty()) continue;
+      std::vector<int32_t> have, fresh;
+      for (int32_t s : *sub) (exists(s) ? have : fresh).push_back(s);
+      if (!have.empty()) out.push_back({kv.first, +1, have});
+      if (!fresh.empty()) out.push_back({kv.first, +1, fresh});
+      for (int32_t s : *sub) created.insert(s);
+      created.insert(kv.first);
+    }
+  }
+  return SR_OK;
+}
+
+// Sequential validation of a batch against the current graph (no mutation).
+simrank_status validate(simrank_ctx* h, const simrank_update* u, int64_t count, int* n_after) {
+  std::unordered_map<uint64_t, char> overlay;
+  int n_sim = h->n_cur;
+  for (int64_t t = 0; t < count; ++t) {
+    const int32_t s = u[t].src, d = u[t].dst;
+    const std::string at = " (update " + std::to_string(t) + ": " + std::to_string(s) + " -> " +
+                           std::to_string(d) + ")";
+    if (u[t].op != 1 && u[t].op != -1) return fail(h, SR_ERR_ARG, "op must be +1 or -1" + at);
+    if (s < 0 || d < 0) return fail(h, SR_ERR_ARG, "negative node id" + at);
+    if (s == d) return fail(h, SR_ERR_EDGE_EXISTS, "self-loop" + at);
+    int lo = std::min(s, d), hi = std::max(s, d);
+    for (int x : {lo, hi}) {
+      if (x >= n_sim) {
+        if (x != n_sim) return fail(h, SR_ERR_ARG, "new node ids must be contiguous" + at);
+        if (u[t].op < 0) return fail(h, SR_ERR_EDGE_MISSING, "deleting an absent edge" + at);
+        if (n_sim + 1 > h->n_cap) return fail(h, SR_ERR_CAPACITY, "n_capacity exceeded" + at);
+        ++n_sim;
+      }
+    }
+    const uint64_t k = ekey(s, d);
+    bool present;
+    auto it = overlay.find(k);
+    if (it != overlay.end())
+      present = it->second != 0;
+    else
+      present = h->edges.count(k) != 0;
+    if (u[t].op > 0) {
+      if (present) return fail(h, SR_ERR_EDGE_EXISTS, "inserting an existing edge" + at);
+      overlay[k] = 1;
+    } else {
+      if (!present) return fail(h, SR_ERR_EDGE_MISSING, "deleting an absent edge" + at);
+      overlay[k] = 0;
+    }
+  }
+  *n_after = n_sim;
+  return SR_OK;
+}
+
+simrank_status ensure_dev_capacity(simrank_ctx* h, int64_t nsrc, int64_t nops) {
+  if (nsrc > h->srcs_cap) {
+    if (h->d_srcs) cudaFree(h->d_srcs);
+    h->srcs_cap = std::max<int64_t>(nsrc, 2 * h->srcs_cap);
+    CUDA_TRY(h, dev_alloc(&h->d_srcs, (size_t)h->srcs_cap));
+  }
+  if (nops > h->ops_cap) {
+    if (h->d_ops) cudaFree(h->d_ops);
+    h->ops_cap = std::max<int64_t>(nops, 2 * h->ops_cap);
+    CUDA_TRY(h, dev_alloc(&h->d_ops, (size_t)h->ops_cap));
+  }
+  return SR_OK;
+}
+
+// Grows a device column pool to hold the host mirror's pool (rare).
+simrank_status grow_pool(simrank_ctx* h, DevAdj& D, const HostAdj& A) {
+  if (A.used <= D.pool_cap) return SR_OK;
+  const int64_t cap = std::max<int64_t>((int64_t)A.pool.size(), A.used * 2);
+  int32_t* np = nullptr;
+  CUDA_TRY(h, dev_alloc(&np, (size_t)cap));
+  CUDA_TRY(h, cudaMemcpyAsync(np, D.col, (size_t)D.pool_cap * sizeof(int32_t),
+                              cudaMemcpyDeviceToDevice, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  cudaFree(D.col);
+  D.col = np;
+  D.pool_cap = cap;
+  return SR_OK;
+}
+
+std::pair<cudaEvent_t, cudaEvent_t>* next_event_pair(simrank_ctx* h) {
+  if (h->events_used == h->events.size()) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return nullptr;
+    if (cudaEventCreate(&b) != cudaSuccess) return nullptr;
+    h->events.push_back({a, b});
+  }
+  return &h->events[h->events_used++];
+}
+
+void harvest_events(simrank_ctx* h) {
+  for (size_t e = 0; e < h->events_used; ++e) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->events[e].first, h->events[e].second) == cudaSuccess)
+      h->prof_ms += ms;
+  }
+  h->events_used = 0;
+}
+
+void* panel_for_s(simrank_ctx* h) {
+  return h->cfg.s_precision == 64 ? (void*)h->P64 : (void*)h->P32;
+}
+
+simrank_status s_update_launch(simrank_ctx* h, int k0, int k1, int use_masks) {
+  std::pair<cudaEvent_t, cudaEvent_t>* ev = nullptr;
+  if (h->cfg.profile) {
+    if (h->events_used >= 4096) {
+      CUDA_TRY(h, cudaStreamSynchronize(h->st));
+      harvest_events(h);
+    }
+    ev = next_event_pair(h);
+    if (!ev) return fail(h, SR_ERR_CUDA, "cudaEventCreate failed");
+    CUDA_TRY(h, cudaEventRecord(ev->first, h->st));
+  }
+  launch_s_update(h->S, h->cfg.s_precision, h->ld, panel_for_s(h), h->K1, h->tiles, h->ntiles,
+                  h->mXi, h->mEta, k0, k1, use_masks, h->n_cur, h->counters,
+                  s_update_grid(h->cfg.s_precision, h->num_sms), h->st);
+  LAUNCH_CHECK(h);
+  if (ev) CUDA_TRY(h, cudaEventRecord(ev->second, h->st));
+  h->prof_launches += 1;
+  h->launches += 1;
+  return SR_OK;
+}
+
+// One rank-one update of the current S for the sink block (srcs at d_srcs +
+// src_off, delta of them) into sink j, op = +1/-1, old in-degree d_j; the
+// graph patch ops [op_begin, op_end) turn the old graph into the new one.
+simrank_status run_rank_one(simrank_ctx* h, int64_t src_off, int delta, int j, int op, int d_j,
+                            int64_t op_begin, int64_t op_end) {
+  const int nT = (h->n_cur + PT - 1) / PT;
+  const double C = h->cfg.C;
+  launch_gather_rows(h->S, h->cfg.s_precision, h->ld, h->d_srcs + src_off, delta, j, nT * PT,
+                     h->sI, h->sJ, h->scal, h->st);
+  launch_gamma(h->din, h->sI, h->sJ, h->scal, j, delta, op, d_j, C, nT, h->K1, h->P64,
+               h->cfg.s_precision == 64 ? nullptr : h->P32, h->mXi, h->mEta, h->st);
+  launch_patch(h->d_ops, op_begin, op_end, h->din, h->dout, h->st);
+  for (int k = 0; k < h->cfg.K; ++k)
+    launch_chain_step(h->din, k, C, nT, h->K1, h->P64,
+                      h->cfg.s_precision == 64 ? nullptr : h->P32, h->mXi, h->mEta, h->st);
+  LAUNCH_CHECK(h);
+  h->launches += 2 + (op_end > op_begin ? 1 : 0) + h->cfg.K;
+  CUDA_TRY(h, cudaMemsetAsync(h->ntiles, 0, sizeof(int), h->st));
+  const bool plain = h->cfg.s_update == SR_SUPDATE_PLAIN;
+  launch_tile_list(h->mXi, h->mEta, nT, (plain || !h->cfg.aff) ? 0 : 1, h->tiles, h->ntiles, h->st);
+  LAUNCH_CHECK(h);
+  h->launches += 1;
+  simrank_status s;
+  if (plain) {
+    for (int k = 0; k < h->K1; ++k)
+      if ((s = s_update_launch(h, k, k + 1, 0)) != SR_OK) return s;
+  } else {
+    if ((s = s_update_launch(h, 0, h->K1, h->cfg.aff ? 1 : 0)) != SR_OK) return s;
+  }
+  h->stats.rank_one_updates += 1;
+  h->stats.tiles_total += (int64_t)nT * (nT + 1) / 2;
+  return SR_OK;
+}
+
+// Jacobi sweeps of Eq. 1 starting from the current S, in FP64 work buffers
+// when three of them fit in `fp64_budget` bytes (or S itself is FP64), else
+// in FP32 storage with FP64 accumulation.  Stops when a sweep changes S by
+// less than `tol` (max-abs) or after max_sweeps; S is symmetrised at the end.
+simrank_status jacobi_sweeps(simrank_ctx* h, int max_sweeps, double tol, double* last_diff,
+                             int* sweeps_done) {
+  const int sp = h->cfg.s_precision;
+  const size_t elems = (size_t)h->n_pad * h->ld;
+  const size_t fp64_budget = (size_t)48 << 30;
+  const int wp = (sp == 64 || 3 * elems * 8 <= fp64_budget) ? 64 : 32;
+  const size_t bytes = elems * (wp == 64 ? 8 : 4);
+  void* bufs[3] = {nullptr, nullptr, nullptr};
+  const bool alias = (wp == sp);
+  for (int b = (alias ? 1 : 0); b < 3; ++b) {
+    if (cudaMalloc(&bufs[b], bytes) != cudaSuccess) {
+      for (void* p : bufs)
+        if (p) cudaFree(p);
+      return fail(h, SR_ERR_OOM, "cudaMalloc of Jacobi buffers failed");
+    }
+  }
+  if (alias)
+    bufs[0] = h->S;
+  else
+    launch_convert(h->S, sp, bufs[0], wp, (int64_t)elems, h->st);
+  cudaMemsetAsync(bufs[1], 0, bytes, h->st);
+  cudaMemsetAsync(bufs[2], 0, bytes, h->st);
+  void *A = bufs[0], *B = bufs[1], *T = bufs[2];
+  double diff = INFINITY;
+  int it = 0;
+  cudaError_t e = cudaGetLastError();
+  const float* w = h->weighted ? h->d_in_w : nullptr;
+  while (e == cudaSuccess && it < max_sweeps) {
+    launch_spmm_rows(h->din, w, h->d_wsum, A, wp, h->ld, B, wp, h->ld, h->n_pad, h->n_pad, 1.0,
+                     0.0, 0, h->st);
+    launch_transpose(B, T, wp, h->n_pad, h->ld, h->st);
+    launch_spmm_rows(h->din, w, h->d_wsum, T, wp, h->ld, B, wp, h->ld, h->n_pad, h->n_pad,
+                     h->cfg.C, 1.0 - h->cfg.C, h->n_cap, h->st);
+    cudaMemsetAsync(h->diffbits, 0, sizeof(unsigned long long), h->st);
+    launch_maxdiff(A, B, wp, h->n_pad, h->ld, h->diffbits, h->st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) break;
+    std::swap(A, B);
+    ++it;
+    unsigned long long bits = 0;
+    e = cudaMemcpyAsync(&bits, h->diffbits, sizeof(bits), cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) break;
+    std::memcpy(&diff, &bits, sizeof(diff));
+    if (diff < tol) break;
+  }
+  if (e == cudaSuccess) {
+    launch_symmetrize(A, wp, h->n_pad, h->ld, h->st);
+    if (!alias) launch_convert(A, wp, h->S, sp, (int64_t)elems, h->st);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  // bufs[] holds three distinct buffers (bufs[0] is the old S when aliasing);
+  // keep the result as S when aliasing and free every other buffer once.
+  if (alias && e == cudaSuccess) h->S = A;
+  for (int b = 0; b < 3; ++b)
+    if (bufs[b] && bufs[b] != h->S) cudaFree(bufs[b]);
+  if (e != cudaSuccess)
+    return fail(h, SR_ERR_CUDA, std::string("Jacobi sweep: ") + cudaGetErrorString(e));
+  *last_diff = diff;
+  *sweeps_done = it;
+  return SR_OK;
+}
+
+void free_ctx(simrank_ctx* h) {
+  if (!h) return;
+  void* ptrs[] = {h->din.start, h->din.len,  h->din.col,   h->dout.start, h->dout.len,
+                  h->dout.col,  h->d_in_w,   h->d_wsum,    h->S,          h->P64,
+                  h->P32,       h->mXi,      h->mEta,      h->tiles,      h->ntiles,
+                  h->sI,        h->sJ,       h->scal,      h->counters,   h->diffbits,
+                  h->d_srcs,    h->d_ops,    h->d_cols};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (auto& e : h->events) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  delete h;
+}
+
+}  // namespace
+
+extern "C" {
+
+simrank_status simrank_default_config(simrank_config* cfg) {
+  if (!cfg) return SR_ERR_ARG;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->C = 0.6;
+  cfg->K = 15;
+  cfg->s_precision = 32;
+  cfg->mode = SR_MODE_DENSE;
+  cfg->n_capacity = 0;
+  cfg->aff = 1;
+  cfg->apply = SR_APPLY_UNIT;
+  cfg->s_update = SR_SUPDATE_FUSED;
+  cfg->tc = 0;
+  cfg->init_max_sweeps = 400;
+  cfg->init_tol = 0.0;  // 0 = precision default
+  cfg->profile = 0;
+  cfg->timeout_iters = 0;
+  cfg->cuda_stream = nullptr;
+  return SR_OK;
+}
+
+simrank_status simrank_init(const simrank_config* cfg_in, int32_t n, int64_t m, const int32_t* src,
+                            const int32_t* dst, const float* weight, const void* S0,
+                            simrank_t* out) {
+  if (!cfg_in || !out) return fail(nullptr, SR_ERR_ARG, "null config or output handle");
+  *out = nullptr;
+  simrank_config cfg = *cfg_in;
+  if (!(cfg.C > 0.0 && cfg.C < 1.0)) return fail(nullptr, SR_ERR_ARG, "C must be in (0, 1)");
+  if (cfg.K < 0 || cfg.K > 1023) return fail(nullptr, SR_ERR_ARG, "K must be in [0, 1023]");
+  if (cfg.s_precision != 32 && cfg.s_precision != 64)
+    return fail(nullptr, SR_ERR_ARG, "s_precision must be 32 or 64");
+  if (cfg.mode != SR_MODE_DENSE)
+    return fail(nullptr, SR_ERR_UNSUPPORTED, "only SR_MODE_DENSE is available in this build");
+  if (n < 1 || m < 0) return fail(nullptr, SR_ERR_ARG, "need n >= 1 and m >= 0");
+  if (m > 0 && (!src || !dst)) return fail(nullptr, SR_ERR_ARG, "null edge arrays");
+  if (cfg.n_capacity == 0) cfg.n_capacity = n;
+  if (cfg.n_capacity < n) return fail(nullptr, SR_ERR_ARG, "n_capacity < n");
+  if ((int64_t)cfg.n_capacity > (int64_t)65535 * PT)
+    return fail(nullptr, SR_ERR_ARG, "n_capacity too large for 16-bit tile indices");
+  if (cfg.apply < 0 || cfg.apply > 2) return fail(nullptr, SR_ERR_ARG, "bad apply mode");
+  if (cfg.apply == SR_APPLY_ONE_SHOT)
+    return fail(nullptr, SR_ERR_UNSUPPORTED, "one-shot batches are not available in this build");
+  if (cfg.init_tol <= 0.0) cfg.init_tol = 1e-13;
+  if (cfg.init_max_sweeps <= 0) cfg.init_max_sweeps = 400;
+
+  simrank_ctx* h = new (std::nothrow) simrank_ctx();
+  if (!h) return fail(nullptr, SR_ERR_OOM, "host allocation failed");
+  h->cfg = cfg;
+  h->st = (cudaStream_t)cfg.cuda_stream;
+  h->n_cur = n;
+  h->n_cap = cfg.n_capacity;
+  h->n_pad = ((cfg.n_capacity + PT - 1) / PT) * PT;
+  h->nT_cap = h->n_pad / PT;
+  h->ld = h->n_pad;
+  h->K1 = cfg.K + 1;
+  h->weighted = weight != nullptr;
+
+  auto bail = [&](simrank_status s) {
+    g_init_error = h->err;
+    free_ctx(h);
+    return s;
+  };
+  if (cudaGetDevice(&h->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess)
+    return bail(fail(h, SR_ERR_CUDA, "no CUDA device"));
+
+  // --- host graph, validated
+  std::vector<std::vector<int32_t>> in_rows(h->n_pad), out_rows(h->n_pad);
+  std::vector<std::vector<float>> in_w(h->weighted ? h->n_pad : 0);
+  h->edges.reserve((size_t)m * 2 + 16);
+  for (int64_t e = 0; e < m; ++e) {
+    const int32_t s = src[e], d = dst[e];
+    if (s < 0 || d < 0 || s >= n || d >= n)
+      return bail(fail(h, SR_ERR_ARG, "edge " + std::to_string(e) + " has an id outside [0, n)"));
+    if (s == d) return bail(fail(h, SR_ERR_EDGE_EXISTS, "self-loop at edge " + std::to_string(e)));
+    if (!h->edges.insert(ekey(s, d)).second)
+      return bail(fail(h, SR_ERR_EDGE_EXISTS, "duplicate edge " + std::to_string(e)));
+    if (h->weighted && !(weight[e] > 0.0f))
+      return bail(fail(h, SR_ERR_ARG, "edge weights must be > 0"));
+    in_rows[d].push_back(s);
+    out_rows[s].push_back(d);
+    if (h->weighted) in_w[d].push_back(weight[e]);
+  }
+  build_adj(h->hin, h->n_pad, in_rows);
+  build_adj(h->hout, h->n_pad, out_rows);
+
+  // --- device graph
+  auto upload_adj = [&](DevAdj& D, const HostAdj& A) -> simrank_status {
+    D.pool_cap = (int64_t)A.pool.size();
+    CUDA_TRY(h, dev_alloc(&D.start, (size_t)h->n_pad));
+    CUDA_TRY(h, dev_alloc(&D.len, (size_t)h->n_pad));
+    CUDA_TRY(h, dev_alloc(&D.col, (size_t)D.pool_cap));
+    CUDA_TRY(h, cudaMemcpy(D.start, A.start.data(), A.start.size() * sizeof(int64_t),
+                           cudaMemcpyHostToDevice));
+    CUDA_TRY(h, cudaMemcpy(D.len, A.len.data(), A.len.size() * sizeof(int32_t),
+                           cudaMemcpyHostToDevice));
+    CUDA_TRY(h, cudaMemcpy(D.col, A.pool.data(), A.pool.size() * sizeof(int32_t),
+                           cudaMemcpyHostToDevice));
+    return SR_OK;
+  };
+  simrank_status s;
+  if ((s = upload_adj(h->din, h->hin)) != SR_OK) return bail(s);
+  if ((s = upload_adj(h->dout, h->hout)) != SR_OK) return bail(s);
+  if (h->weighted) {
+    std::vector<float> wpool(h->hin.pool.size(), 0.f);
+    std::vector<double> wsum(h->n_pad, 0.0);
+    for (int a = 0; a < h->n_pad; ++a) {
+      for (size_t e = 0; e < in_w[a].size(); ++e) {
+        wpool[h->hin.start[a] + e] = in_w[a][e];
+        wsum[a] += in_w[a][e];
+      }
+    }
+    if (cudaMalloc(&h->d_in_w, wpool.size() * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&h->d_wsum, wsum.size() * sizeof(double)) != cudaSuccess)
+      return bail(fail(h, SR_ERR_OOM, "cudaMalloc of weights failed"));
+    cudaMemcpy(h->d_in_w, wpool.data(), wpool.size() * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemcpy(h->d_wsum, wsum.data(), wsum.size() * sizeof(double), cudaMemcpyHostToDevice);
+  }
+
+  // --- S, panels, masks
+  const size_t eb = (size_t)elem_bytes(h);
+  const size_t s_bytes = (size_t)h->n_pad * h->ld * eb;
+  if (cudaMalloc(&h->S, s_bytes) != cudaSuccess)
+    return bail(fail(h, SR_ERR_OOM, "cudaMalloc of S (" + std::to_string(s_bytes) + " bytes) failed"));
+  const size_t panel_elems = (size_t)h->nT_cap * 2 * h->K1 * PT;
+  if (dev_alloc(&h->P64, panel_elems) != cudaSuccess ||
+      (cfg.s_precision == 32 && dev_alloc(&h->P32, panel_elems) != cudaSuccess) ||
+      dev_alloc(&h->mXi, (size_t)h->nT_cap) != cudaSuccess ||
+      dev_alloc(&h->mEta, (size_t)h->nT_cap) != cudaSuccess ||
+      dev_alloc(&h->tiles, (size_t)h->nT_cap * (h->nT_cap + 1) / 2) != cudaSuccess ||
+      dev_alloc(&h->ntiles, 1) != cudaSuccess || dev_alloc(&h->sI, (size_t)h->n_pad) != cudaSuccess ||
+      dev_alloc(&h->sJ, (size_t)h->n_pad) != cudaSuccess || dev_alloc(&h->scal, 8) != cudaSuccess ||
+      dev_alloc(&h->counters, CNT_N) != cudaSuccess || dev_alloc(&h->diffbits, 1) != cudaSuccess)
+    return bail(fail(h, SR_ERR_OOM, "cudaMalloc of work buffers failed"));
+  cudaMemsetAsync(h->P64, 0, panel_elems * sizeof(double), h->st);
+  if (h->P32) cudaMemsetAsync(h->P32, 0, panel_elems * sizeof(float), h->st);
+  cudaMemsetAsync(h->mXi, 0, h->nT_cap * sizeof(uint64_t), h->st);
+  cudaMemsetAsync(h->mEta, 0, h->nT_cap * sizeof(uint64_t), h->st);
+  cudaMemsetAsync(h->counters, 0, CNT_N * sizeof(int64_t), h->st);
+  cudaMemsetAsync(h->S, 0, s_bytes, h->st);
+
+  if (S0) {
+    cudaError_t e = cudaMemcpy2DAsync(h->S, h->ld * eb, S0, (size_t)n * eb, (size_t)n * eb, n,
+                                      cudaMemcpyHostToDevice, h->st);
+    if (e != cudaSuccess) return bail(fail(h, SR_ERR_CUDA, "upload of S0 failed"));
+    launch_set_diag(h->S, cfg.s_precision, n, h->n_cap, h->ld, 1.0 - cfg.C, h->st);
+    if (cudaStreamSynchronize(h->st) != cudaSuccess)
+      return bail(fail(h, SR_ERR_CUDA, "init synchronisation failed"));
+  } else {
+    // start from (1 - C) I on the whole capacity
+    launch_set_diag(h->S, cfg.s_precision, 0, h->n_cap, h->ld, 1.0 - cfg.C, h->st);
+    double diff = 0.0;
+    int sweeps = 0;
+    if ((s = jacobi_sweeps(h, cfg.init_max_sweeps, cfg.init_tol, &diff, &sweeps)) != SR_OK)
+      return bail(s);
+    h->stats.init_residual = diff;
+    h->stats.init_sweeps = sweeps;
+    if (!(diff < cfg.init_tol))
+      return bail(fail(h, SR_ERR_NOT_CONVERGED,
+                       "Jacobi init stopped at max-abs change " + std::to_string(diff)));
+  }
+  *out = h;
+  return SR_OK;
+}
+
+simrank_status simrank_apply_updates(simrank_t h, const simrank_update* u, int64_t count) {
+  if (!h) return fail(nullptr, SR_ERR_ARG, "null handle");
+  if (count < 0 || (count > 0 && !u)) return fail(h, SR_ERR_ARG, "bad update array");
+  if (count == 0) return SR_OK;
+  if (h->weighted) return fail(h, SR_ERR_UNSUPPORTED, "updates on a weighted graph");
+  int n_after = h->n_cur;
+  simrank_status s = validate(h, u, count, &n_after);
+  if (s != SR_OK) return s;
+
+  // Plan the rank-one updates: (sink, op, sources, d_j, patch op range).
+  struct R1 {
+    int32_t sink, op, d_j, delta;
+    int64_t src_off, op_begin, op_end;
+  };
+  std::vector<R1> plan;
+  std::vector<int32_t> srcs;
+  std::vector<PatchOp> ops;
+  const int n_old = h->n_cur;
+  auto add_r1 = [&](int32_t j, int32_t op, const std::vector<int32_t>& I) {
+    R1 r;
+    r.sink = j;
+    r.op = op;
+    r.d_j = h->hin.len[j];
+    r.delta = (int)I.size();
+    r.src_off = (int64_t)srcs.size();
+    r.op_begin = (int64_t)ops.size();
+    for (int32_t i : I) {
+      srcs.push_back(i);
+      if (op > 0) {
+        adj_append(h->hin, j, i, ops, true);
+        adj_append(h->hout, i, j, ops, false);
+        h->edges.insert(ekey(i, j));
+      } else {
+        adj_remove(h->hin, j, i, ops, true);
+        adj_remove(h->hout, i, j, ops, false);
+        h->edges.erase(ekey(i, j));
+      }
+    }
+    r.op_end = (int64_t)ops.size();
+    plan.push_back(r);
+  };
+  if (h->cfg.apply == SR_APPLY_UNIT) {
+    for (int64_t t = 0; t < count; ++t) add_r1(u[t].dst, u[t].op, {u[t].src});
+  } else {
+    std::vector<Block> blocks;
+    std::string msg;
+    if ((s = plan_blocks(u, count, n_old, blocks, msg)) != SR_OK) return fail(h, s, msg);
+    for (const Block& b : blocks) add_r1(b.sink, b.op, b.srcs);
+  }
+  h->n_cur = n_after;
+  if ((s = grow_pool(h, h->din, h->hin)) != SR_OK) return s;
+  if ((s = grow_pool(h, h->dout, h->hout)) != SR_OK) return s;
+  if ((s = ensure_dev_capacity(h, (int64_t)srcs.size(), (int64_t)ops.size())) != SR_OK) return s;
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_srcs, srcs.data(), srcs.size() * sizeof(int32_t),
+                              cudaMemcpyHostToDevice, h->st));
+  if (!ops.empty())
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_ops, ops.data(), ops.size() * sizeof(PatchOp),
+                                cudaMemcpyHostToDevice, h->st));
+  // the staging vectors must outlive the asynchronous copies
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  for (const R1& r : plan) {
+    if ((s = run_rank_one(h, r.src_off, r.delta, r.sink, r.op, r.d_j, r.op_begin, r.op_end)) !=
+        SR_OK)
+      return s;
+  }
+  h->stats.updates += count;
+  return SR_OK;
+}
+
+simrank_status simrank_columns(simrank_t h, const int32_t* cols, int32_t ncols, void* out,
+                               int32_t out_on_device, int32_t out_fp64) {
+  if (!h) return fail(nullptr, SR_ERR_ARG, "null handle");
+  if (ncols < 0 || (ncols > 0 && (!cols || !out))) return fail(h, SR_ERR_ARG, "bad column request");
+  for (int c = 0; c < ncols; ++c)
+    if (cols[c] < 0 || cols[c] >= h->n_cur) return fail(h, SR_ERR_ARG, "column id out of range");
+  if (ncols == 0) return SR_OK;
+  if (ncols > h->cols_cap) {
+    if (h->d_cols) cudaFree(h->d_cols);
+    h->cols_cap = ncols;
+    CUDA_TRY(h, dev_alloc(&h->d_cols, (size_t)ncols));
+  }
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_cols, cols, ncols * sizeof(int32_t), cudaMemcpyHostToDevice,
+                              h->st));
+  const size_t ob = (size_t)h->n_cur * ncols * (out_fp64 ? 8 : 4);
+  if (out_on_device) {
+    launch_copy_cols(h->S, h->cfg.s_precision, h->ld, h->d_cols, ncols, h->n_cur, out, out_fp64,
+                     h->st);
+    LAUNCH_CHECK(h);
+    CUDA_TRY(h, cudaStreamSynchronize(h->st));  // cols staging reuse safety
+    return SR_OK;
+  }
+  void* tmp = nullptr;
+  CUDA_TRY(h, cudaMalloc(&tmp, ob));
+  launch_copy_cols(h->S, h->cfg.s_precision, h->ld, h->d_cols, ncols, h->n_cur, tmp, out_fp64,
+                   h->st);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, ob, cudaMemcpyDeviceToHost, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return fail(h, SR_ERR_CUDA, std::string("columns: ") + cudaGetErrorString(e));
+  return SR_OK;
+}
+
+int32_t simrank_num_nodes(simrank_t h) { return h ? h->n_cur : -1; }
+
+const char* simrank_last_error(simrank_t h) { return h ? h->err.c_str() : g_init_error.c_str(); }
+
+simrank_status simrank_sync(simrank_t h) {
+  if (!h) return fail(nullptr, SR_ERR_ARG, "null handle");
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return SR_OK;
+}
+
+void simrank_destroy(simrank_t h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->st);
+  free_ctx(h);
+}
+
+simrank_status simrank_get_stats(simrank_t h, simrank_stats* out) {
+  if (!h || !out) return fail(h, SR_ERR_ARG, "null argument");
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  harvest_events(h);
+  int64_t c[CNT_N];
+  CUDA_TRY(h, cudaMemcpy(c, h->counters, sizeof(c), cudaMemcpyDeviceToHost));
+  simrank_stats r = h->stats;
+  r.tiles_touched = c[CNT_TILES_TOUCHED];
+  r.s_bytes = c[CNT_S_BYTES];
+  r.panel_bytes = c[CNT_PANEL_BYTES];
+  r.s_update_launches = h->prof_launches;
+  r.kernel_launches = h->launches;
+  r.s_update_ms = h->prof_ms;
+  *out = r;
+  return SR_OK;
+}
+
+simrank_status simrank_reanchor(simrank_t h, int32_t sweeps, double* max_change) {
+  if (!h) return fail(nullptr, SR_ERR_ARG, "null handle");
+  if (sweeps <= 0) return fail(h, SR_ERR_ARG, "sweeps must be positive");
+  double diff = 0.0;
+  int done = 0;
+  simrank_status s = jacobi_sweeps(h, sweeps, 0.0, &diff, &done);
+  if (s != SR_OK) return s;
+  h->stats.init_residual = diff;
+  h->stats.init_sweeps = done;
+  if (max_change) *max_change = diff;
+  return SR_OK;
+}
+
+simrank_status simrank_plan_batch(const simrank_update* u, int64_t count, int32_t n_old,
+                                  int32_t max_blocks, int32_t* nblocks, int32_t* block_sink,
+                                  int32_t* block_op, int64_t* block_off, int32_t* block_src) {
+  if (count < 0 || (count > 0 && !u) || !nblocks) return SR_ERR_ARG;
+  std::vector<Block> blocks;
+  std::string msg;
+  simrank_status s = plan_blocks(u, count, n_old, blocks, msg);
+  if (s != SR_OK) {
+    g_init_error = msg;
+    return s;
+  }
+  *nblocks = (int32_t)blocks.size();
+  if ((int32_t)blocks.size() > max_blocks) return SR_ERR_ARG;
+  int64_t off = 0;
+  for (size_t b = 0; b < blocks.size(); ++b) {
+    block_sink[b] = blocks[b].sink;
+    block_op[b] = blocks[b].op;
+    block_off[b] = off;
+    for (int32_t x : blocks[b].srcs) block_src[off++] = x;
+  }
+  block_off[blocks.size()] = off;
+  return SR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,207 @@
+// Fused S update (Alg 1 final step, Alg 2 with Thm 4 pruning):
+//   S <- S + M_K + M_K^T,  M_K = sum_{k=0}^{K} xi_k eta_k^T,
+// applied as one read-modify-write pass per affected tile pair (I <= J): the
+// CTA forms Delta_IJ = sum_k xi_k[I] eta_k[J]^T + eta_k[I] xi_k[J]^T once and
+// adds it to S[I,J] and, transposed, to S[J,I] (Delta S is symmetric), so
+// each entry of the upper triangle costs 2(K+1) FMAs for two S entries.
+#include "sr_internal.h"
+
+namespace sr {
+
+namespace {
+
+// 256 threads as 16 x 16; thread (tx, ty) owns rows {ty*4+q, 64+ty*4+q} and
+// columns {tx*4+q, 64+tx*4+q}, q < 4, of the 128 x 128 tile, so every
+// float4 access of a warp covers 256 contiguous bytes.
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  using type = float4;
+};
+template <>
+struct Vec4<double> {
+  using type = double4;
+};
+
+template <typename T>
+__device__ __forceinline__ void ld4(const T* p, T (&v)[4]) {
+  const typename Vec4<T>::type x = *reinterpret_cast<const typename Vec4<T>::type*>(p);
+  v[0] = x.x;
+  v[1] = x.y;
+  v[2] = x.z;
+  v[3] = x.w;
+}
+template <typename T>
+__device__ __forceinline__ void ld4p(const T* p, T* v) {
+  const typename Vec4<T>::type x = *reinterpret_cast<const typename Vec4<T>::type*>(p);
+  v[0] = x.x;
+  v[1] = x.y;
+  v[2] = x.z;
+  v[3] = x.w;
+}
+template <typename T>
+__device__ __forceinline__ void st4(T* p, const T (&v)[4]) {
+  typename Vec4<T>::type x;
+  x.x = v[0];
+  x.y = v[1];
+  x.z = v[2];
+  x.w = v[3];
+  *reinterpret_cast<typename Vec4<T>::type*>(p) = x;
+}
+
+template <typename T, int KC, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+    k_s_update(T* __restrict__ S, int64_t ld, const T* __restrict__ P, int K1,
+               const uint32_t* __restrict__ tiles, const int* __restrict__ ntiles,
+               const uint64_t* __restrict__ mXi, const uint64_t* __restrict__ mEta, int k0g,
+               int k1g, int use_masks, int n, unsigned long long* __restrict__ counters) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* sXiI = reinterpret_cast<T*>(smem_raw);
+  T* sEtaI = sXiI + KC * PT;
+  T* sXiJ = sEtaI + KC * PT;
+  T* sEtaJ = sXiJ + KC * PT;
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int nt = *ntiles;
+  unsigned long long my_tiles = 0, my_bytes = 0;
+  for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+    const uint32_t pr = tiles[t];
+    const int I = (int)(pr >> 16), J = (int)(pr & 0xffffu);
+    const uint64_t a1 = use_masks ? (mXi[I] & mEta[J]) : ~0ull;  // xi_I eta_J^T
+    const uint64_t a2 = use_masks ? (mEta[I] & mXi[J]) : ~0ull;  // eta_I xi_J^T
+    T acc[8][8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) acc[r][c] = T(0);
+
+    for (int kb = k0g; kb < k1g; kb += KC) {
+      const int kc = min(KC, k1g - kb);
+      __syncthreads();  // previous chunk / tile fully consumed
+      // copy kc x 128 entries of xi and eta for tiles I and J
+      const int nvec = kc * PT / 4;
+      const T* gXiI = P + ((int64_t)I * 2 + 0) * K1 * PT + (int64_t)kb * PT;
+      const T* gEtaI = P + ((int64_t)I * 2 + 1) * K1 * PT + (int64_t)kb * PT;
+      const T* gXiJ = P + ((int64_t)J * 2 + 0) * K1 * PT + (int64_t)kb * PT;
+      const T* gEtaJ = P + ((int64_t)J * 2 + 1) * K1 * PT + (int64_t)kb * PT;
+      using V = typename Vec4<T>::type;
+      for (int e = tid; e < nvec; e += 256) {
+        reinterpret_cast<V*>(sXiI)[e] = reinterpret_cast<const V*>(gXiI)[e];
+        reinterpret_cast<V*>(sEtaI)[e] = reinterpret_cast<const V*>(gEtaI)[e];
+        reinterpret_cast<V*>(sXiJ)[e] = reinterpret_cast<const V*>(gXiJ)[e];
+        reinterpret_cast<V*>(sEtaJ)[e] = reinterpret_cast<const V*>(gEtaJ)[e];
+      }
+      __syncthreads();
+      for (int kk = 0; kk < kc; ++kk) {
+        const uint64_t bit = 1ull << ((kb + kk) & 63);
+        const bool p1 = (a1 & bit) != 0, p2 = (a2 & bit) != 0;
+        if (!(p1 || p2)) continue;
+        T rx[8], re[8], cx[8], ce[8];
+        ld4p(sXiI + kk * PT + ty * 4, &rx[0]);
+        ld4p(sXiI + kk * PT + 64 + ty * 4, &rx[4]);
+        ld4p(sEtaI + kk * PT + ty * 4, &re[0]);
+        ld4p(sEtaI + kk * PT + 64 + ty * 4, &re[4]);
+        ld4p(sXiJ + kk * PT + tx * 4, &cx[0]);
+        ld4p(sXiJ + kk * PT + 64 + tx * 4, &cx[4]);
+        ld4p(sEtaJ + kk * PT + tx * 4, &ce[0]);
+        ld4p(sEtaJ + kk * PT + 64 + tx * 4, &ce[4]);
+        if (p1) {
+#pragma unroll
+          for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[r][c] = fma(rx[r], ce[c], acc[r][c]);
+        }
+        if (p2) {
+#pragma unroll
+          for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[r][c] = fma(re[r], cx[c], acc[r][c]);
+        }
+      }
+    }
+
+    // S[I, J] += Delta (rows r, columns c)
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int row = I * PT + ((r < 4) ? ty * 4 + r : 64 + ty * 4 + (r - 4));
+      T* p = S + (int64_t)row * ld + (int64_t)J * PT;
+      T v0[4], v1[4];
+      ld4(p + tx * 4, v0);
+      ld4(p + 64 + tx * 4, v1);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        v0[q] += acc[r][q];
+        v1[q] += acc[r][4 + q];
+      }
+      st4(p + tx * 4, v0);
+      st4(p + 64 + tx * 4, v1);
+    }
+    if (I != J) {
+      // S[J, I] += Delta^T
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int row = J * PT + ((c < 4) ? tx * 4 + c : 64 + tx * 4 + (c - 4));
+        T* p = S + (int64_t)row * ld + (int64_t)I * PT;
+        T v0[4], v1[4];
+        ld4(p + ty * 4, v0);
+        ld4(p + 64 + ty * 4, v1);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          v0[q] += acc[q][c];
+          v1[q] += acc[4 + q][c];
+        }
+        st4(p + ty * 4, v0);
+        st4(p + 64 + ty * 4, v1);
+      }
+    }
+    if (tid == 0) {
+      const long long vr = max(0, min(PT, n - I * PT)), vc = max(0, min(PT, n - J * PT));
+      my_tiles += 1;
+      my_bytes += (unsigned long long)(vr * vc) * 2ull * sizeof(T) * (I == J ? 1ull : 2ull);
+    }
+  }
+  if (tid == 0 && my_tiles) {
+    atomicAdd(&counters[CNT_TILES_TOUCHED], my_tiles);
+    atomicAdd(&counters[CNT_S_BYTES], my_bytes);
+    atomicAdd(&counters[CNT_PANEL_BYTES],
+              my_tiles * 4ull * (unsigned long long)(k1g - k0g) * PT * sizeof(T));
+  }
+}
+
+constexpr int KC_F32 = 32;
+constexpr int KC_F64 = 16;
+
+}  // namespace
+
+int s_update_grid(int s_prec, int num_sms) { return num_sms * (s_prec == 64 ? 1 : 2); }
+
+void launch_s_update(void* S, int s_prec, int64_t ld, const void* P, int K1, const uint32_t* tiles,
+                     const int* ntiles, const uint64_t* mXi, const uint64_t* mEta, int k0, int k1,
+                     int use_masks, int n, int64_t* counters, int grid, cudaStream_t st) {
+  if (s_prec == 64) {
+    const size_t smem = 4ull * KC_F64 * PT * sizeof(double);
+    static bool attr64 = false;
+    if (!attr64) {
+      cudaFuncSetAttribute(k_s_update<double, KC_F64, 1>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr64 = true;
+    }
+    k_s_update<double, KC_F64, 1><<<grid, 256, smem, st>>>(
+        (double*)S, ld, (const double*)P, K1, tiles, ntiles, mXi, mEta, k0, k1, use_masks, n,
+        (unsigned long long*)counters);
+  } else {
+    const size_t smem = 4ull * KC_F32 * PT * sizeof(float);
+    static bool attr32 = false;
+    if (!attr32) {
+      cudaFuncSetAttribute(k_s_update<float, KC_F32, 2>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr32 = true;
+    }
+    k_s_update<float, KC_F32, 2><<<grid, 256, smem, st>>>(
+        (float*)S, ld, (const float*)P, K1, tiles, ntiles, mXi, mEta, k0, k1, use_masks, n,
+        (unsigned long long*)counters);
+  }
+}
+
+}  // namespace sr

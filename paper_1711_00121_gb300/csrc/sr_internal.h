@@ -1,0 +1,124 @@
+// Internal declarations of libsimrank (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <unordered_set>
+#include <vector>
+
+#include "../../include/simrank.h"
+
+namespace sr {
+
+// Edge of an S tile and height of a panel block.  S is padded to a multiple
+// of PT in both dimensions; panels are stored tile-blocked:
+//   panel[((T * 2 + which) * K1 + k) * PT + r]   for node a = T * PT + r,
+// which = 0 for xi_k, 1 for eta_k, k = 0..K (K1 = K + 1 terms).
+constexpr int PT = 128;
+
+inline int64_t panel_index(int64_t node, int which, int k, int K1) {
+  return (((node / PT) * 2 + which) * (int64_t)K1 + k) * PT + (node % PT);
+}
+
+// Graph patch operation applied on the device in order (exact integer work).
+struct PatchOp {
+  int32_t kind;  // see PatchKind
+  int32_t v;     // value (col id, length) or copy length
+  int64_t a;     // destination index
+  int64_t b;     // source index / start value
+};
+enum PatchKind : int32_t {
+  PK_IN_COL = 0,    // in_col[a] = v
+  PK_OUT_COL = 1,   // out_col[a] = v
+  PK_IN_LEN = 2,    // in_len[a] = v
+  PK_OUT_LEN = 3,   // out_len[a] = v
+  PK_IN_START = 4,  // in_start[a] = b
+  PK_OUT_START = 5, // out_start[a] = b
+  PK_IN_COPY = 6,   // in_col[a .. a+v) = in_col[b .. b+v)
+  PK_OUT_COPY = 7,  // out_col[a .. a+v) = out_col[b .. b+v)
+};
+
+// Adjacency lists with per-row slack, mirrored bit-for-bit on host and device.
+struct HostAdj {
+  std::vector<int64_t> start;
+  std::vector<int32_t> len, cap;
+  std::vector<int32_t> pool;
+  int64_t used = 0;
+};
+
+struct DevAdj {
+  int64_t* start = nullptr;
+  int32_t* len = nullptr;
+  int32_t* col = nullptr;
+  int64_t pool_cap = 0;
+};
+
+// Device counters (int64): see Counter.
+enum Counter : int {
+  CNT_TILES_TOUCHED = 0,
+  CNT_S_BYTES = 1,
+  CNT_PANEL_BYTES = 2,
+  CNT_STATUS = 3,
+  CNT_N = 8
+};
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (defined in the .cu files).  All are asynchronous on `st`.
+// ---------------------------------------------------------------------------
+
+// sI[a] = sum_t S[I[t], a], sJ[a] = S[j, a] (a < n_pad, FP64);
+// scal[0] = sum_{t,t'} S[I[t], I[t']], scal[1] = S[j, j].
+void launch_gather_rows(const void* S, int s_prec, int64_t ld, const int32_t* I, int delta, int j,
+                        int n_pad, double* sI, double* sJ, double* scal, cudaStream_t st);
+
+// gamma of Thm 3 / Thm 9 / Table 2 on the OLD graph; writes xi_0 = C e_j and
+// eta_0 = gamma into the panels (FP64 and, for FP32 S, FP32) and writes the
+// k = 0 AFF mask words of tiles [0, nT).
+void launch_gamma(const DevAdj& in, const double* sI, const double* sJ, const double* scal, int j,
+                  int delta, int op, int d_j, double C, int nT, int K1, double* P64, float* P32,
+                  uint64_t* mXi, uint64_t* mEta, cudaStream_t st);
+
+// Apply patch ops [begin, end) to the device adjacency (one CTA, in order).
+void launch_patch(const PatchOp* ops, int64_t begin, int64_t end, DevAdj in, DevAdj out,
+                  cudaStream_t st);
+
+// One step of the xi/eta recurrence on the NEW graph (Eq. 16a):
+// xi_{k+1} = C Q xi_k, eta_{k+1} = Q eta_k; ORs bit (k+1) % 64 into the AFF masks.
+void launch_chain_step(const DevAdj& in, int k, double C, int nT, int K1, double* P64, float* P32,
+                       uint64_t* mXi, uint64_t* mEta, cudaStream_t st);
+
+// Affected tile pairs (I <= J) of Thm 4 at tile granularity.
+void launch_tile_list(const uint64_t* mXi, const uint64_t* mEta, int nT, int aff, uint32_t* tiles,
+                      int* ntiles, cudaStream_t st);
+
+// S[I,J] += sum_{k in [k0,k1)} xi_k[I] eta_k[J]^T + eta_k[I] xi_k[J]^T, and the
+// mirrored tile S[J,I], over the tile list.  n = current node count (for the
+// algorithmic byte counters).
+void launch_s_update(void* S, int s_prec, int64_t ld, const void* P, int K1, const uint32_t* tiles,
+                     const int* ntiles, const uint64_t* mXi, const uint64_t* mEta, int k0, int k1,
+                     int use_masks, int n, int64_t* counters, int grid, cudaStream_t st);
+// Largest useful persistent grid for launch_s_update on this device.
+int s_update_grid(int s_prec, int num_sms);
+
+// Jacobi sweep pieces for Eq. 1 (init / re-anchor).
+// Y[a, :] = scale * sum_b Q[a, b] X[b, :] + diag * e_a (the diagonal term only
+// for a < n_diag), rows a < n_rows, columns < ncols (a multiple of 4).
+void launch_spmm_rows(const DevAdj& in, const float* w, const double* wsum, const void* X,
+                      int x_prec, int64_t ldx, void* Y, int y_prec, int64_t ldy, int n_rows,
+                      int ncols, double scale, double diag, int n_diag, cudaStream_t st);
+void launch_transpose(const void* A, void* B, int prec, int n_pad, int64_t ld, cudaStream_t st);
+// *out_bits = max(*out_bits, max |A - B|) over the n x n block (as double bits)
+void launch_maxdiff(const void* A, const void* B, int prec, int n, int64_t ld,
+                    unsigned long long* out_bits, cudaStream_t st);
+void launch_symmetrize(void* A, int prec, int n_pad, int64_t ld, cudaStream_t st);
+// B[e] = A[e] for e < count, converting between FP32 and FP64.
+void launch_convert(const void* A, int a_prec, void* B, int b_prec, int64_t count, cudaStream_t st);
+void launch_set_diag(void* A, int prec, int from, int to, int64_t ld, double value, cudaStream_t st);
+
+// out[c * n + a] = S[cols[c], a]  (column c of the symmetric S)
+void launch_copy_cols(const void* S, int s_prec, int64_t ld, const int32_t* cols, int ncols, int n,
+                      void* out, int out_fp64, cudaStream_t st);
+
+}  // namespace sr

@@ -1,0 +1,77 @@
+"""C ABI checks that need no GPU: the library loads, exports every symbol
+declared in include/simrank.h, and its host-only batch planner matches the
+oracle's §8 partition."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1711_00121_gb300 as P
+from oracle import simrank_oracle as O
+from synth import er_graph, batch_with_new_nodes
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            txt = open(os.path.join(inc, f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(simrank_[a-z_0-9]+)\s*\(", txt))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    L = P.lib()
+    decl = declared_symbols()
+    assert decl, "no declarations found"
+    for name in sorted(decl):
+        assert hasattr(L, name), name
+    assert decl == set(P.SIGNATURES), decl ^ set(P.SIGNATURES)
+
+
+def test_struct_sizes_match_header():
+    # simrank_update is 16 bytes; config / stats layouts are fixed by the header
+    import ctypes
+    assert ctypes.sizeof(P.Update) == 16
+    assert ctypes.sizeof(P.Config) == 8 + 4 * 10 + 8 + 4 + 4 + 8 + 8 + 32
+    assert ctypes.sizeof(P.Stats) == 8 * 8 + 8 + 8 + 4 + 28
+
+
+def _expand_oracle(ups, n_old):
+    plus, minus = O.net_update(ups)
+    dels, ins = O.partition_similar_sink(plus, minus, lambda x: x < n_old)
+    out = [(j, -1, list(srcs)) for j, srcs in dels]
+    exists = set(range(n_old))
+    for j, srcs in ins:
+        for _, part in O.block_case(srcs, j, lambda x: x in exists):
+            out.append((j, 1, list(part)))
+            exists.update(part)
+            exists.add(j)
+    return out
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_plan_batch_matches_oracle_partition(seed):
+    n = 40
+    s, d = er_graph(n, 120, seed)
+    ups, _ = batch_with_new_nodes(n, s, d, 60, seed, frac_new=0.3, reuse_target=0.5)
+    # add cancelling pairs
+    extra = []
+    for t in range(5):
+        i, j = int(ups[t][0]), int(ups[t][1])
+        if ups[t][2] > 0:
+            extra += [(i, j, -1), (i, j, 1)]
+    allu = ups.tolist() + extra
+    got = P.plan_batch(allu, n)
+    want = _expand_oracle(allu, n)
+    assert got == want
+
+
+def test_plan_batch_rejects_bad_net_count():
+    with pytest.raises(P.SimrankError):
+        P.plan_batch([(0, 1, 1), (0, 1, 1)], 5)
