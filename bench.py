@@ -107,10 +107,10 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def make_streams(total_steps):
+def make_streams(total_steps, per_step=UPDATES_PER_STEP):
     s, d = chung_lu_digraph(N, M, GAMMA, GAMMA, SEED_GRAPH)
     es = EdgeSet(N, s, d)
-    streams = [update_stream(N, s, d, UPDATES_PER_STEP, SEED_STREAM + t, edge_set=es)
+    streams = [update_stream(N, s, d, per_step, SEED_STREAM + t, edge_set=es)
                for t in range(total_steps)]
     return s, d, streams
 
@@ -174,7 +174,8 @@ def run_gpu(args, rank, world):
         dist.init_process_group("nccl")
     stream = torch.cuda.Stream()
     total = args.warmup + args.steps
-    s, d, streams = make_streams(total)
+    per_step = args.updates_per_step
+    s, d, streams = make_streams(total, per_step)
     # all-or-nothing per step: pack the per-step update arrays in pinned memory
     packed = []
     for st in streams:
@@ -226,7 +227,7 @@ def run_gpu(args, rank, world):
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
     sr2.close()
-    e2e_val = args.steps * UPDATES_PER_STEP / e2e_s
+    e2e_val = args.steps * per_step / e2e_s
     # max over ranks
     ms_t = torch.tensor([ms], device="cuda")
     e2e_t = torch.tensor([e2e_s], device="cuda")
@@ -235,7 +236,7 @@ def run_gpu(args, rank, world):
         dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
     ms = float(ms_t.item())
     e2e_s = float(e2e_t.item())
-    updates = args.steps * UPDATES_PER_STEP * world
+    updates = args.steps * per_step * world
     value = updates / (ms / 1000.0)
     e2e_val = updates / e2e_s
     launches = st1["s_update_launches"] - st0["s_update_launches"]
@@ -251,7 +252,7 @@ def run_gpu(args, rank, world):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N, "m": M, "C": C, "K": K,
-                   "updates_per_step": UPDATES_PER_STEP,
+                   "updates_per_step": per_step,
                    "l2": "inputs larger than L2 (S is 1.6 GB FP32)",
                    "aff_tile_fraction": tiles_touched / max(tiles_total, 1),
                    "hbm_gbs_step": alg_bytes / (ms / 1000.0) / 1e9,
@@ -285,6 +286,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--updates-per-step", type=int, default=UPDATES_PER_STEP,
+                    help="batch size of one step (the benchmarked workload uses 1000)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -82,15 +82,16 @@ typedef struct simrank_config {
   int32_t tc;             /* one-shot batch form: 0 = CUDA-core FFMA update, 1 = tensor cores (3xTF32 split) */
   int32_t init_max_sweeps;/* cap on Jacobi sweeps of Eq. 1 at init / re-anchor */
   double init_tol;        /* init stops when a sweep changes S by less than this (max-abs) */
-  int32_t profile;        /* 1: time every S-update launch with CUDA events (simrank_get_profile) */
-  int32_t reserved0;
+  int32_t profile;        /* 1: time every S-update launch with CUDA events (simrank_get_stats) */
+  int32_t relabel;        /* 1: store nodes of in-degree 0 after the others, so that rows that no
+                             update can reach (Thm 4) fill whole tiles; ids in the ABI are unchanged */
   int64_t timeout_iters;  /* bound on any device spin-wait (0 = library default) */
   void* cuda_stream;      /* cudaStream_t for all work of this handle; NULL = default stream */
   int32_t reserved[8];
 } simrank_config;
 
 /* Fills *cfg with defaults: C = 0.6, K = 15, s_precision = 32, dense, aff = 1,
- * unit apply, fused update, init_tol = 1e-12 (FP64) / 1e-7 (FP32). */
+ * relabel = 1, unit apply, fused update, init_tol = 1e-13, 400 init sweeps. */
 simrank_status simrank_default_config(simrank_config* cfg);
 
 /* Creates a handle for the graph (src[e] -> dst[e]), e < m, on n nodes.

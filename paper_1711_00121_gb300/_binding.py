@@ -37,7 +37,7 @@ class Config(ctypes.Structure):
         ("mode", ctypes.c_int32), ("n_capacity", ctypes.c_int32), ("aff", ctypes.c_int32),
         ("apply", ctypes.c_int32), ("s_update", ctypes.c_int32), ("tc", ctypes.c_int32),
         ("init_max_sweeps", ctypes.c_int32), ("init_tol", ctypes.c_double),
-        ("profile", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+        ("profile", ctypes.c_int32), ("relabel", ctypes.c_int32),
         ("timeout_iters", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
         ("reserved", ctypes.c_int32 * 8),
     ]

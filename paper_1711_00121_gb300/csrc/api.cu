@@ -37,7 +37,11 @@ struct simrank_ctx {
   int n_cur = 0, n_cap = 0, n_pad = 0, nT_cap = 0, K1 = 0;
   int64_t ld = 0;
   bool weighted = false;
-  // host mirror of the graph
+  // caller id <-> storage id (identity unless cfg.relabel)
+  bool relabeled = false;
+  std::vector<int32_t> ext2int, int2ext;
+  int32_t* d_ext2int = nullptr;
+  // host mirror of the graph (storage ids)
   HostAdj hin, hout;
   std::unordered_set<uint64_t> edges;
   // device graph
@@ -238,9 +242,14 @@ simrank_status plan_blocks(const simrank_update* u, int64_t count, int32_t n_old
 }
 
 // Sequential validation of a batch against the current graph (no mutation).
+// New nodes are the ids >= n_cur that the batch names; as a set they must be
+// exactly n_cur, n_cur + 1, ... (in any order of appearance) and stay below
+// n_capacity.  An edge may be deleted only if present at that point of the
+// sequence.
 simrank_status validate(simrank_ctx* h, const simrank_update* u, int64_t count, int* n_after) {
   std::unordered_map<uint64_t, char> overlay;
-  int n_sim = h->n_cur;
+  int max_id = h->n_cur - 1;
+  std::unordered_set<int32_t> fresh;
   for (int64_t t = 0; t < count; ++t) {
     const int32_t s = u[t].src, d = u[t].dst;
     const std::string at = " (update " + std::to_string(t) + ": " + std::to_string(s) + " -> " +
@@ -248,13 +257,11 @@ simrank_status validate(simrank_ctx* h, const simrank_update* u, int64_t count, 
     if (u[t].op != 1 && u[t].op != -1) return fail(h, SR_ERR_ARG, "op must be +1 or -1" + at);
     if (s < 0 || d < 0) return fail(h, SR_ERR_ARG, "negative node id" + at);
     if (s == d) return fail(h, SR_ERR_EDGE_EXISTS, "self-loop" + at);
-    int lo = std::min(s, d), hi = std::max(s, d);
-    for (int x : {lo, hi}) {
-      if (x >= n_sim) {
-        if (x != n_sim) return fail(h, SR_ERR_ARG, "new node ids must be contiguous" + at);
-        if (u[t].op < 0) return fail(h, SR_ERR_EDGE_MISSING, "deleting an absent edge" + at);
-        if (n_sim + 1 > h->n_cap) return fail(h, SR_ERR_CAPACITY, "n_capacity exceeded" + at);
-        ++n_sim;
+    for (int32_t x : {s, d}) {
+      if (x >= h->n_cur) {
+        if (x >= h->n_cap) return fail(h, SR_ERR_CAPACITY, "n_capacity exceeded" + at);
+        fresh.insert(x);
+        max_id = std::max(max_id, (int)x);
       }
     }
     const uint64_t k = ekey(s, d);
@@ -272,7 +279,10 @@ simrank_status validate(simrank_ctx* h, const simrank_update* u, int64_t count, 
       overlay[k] = 0;
     }
   }
-  *n_after = n_sim;
+  if ((int64_t)fresh.size() != (int64_t)max_id + 1 - h->n_cur)
+    return fail(h, SR_ERR_ARG, "new node ids must be contiguous from n_cur = " +
+                                   std::to_string(h->n_cur));
+  *n_after = max_id + 1;
   return SR_OK;
 }
 
@@ -457,7 +467,7 @@ void free_ctx(simrank_ctx* h) {
                   h->dout.col,  h->d_in_w,   h->d_wsum,    h->S,          h->P64,
                   h->P32,       h->mXi,      h->mEta,      h->tiles,      h->ntiles,
                   h->sI,        h->sJ,       h->scal,      h->counters,   h->diffbits,
-                  h->d_srcs,    h->d_ops,    h->d_cols};
+                  h->d_srcs,    h->d_ops,    h->d_cols,     h->d_ext2int};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& e : h->events) {
@@ -486,6 +496,7 @@ simrank_status simrank_default_config(simrank_config* cfg) {
   cfg->init_max_sweeps = 400;
   cfg->init_tol = 0.0;  // 0 = precision default
   cfg->profile = 0;
+  cfg->relabel = 1;
   cfg->timeout_iters = 0;
   cfg->cuda_stream = nullptr;
   return SR_OK;
@@ -536,7 +547,31 @@ simrank_status simrank_init(const simrank_config* cfg_in, int32_t n, int64_t m, 
       cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess)
     return bail(fail(h, SR_ERR_CUDA, "no CUDA device"));
 
-  // --- host graph, validated
+  // --- caller id -> storage id: with relabel, nodes that have in-degree 0
+  // go after all others (their rows and columns of S are outside every
+  // affected area, Thm 4), keeping ascending order inside both groups.
+  h->ext2int.resize(h->n_cap);
+  h->int2ext.resize(h->n_cap);
+  for (int x = 0; x < h->n_cap; ++x) h->ext2int[x] = h->int2ext[x] = x;
+  if (cfg.relabel && m > 0) {
+    std::vector<char> has_in(n, 0);
+    for (int64_t e = 0; e < m; ++e)
+      if (dst[e] >= 0 && dst[e] < n) has_in[dst[e]] = 1;
+    int next = 0;
+    for (int pass = 1; pass >= 0; --pass)
+      for (int x = 0; x < n; ++x)
+        if (has_in[x] == pass) h->ext2int[x] = next++;
+    for (int x = 0; x < n; ++x) h->int2ext[h->ext2int[x]] = x;
+    h->relabeled = true;
+  }
+  if (h->relabeled) {
+    if (dev_alloc(&h->d_ext2int, (size_t)h->n_cap) != cudaSuccess ||
+        cudaMemcpy(h->d_ext2int, h->ext2int.data(), h->n_cap * sizeof(int32_t),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(fail(h, SR_ERR_OOM, "cudaMalloc of the id map failed"));
+  }
+
+  // --- host graph (storage ids), validated
   std::vector<std::vector<int32_t>> in_rows(h->n_pad), out_rows(h->n_pad);
   std::vector<std::vector<float>> in_w(h->weighted ? h->n_pad : 0);
   h->edges.reserve((size_t)m * 2 + 16);
@@ -549,9 +584,18 @@ simrank_status simrank_init(const simrank_config* cfg_in, int32_t n, int64_t m, 
       return bail(fail(h, SR_ERR_EDGE_EXISTS, "duplicate edge " + std::to_string(e)));
     if (h->weighted && !(weight[e] > 0.0f))
       return bail(fail(h, SR_ERR_ARG, "edge weights must be > 0"));
-    in_rows[d].push_back(s);
-    out_rows[s].push_back(d);
-    if (h->weighted) in_w[d].push_back(weight[e]);
+    const int32_t si = h->ext2int[s], di = h->ext2int[d];
+    in_rows[di].push_back(si);
+    out_rows[si].push_back(di);
+    if (h->weighted) in_w[di].push_back(weight[e]);
+  }
+  if (h->relabeled) {
+    // the duplicate check above ran on caller ids; keep the edge set in storage ids
+    std::unordered_set<uint64_t> mapped;
+    mapped.reserve(h->edges.size() * 2 + 16);
+    for (uint64_t k : h->edges)
+      mapped.insert(ekey(h->ext2int[(int32_t)(k >> 32)], h->ext2int[(int32_t)(k & 0xffffffffu)]));
+    h->edges.swap(mapped);
   }
   build_adj(h->hin, h->n_pad, in_rows);
   build_adj(h->hout, h->n_pad, out_rows);
@@ -612,8 +656,21 @@ simrank_status simrank_init(const simrank_config* cfg_in, int32_t n, int64_t m, 
   cudaMemsetAsync(h->S, 0, s_bytes, h->st);
 
   if (S0) {
-    cudaError_t e = cudaMemcpy2DAsync(h->S, h->ld * eb, S0, (size_t)n * eb, (size_t)n * eb, n,
+    const void* src_S = S0;
+    std::vector<unsigned char> perm_S;
+    if (h->relabeled) {
+      perm_S.resize((size_t)n * n * eb);
+      for (int r = 0; r < n; ++r) {
+        const unsigned char* row = (const unsigned char*)S0 + (size_t)h->int2ext[r] * n * eb;
+        unsigned char* dstrow = perm_S.data() + (size_t)r * n * eb;
+        for (int c = 0; c < n; ++c)
+          std::memcpy(dstrow + (size_t)c * eb, row + (size_t)h->int2ext[c] * eb, eb);
+      }
+      src_S = perm_S.data();
+    }
+    cudaError_t e = cudaMemcpy2DAsync(h->S, h->ld * eb, src_S, (size_t)n * eb, (size_t)n * eb, n,
                                       cudaMemcpyHostToDevice, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     if (e != cudaSuccess) return bail(fail(h, SR_ERR_CUDA, "upload of S0 failed"));
     launch_set_diag(h->S, cfg.s_precision, n, h->n_cap, h->ld, 1.0 - cfg.C, h->st);
     if (cudaStreamSynchronize(h->st) != cudaSuccess)
@@ -640,8 +697,16 @@ simrank_status simrank_apply_updates(simrank_t h, const simrank_update* u, int64
   if (count < 0 || (count > 0 && !u)) return fail(h, SR_ERR_ARG, "bad update array");
   if (count == 0) return SR_OK;
   if (h->weighted) return fail(h, SR_ERR_UNSUPPORTED, "updates on a weighted graph");
+  // caller ids -> storage ids (new ids >= n_cur map to themselves)
+  std::vector<simrank_update> um(u, u + count);
+  auto to_int = [&](int32_t x) { return (x >= 0 && x < h->n_cap) ? h->ext2int[x] : x; };
+  if (h->relabeled)
+    for (auto& v : um) {
+      v.src = to_int(v.src);
+      v.dst = to_int(v.dst);
+    }
   int n_after = h->n_cur;
-  simrank_status s = validate(h, u, count, &n_after);
+  simrank_status s = validate(h, um.data(), count, &n_after);
   if (s != SR_OK) return s;
 
   // Plan the rank-one updates: (sink, op, sources, d_j, patch op range).
@@ -677,12 +742,16 @@ simrank_status simrank_apply_updates(simrank_t h, const simrank_update* u, int64
     plan.push_back(r);
   };
   if (h->cfg.apply == SR_APPLY_UNIT) {
-    for (int64_t t = 0; t < count; ++t) add_r1(u[t].dst, u[t].op, {u[t].src});
+    for (int64_t t = 0; t < count; ++t) add_r1(um[t].dst, um[t].op, {um[t].src});
   } else {
+    // the canonical block order is defined on caller ids
     std::vector<Block> blocks;
     std::string msg;
     if ((s = plan_blocks(u, count, n_old, blocks, msg)) != SR_OK) return fail(h, s, msg);
-    for (const Block& b : blocks) add_r1(b.sink, b.op, b.srcs);
+    for (Block& b : blocks) {
+      for (int32_t& x : b.srcs) x = to_int(x);
+      add_r1(to_int(b.sink), b.op, b.srcs);
+    }
   }
   h->n_cur = n_after;
   if ((s = grow_pool(h, h->din, h->hin)) != SR_OK) return s;
@@ -711,6 +780,10 @@ simrank_status simrank_columns(simrank_t h, const int32_t* cols, int32_t ncols, 
   for (int c = 0; c < ncols; ++c)
     if (cols[c] < 0 || cols[c] >= h->n_cur) return fail(h, SR_ERR_ARG, "column id out of range");
   if (ncols == 0) return SR_OK;
+  std::vector<int32_t> icols(cols, cols + ncols);
+  for (int32_t& x : icols) x = h->ext2int[x];
+  cols = icols.data();
+  const int32_t* perm = h->relabeled ? h->d_ext2int : nullptr;
   if (ncols > h->cols_cap) {
     if (h->d_cols) cudaFree(h->d_cols);
     h->cols_cap = ncols;
@@ -720,16 +793,16 @@ simrank_status simrank_columns(simrank_t h, const int32_t* cols, int32_t ncols, 
                               h->st));
   const size_t ob = (size_t)h->n_cur * ncols * (out_fp64 ? 8 : 4);
   if (out_on_device) {
-    launch_copy_cols(h->S, h->cfg.s_precision, h->ld, h->d_cols, ncols, h->n_cur, out, out_fp64,
-                     h->st);
+    launch_copy_cols(h->S, h->cfg.s_precision, h->ld, h->d_cols, perm, ncols, h->n_cur, out,
+                     out_fp64, h->st);
     LAUNCH_CHECK(h);
     CUDA_TRY(h, cudaStreamSynchronize(h->st));  // cols staging reuse safety
     return SR_OK;
   }
   void* tmp = nullptr;
   CUDA_TRY(h, cudaMalloc(&tmp, ob));
-  launch_copy_cols(h->S, h->cfg.s_precision, h->ld, h->d_cols, ncols, h->n_cur, tmp, out_fp64,
-                   h->st);
+  launch_copy_cols(h->S, h->cfg.s_precision, h->ld, h->d_cols, perm, ncols, h->n_cur, tmp,
+                   out_fp64, h->st);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, ob, cudaMemcpyDeviceToHost, h->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);

@@ -50,80 +50,163 @@ __global__ void k_gather_rows(const T* __restrict__ S, int64_t ld, const int32_t
   }
 }
 
-// One CTA per 128-row tile; 16 warps x 8 rows.  Every CTA first recomputes
-// w_j = (1/delta) [Q]_{j,*} S_{*,I} (needed by lambda, Eq. 29b) from row j
-// of the old CSR, then each warp forms w_a = (1/delta) [Q]_{a,*} S_{*,I} for
-// its rows and the gamma entry of the branch (op, d_j).
-__global__ void __launch_bounds__(512) k_gamma(DevAdj in, const double* __restrict__ sI,
-                                               const double* __restrict__ sJ,
-                                               const double* __restrict__ scal, int j, int delta,
-                                               int op, int d_j, double C, int K1,
-                                               double* __restrict__ P64, float* __restrict__ P32,
-                                               uint64_t* __restrict__ mXi,
-                                               uint64_t* __restrict__ mEta) {
-  __shared__ double red[16];
+// Per-tile sparse gather used by the gamma and chain kernels.  One CTA owns
+// the 128 rows of tile T; the nonzeros of those rows are flattened (row
+// offsets by an exclusive scan in shared memory) and split into contiguous
+// runs, one per thread, so rows of any length - including hub rows with
+// thousands of in-neighbours - are spread over the whole CTA.  Each thread
+// sums its run in registers and flushes one partial sum per row it touches
+// into shared accumulators.  NV = number of gathered vectors (1 or 2).
+constexpr int GT = 256;  // threads of a gather CTA
+
+struct TileRows {
+  int64_t start[PT];
+  int len[PT];
+  int off[PT + 1];
+};
+
+__device__ __forceinline__ void tile_rows_load(const DevAdj& in, int T, TileRows& tr) {
+  const int tid = threadIdx.x;
+  if (tid < PT) {
+    tr.start[tid] = in.start[T * PT + tid];
+    tr.len[tid] = in.len[T * PT + tid];
+  }
+  __syncthreads();
+  if (tid < 32) {
+    // exclusive scan of 128 lengths by one warp (4 per lane)
+    int v[4], sum = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      v[q] = tr.len[tid * 4 + q];
+      sum += v[q];
+    }
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (tid >= o) incl += y;
+    }
+    int run = incl - sum;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      tr.off[tid * 4 + q] = run;
+      run += v[q];
+    }
+    if (tid == 31) tr.off[PT] = incl;
+  }
+  __syncthreads();
+}
+
+// acc[v][r] += sum over nonzeros b of row r of X_v[b], X_v given by gather(v, b)
+template <int NV, typename G>
+__device__ __forceinline__ void tile_gather(const DevAdj& in, const TileRows& tr, G gather,
+                                            double (*acc)[PT]) {
+  const int tid = threadIdx.x;
+  for (int r = tid; r < PT; r += GT)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v][r] = 0.0;
+  __syncthreads();
+  const int total = tr.off[PT];
+  const int per = (total + GT - 1) / GT;
+  const int e0 = tid * per;
+  const int e1 = min(total, e0 + per);
+  if (e0 < e1) {
+    int lo = 0, hi = PT;  // find r with off[r] <= e0 < off[r+1]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (tr.off[mid] <= e0) lo = mid; else hi = mid;
+    }
+    int r = lo;
+    double part[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) part[v] = 0.0;
+    for (int e = e0; e < e1; ++e) {
+      while (e >= tr.off[r + 1]) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          if (part[v] != 0.0) atomicAdd(&acc[v][r], part[v]);
+          part[v] = 0.0;
+        }
+        ++r;
+      }
+      const int b = in.col[tr.start[r] + (e - tr.off[r])];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) part[v] += gather(v, b);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+      if (part[v] != 0.0) atomicAdd(&acc[v][r], part[v]);
+  }
+  __syncthreads();
+}
+
+// gamma of Thm 3 (insert), Thm 9 (delete) and Table 2 (sink blocks) for the
+// rows of tile T, on the OLD graph: w = (1/delta) Q S_{*,I}, lambda from
+// Eq. 29b with w_j (row j recomputed by every CTA), then the gamma branch.
+__global__ void __launch_bounds__(GT) k_gamma(DevAdj in, const double* __restrict__ sI,
+                                              const double* __restrict__ sJ,
+                                              const double* __restrict__ scal, int j, int delta,
+                                              int op, int d_j, double C, int K1,
+                                              double* __restrict__ P64, float* __restrict__ P32,
+                                              uint64_t* __restrict__ mXi,
+                                              uint64_t* __restrict__ mEta) {
+  __shared__ TileRows tr;
+  __shared__ double acc[1][PT];
+  __shared__ double red[GT / 32];
   __shared__ int any_eta;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) any_eta = 0;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int T = blockIdx.x;
+  if (tid == 0) any_eta = 0;
   // w_j over row j of the old graph
-  double acc = 0.0;
+  double a = 0.0;
   const int64_t js = in.start[j];
   const int jl = in.len[j];
-  for (int e = threadIdx.x; e < jl; e += blockDim.x) acc += sI[in.col[js + e]];
-  acc = warp_sum(acc);
-  if (lane == 0) red[warp] = acc;
-  __syncthreads();
+  for (int e = tid; e < jl; e += GT) a += sI[in.col[js + e]];
+  a = warp_sum(a);
+  if (lane == 0) red[warp] = a;
+  tile_rows_load(in, T, tr);  // contains __syncthreads
   double wj = 0.0;
-  for (int w = 0; w < 16; ++w) wj += red[w];
-  wj = (jl > 0) ? wj / ((double)delta * (double)jl) : 0.0;
-  const double S_II = scal[0], S_jj = scal[1];
+  for (int w = 0; w < GT / 32; ++w) wj += red[w];
   const double dl = (double)delta;
+  wj = (jl > 0) ? wj / (dl * (double)jl) : 0.0;
+  const double S_II = scal[0], S_jj = scal[1];
   const double lam = S_II / (dl * dl) + S_jj / C - 2.0 * wj - 1.0 / C + 1.0;
-
-  const int T = blockIdx.x;
-  bool nz = false;
-  for (int rr = 0; rr < 8; ++rr) {
-    const int r = warp * 8 + rr;
-    const int a = T * PT + r;
-    const int64_t st = in.start[a];
-    const int len = in.len[a];
-    double s = 0.0;
-    for (int e = lane; e < len; e += 32) s += sI[in.col[st + e]];
-    s = warp_sum(s);
-    const double w = (len > 0) ? s / (dl * (double)len) : 0.0;
-    const double ej = (a == j) ? 1.0 : 0.0;
+  tile_gather<1>(in, tr, [&](int, int b) { return sI[b]; }, acc);
+  if (tid < PT) {
+    const int r = tid;
+    const int ai = T * PT + r;
+    const int len = tr.len[r];
+    const double w = (len > 0) ? acc[0][r] / (dl * (double)len) : 0.0;
+    const double ej = (ai == j) ? 1.0 : 0.0;
     double g;
     if (op > 0) {
       if (d_j == 0) {
         g = w + S_II / (2.0 * dl * dl) * ej;
       } else {
         const double dd = (double)d_j + dl;
-        g = (dl / dd) * (w - sJ[a] / C + (lam * dl / (2.0 * dd) + 1.0 / C - 1.0) * ej);
+        g = (dl / dd) * (w - sJ[ai] / C + (lam * dl / (2.0 * dd) + 1.0 / C - 1.0) * ej);
       }
     } else {
       if (d_j == delta) {
         g = -w + S_II / (2.0 * dl * dl) * ej;
       } else {
         const double dd = (double)d_j - dl;
-        g = (dl / dd) * (sJ[a] / C - w + (lam * dl / (2.0 * dd) - 1.0 / C + 1.0) * ej);
+        g = (dl / dd) * (sJ[ai] / C - w + (lam * dl / (2.0 * dd) - 1.0 / C + 1.0) * ej);
       }
     }
-    if (lane == 0) {
-      const int64_t bx = ((int64_t)T * 2 + 0) * K1 * PT + r;  // xi_0 entry
-      const int64_t be = ((int64_t)T * 2 + 1) * K1 * PT + r;  // eta_0 entry
-      const double x0 = (a == j) ? C : 0.0;
-      P64[bx] = x0;
-      P64[be] = g;
-      if (P32) {
-        P32[bx] = (float)x0;
-        P32[be] = (float)g;
-      }
-      nz = nz || (g != 0.0);
+    const int64_t bx = ((int64_t)T * 2 + 0) * K1 * PT + r;  // xi_0 entry
+    const int64_t be = ((int64_t)T * 2 + 1) * K1 * PT + r;  // eta_0 entry
+    const double x0 = (ai == j) ? C : 0.0;
+    P64[bx] = x0;
+    P64[be] = g;
+    if (P32) {
+      P32[bx] = (float)x0;
+      P32[be] = (float)g;
     }
+    if (g != 0.0) any_eta = 1;
   }
-  if (lane == 0 && nz) any_eta = 1;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     mXi[T] = (T == j / PT) ? 1ull : 0ull;
     mEta[T] = any_eta ? 1ull : 0ull;
   }
@@ -155,57 +238,47 @@ __global__ void k_patch(const PatchOp* __restrict__ ops, int64_t begin, int64_t 
 }
 
 // xi_{k+1}[a] = C * mean_{b in I(a)} xi_k[b], eta_{k+1}[a] = mean_{b in I(a)} eta_k[b]
-// on the patched (new) CSR; one CTA per 128-row tile.
-__global__ void __launch_bounds__(512) k_chain_step(DevAdj in, int k, double C, int K1,
-                                                    double* __restrict__ P64,
-                                                    float* __restrict__ P32,
-                                                    uint64_t* __restrict__ mXi,
-                                                    uint64_t* __restrict__ mEta) {
+// on the patched (new) CSR; one CTA per 128-row tile (Eq. 16a).
+__global__ void __launch_bounds__(GT) k_chain_step(DevAdj in, int k, double C, int K1,
+                                                   double* __restrict__ P64,
+                                                   float* __restrict__ P32,
+                                                   uint64_t* __restrict__ mXi,
+                                                   uint64_t* __restrict__ mEta) {
+  __shared__ TileRows tr;
+  __shared__ double acc[2][PT];
   __shared__ int any_x, any_e;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) {
+  const int tid = threadIdx.x;
+  const int T = blockIdx.x;
+  if (tid == 0) {
     any_x = 0;
     any_e = 0;
   }
-  __syncthreads();
-  const int T = blockIdx.x;
-  bool nzx = false, nze = false;
-  for (int rr = 0; rr < 8; ++rr) {
-    const int r = warp * 8 + rr;
-    const int a = T * PT + r;
-    const int64_t st = in.start[a];
-    const int len = in.len[a];
-    double sx = 0.0, se = 0.0;
-    for (int e = lane; e < len; e += 32) {
-      const int b = in.col[st + e];
-      const int64_t base = ((int64_t)(b / PT) * 2) * K1 * PT + (int64_t)k * PT + (b % PT);
-      sx += P64[base];
-      se += P64[base + (int64_t)K1 * PT];
+  tile_rows_load(in, T, tr);
+  const double* __restrict__ src = P64;
+  tile_gather<2>(in, tr,
+                 [&](int v, int b) {
+                   return src[(((int64_t)(b / PT) * 2 + v) * K1 + k) * PT + (b % PT)];
+                 },
+                 acc);
+  if (tid < PT) {
+    const int r = tid;
+    const int len = tr.len[r];
+    const double inv = (len > 0) ? 1.0 / (double)len : 0.0;
+    const double x = C * acc[0][r] * inv;
+    const double y = acc[1][r] * inv;
+    const int64_t bx = ((int64_t)T * 2 + 0) * K1 * PT + (int64_t)(k + 1) * PT + r;
+    const int64_t be = bx + (int64_t)K1 * PT;
+    P64[bx] = x;
+    P64[be] = y;
+    if (P32) {
+      P32[bx] = (float)x;
+      P32[be] = (float)y;
     }
-    sx = warp_sum(sx);
-    se = warp_sum(se);
-    if (lane == 0) {
-      const double inv = (len > 0) ? 1.0 / (double)len : 0.0;
-      const double x = C * sx * inv;
-      const double y = se * inv;
-      const int64_t bx = ((int64_t)T * 2 + 0) * K1 * PT + (int64_t)(k + 1) * PT + r;
-      const int64_t be = bx + (int64_t)K1 * PT;
-      P64[bx] = x;
-      P64[be] = y;
-      if (P32) {
-        P32[bx] = (float)x;
-        P32[be] = (float)y;
-      }
-      nzx = nzx || (x != 0.0);
-      nze = nze || (y != 0.0);
-    }
-  }
-  if (lane == 0) {
-    if (nzx) any_x = 1;
-    if (nze) any_e = 1;
+    if (x != 0.0) any_x = 1;
+    if (y != 0.0) any_e = 1;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     const unsigned long long bit = 1ull << ((k + 1) & 63);
     if (any_x) atomicOr((unsigned long long*)&mXi[T], bit);
     if (any_e) atomicOr((unsigned long long*)&mEta[T], bit);
@@ -248,7 +321,7 @@ void launch_gather_rows(const void* S, int s_prec, int64_t ld, const int32_t* I,
 void launch_gamma(const DevAdj& in, const double* sI, const double* sJ, const double* scal, int j,
                   int delta, int op, int d_j, double C, int nT, int K1, double* P64, float* P32,
                   uint64_t* mXi, uint64_t* mEta, cudaStream_t st) {
-  k_gamma<<<nT, 512, 0, st>>>(in, sI, sJ, scal, j, delta, op, d_j, C, K1, P64, P32, mXi, mEta);
+  k_gamma<<<nT, GT, 0, st>>>(in, sI, sJ, scal, j, delta, op, d_j, C, K1, P64, P32, mXi, mEta);
 }
 
 void launch_patch(const PatchOp* ops, int64_t begin, int64_t end, DevAdj in, DevAdj out,
@@ -258,7 +331,7 @@ void launch_patch(const PatchOp* ops, int64_t begin, int64_t end, DevAdj in, Dev
 
 void launch_chain_step(const DevAdj& in, int k, double C, int nT, int K1, double* P64, float* P32,
                        uint64_t* mXi, uint64_t* mEta, cudaStream_t st) {
-  k_chain_step<<<nT, 512, 0, st>>>(in, k, C, K1, P64, P32, mXi, mEta);
+  k_chain_step<<<nT, GT, 0, st>>>(in, k, C, K1, P64, P32, mXi, mEta);
 }
 
 void launch_tile_list(const uint64_t* mXi, const uint64_t* mEta, int nT, int aff, uint32_t* tiles,

@@ -149,12 +149,16 @@ __global__ void k_convert(const TA* __restrict__ A, TB* __restrict__ B, int64_t 
     B[e] = (TB)A[e];
 }
 
+// out[c * n + a] = S[cols[c], perm[a]] (perm = caller id -> storage id, or identity)
 template <typename TS, typename TO>
 __global__ void k_copy_cols(const TS* __restrict__ S, int64_t ld, const int32_t* __restrict__ cols,
-                            int n, TO* __restrict__ out) {
+                            const int32_t* __restrict__ perm, int n, TO* __restrict__ out) {
   const int c = blockIdx.y;
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
-  if (a < n) out[(int64_t)c * n + a] = (TO)S[(int64_t)cols[c] * ld + a];
+  if (a < n) {
+    const int p = perm ? perm[a] : a;
+    out[(int64_t)c * n + a] = (TO)S[(int64_t)cols[c] * ld + p];
+  }
 }
 
 }  // namespace
@@ -224,20 +228,20 @@ void launch_convert(const void* A, int a_prec, void* B, int b_prec, int64_t coun
     k_convert<float, float><<<blocks, 256, 0, st>>>((const float*)A, (float*)B, count);
 }
 
-void launch_copy_cols(const void* S, int s_prec, int64_t ld, const int32_t* cols, int ncols, int n,
-                      void* out, int out_fp64, cudaStream_t st) {
+void launch_copy_cols(const void* S, int s_prec, int64_t ld, const int32_t* cols, const int32_t* perm,
+                      int ncols, int n, void* out, int out_fp64, cudaStream_t st) {
   if (ncols <= 0 || n <= 0) return;
   dim3 grid((n + 255) / 256, ncols);
   if (s_prec == 64) {
     if (out_fp64)
-      k_copy_cols<double, double><<<grid, 256, 0, st>>>((const double*)S, ld, cols, n, (double*)out);
+      k_copy_cols<double, double><<<grid, 256, 0, st>>>((const double*)S, ld, cols, perm, n, (double*)out);
     else
-      k_copy_cols<double, float><<<grid, 256, 0, st>>>((const double*)S, ld, cols, n, (float*)out);
+      k_copy_cols<double, float><<<grid, 256, 0, st>>>((const double*)S, ld, cols, perm, n, (float*)out);
   } else {
     if (out_fp64)
-      k_copy_cols<float, double><<<grid, 256, 0, st>>>((const float*)S, ld, cols, n, (double*)out);
+      k_copy_cols<float, double><<<grid, 256, 0, st>>>((const float*)S, ld, cols, perm, n, (double*)out);
     else
-      k_copy_cols<float, float><<<grid, 256, 0, st>>>((const float*)S, ld, cols, n, (float*)out);
+      k_copy_cols<float, float><<<grid, 256, 0, st>>>((const float*)S, ld, cols, perm, n, (float*)out);
   }
 }
 

@@ -50,6 +50,10 @@ __device__ __forceinline__ void st4(T* p, const T (&v)[4]) {
   *reinterpret_cast<typename Vec4<T>::type*>(p) = x;
 }
 
+// Row pitch (elements) of the Delta tile staged in shared memory; odd, so
+// that both a row sweep and a column sweep of a warp hit 32 distinct banks.
+constexpr int DP = PT + 1;
+
 template <typename T, int KC, int MINB>
 __global__ void __launch_bounds__(256, MINB)
     k_s_update(T* __restrict__ S, int64_t ld, const T* __restrict__ P, int K1,
@@ -61,6 +65,7 @@ __global__ void __launch_bounds__(256, MINB)
   T* sEtaI = sXiI + KC * PT;
   T* sXiJ = sEtaI + KC * PT;
   T* sEtaJ = sXiJ + KC * PT;
+  T* sD = sEtaJ + KC * PT;  // [PT][DP] Delta tile
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int nt = *ntiles;
@@ -76,10 +81,13 @@ __global__ void __launch_bounds__(256, MINB)
 #pragma unroll
       for (int c = 0; c < 8; ++c) acc[r][c] = T(0);
 
+    // ---- phase 1: Delta_IJ = sum_k xi_k[I] eta_k[J]^T + eta_k[I] xi_k[J]^T (registers)
     for (int kb = k0g; kb < k1g; kb += KC) {
       const int kc = min(KC, k1g - kb);
-      __syncthreads();  // previous chunk / tile fully consumed
-      // copy kc x 128 entries of xi and eta for tiles I and J
+      uint64_t chunk = 0;
+      for (int kk = 0; kk < kc; ++kk) chunk |= 1ull << ((kb + kk) & 63);
+      if (((a1 | a2) & chunk) == 0) continue;  // no active term in this chunk
+      __syncthreads();  // previous chunk fully consumed
       const int nvec = kc * PT / 4;
       const T* gXiI = P + ((int64_t)I * 2 + 0) * K1 * PT + (int64_t)kb * PT;
       const T* gEtaI = P + ((int64_t)I * 2 + 1) * K1 * PT + (int64_t)kb * PT;
@@ -121,38 +129,56 @@ __global__ void __launch_bounds__(256, MINB)
       }
     }
 
-    // S[I, J] += Delta (rows r, columns c)
+    // ---- phase 2: stage Delta in shared memory
+    __syncthreads();  // previous tile's phase 3/4 readers are done with sD
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-      const int row = I * PT + ((r < 4) ? ty * 4 + r : 64 + ty * 4 + (r - 4));
-      T* p = S + (int64_t)row * ld + (int64_t)J * PT;
-      T v0[4], v1[4];
-      ld4(p + tx * 4, v0);
-      ld4(p + 64 + tx * 4, v1);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        v0[q] += acc[r][q];
-        v1[q] += acc[r][4 + q];
-      }
-      st4(p + tx * 4, v0);
-      st4(p + 64 + tx * 4, v1);
-    }
-    if (I != J) {
-      // S[J, I] += Delta^T
+      const int row = (r < 4) ? ty * 4 + r : 64 + ty * 4 + (r - 4);
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
-        const int row = J * PT + ((c < 4) ? tx * 4 + c : 64 + tx * 4 + (c - 4));
-        T* p = S + (int64_t)row * ld + (int64_t)I * PT;
-        T v0[4], v1[4];
-        ld4(p + ty * 4, v0);
-        ld4(p + 64 + ty * 4, v1);
+        const int col = (c < 4) ? tx * 4 + c : 64 + tx * 4 + (c - 4);
+        sD[row * DP + col] = acc[r][c];
+      }
+    }
+    __syncthreads();
+
+    // ---- phase 3: S[I, J] += Delta, one 512-byte row segment per warp access
+    {
+      constexpr int NQ = PT * PT / 4 / 256;  // 16 vectors of 4 per thread
+      T v[NQ][4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          v0[q] += acc[q][c];
-          v1[q] += acc[4 + q][c];
+      for (int q = 0; q < NQ; ++q) {
+        const int idx = tid + 256 * q;
+        const int row = idx >> 5, c4 = (idx & 31) * 4;
+        ld4p(S + (int64_t)(I * PT + row) * ld + (int64_t)J * PT + c4, v[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int idx = tid + 256 * q;
+        const int row = idx >> 5, c4 = (idx & 31) * 4;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[q][e] += sD[row * DP + c4 + e];
+        st4(S + (int64_t)(I * PT + row) * ld + (int64_t)J * PT + c4, v[q]);
+      }
+    }
+    // ---- phase 4: S[J, I] += Delta^T, a warp covers 32 consecutive columns
+    if (I != J) {
+      constexpr int NB = 16;  // loads in flight per thread
+#pragma unroll 1
+      for (int base = 0; base < PT * PT / 256; base += NB) {
+        T v[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+          const int e = tid + 256 * (base + q);
+          const int c = e >> 7, r = e & 127;
+          v[q] = S[(int64_t)(J * PT + c) * ld + (int64_t)I * PT + r];
         }
-        st4(p + ty * 4, v0);
-        st4(p + 64 + ty * 4, v1);
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+          const int e = tid + 256 * (base + q);
+          const int c = e >> 7, r = e & 127;
+          S[(int64_t)(J * PT + c) * ld + (int64_t)I * PT + r] = v[q] + sD[r * DP + c];
+        }
       }
     }
     if (tid == 0) {
@@ -169,7 +195,7 @@ __global__ void __launch_bounds__(256, MINB)
   }
 }
 
-constexpr int KC_F32 = 32;
+constexpr int KC_F32 = 16;
 constexpr int KC_F64 = 16;
 
 }  // namespace
@@ -180,7 +206,7 @@ void launch_s_update(void* S, int s_prec, int64_t ld, const void* P, int K1, con
                      const int* ntiles, const uint64_t* mXi, const uint64_t* mEta, int k0, int k1,
                      int use_masks, int n, int64_t* counters, int grid, cudaStream_t st) {
   if (s_prec == 64) {
-    const size_t smem = 4ull * KC_F64 * PT * sizeof(double);
+    const size_t smem = (4ull * KC_F64 * PT + (size_t)PT * DP) * sizeof(double);
     static bool attr64 = false;
     if (!attr64) {
       cudaFuncSetAttribute(k_s_update<double, KC_F64, 1>,
@@ -191,7 +217,7 @@ void launch_s_update(void* S, int s_prec, int64_t ld, const void* P, int K1, con
         (double*)S, ld, (const double*)P, K1, tiles, ntiles, mXi, mEta, k0, k1, use_masks, n,
         (unsigned long long*)counters);
   } else {
-    const size_t smem = 4ull * KC_F32 * PT * sizeof(float);
+    const size_t smem = (4ull * KC_F32 * PT + (size_t)PT * DP) * sizeof(float);
     static bool attr32 = false;
     if (!attr32) {
       cudaFuncSetAttribute(k_s_update<float, KC_F32, 2>,

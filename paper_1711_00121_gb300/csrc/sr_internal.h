@@ -117,8 +117,9 @@ void launch_symmetrize(void* A, int prec, int n_pad, int64_t ld, cudaStream_t st
 void launch_convert(const void* A, int a_prec, void* B, int b_prec, int64_t count, cudaStream_t st);
 void launch_set_diag(void* A, int prec, int from, int to, int64_t ld, double value, cudaStream_t st);
 
-// out[c * n + a] = S[cols[c], a]  (column c of the symmetric S)
-void launch_copy_cols(const void* S, int s_prec, int64_t ld, const int32_t* cols, int ncols, int n,
-                      void* out, int out_fp64, cudaStream_t st);
+// out[c * n + a] = S[cols[c], perm[a]]  (column c of the symmetric S in caller
+// order; perm maps caller ids to storage ids, nullptr = identity)
+void launch_copy_cols(const void* S, int s_prec, int64_t ld, const int32_t* cols, const int32_t* perm,
+                      int ncols, int n, void* out, int out_fp64, cudaStream_t st);
 
 }  // namespace sr
