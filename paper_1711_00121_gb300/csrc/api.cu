@@ -68,6 +68,11 @@ struct simrank_ctx {
   int64_t ops_cap = 0;
   int32_t* d_cols = nullptr;
   int64_t cols_cap = 0;
+  // one-shot batch scratch (grow-only)
+  struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+  } ob[12];
   // profiling
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
   size_t events_used = 0;
@@ -367,7 +372,7 @@ simrank_status run_rank_one(simrank_ctx* h, int64_t src_off, int delta, int j, i
   const int nT = (h->n_cur + PT - 1) / PT;
   const double C = h->cfg.C;
   launch_gather_rows(h->S, h->cfg.s_precision, h->ld, h->d_srcs + src_off, delta, j, nT * PT,
-                     h->sI, h->sJ, h->scal, h->st);
+                     h->din, h->sI, h->sJ, h->scal, h->st);
   launch_gamma(h->din, h->sI, h->sJ, h->scal, j, delta, op, d_j, C, nT, h->K1, h->P64,
                h->cfg.s_precision == 64 ? nullptr : h->P32, h->mXi, h->mEta, h->st);
   launch_patch(h->d_ops, op_begin, op_end, h->din, h->dout, h->st);
@@ -461,6 +466,206 @@ simrank_status jacobi_sweeps(simrank_ctx* h, int max_sweeps, double tol, double*
   return SR_OK;
 }
 
+simrank_status ob_ensure(simrank_ctx* h, int slot, size_t bytes) {
+  auto& b = h->ob[slot];
+  if (b.bytes >= bytes) return SR_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  CUDA_TRY(h, cudaMalloc(&b.p, std::max<size_t>(bytes, 256)));
+  b.bytes = bytes;
+  return SR_OK;
+}
+
+// The whole batch as one rank-2r update (proof of Thm 2 with dQ = U V^T over
+// the r distinct sinks).  `plus` / `minus` hold the net insertions and
+// deletions per sink (storage ids); `ops` turn the old graph into the new one.
+simrank_status run_one_shot(simrank_ctx* h, const std::map<int32_t, std::vector<int32_t>>& plus,
+                            const std::map<int32_t, std::vector<int32_t>>& minus,
+                            const std::vector<PatchOp>& ops) {
+  std::map<int32_t, std::pair<std::vector<int32_t>, std::vector<int32_t>>> sinks;
+  for (auto& kv : plus) sinks[kv.first].first = kv.second;
+  for (auto& kv : minus) sinks[kv.first].second = kv.second;
+  const int r = (int)sinks.size();
+  if (r == 0) return SR_OK;
+  const double C = h->cfg.C;
+  const int sp = h->cfg.s_precision;
+  std::vector<int32_t> sink_id, src;
+  std::vector<int8_t> sign;
+  std::vector<int64_t> off{0};
+  std::vector<double> av, bv;
+  for (auto& kv : sinks) {
+    const int32_t j = kv.first;
+    const auto& ins = kv.second.first;
+    const auto& del = kv.second.second;
+    // old in-degree: the mirror already holds the new graph, undo the net change
+    const int d_new = h->hin.len[j];
+    const int d_old = d_new - (int)ins.size() + (int)del.size();
+    double a, b;
+    if (d_old == 0) {
+      a = 0.0;
+      b = 1.0 / d_new;
+    } else if (d_new == 0) {
+      a = -1.0;
+      b = 0.0;
+    } else {
+      a = (double)d_old / d_new - 1.0;
+      b = 1.0 / d_new;
+    }
+    sink_id.push_back(j);
+    av.push_back(a);
+    bv.push_back(b);
+    for (int32_t x : ins) {
+      src.push_back(x);
+      sign.push_back(1);
+    }
+    if (d_new > 0)
+      for (int32_t x : del) {
+        src.push_back(x);
+        sign.push_back(-1);
+      }
+    off.push_back((int64_t)src.size());
+  }
+  const int n_pad = h->n_pad;
+  const int rp = (r + 3) / 4 * 4;
+  const int64_t nr = (int64_t)n_pad * rp;
+  simrank_status s;
+  // 0: small host->device arrays, 1: Zc / Yc, 2: Z, 3: Y, 4: Wc, 5: Lambda, 6/7: X ping-pong
+  const size_t small = (size_t)r * (4 + 8 + 8 + 8) + src.size() * 5 + 1024;
+  if ((s = ob_ensure(h, 0, small)) != SR_OK) return s;
+  if ((s = ob_ensure(h, 1, (size_t)nr * 8)) != SR_OK) return s;
+  if ((s = ob_ensure(h, 2, (size_t)nr * 8)) != SR_OK) return s;
+  if ((s = ob_ensure(h, 3, (size_t)nr * 8)) != SR_OK) return s;
+  if ((s = ob_ensure(h, 4, (size_t)nr * 8)) != SR_OK) return s;
+  if ((s = ob_ensure(h, 5, (size_t)r * r * 8)) != SR_OK) return s;
+  if ((s = ob_ensure(h, 6, (size_t)nr * 2 * 8)) != SR_OK) return s;
+  if ((s = ob_ensure(h, 7, (size_t)nr * 2 * 8)) != SR_OK) return s;
+  unsigned char* sm = (unsigned char*)h->ob[0].p;
+  int32_t* d_sinks = (int32_t*)sm;
+  double* d_av = (double*)(sm + (((size_t)r * 4 + 7) / 8) * 8);
+  double* d_bv = d_av + r;
+  int64_t* d_off = (int64_t*)(d_bv + r);
+  int32_t* d_src = (int32_t*)(d_off + r + 1);
+  int8_t* d_sign = (int8_t*)(d_src + src.size());
+  CUDA_TRY(h, cudaMemcpyAsync(d_sinks, sink_id.data(), r * 4, cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(d_av, av.data(), r * 8, cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(d_bv, bv.data(), r * 8, cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(d_off, off.data(), (r + 1) * 8, cudaMemcpyHostToDevice, h->st));
+  if (!src.empty()) {
+    CUDA_TRY(h, cudaMemcpyAsync(d_src, src.data(), src.size() * 4, cudaMemcpyHostToDevice, h->st));
+    CUDA_TRY(h, cudaMemcpyAsync(d_sign, sign.data(), src.size(), cudaMemcpyHostToDevice, h->st));
+  }
+  double* Zc = (double*)h->ob[1].p;
+  double* Z = (double*)h->ob[2].p;
+  double* Y = (double*)h->ob[3].p;
+  double* Wc = (double*)h->ob[4].p;
+  double* Lam = (double*)h->ob[5].p;
+  double* X = (double*)h->ob[6].p;
+  double* Xn = (double*)h->ob[7].p;
+  CUDA_TRY(h, cudaMemsetAsync(Z, 0, (size_t)nr * 8, h->st));
+  CUDA_TRY(h, cudaMemsetAsync(Y, 0, (size_t)nr * 8, h->st));
+  // Z = sum of signed source rows, Y = Q Z on the OLD graph
+  launch_signed_rows(h->S, sp, h->ld, d_src, d_sign, d_off, r, n_pad, Zc, h->st);
+  launch_transpose_rect(Zc, n_pad, Z, rp, r, n_pad, h->st);
+  launch_spmm_rows(h->din, nullptr, nullptr, Z, 64, rp, Y, 64, rp, n_pad, rp, 1.0, 0.0, 0, h->st);
+  launch_transpose_rect(Y, rp, Zc, n_pad, n_pad, r, h->st);  // Yc into buffer 1
+  launch_lambda(h->S, sp, h->ld, d_sinks, d_av, d_bv, Y, Z, rp, d_src, d_sign, d_off, r, C, Lam,
+                h->st);
+  launch_w_assemble(h->S, sp, h->ld, d_sinks, d_av, d_bv, Zc, Lam, r, n_pad, C, Wc, h->st);
+  LAUNCH_CHECK(h);
+  h->launches += 7;
+  // the graph becomes the new one
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_ops, ops.data(), ops.size() * sizeof(PatchOp),
+                              cudaMemcpyHostToDevice, h->st));
+  launch_patch(h->d_ops, 0, (int64_t)ops.size(), h->din, h->dout, h->st);
+  // X_0 = [C U | W] (row-major, 2 rp columns)
+  const int64_t ldx = 2 * rp;
+  CUDA_TRY(h, cudaMemsetAsync(X, 0, (size_t)nr * 2 * 8, h->st));
+  CUDA_TRY(h, cudaMemsetAsync(Xn, 0, (size_t)nr * 2 * 8, h->st));
+  launch_xi0(d_sinks, r, C, X, ldx, h->st);
+  launch_transpose_rect(Wc, n_pad, X + rp, ldx, r, n_pad, h->st);
+  LAUNCH_CHECK(h);
+  h->launches += 3;
+
+  // k-groups: as many terms per S pass as fit an operand budget
+  const bool tc = h->cfg.tc != 0 && sp == 32;
+  const int nT = (h->n_cur + PT - 1) / PT;
+  const size_t budget = (size_t)8 << 30;
+  const size_t per_k = tc ? (size_t)n_pad * 2 * (size_t)((r + 31) / 32 * 32) * 4 * 2
+                          : (size_t)n_pad * 2 * (size_t)r * (sp == 64 ? 8 : 4);
+  const int g = (int)std::max<size_t>(1, std::min<size_t>((size_t)h->K1, budget / per_k));
+  const int rg = tc ? ((g * r + 31) / 32) * 32 : g * r;
+  const int64_t kd = 2 * (int64_t)rg;
+  if (tc) {
+    if ((s = ob_ensure(h, 8, (size_t)n_pad * kd * 4)) != SR_OK) return s;
+    if ((s = ob_ensure(h, 9, (size_t)n_pad * kd * 4)) != SR_OK) return s;
+  } else {
+    if ((s = ob_ensure(h, 8, (size_t)h->nT_cap * 2 * (size_t)(g * r) * PT * (sp == 64 ? 8 : 4))) !=
+        SR_OK)
+      return s;
+  }
+  const long long wait_limit = h->cfg.timeout_iters > 0 ? h->cfg.timeout_iters : (1ll << 24);
+  int slot = 0;
+  for (int k = 0; k <= h->cfg.K; ++k) {
+    if (k > 0) {
+      launch_spmm_rows(h->din, nullptr, nullptr, X, 64, ldx, Xn, 64, ldx, n_pad, rp, C, 0.0, 0, h->st);
+      launch_spmm_rows(h->din, nullptr, nullptr, X + rp, 64, ldx, Xn + rp, 64, ldx, n_pad, rp, 1.0,
+                       0.0, 0, h->st);
+      std::swap(X, Xn);
+      h->launches += 2;
+    }
+    if (slot == 0) {
+      if (tc) {
+        CUDA_TRY(h, cudaMemsetAsync(h->ob[8].p, 0, (size_t)n_pad * kd * 4, h->st));
+        CUDA_TRY(h, cudaMemsetAsync(h->ob[9].p, 0, (size_t)n_pad * kd * 4, h->st));
+      } else {
+        CUDA_TRY(h, cudaMemsetAsync(h->mXi, 0, h->nT_cap * sizeof(uint64_t), h->st));
+        CUDA_TRY(h, cudaMemsetAsync(h->mEta, 0, h->nT_cap * sizeof(uint64_t), h->st));
+      }
+    }
+    if (tc)
+      launch_pack_tc(X, ldx, rp, r, slot, rg, n_pad, (float*)h->ob[8].p, (float*)h->ob[9].p, kd,
+                     h->st);
+    else
+      launch_pack_ffma(X, ldx, rp, r, slot, g * r, nT, h->ob[8].p, sp, h->mXi, h->mEta, h->st);
+    LAUNCH_CHECK(h);
+    h->launches += 1;
+    ++slot;
+    if (slot == g || k == h->cfg.K) {
+      CUDA_TRY(h, cudaMemsetAsync(h->ntiles, 0, sizeof(int), h->st));
+      launch_tile_list(h->mXi, h->mEta, nT, tc ? 0 : (h->cfg.aff ? 1 : 0), h->tiles, h->ntiles,
+                       h->st);
+      h->launches += 1;
+      std::pair<cudaEvent_t, cudaEvent_t>* ev = nullptr;
+      if (h->cfg.profile) {
+        ev = next_event_pair(h);
+        if (!ev) return fail(h, SR_ERR_CUDA, "cudaEventCreate failed");
+        CUDA_TRY(h, cudaEventRecord(ev->first, h->st));
+      }
+      if (tc) {
+        const int rc = launch_s_update_tc((float*)h->S, h->ld, (const float*)h->ob[8].p,
+                                          (const float*)h->ob[9].p, n_pad, kd, h->tiles, h->ntiles,
+                                          h->n_cur, h->counters, h->num_sms, wait_limit, h->st);
+        if (rc != 0) return fail(h, SR_ERR_CUDA, "tensor-core S update: launch setup failed");
+      } else {
+        launch_s_update(h->S, sp, h->ld, h->ob[8].p, g * r, h->tiles, h->ntiles, h->mXi, h->mEta,
+                        0, slot * r, h->cfg.aff ? 1 : 0, h->n_cur, h->counters,
+                        s_update_grid(sp, h->num_sms), h->st);
+      }
+      LAUNCH_CHECK(h);
+      if (ev) CUDA_TRY(h, cudaEventRecord(ev->second, h->st));
+      h->launches += 1;
+      h->prof_launches += 1;
+      h->stats.tiles_total += (int64_t)nT * (nT + 1) / 2;
+      slot = 0;
+    }
+  }
+  h->stats.rank_one_updates += 0;
+  // keep host staging alive until the copies above have run
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return SR_OK;
+}
+
 void free_ctx(simrank_ctx* h) {
   if (!h) return;
   void* ptrs[] = {h->din.start, h->din.len,  h->din.col,   h->dout.start, h->dout.len,
@@ -470,6 +675,8 @@ void free_ctx(simrank_ctx* h) {
                   h->d_srcs,    h->d_ops,    h->d_cols,     h->d_ext2int};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (auto& b : h->ob)
+    if (b.p) cudaFree(b.p);
   for (auto& e : h->events) {
     cudaEventDestroy(e.first);
     cudaEventDestroy(e.second);
@@ -521,8 +728,8 @@ simrank_status simrank_init(const simrank_config* cfg_in, int32_t n, int64_t m, 
   if ((int64_t)cfg.n_capacity > (int64_t)65535 * PT)
     return fail(nullptr, SR_ERR_ARG, "n_capacity too large for 16-bit tile indices");
   if (cfg.apply < 0 || cfg.apply > 2) return fail(nullptr, SR_ERR_ARG, "bad apply mode");
-  if (cfg.apply == SR_APPLY_ONE_SHOT)
-    return fail(nullptr, SR_ERR_UNSUPPORTED, "one-shot batches are not available in this build");
+  if (cfg.tc && cfg.s_precision != 32)
+    return fail(nullptr, SR_ERR_ARG, "the tensor-core update needs s_precision = 32");
   if (cfg.init_tol <= 0.0) cfg.init_tol = 1e-13;
   if (cfg.init_max_sweeps <= 0) cfg.init_max_sweeps = 400;
 
@@ -741,6 +948,35 @@ simrank_status simrank_apply_updates(simrank_t h, const simrank_update* u, int64
     r.op_end = (int64_t)ops.size();
     plan.push_back(r);
   };
+  if (h->cfg.apply == SR_APPLY_ONE_SHOT) {
+    // net update per sink, in storage ids; then one rank-2r update
+    std::vector<Block> blocks;
+    std::string msg;
+    if ((s = plan_blocks(um.data(), count, n_old, blocks, msg)) != SR_OK) return fail(h, s, msg);
+    std::map<int32_t, std::vector<int32_t>> plus, minus;
+    for (const Block& b : blocks) {
+      auto& dstv = (b.op > 0 ? plus : minus)[b.sink];
+      dstv.insert(dstv.end(), b.srcs.begin(), b.srcs.end());
+      for (int32_t i : b.srcs) {
+        if (b.op > 0) {
+          adj_append(h->hin, b.sink, i, ops, true);
+          adj_append(h->hout, i, b.sink, ops, false);
+          h->edges.insert(ekey(i, b.sink));
+        } else {
+          adj_remove(h->hin, b.sink, i, ops, true);
+          adj_remove(h->hout, i, b.sink, ops, false);
+          h->edges.erase(ekey(i, b.sink));
+        }
+      }
+    }
+    h->n_cur = n_after;
+    if ((s = grow_pool(h, h->din, h->hin)) != SR_OK) return s;
+    if ((s = grow_pool(h, h->dout, h->hout)) != SR_OK) return s;
+    if ((s = ensure_dev_capacity(h, 1, (int64_t)ops.size())) != SR_OK) return s;
+    if ((s = run_one_shot(h, plus, minus, ops)) != SR_OK) return s;
+    h->stats.updates += count;
+    return SR_OK;
+  }
   if (h->cfg.apply == SR_APPLY_UNIT) {
     for (int64_t t = 0; t < count; ++t) add_r1(um[t].dst, um[t].op, {um[t].src});
   } else {
@@ -818,6 +1054,9 @@ const char* simrank_last_error(simrank_t h) { return h ? h->err.c_str() : g_init
 simrank_status simrank_sync(simrank_t h) {
   if (!h) return fail(nullptr, SR_ERR_ARG, "null handle");
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  int64_t status = 0;
+  CUDA_TRY(h, cudaMemcpy(&status, h->counters + CNT_STATUS, sizeof(status), cudaMemcpyDeviceToHost));
+  if (status != 0) return fail(h, (simrank_status)status, "a bounded device wait ran out");
   return SR_OK;
 }
 

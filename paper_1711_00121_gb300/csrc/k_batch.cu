@@ -1,0 +1,234 @@
+// One-shot batch update (rank-2r Sylvester form).  For a whole batch,
+// dQ = U V^T with U = [e_{j_1} .. e_{j_r}] (the r distinct sinks) and
+// V_t = Q_new[j_t,:]^T - Q[j_t,:]^T.  The proof of Thm 2 (Eq. 23-28) carries
+// over column by column: Delta S = sum_k C^{k+1} Q_new^k T Q_new^kT with
+// T = U W^T + W U^T, W = Q S V + U Lambda / 2, Lambda = V^T S V.  With
+// V_t = a_t Q[j_t,:]^T + b_t e_{D_t} (e_{D_t} = inserted minus deleted sources
+// of sink j_t) and Eq. 33 (Q S Q[j,:]^T = (S_{*,j} - (1-C) e_j) / C), W and
+// Lambda need only the S rows of the batch's endpoints.  These kernels build
+// W and Lambda, the panels Xi_k = C^{k+1} Q_new^k U, H_k = Q_new^k W, and the
+// operand layouts of the two S-update kernels.
+#include "sr_internal.h"
+
+namespace sr {
+
+namespace {
+
+// Zc[t][a] = sum_{e in [off[t], off[t+1])} sign[e] * S[src[e], a]
+template <typename T>
+__global__ void k_signed_rows(const T* __restrict__ S, int64_t ld, const int32_t* __restrict__ src,
+                              const int8_t* __restrict__ sign, const int64_t* __restrict__ off,
+                              int n_pad, double* __restrict__ Zc) {
+  const int t = blockIdx.y;
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n_pad) return;
+  double acc = 0.0;
+  for (int64_t e = off[t]; e < off[t + 1]; ++e) {
+    const double v = (double)S[(int64_t)src[e] * ld + a];
+    acc += sign[e] > 0 ? v : -v;
+  }
+  Zc[(int64_t)t * n_pad + a] = acc;
+}
+
+// B[c * ldb + r] = A[r * lda + c] for r < rows, c < cols (32 x 32 tiles)
+__global__ void k_transpose_rect(const double* __restrict__ A, int64_t lda, double* __restrict__ B,
+                                 int64_t ldb, int rows, int cols) {
+  __shared__ double tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int q = threadIdx.y; q < 32; q += 8) {
+    const int r = r0 + q, c = c0 + threadIdx.x;
+    tile[q][threadIdx.x] = (r < rows && c < cols) ? A[(int64_t)r * lda + c] : 0.0;
+  }
+  __syncthreads();
+  for (int q = threadIdx.y; q < 32; q += 8) {
+    const int c = c0 + q, r = r0 + threadIdx.x;
+    if (c < cols && r < rows) B[(int64_t)c * ldb + r] = tile[threadIdx.x][q];
+  }
+}
+
+// Lambda[t][u] = V_t^T S V_u with V_t = a_t Q[j_t,:]^T + b_t e_{D_t}:
+//   a_t a_u (S[j_t, j_u] - (1-C) [t == u]) / C      (Eq. 33-34)
+// + a_t b_u Y[j_t][u] + b_t a_u Y[j_u][t]           (Y = Q Z, row-major)
+// + b_t b_u sum_{e in D_t} sign_e Z[src_e][u]       (Z row-major)
+template <typename T>
+__global__ void k_lambda(const T* __restrict__ S, int64_t ld, const int32_t* __restrict__ sinks,
+                         const double* __restrict__ av, const double* __restrict__ bv,
+                         const double* __restrict__ Y, const double* __restrict__ Z, int64_t ldz,
+                         const int32_t* __restrict__ src, const int8_t* __restrict__ sign,
+                         const int64_t* __restrict__ off, int r, double C,
+                         double* __restrict__ Lam) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.y;
+  if (u >= r) return;
+  const int jt = sinks[t], ju = sinks[u];
+  const double at = av[t], au = av[u], bt = bv[t], bu = bv[u];
+  double v = at * au * ((double)S[(int64_t)jt * ld + ju] - (t == u ? 1.0 - C : 0.0)) / C;
+  v += at * bu * Y[(int64_t)jt * ldz + u] + bt * au * Y[(int64_t)ju * ldz + t];
+  double d = 0.0;
+  for (int64_t e = off[t]; e < off[t + 1]; ++e) {
+    const double z = Z[(int64_t)src[e] * ldz + u];
+    d += sign[e] > 0 ? z : -z;
+  }
+  v += bt * bu * d;
+  Lam[(int64_t)t * r + u] = v;
+}
+
+// Wc[t][a] = a_t (S[j_t, a] - (1-C) [a == j_t]) / C + b_t Yc[t][a]
+template <typename T>
+__global__ void k_w_assemble(const T* __restrict__ S, int64_t ld, const int32_t* __restrict__ sinks,
+                             const double* __restrict__ av, const double* __restrict__ bv,
+                             const double* __restrict__ Yc, int n_pad, double C,
+                             double* __restrict__ Wc) {
+  const int t = blockIdx.y;
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n_pad) return;
+  const int jt = sinks[t];
+  const double s = (double)S[(int64_t)jt * ld + a] - (a == jt ? 1.0 - C : 0.0);
+  Wc[(int64_t)t * n_pad + a] = av[t] * s / C + bv[t] * Yc[(int64_t)t * n_pad + a];
+}
+
+// Wc[t][j_u] += Lambda[u][t] / 2  (the U Lambda / 2 term of W; sinks are distinct)
+__global__ void k_w_lambda(const int32_t* __restrict__ sinks, const double* __restrict__ Lam, int r,
+                           int n_pad, double* __restrict__ Wc) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int u = blockIdx.y;
+  if (t >= r) return;
+  Wc[(int64_t)t * n_pad + sinks[u]] += 0.5 * Lam[(int64_t)u * r + t];
+}
+
+// X0 (row-major, ldx): X0[j_t][t] = C for the xi half (columns [0, r))
+__global__ void k_xi0(const int32_t* __restrict__ sinks, int r, double C, double* __restrict__ X0,
+                      int64_t ldx) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < r) X0[(int64_t)sinks[t] * ldx + t] = C;
+}
+
+// Panels for the CUDA-core S update from X_k (row-major FP64, xi half at
+// column 0, eta half at column rh): term = slot * r + t of the tile-blocked
+// layout P[T][which][term][128] with `terms` terms; ORs AFF bits (term % 64).
+template <typename TP>
+__global__ void k_pack_ffma(const double* __restrict__ X, int64_t ldx, int rh, int r, int slot,
+                            int terms, int nT, TP* __restrict__ Pn, uint64_t* __restrict__ mXi,
+                            uint64_t* __restrict__ mEta) {
+  // block: 128 rows of tile T, threads over (row, t) with row fastest
+  const int T = blockIdx.x;
+  const int t = blockIdx.y * 2 + (threadIdx.x >> 7);
+  const int row = threadIdx.x & 127;
+  __shared__ int anyx[2], anye[2];
+  if (threadIdx.x < 2) {
+    anyx[threadIdx.x] = 0;
+    anye[threadIdx.x] = 0;
+  }
+  __syncthreads();
+  if (t < r) {
+    const int64_t a = (int64_t)T * PT + row;
+    const double x = X[a * ldx + t];
+    const double e = X[a * ldx + rh + t];
+    const int term = slot * r + t;
+    Pn[(((int64_t)T * 2 + 0) * terms + term) * PT + row] = (TP)x;
+    Pn[(((int64_t)T * 2 + 1) * terms + term) * PT + row] = (TP)e;
+    if (x != 0.0) anyx[threadIdx.x >> 7] = 1;
+    if (e != 0.0) anye[threadIdx.x >> 7] = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 && blockIdx.y * 2 + threadIdx.x < r) {
+    const int term = slot * r + blockIdx.y * 2 + threadIdx.x;
+    const unsigned long long bit = 1ull << (term & 63);
+    if (anyx[threadIdx.x]) atomicOr((unsigned long long*)&mXi[T], bit);
+    if (anye[threadIdx.x]) atomicOr((unsigned long long*)&mEta[T], bit);
+  }
+}
+
+// Round to TF32 (10 explicit mantissa bits), round-to-nearest-even on the
+// dropped 13 bits; the result is an FP32 value whose low 13 bits are zero.
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t u = __float_as_uint(x);
+  if ((u & 0x7f800000u) == 0x7f800000u) return x;  // inf / nan unchanged
+  const uint32_t lsb = (u >> 13) & 1u;
+  u += 0x0fffu + lsb;
+  u &= 0xffffe000u;
+  return __uint_as_float(u);
+}
+
+// Operands of the tensor-core S update from X_k: row-major A_hi, A_lo with
+// kd columns; xi terms at column slot * r + t, eta terms at rg + slot * r + t.
+// A value x is split as hi = tf32(x), lo = tf32(x - hi).
+__global__ void k_pack_tc(const double* __restrict__ X, int64_t ldx, int rh, int r, int slot,
+                          int rg, int n_rows, float* __restrict__ Ahi, float* __restrict__ Alo,
+                          int64_t kd) {
+  const int64_t a = blockIdx.x;
+  const int t = blockIdx.y * blockDim.x + threadIdx.x;
+  if (t >= r || a >= n_rows) return;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const float x = (float)X[a * ldx + h * rh + t];
+    const float hi = tf32_round(x);
+    const float lo = tf32_round(x - hi);
+    const int64_t c = (int64_t)h * rg + (int64_t)slot * r + t;
+    Ahi[a * kd + c] = hi;
+    Alo[a * kd + c] = lo;
+  }
+}
+
+}  // namespace
+
+void launch_signed_rows(const void* S, int s_prec, int64_t ld, const int32_t* src, const int8_t* sign,
+                        const int64_t* off, int r, int n_pad, double* Zc, cudaStream_t st) {
+  dim3 grid((n_pad + 255) / 256, r);
+  if (s_prec == 64)
+    k_signed_rows<double><<<grid, 256, 0, st>>>((const double*)S, ld, src, sign, off, n_pad, Zc);
+  else
+    k_signed_rows<float><<<grid, 256, 0, st>>>((const float*)S, ld, src, sign, off, n_pad, Zc);
+}
+
+void launch_transpose_rect(const double* A, int64_t lda, double* B, int64_t ldb, int rows, int cols,
+                           cudaStream_t st) {
+  dim3 grid((cols + 31) / 32, (rows + 31) / 32), block(32, 8);
+  k_transpose_rect<<<grid, block, 0, st>>>(A, lda, B, ldb, rows, cols);
+}
+
+void launch_lambda(const void* S, int s_prec, int64_t ld, const int32_t* sinks, const double* av,
+                   const double* bv, const double* Y, const double* Z, int64_t ldz,
+                   const int32_t* src, const int8_t* sign, const int64_t* off, int r, double C,
+                   double* Lam, cudaStream_t st) {
+  dim3 grid((r + 127) / 128, r);
+  if (s_prec == 64)
+    k_lambda<double><<<grid, 128, 0, st>>>((const double*)S, ld, sinks, av, bv, Y, Z, ldz, src, sign,
+                                          off, r, C, Lam);
+  else
+    k_lambda<float><<<grid, 128, 0, st>>>((const float*)S, ld, sinks, av, bv, Y, Z, ldz, src, sign,
+                                         off, r, C, Lam);
+}
+
+void launch_w_assemble(const void* S, int s_prec, int64_t ld, const int32_t* sinks, const double* av,
+                       const double* bv, const double* Yc, const double* Lam, int r, int n_pad,
+                       double C, double* Wc, cudaStream_t st) {
+  dim3 grid((n_pad + 255) / 256, r);
+  if (s_prec == 64)
+    k_w_assemble<double><<<grid, 256, 0, st>>>((const double*)S, ld, sinks, av, bv, Yc, n_pad, C, Wc);
+  else
+    k_w_assemble<float><<<grid, 256, 0, st>>>((const float*)S, ld, sinks, av, bv, Yc, n_pad, C, Wc);
+  dim3 g2((r + 127) / 128, r);
+  k_w_lambda<<<g2, 128, 0, st>>>(sinks, Lam, r, n_pad, Wc);
+}
+
+void launch_xi0(const int32_t* sinks, int r, double C, double* X0, int64_t ldx, cudaStream_t st) {
+  k_xi0<<<(r + 127) / 128, 128, 0, st>>>(sinks, r, C, X0, ldx);
+}
+
+void launch_pack_ffma(const double* X, int64_t ldx, int rh, int r, int slot, int terms, int nT,
+                      void* Pn, int p_prec, uint64_t* mXi, uint64_t* mEta, cudaStream_t st) {
+  dim3 grid(nT, (r + 1) / 2);
+  if (p_prec == 64)
+    k_pack_ffma<double><<<grid, 256, 0, st>>>(X, ldx, rh, r, slot, terms, nT, (double*)Pn, mXi, mEta);
+  else
+    k_pack_ffma<float><<<grid, 256, 0, st>>>(X, ldx, rh, r, slot, terms, nT, (float*)Pn, mXi, mEta);
+}
+
+void launch_pack_tc(const double* X, int64_t ldx, int rh, int r, int slot, int rg, int n_rows,
+                    float* Ahi, float* Alo, int64_t kd, cudaStream_t st) {
+  dim3 grid(n_rows, (r + 127) / 128);
+  k_pack_tc<<<grid, 128, 0, st>>>(X, ldx, rh, r, slot, rg, n_rows, Ahi, Alo, kd);
+}
+
+}  // namespace sr

@@ -17,9 +17,11 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Block 0 also forms w_j = (1/delta) [Q]_{j,*} S_{*,I} on the old graph
+// (= (1/(delta d_j)) sum_{b in I(j)} sum_t S[I[t], b]) for lambda (Eq. 29b).
 template <typename T>
 __global__ void k_gather_rows(const T* __restrict__ S, int64_t ld, const int32_t* __restrict__ I,
-                              int delta, int j, int n_pad, double* __restrict__ sI,
+                              int delta, int j, int n_pad, DevAdj in, double* __restrict__ sI,
                               double* __restrict__ sJ, double* __restrict__ scal) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a < n_pad) {
@@ -29,22 +31,39 @@ __global__ void k_gather_rows(const T* __restrict__ S, int64_t ld, const int32_t
     sJ[a] = ld_s(S + (int64_t)j * ld + a);
   }
   if (blockIdx.x == 0) {
-    __shared__ double red[32];
+    __shared__ double red[2][32];
     double acc = 0.0;
     const int64_t tot = (int64_t)delta * delta;
+#pragma unroll 4
     for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
       const int t = (int)(e / delta), u = (int)(e % delta);
       acc += ld_s(S + (int64_t)I[t] * ld + I[u]);
     }
+    const int64_t js = in.start[j];
+    const int jl = in.len[j];
+    const int64_t tot2 = (int64_t)delta * jl;
+    double wj = 0.0;
+#pragma unroll 8
+    for (int64_t e = threadIdx.x; e < tot2; e += blockDim.x) {
+      const int t = (int)(e / jl), u = (int)(e % jl);
+      wj += ld_s(S + (int64_t)I[t] * ld + in.col[js + u]);
+    }
     acc = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    wj = warp_sum(wj);
+    if ((threadIdx.x & 31) == 0) {
+      red[0][threadIdx.x >> 5] = acc;
+      red[1][threadIdx.x >> 5] = wj;
+    }
     __syncthreads();
     if (threadIdx.x < 32) {
-      double v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+      double v = (threadIdx.x < (blockDim.x >> 5)) ? red[0][threadIdx.x] : 0.0;
+      double w = (threadIdx.x < (blockDim.x >> 5)) ? red[1][threadIdx.x] : 0.0;
       v = warp_sum(v);
+      w = warp_sum(w);
       if (threadIdx.x == 0) {
         scal[0] = v;
         scal[1] = ld_s(S + (int64_t)j * ld + j);
+        scal[2] = (jl > 0) ? w / ((double)delta * (double)jl) : 0.0;
       }
     }
   }
@@ -57,7 +76,7 @@ __global__ void k_gather_rows(const T* __restrict__ S, int64_t ld, const int32_t
 // thousands of in-neighbours - are spread over the whole CTA.  Each thread
 // sums its run in registers and flushes one partial sum per row it touches
 // into shared accumulators.  NV = number of gathered vectors (1 or 2).
-constexpr int GT = 256;  // threads of a gather CTA
+constexpr int GT = 512;  // threads of a gather CTA
 
 struct TileRows {
   int64_t start[PT];
@@ -120,18 +139,42 @@ __device__ __forceinline__ void tile_gather(const DevAdj& in, const TileRows& tr
     double part[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) part[v] = 0.0;
-    for (int e = e0; e < e1; ++e) {
-      while (e >= tr.off[r + 1]) {
+    // batches of 8 nonzeros: all column loads, then all gathers, are independent
+    constexpr int B = 8;
+    for (int e = e0; e < e1; e += B) {
+      int rr[B], bb[B];
+      int rc = r;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          if (part[v] != 0.0) atomicAdd(&acc[v][r], part[v]);
-          part[v] = 0.0;
+      for (int q = 0; q < B; ++q) {
+        const int ee = e + q;
+        if (ee < e1) {
+          while (ee >= tr.off[rc + 1]) ++rc;
+          rr[q] = rc;
+          bb[q] = in.col[tr.start[rc] + (ee - tr.off[rc])];
+        } else {
+          rr[q] = -1;
+          bb[q] = 0;
         }
-        ++r;
       }
-      const int b = in.col[tr.start[r] + (e - tr.off[r])];
+      double xv[NV][B];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) part[v] += gather(v, b);
+      for (int q = 0; q < B; ++q)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) xv[v][q] = (rr[q] >= 0) ? gather(v, bb[q]) : 0.0;
+#pragma unroll
+      for (int q = 0; q < B; ++q) {
+        if (rr[q] < 0) break;
+        if (rr[q] != r) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            if (part[v] != 0.0) atomicAdd(&acc[v][r], part[v]);
+            part[v] = 0.0;
+          }
+          r = rr[q];
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) part[v] += xv[v][q];
+      }
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v)
@@ -152,24 +195,13 @@ __global__ void __launch_bounds__(GT) k_gamma(DevAdj in, const double* __restric
                                               uint64_t* __restrict__ mEta) {
   __shared__ TileRows tr;
   __shared__ double acc[1][PT];
-  __shared__ double red[GT / 32];
   __shared__ int any_eta;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   const int T = blockIdx.x;
   if (tid == 0) any_eta = 0;
-  // w_j over row j of the old graph
-  double a = 0.0;
-  const int64_t js = in.start[j];
-  const int jl = in.len[j];
-  for (int e = tid; e < jl; e += GT) a += sI[in.col[js + e]];
-  a = warp_sum(a);
-  if (lane == 0) red[warp] = a;
   tile_rows_load(in, T, tr);  // contains __syncthreads
-  double wj = 0.0;
-  for (int w = 0; w < GT / 32; ++w) wj += red[w];
   const double dl = (double)delta;
-  wj = (jl > 0) ? wj / (dl * (double)jl) : 0.0;
-  const double S_II = scal[0], S_jj = scal[1];
+  const double S_II = scal[0], S_jj = scal[1], wj = scal[2];
   const double lam = S_II / (dl * dl) + S_jj / C - 2.0 * wj - 1.0 / C + 1.0;
   tile_gather<1>(in, tr, [&](int, int b) { return sI[b]; }, acc);
   if (tid < PT) {
@@ -307,15 +339,16 @@ __global__ void k_tile_list(const uint64_t* __restrict__ mXi, const uint64_t* __
 }  // namespace
 
 void launch_gather_rows(const void* S, int s_prec, int64_t ld, const int32_t* I, int delta, int j,
-                        int n_pad, double* sI, double* sJ, double* scal, cudaStream_t st) {
+                        int n_pad, const DevAdj& in, double* sI, double* sJ, double* scal,
+                        cudaStream_t st) {
   const int threads = 256;
   const int blocks = (n_pad + threads - 1) / threads;
   if (s_prec == 64)
-    k_gather_rows<double><<<blocks, threads, 0, st>>>((const double*)S, ld, I, delta, j, n_pad, sI,
-                                                      sJ, scal);
+    k_gather_rows<double><<<blocks, threads, 0, st>>>((const double*)S, ld, I, delta, j, n_pad, in,
+                                                      sI, sJ, scal);
   else
-    k_gather_rows<float><<<blocks, threads, 0, st>>>((const float*)S, ld, I, delta, j, n_pad, sI,
-                                                     sJ, scal);
+    k_gather_rows<float><<<blocks, threads, 0, st>>>((const float*)S, ld, I, delta, j, n_pad, in,
+                                                     sI, sJ, scal);
 }
 
 void launch_gamma(const DevAdj& in, const double* sI, const double* sJ, const double* scal, int j,

@@ -161,24 +161,23 @@ __global__ void __launch_bounds__(256, MINB)
         st4(S + (int64_t)(I * PT + row) * ld + (int64_t)J * PT + c4, v[q]);
       }
     }
-    // ---- phase 4: S[J, I] += Delta^T, a warp covers 32 consecutive columns
+    // ---- phase 4: S[J, I] += Delta^T; a warp covers one 512-byte row segment
+    // (lane -> 4 consecutive columns), 16 vector loads in flight per thread
     if (I != J) {
-      constexpr int NB = 16;  // loads in flight per thread
-#pragma unroll 1
-      for (int base = 0; base < PT * PT / 256; base += NB) {
-        T v[NB];
+      constexpr int NQ = PT * PT / 4 / 256;
+      const int lane = tid & 31, warp = tid >> 5;
+      T v[NQ][4];
 #pragma unroll
-        for (int q = 0; q < NB; ++q) {
-          const int e = tid + 256 * (base + q);
-          const int c = e >> 7, r = e & 127;
-          v[q] = S[(int64_t)(J * PT + c) * ld + (int64_t)I * PT + r];
-        }
+      for (int q = 0; q < NQ; ++q) {
+        const int c = warp + 8 * q;
+        ld4p(S + (int64_t)(J * PT + c) * ld + (int64_t)I * PT + lane * 4, v[q]);
+      }
 #pragma unroll
-        for (int q = 0; q < NB; ++q) {
-          const int e = tid + 256 * (base + q);
-          const int c = e >> 7, r = e & 127;
-          S[(int64_t)(J * PT + c) * ld + (int64_t)I * PT + r] = v[q] + sD[r * DP + c];
-        }
+      for (int q = 0; q < NQ; ++q) {
+        const int c = warp + 8 * q;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[q][e] += sD[(lane * 4 + e) * DP + c];
+        st4(S + (int64_t)(J * PT + c) * ld + (int64_t)I * PT + lane * 4, v[q]);
       }
     }
     if (tid == 0) {

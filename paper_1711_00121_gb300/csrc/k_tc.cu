@@ -1,0 +1,337 @@
+// Tensor-core (tcgen05) symmetric rank-update of S for the one-shot batch form:
+//   S[I,J] += D_IJ,  S[J,I] += D_IJ^T  (I <= J),   D = A B^T,
+// where row a of A is [xi terms | eta terms] and row a of B is the same row
+// with its two halves swapped, so A B^T = Xi H^T + H Xi^T (proof of Thm 2,
+// Eq. 23-28, applied to all sinks of a batch).  FP32 accuracy from the TF32
+// tensor pipe with the 3-term split x = hi + lo:
+//   D = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T,  accumulated in FP32 (TMEM).
+//
+// One CTA per SM, persistent over the tile-pair list.  Warp 0 issues TMA loads
+// (128 x 32 FP32 boxes, 128-byte swizzle) into a 3-stage ring; warp 1 owns the
+// TMEM accumulator (128 lanes x 128 columns) and issues tcgen05.mma (M = 128,
+// N = 128, K = 8); warps 2-5 read the accumulator with tcgen05.ld and update S
+// in HBM.  Every mbarrier wait is bounded: on timeout the kernel records a
+// status word, skips the remaining work and still frees its TMEM.
+#include <cuda.h>
+
+#include "sr_internal.h"
+
+namespace sr {
+
+namespace {
+
+constexpr int TM = 128;            // rows of an S tile (M)
+constexpr int TN = 128;            // columns of an S tile (N)
+constexpr int KCH = 32;            // FP32 elements of K per stage (one 128-byte swizzle row)
+constexpr int STAGES = 3;
+constexpr int OPB = TM * KCH * 4;  // bytes of one operand box: 16 KB
+constexpr int STAGE_BYTES = 4 * OPB;
+constexpr int TC_THREADS = 192;
+constexpr uint32_t TMEM_COLS = 128;
+
+// tcgen05 instruction descriptor, kind::tf32: D = F32, A = B = TF32, both
+// K-major, N = 128, M = 128.
+constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                           ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Bounded wait for the phase of `parity` to complete.  Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit,
+                                          volatile int* abort_flag) {
+  for (long long it = 0; it < limit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((it & 1023) == 1023 && *abort_flag) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(16u >> 4) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_s_update_tc(const __grid_constant__ CUtensorMap tm_hi,
+                  const __grid_constant__ CUtensorMap tm_lo, float* __restrict__ S, int64_t ld,
+                  const uint32_t* __restrict__ tiles, const int* __restrict__ ntiles, int nkb,
+                  long long wait_limit, int n, unsigned long long* __restrict__ counters) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES];
+  __shared__ __align__(8) uint64_t bar_acc_full, bar_acc_empty;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const int nt = *ntiles;
+  const int half = nkb / 2;  // B row = A row with its halves swapped
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&bar_full[s]), 1);
+      mbar_init(smem_u32(&bar_empty[s]), 1);
+    }
+    mbar_init(smem_u32(&bar_acc_full), 1);
+    mbar_init(smem_u32(&bar_acc_empty), 128);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  bool ok = true;
+
+  if (warp == 0) {
+    // ---------------- TMA producer
+    if (lane == 0) {
+      uint32_t it = 0;
+      for (int t = blockIdx.x; t < nt && ok; t += gridDim.x) {
+        const uint32_t pr = tiles[t];
+        const int I = (int)(pr >> 16), J = (int)(pr & 0xffffu);
+        for (int kb = 0; kb < nkb && ok; ++kb, ++it) {
+          const int s = it % STAGES;
+          const uint32_t ph = (it / STAGES) & 1u;
+          if (!mbar_wait(smem_u32(&bar_empty[s]), ph ^ 1u, wait_limit, &abort_flag)) {
+            ok = false;
+            break;
+          }
+          const uint32_t st = base + s * STAGE_BYTES;
+          const uint32_t fb = smem_u32(&bar_full[s]);
+          mbar_expect_tx(fb, STAGE_BYTES);
+          const int kb_b = kb < half ? kb + half : kb - half;
+          tma_load_2d(st + 0 * OPB, &tm_hi, kb * KCH, I * TM, fb);
+          tma_load_2d(st + 1 * OPB, &tm_lo, kb * KCH, I * TM, fb);
+          tma_load_2d(st + 2 * OPB, &tm_hi, kb_b * KCH, J * TN, fb);
+          tma_load_2d(st + 3 * OPB, &tm_lo, kb_b * KCH, J * TN, fb);
+        }
+      }
+      if (!ok) abort_flag = 1;
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      uint32_t it = 0, tl = 0;
+      for (int t = blockIdx.x; t < nt && ok; t += gridDim.x, ++tl) {
+        if (!mbar_wait(smem_u32(&bar_acc_empty), (tl & 1u) ^ 1u, wait_limit, &abort_flag)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = it % STAGES;
+          const uint32_t ph = (it / STAGES) & 1u;
+          if (!mbar_wait(smem_u32(&bar_full[s]), ph, wait_limit, &abort_flag)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t st = base + s * STAGE_BYTES;
+          const uint64_t a_hi = smem_desc(st + 0 * OPB), a_lo = smem_desc(st + 1 * OPB);
+          const uint64_t b_hi = smem_desc(st + 2 * OPB), b_lo = smem_desc(st + 3 * OPB);
+#pragma unroll
+          for (int kk = 0; kk < KCH / 8; ++kk) {
+            const uint64_t adv = (uint64_t)(kk * 32) >> 4;  // 8 TF32 = 32 bytes along K
+            const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
+            mma_tf32(tmem, a_hi + adv, b_hi + adv, first);
+            mma_tf32(tmem, a_hi + adv, b_lo + adv, 1u);
+            mma_tf32(tmem, a_lo + adv, b_hi + adv, 1u);
+          }
+          mma_commit(smem_u32(&bar_empty[s]));  // stage reusable once these MMAs finish
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&bar_acc_full));
+      }
+      if (!ok) abort_flag = 1;
+    }
+  } else {
+    // ---------------- epilogue: warps 2..5, TMEM lanes 32 * (warp % 4) ..
+    const int quarter = warp & 3;
+    const int row = quarter * 32 + lane;
+    uint32_t tl = 0;
+    unsigned long long my_tiles = 0, my_bytes = 0;
+    for (int t = blockIdx.x; t < nt; t += gridDim.x, ++tl) {
+      if (!mbar_wait(smem_u32(&bar_acc_full), tl & 1u, wait_limit, &abort_flag)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t pr = tiles[t];
+      const int I = (int)(pr >> 16), J = (int)(pr & 0xffffu);
+      float* srow = S + (int64_t)(I * TM + row) * ld + (int64_t)J * TN;
+#pragma unroll 1
+      for (int c0 = 0; c0 < TN; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+        for (int q = 0; q < 32; q += 4) {
+          float4 x = *reinterpret_cast<float4*>(srow + c0 + q);
+          x.x += v[q];
+          x.y += v[q + 1];
+          x.z += v[q + 2];
+          x.w += v[q + 3];
+          *reinterpret_cast<float4*>(srow + c0 + q) = x;
+        }
+        if (I != J) {
+          // S[J*128 + c][I*128 + row]: the warp's 32 lanes cover 128 contiguous bytes
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            float* p = S + (int64_t)(J * TN + c0 + q) * ld + (int64_t)I * TM + row;
+            *p += v[q];
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(smem_u32(&bar_acc_empty));
+      if (threadIdx.x == 64) {
+        const long long vr = max(0, min(TM, n - I * TM)), vc = max(0, min(TN, n - J * TN));
+        my_tiles += 1;
+        my_bytes += (unsigned long long)(vr * vc) * 8ull * (I == J ? 1ull : 2ull);
+      }
+    }
+    if (!ok) abort_flag = 1;
+    if (threadIdx.x == 64 && my_tiles) {
+      atomicAdd(&counters[CNT_TILES_TOUCHED], my_tiles);
+      atomicAdd(&counters[CNT_S_BYTES], my_bytes);
+    }
+  }
+
+  __syncthreads();
+  if (threadIdx.x == 0 && abort_flag) atomicExch(&counters[CNT_STATUS], (unsigned long long)SR_ERR_TIMEOUT);
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS));
+  }
+}
+
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                              CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                              CUtensorMapFloatOOBfill);
+
+EncodeFn encode_fn() {
+  static EncodeFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeFn)p;
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, float* ptr, int64_t rows, int64_t kd) {
+  EncodeFn f = encode_fn();
+  if (!f) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)kd, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)kd * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)KCH, (cuuint32_t)TM};
+  const cuuint32_t estr[2] = {1, 1};
+  return f(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, ptr, dims, strides, box, estr,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+// A_hi / A_lo: row-major [n_rows][kd] FP32 (TF32 values), kd a multiple of
+// 2 * 32; the B operand is A with its two column halves swapped.
+int launch_s_update_tc(float* S, int64_t ld, const float* Ahi, const float* Alo, int64_t n_rows,
+                       int64_t kd, const uint32_t* tiles, const int* ntiles, int n,
+                       int64_t* counters, int grid, long long wait_limit, cudaStream_t st) {
+  if (kd % (2 * KCH) != 0 || n_rows % TM != 0) return 1;
+  CUtensorMap mhi, mlo;
+  if (!make_map(&mhi, const_cast<float*>(Ahi), n_rows, kd)) return 2;
+  if (!make_map(&mlo, const_cast<float*>(Alo), n_rows, kd)) return 2;
+  const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_s_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  k_s_update_tc<<<grid, TC_THREADS, smem, st>>>(mhi, mlo, S, ld, tiles, ntiles, (int)(kd / KCH),
+                                                wait_limit, n, (unsigned long long*)counters);
+  return 0;
+}
+
+}  // namespace sr

@@ -69,9 +69,11 @@ enum Counter : int {
 // ---------------------------------------------------------------------------
 
 // sI[a] = sum_t S[I[t], a], sJ[a] = S[j, a] (a < n_pad, FP64);
-// scal[0] = sum_{t,t'} S[I[t], I[t']], scal[1] = S[j, j].
+// scal[0] = sum_{t,t'} S[I[t], I[t']], scal[1] = S[j, j],
+// scal[2] = w_j = (1/delta) [Q]_{j,*} S_{*,I} on the graph `in` (the old one).
 void launch_gather_rows(const void* S, int s_prec, int64_t ld, const int32_t* I, int delta, int j,
-                        int n_pad, double* sI, double* sJ, double* scal, cudaStream_t st);
+                        int n_pad, const DevAdj& in, double* sI, double* sJ, double* scal,
+                        cudaStream_t st);
 
 // gamma of Thm 3 / Thm 9 / Table 2 on the OLD graph; writes xi_0 = C e_j and
 // eta_0 = gamma into the panels (FP64 and, for FP32 S, FP32) and writes the
@@ -121,5 +123,32 @@ void launch_set_diag(void* A, int prec, int from, int to, int64_t ld, double val
 // order; perm maps caller ids to storage ids, nullptr = identity)
 void launch_copy_cols(const void* S, int s_prec, int64_t ld, const int32_t* cols, const int32_t* perm,
                       int ncols, int n, void* out, int out_fp64, cudaStream_t st);
+
+// ---- one-shot batch (rank-2r) pieces, k_batch.cu
+// Zc[t][a] = sum_{e in block t} sign[e] * S[src[e], a], a < n_pad
+void launch_signed_rows(const void* S, int s_prec, int64_t ld, const int32_t* src, const int8_t* sign,
+                        const int64_t* off, int r, int n_pad, double* Zc, cudaStream_t st);
+// B[c * ldb + r] = A[r * lda + c]
+void launch_transpose_rect(const double* A, int64_t lda, double* B, int64_t ldb, int rows, int cols,
+                           cudaStream_t st);
+// Lambda = V^T S V (r x r) from S rows of the sinks, Y = Q Z and Z (row-major, ldz)
+void launch_lambda(const void* S, int s_prec, int64_t ld, const int32_t* sinks, const double* av,
+                   const double* bv, const double* Y, const double* Z, int64_t ldz,
+                   const int32_t* src, const int8_t* sign, const int64_t* off, int r, double C,
+                   double* Lam, cudaStream_t st);
+// Wc[t][a] = a_t (S[j_t,a] - (1-C)[a==j_t]) / C + b_t Yc[t][a] + Lambda[u][t]/2 [a == j_u]
+void launch_w_assemble(const void* S, int s_prec, int64_t ld, const int32_t* sinks, const double* av,
+                       const double* bv, const double* Yc, const double* Lam, int r, int n_pad,
+                       double C, double* Wc, cudaStream_t st);
+void launch_xi0(const int32_t* sinks, int r, double C, double* X0, int64_t ldx, cudaStream_t st);
+void launch_pack_ffma(const double* X, int64_t ldx, int rh, int r, int slot, int terms, int nT,
+                      void* Pn, int p_prec, uint64_t* mXi, uint64_t* mEta, cudaStream_t st);
+void launch_pack_tc(const double* X, int64_t ldx, int rh, int r, int slot, int rg, int n_rows,
+                    float* Ahi, float* Alo, int64_t kd, cudaStream_t st);
+// tcgen05 symmetric update S += A B^T (B = A with halves swapped), 3xTF32; returns
+// 0 on launch, 1 for a bad shape, 2 if no tensor map could be encoded.
+int launch_s_update_tc(float* S, int64_t ld, const float* Ahi, const float* Alo, int64_t n_rows,
+                       int64_t kd, const uint32_t* tiles, const int* ntiles, int n,
+                       int64_t* counters, int grid, long long wait_limit, cudaStream_t st);
 
 }  // namespace sr
