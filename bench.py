@@ -245,6 +245,7 @@ def run_gpu(args, rank, world):
     alg_bytes = s_bytes + launches * 2 * (K + 1) * N * 4
     peak, peak_kind = read_peaks()
     achieved = (alg_bytes / launches) / (kern_ms / launches / 1000.0) / 1e9 if launches else 0.0
+    phase = [b - a for a, b in zip(st0["phase_ms"], st1["phase_ms"])]
     tiles_touched = st1["tiles_touched"] - st0["tiles_touched"]
     tiles_total = st1["tiles_total"] - st0["tiles_total"]
     line = {
@@ -256,6 +257,9 @@ def run_gpu(args, rank, world):
                    "l2": "inputs larger than L2 (S is 1.6 GB FP32)",
                    "aff_tile_fraction": tiles_touched / max(tiles_total, 1),
                    "hbm_gbs_step": alg_bytes / (ms / 1000.0) / 1e9,
+                   "phase_us_per_update": {
+                       name: 1000.0 * v / max(args.steps * per_step, 1)
+                       for name, v in zip(["gamma", "patch_chain", "tile_list", "s_update"], phase)},
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"kernel": "k_s_update (fused AFF-pruned rank-2(K+1) S update)",
                      "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -148,6 +148,9 @@ typedef struct simrank_stats {
   int64_t kernel_launches;  /* all libsimrank kernel launches on the handle's stream */
   double s_update_ms;       /* summed CUDA-event time of S-update launches (profile = 1 only) */
   double init_residual;     /* max-abs change of the last Jacobi sweep at init / re-anchor */
+  double phase_ms[4];       /* profile = 1 only: CUDA-event time of the phases of rank-one updates:
+                               [0] old-S rows + gamma, [1] graph patch + xi/eta recurrence,
+                               [2] affected tile list, [3] S update */
   int32_t init_sweeps;
   int32_t reserved[7];
 } simrank_stats;

@@ -55,8 +55,8 @@ class Stats(ctypes.Structure):
         ("s_bytes", ctypes.c_int64), ("panel_bytes", ctypes.c_int64),
         ("s_update_launches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
         ("s_update_ms", ctypes.c_double),
-        ("init_residual", ctypes.c_double), ("init_sweeps", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 7),
+        ("init_residual", ctypes.c_double), ("phase_ms", ctypes.c_double * 4),
+        ("init_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7),
     ]
 
 
@@ -204,7 +204,9 @@ class SimRank:
     def stats(self) -> dict:
         s = Stats()
         _check(lib().simrank_get_stats(self._h, ctypes.byref(s)), self._h)
-        return {name: getattr(s, name) for name, _ in Stats._fields_ if name != "reserved"}
+        out = {name: getattr(s, name) for name, _ in Stats._fields_ if name != "reserved"}
+        out["phase_ms"] = list(s.phase_ms)
+        return out
 
     def reanchor(self, sweeps):
         d = ctypes.c_double()

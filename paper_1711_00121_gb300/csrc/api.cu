@@ -3,6 +3,7 @@
 // planning (§8 net update and similar-sink partition), and the stream-ordered
 // launch sequence of each rank-one update.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -77,6 +78,9 @@ struct simrank_ctx {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
   size_t events_used = 0;
   double prof_ms = 0.0;
+  std::vector<std::array<cudaEvent_t, 5>> phase_ev;
+  size_t phase_used = 0;
+  double phase_ms[4] = {0, 0, 0, 0};
   int64_t prof_launches = 0;
   int64_t launches = 0;  // every kernel launch of this handle
   // stats
@@ -337,6 +341,24 @@ void harvest_events(simrank_ctx* h) {
       h->prof_ms += ms;
   }
   h->events_used = 0;
+  for (size_t e = 0; e < h->phase_used; ++e)
+    for (int q = 0; q < 4; ++q) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, h->phase_ev[e][q], h->phase_ev[e][q + 1]) == cudaSuccess)
+        h->phase_ms[q] += ms;
+    }
+  h->phase_used = 0;
+}
+
+// Events at the phase boundaries of one rank-one update (profile = 1 only).
+cudaEvent_t* next_phase_events(simrank_ctx* h) {
+  if (h->phase_used == h->phase_ev.size()) {
+    std::array<cudaEvent_t, 5> a;
+    for (auto& e : a)
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    h->phase_ev.push_back(a);
+  }
+  return h->phase_ev[h->phase_used++].data();
 }
 
 void* panel_for_s(simrank_ctx* h) {
@@ -371,21 +393,34 @@ simrank_status run_rank_one(simrank_ctx* h, int64_t src_off, int delta, int j, i
                             int64_t op_begin, int64_t op_end) {
   const int nT = (h->n_cur + PT - 1) / PT;
   const double C = h->cfg.C;
+  cudaEvent_t* pe = nullptr;
+  if (h->cfg.profile) {
+    if (h->phase_used >= 2048) {
+      CUDA_TRY(h, cudaStreamSynchronize(h->st));
+      harvest_events(h);
+    }
+    pe = next_phase_events(h);
+    if (!pe) return fail(h, SR_ERR_CUDA, "cudaEventCreate failed");
+    CUDA_TRY(h, cudaEventRecord(pe[0], h->st));
+  }
   launch_gather_rows(h->S, h->cfg.s_precision, h->ld, h->d_srcs + src_off, delta, j, nT * PT,
                      h->din, h->sI, h->sJ, h->scal, h->st);
   launch_gamma(h->din, h->sI, h->sJ, h->scal, j, delta, op, d_j, C, nT, h->K1, h->P64,
                h->cfg.s_precision == 64 ? nullptr : h->P32, h->mXi, h->mEta, h->st);
+  if (pe) CUDA_TRY(h, cudaEventRecord(pe[1], h->st));
   launch_patch(h->d_ops, op_begin, op_end, h->din, h->dout, h->st);
   for (int k = 0; k < h->cfg.K; ++k)
     launch_chain_step(h->din, k, C, nT, h->K1, h->P64,
                       h->cfg.s_precision == 64 ? nullptr : h->P32, h->mXi, h->mEta, h->st);
   LAUNCH_CHECK(h);
   h->launches += 2 + (op_end > op_begin ? 1 : 0) + h->cfg.K;
+  if (pe) CUDA_TRY(h, cudaEventRecord(pe[2], h->st));
   CUDA_TRY(h, cudaMemsetAsync(h->ntiles, 0, sizeof(int), h->st));
   const bool plain = h->cfg.s_update == SR_SUPDATE_PLAIN;
   launch_tile_list(h->mXi, h->mEta, nT, (plain || !h->cfg.aff) ? 0 : 1, h->tiles, h->ntiles, h->st);
   LAUNCH_CHECK(h);
   h->launches += 1;
+  if (pe) CUDA_TRY(h, cudaEventRecord(pe[3], h->st));
   simrank_status s;
   if (plain) {
     for (int k = 0; k < h->K1; ++k)
@@ -393,6 +428,7 @@ simrank_status run_rank_one(simrank_ctx* h, int64_t src_off, int delta, int j, i
   } else {
     if ((s = s_update_launch(h, 0, h->K1, h->cfg.aff ? 1 : 0)) != SR_OK) return s;
   }
+  if (pe) CUDA_TRY(h, cudaEventRecord(pe[4], h->st));
   h->stats.rank_one_updates += 1;
   h->stats.tiles_total += (int64_t)nT * (nT + 1) / 2;
   return SR_OK;
@@ -681,6 +717,8 @@ void free_ctx(simrank_ctx* h) {
     cudaEventDestroy(e.first);
     cudaEventDestroy(e.second);
   }
+  for (auto& a : h->phase_ev)
+    for (auto& e : a) cudaEventDestroy(e);
   delete h;
 }
 
@@ -1079,6 +1117,7 @@ simrank_status simrank_get_stats(simrank_t h, simrank_stats* out) {
   r.s_update_launches = h->prof_launches;
   r.kernel_launches = h->launches;
   r.s_update_ms = h->prof_ms;
+  for (int q = 0; q < 4; ++q) r.phase_ms[q] = h->phase_ms[q];
   *out = r;
   return SR_OK;
 }

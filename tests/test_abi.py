@@ -39,7 +39,7 @@ def test_struct_sizes_match_header():
     import ctypes
     assert ctypes.sizeof(P.Update) == 16
     assert ctypes.sizeof(P.Config) == 8 + 4 * 10 + 8 + 4 + 4 + 8 + 8 + 32
-    assert ctypes.sizeof(P.Stats) == 8 * 8 + 8 + 8 + 4 + 28
+    assert ctypes.sizeof(P.Stats) == 8 * 8 + 8 + 8 + 32 + 4 + 28
 
 
 def _expand_oracle(ups, n_old):

@@ -67,7 +67,9 @@ def test_one_shot_fp32_vs_definition(P, tc):
     want = O.one_shot_batch(n_final, s, d, ns, nd, Sp, C, K)
     got = sr.dense()
     assert maxabs(got, want) < TOL32
-    assert maxabs(got, got.T) < 1e-7
+    # S is symmetric (Eq. 1); in FP32 the diagonal tiles of the tensor-core
+    # update accumulate D[r][c] and D[c][r] in different orders
+    assert maxabs(got, got.T) < TOL32
 
 
 def test_one_shot_tc_matches_ffma_many_chunks(P):
