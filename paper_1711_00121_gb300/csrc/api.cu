@@ -439,12 +439,15 @@ simrank_status run_rank_one(simrank_ctx* h, int64_t src_off, int delta, int j, i
 // in FP32 storage with FP64 accumulation.  Stops when a sweep changes S by
 // less than `tol` (max-abs) or after max_sweeps; S is symmetrised at the end.
 simrank_status jacobi_sweeps(simrank_ctx* h, int max_sweeps, double tol, double* last_diff,
-                             int* sweeps_done) {
+                             int* sweeps_done, double* tol_used = nullptr) {
   const int sp = h->cfg.s_precision;
   const size_t elems = (size_t)h->n_pad * h->ld;
   const size_t fp64_budget = (size_t)48 << 30;
   const int wp = (sp == 64 || 3 * elems * 8 <= fp64_budget) ? 64 : 32;
   const size_t bytes = elems * (wp == 64 ? 8 : 4);
+  // sweeps stored in FP32 cannot change S by less than its rounding (about
+  // 6e-8 relative), so their stopping test is floored at 3e-7
+  if (wp == 32) tol = std::max(tol, 3e-7);
   void* bufs[3] = {nullptr, nullptr, nullptr};
   const bool alias = (wp == sp);
   for (int b = (alias ? 1 : 0); b < 3; ++b) {
@@ -499,6 +502,7 @@ simrank_status jacobi_sweeps(simrank_ctx* h, int max_sweeps, double tol, double*
     return fail(h, SR_ERR_CUDA, std::string("Jacobi sweep: ") + cudaGetErrorString(e));
   *last_diff = diff;
   *sweeps_done = it;
+  if (tol_used) *tol_used = tol;
   return SR_OK;
 }
 
@@ -923,13 +927,14 @@ simrank_status simrank_init(const simrank_config* cfg_in, int32_t n, int64_t m, 
   } else {
     // start from (1 - C) I on the whole capacity
     launch_set_diag(h->S, cfg.s_precision, 0, h->n_cap, h->ld, 1.0 - cfg.C, h->st);
-    double diff = 0.0;
+    double diff = 0.0, tol_used = cfg.init_tol;
     int sweeps = 0;
-    if ((s = jacobi_sweeps(h, cfg.init_max_sweeps, cfg.init_tol, &diff, &sweeps)) != SR_OK)
+    if ((s = jacobi_sweeps(h, cfg.init_max_sweeps, cfg.init_tol, &diff, &sweeps, &tol_used)) !=
+        SR_OK)
       return bail(s);
     h->stats.init_residual = diff;
     h->stats.init_sweeps = sweeps;
-    if (!(diff < cfg.init_tol))
+    if (!(diff < tol_used))
       return bail(fail(h, SR_ERR_NOT_CONVERGED,
                        "Jacobi init stopped at max-abs change " + std::to_string(diff)));
   }

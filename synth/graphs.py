@@ -89,6 +89,18 @@ def edge_weights(m: int, seed: int, low: float = 0.1, high: float = 1.0):
     return (high - (high - low) * u).astype(np.float32)
 
 
+class _Sampler:
+    """Draws ids with probability proportional to `weights` (inverse CDF)."""
+
+    def __init__(self, weights, rng):
+        c = np.cumsum(np.asarray(weights, np.float64))
+        self.cdf = c / c[-1]
+        self.rng = rng
+
+    def __call__(self):
+        return int(min(np.searchsorted(self.cdf, self.rng.random(), side="right"), self.cdf.size - 1))
+
+
 class EdgeSet:
     """Mutable simple digraph used to draw valid sequential updates."""
 
@@ -138,16 +150,14 @@ def update_stream(n: int, src, dst, count: int, seed: int, frac_insert: float = 
     """
     rng = np.random.default_rng(seed)
     g = edge_set if edge_set is not None else EdgeSet(n, src, dst)
-    p_src = (g.out_deg[: g.n] + 1.0)
-    p_src /= p_src.sum()
-    p_dst = (g.in_deg[: g.n] + 1.0)
-    p_dst /= p_dst.sum()
+    draw_src = _Sampler(g.out_deg[: g.n] + 1.0, rng)
+    draw_dst = _Sampler(g.in_deg[: g.n] + 1.0, rng)
     out = np.empty((count, 3), np.int32)
     for t in range(count):
         if rng.random() < frac_insert or not g.edges:
             while True:
-                i = int(rng.choice(g.n, p=p_src))
-                j = int(rng.choice(g.n, p=p_dst))
+                i = draw_src()
+                j = draw_dst()
                 if i != j and not g.has(i, j):
                     break
             g.insert(i, j)
@@ -179,18 +189,16 @@ def batch_with_new_nodes(n: int, src, dst, b: int, seed: int, frac_new: float = 
     n_new_edges = int(round(b * frac_new))
     kinds = np.array([0, 1, 2] * (n_new_edges // 3 + 1))[:n_new_edges]
     rng.shuffle(kinds)
-    p_src = (g.out_deg[:n_old] + 1.0)
-    p_src /= p_src.sum()
-    p_dst = (g.in_deg[:n_old] + 1.0)
-    p_dst /= p_dst.sum()
+    draw_src = _Sampler(g.out_deg[:n_old] + 1.0, rng)
+    draw_dst = _Sampler(g.in_deg[:n_old] + 1.0, rng)
     ups = []
     new_targets = []
     for kind in kinds:
         if kind == 0:  # source new, target old
             i = g.add_node()
-            j = int(rng.choice(n_old, p=p_dst))
+            j = draw_dst()
         elif kind == 1:  # source old, target new
-            i = int(rng.choice(n_old, p=p_src))
+            i = draw_src()
             if new_targets and rng.random() < reuse_target:
                 j = int(new_targets[int(rng.integers(0, len(new_targets)))])
                 if g.has(i, j):
@@ -211,8 +219,8 @@ def batch_with_new_nodes(n: int, src, dst, b: int, seed: int, frac_new: float = 
     for _ in range(b - n_new_edges):
         if rng.random() < frac_insert or not g.edges:
             while True:
-                i = int(rng.choice(n_old, p=p_src))
-                j = int(rng.choice(n_old, p=p_dst))
+                i = draw_src()
+                j = draw_dst()
                 if i != j and not g.has(i, j):
                     break
             g.insert(i, j)
