@@ -175,6 +175,41 @@ simrank_status simrank_plan_batch(const simrank_update* u, int64_t count, int32_
                                   int32_t max_blocks, int32_t* nblocks, int32_t* block_sink,
                                   int32_t* block_op, int64_t* block_off, int32_t* block_src);
 
+/* One edge update of a caller-owned dense S and graph, allocating nothing.
+ * The paper has no counterpart: this is for callers that cannot allocate
+ * device memory when they apply an update - code embedded in a host
+ * application whose device memory is owned by another allocator (a
+ * framework's caching pool, a budget enforced by the host), or latency-bound
+ * loops that must not stall on cudaMalloc / cudaFree.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine: its scratch lives in one
+ * fixed __device__ array of this library (6.2 MiB, held by every GPU
+ * that loads the library until the process exits), which limits it to
+ * n <= 8192 nodes and K <= 31; larger sizes return SR_ERR_ARG.
+ *
+ * Applies the insertion (op = +1) or deletion (op = -1) of the edge i -> j
+ * (0 <= i, j < n, i != j) to S in place, as Alg 1 / Thm 9 at truncation K with
+ * the fused, affected-area-pruned S update of simrank_apply_updates.
+ *  S: device, FP32 or FP64 (s_precision = 32 / 64), row-major with row pitch
+ *     ld elements; ld is a multiple of 128 and >= n rounded up to 128, S holds
+ *     that many rows, and the padding rows and columns are zero.  On entry S
+ *     is the SimRank matrix of the old graph (the fixed point of Eq. 1).
+ *  old_row_ptr[n+1] (int64), old_col: device CSR of the in-lists of the old
+ *     graph (row a lists every b with an edge b -> a); new_row_ptr / new_col
+ *     the same for the graph after the update.  d_j is the old in-degree of j.
+ *  cuda_stream: the stream all work is queued on (NULL = default stream).
+ * Returns once the work is queued; errors are reported through
+ * simrank_last_error(NULL).  All calls share the one scratch array, which
+ * keeps the last call's contents (the parts that must start at zero are
+ * cleared by each call): calls whose work overlaps on the GPU, from any
+ * thread or stream, race and give wrong results.  The first call on each
+ * device looks up the array's device address once (cudaGetSymbolAddress);
+ * make that first call before any stream capture. */
+simrank_status simrank_update_noalloc(int32_t n, int64_t ld, void* S, int32_t s_precision,
+                                      const int64_t* old_row_ptr, const int32_t* old_col,
+                                      const int64_t* new_row_ptr, const int32_t* new_col,
+                                      int32_t i, int32_t j, int32_t op, int32_t d_j, double C,
+                                      int32_t K, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

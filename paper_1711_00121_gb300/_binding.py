@@ -79,6 +79,8 @@ SIGNATURES = {
     "simrank_get_stats": (_I32, [_P, ctypes.POINTER(Stats)]),
     "simrank_reanchor": (_I32, [_P, _I32, ctypes.POINTER(ctypes.c_double)]),
     "simrank_plan_batch": (_I32, [_P, _I64, _I32, _I32, ctypes.POINTER(_I32), _P, _P, _P, _P]),
+    "simrank_update_noalloc": (_I32, [_I32, _I64, _P, _I32, _P, _P, _P, _P, _I32, _I32, _I32, _I32,
+                                      ctypes.c_double, _I32, _P]),
 }
 
 _lib = None

@@ -23,12 +23,11 @@ namespace {
 
 thread_local std::string g_init_error;
 
-struct DevBuf {
-  void* p = nullptr;
-  size_t bytes = 0;
-};
-
 }  // namespace
+
+namespace sr {
+void set_global_error(const std::string& msg) { g_init_error = msg; }
+}  // namespace sr
 
 struct simrank_ctx {
   simrank_config cfg{};

@@ -64,6 +64,9 @@ enum Counter : int {
   CNT_N = 8
 };
 
+// Sets the message that simrank_last_error(NULL) returns on this thread.
+void set_global_error(const std::string& msg);
+
 // ---------------------------------------------------------------------------
 // Kernel launchers (defined in the .cu files).  All are asynchronous on `st`.
 // ---------------------------------------------------------------------------
