@@ -87,7 +87,9 @@ typedef struct simrank_config {
                              update can reach (Thm 4) fill whole tiles; ids in the ABI are unchanged */
   int64_t timeout_iters;  /* bound on any device spin-wait (0 = library default) */
   void* cuda_stream;      /* cudaStream_t for all work of this handle; NULL = default stream */
-  int32_t reserved[8];
+  int32_t s_kernel;       /* CUDA-core S update with S in FP32: 0 = warp-specialised (math and
+                             memory warps overlap), 1 = single-role kernel */
+  int32_t reserved[7];
 } simrank_config;
 
 /* Fills *cfg with defaults: C = 0.6, K = 15, s_precision = 32, dense, aff = 1,

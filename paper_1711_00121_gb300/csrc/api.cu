@@ -323,6 +323,11 @@ simrank_status grow_pool(simrank_ctx* h, DevAdj& D, const HostAdj& A) {
   return SR_OK;
 }
 
+// Iteration bound of every device-side wait of this handle.
+long long wait_limit(const simrank_ctx* h) {
+  return h->cfg.timeout_iters > 0 ? h->cfg.timeout_iters : (1ll << 24);
+}
+
 std::pair<cudaEvent_t, cudaEvent_t>* next_event_pair(simrank_ctx* h) {
   if (h->events_used == h->events.size()) {
     cudaEvent_t a, b;
@@ -375,9 +380,11 @@ simrank_status s_update_launch(simrank_ctx* h, int k0, int k1, int use_masks) {
     if (!ev) return fail(h, SR_ERR_CUDA, "cudaEventCreate failed");
     CUDA_TRY(h, cudaEventRecord(ev->first, h->st));
   }
+  const bool ws = h->cfg.s_precision == 32 && h->cfg.s_kernel == 0;
   launch_s_update(h->S, h->cfg.s_precision, h->ld, panel_for_s(h), h->K1, h->tiles, h->ntiles,
                   h->mXi, h->mEta, k0, k1, use_masks, h->n_cur, h->counters,
-                  s_update_grid(h->cfg.s_precision, h->num_sms), h->st);
+                  s_update_grid(h->cfg.s_precision, h->num_sms, ws), h->st,
+                  ws ? wait_limit(h) : 0);
   LAUNCH_CHECK(h);
   if (ev) CUDA_TRY(h, cudaEventRecord(ev->second, h->st));
   h->prof_launches += 1;
@@ -643,7 +650,7 @@ simrank_status run_one_shot(simrank_ctx* h, const std::map<int32_t, std::vector<
         SR_OK)
       return s;
   }
-  const long long wait_limit = h->cfg.timeout_iters > 0 ? h->cfg.timeout_iters : (1ll << 24);
+  const long long wait_limit = ::wait_limit(h);
   int slot = 0;
   for (int k = 0; k <= h->cfg.K; ++k) {
     if (k > 0) {
@@ -687,9 +694,10 @@ simrank_status run_one_shot(simrank_ctx* h, const std::map<int32_t, std::vector<
                                           h->n_cur, h->counters, h->num_sms, wait_limit, h->st);
         if (rc != 0) return fail(h, SR_ERR_CUDA, "tensor-core S update: launch setup failed");
       } else {
+        const bool ws = sp == 32 && h->cfg.s_kernel == 0;
         launch_s_update(h->S, sp, h->ld, h->ob[8].p, g * r, h->tiles, h->ntiles, h->mXi, h->mEta,
                         0, slot * r, h->cfg.aff ? 1 : 0, h->n_cur, h->counters,
-                        s_update_grid(sp, h->num_sms), h->st);
+                        s_update_grid(sp, h->num_sms, ws), h->st, ws ? wait_limit : 0);
       }
       LAUNCH_CHECK(h);
       if (ev) CUDA_TRY(h, cudaEventRecord(ev->second, h->st));

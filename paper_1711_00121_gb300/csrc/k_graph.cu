@@ -33,20 +33,17 @@ __global__ void k_gather_rows(const T* __restrict__ S, int64_t ld, const int32_t
   if (blockIdx.x == 0) {
     __shared__ double red[2][32];
     double acc = 0.0;
-    const int64_t tot = (int64_t)delta * delta;
-#pragma unroll 4
-    for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
-      const int t = (int)(e / delta), u = (int)(e % delta);
-      acc += ld_s(S + (int64_t)I[t] * ld + I[u]);
+    for (int t = 0; t < delta; ++t) {
+      const T* row = S + (int64_t)I[t] * ld;
+      for (int u = threadIdx.x; u < delta; u += blockDim.x) acc += ld_s(row + I[u]);
     }
     const int64_t js = in.start[j];
     const int jl = in.len[j];
-    const int64_t tot2 = (int64_t)delta * jl;
     double wj = 0.0;
+    for (int t = 0; t < delta; ++t) {
+      const T* row = S + (int64_t)I[t] * ld;
 #pragma unroll 8
-    for (int64_t e = threadIdx.x; e < tot2; e += blockDim.x) {
-      const int t = (int)(e / jl), u = (int)(e % jl);
-      wj += ld_s(S + (int64_t)I[t] * ld + in.col[js + u]);
+      for (int u = threadIdx.x; u < jl; u += blockDim.x) wj += ld_s(row + in.col[js + u]);
     }
     acc = warp_sum(acc);
     wj = warp_sum(wj);
@@ -116,7 +113,34 @@ __device__ __forceinline__ void tile_rows_load(const DevAdj& in, int T, TileRows
   __syncthreads();
 }
 
-// acc[v][r] += sum over nonzeros b of row r of X_v[b], X_v given by gather(v, b)
+// Adds val into acc[key] once per run of equal keys across the lanes of a
+// warp (keys are non-decreasing with the lane index; key < 0 = nothing):
+// a segmented suffix sum by shuffles, then one atomic per segment head.
+template <int NV>
+__device__ __forceinline__ void warp_segment_flush(int key, double (&val)[NV], double (*acc)[PT]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int k2 = __shfl_down_sync(0xffffffffu, key, o);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const double x = __shfl_down_sync(0xffffffffu, val[v], o);
+      if (lane + o < 32 && k2 == key) val[v] += x;
+    }
+  }
+  const int kprev = __shfl_up_sync(0xffffffffu, key, 1);
+  if (key >= 0 && (lane == 0 || kprev != key)) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+      if (val[v] != 0.0) atomicAdd(&acc[v][key], val[v]);
+  }
+}
+
+// acc[v][r] = sum over nonzeros b of row r of X_v[b], X_v given by gather(v, b).
+// Thread t owns the contiguous run of flattened nonzeros [t*per, (t+1)*per):
+// rows that start and end inside its run are stored directly (no other
+// thread touches them); its first and last row may be shared with the
+// neighbouring runs and are combined by warp_segment_flush.
 template <int NV, typename G>
 __device__ __forceinline__ void tile_gather(const DevAdj& in, const TileRows& tr, G gather,
                                             double (*acc)[PT]) {
@@ -129,6 +153,10 @@ __device__ __forceinline__ void tile_gather(const DevAdj& in, const TileRows& tr
   const int per = (total + GT - 1) / GT;
   const int e0 = tid * per;
   const int e1 = min(total, e0 + per);
+  int r_first = -1, r_last = -1;
+  double pf[NV], pl[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) pf[v] = pl[v] = 0.0;
   if (e0 < e1) {
     int lo = 0, hi = PT;  // find r with off[r] <= e0 < off[r+1]
     while (hi - lo > 1) {
@@ -136,6 +164,7 @@ __device__ __forceinline__ void tile_gather(const DevAdj& in, const TileRows& tr
       if (tr.off[mid] <= e0) lo = mid; else hi = mid;
     }
     int r = lo;
+    r_first = r;
     double part[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) part[v] = 0.0;
@@ -165,21 +194,32 @@ __device__ __forceinline__ void tile_gather(const DevAdj& in, const TileRows& tr
       for (int q = 0; q < B; ++q) {
         if (rr[q] < 0) break;
         if (rr[q] != r) {
+          if (r == r_first) {
 #pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            if (part[v] != 0.0) atomicAdd(&acc[v][r], part[v]);
-            part[v] = 0.0;
+            for (int v = 0; v < NV; ++v) pf[v] = part[v];
+          } else {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) acc[v][r] = part[v];  // row wholly inside this run
           }
+#pragma unroll
+          for (int v = 0; v < NV; ++v) part[v] = 0.0;
           r = rr[q];
         }
 #pragma unroll
         for (int v = 0; v < NV; ++v) part[v] += xv[v][q];
       }
     }
+    if (r == r_first) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v)
-      if (part[v] != 0.0) atomicAdd(&acc[v][r], part[v]);
+      for (int v = 0; v < NV; ++v) pf[v] = part[v];
+    } else {
+      r_last = r;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) pl[v] = part[v];
+    }
   }
+  warp_segment_flush<NV>(r_first, pf, acc);
+  warp_segment_flush<NV>(r_last, pl, acc);
   __syncthreads();
 }
 

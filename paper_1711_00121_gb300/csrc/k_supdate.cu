@@ -194,16 +194,238 @@ __global__ void __launch_bounds__(256, MINB)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialised FP32 version: 8 math warps form Delta of tile pair i in
+// shared buffer i % 2 while 8 memory warps apply Delta of tile pair i - 1 to
+// S[I,J] and S[J,I], so the HBM stream never waits for the FMAs.  Hand-off
+// by mbarriers; every wait is bounded and sets a status word on timeout.
+// ---------------------------------------------------------------------------
+constexpr int WS_KC = 16;
+constexpr int WS_THREADS = 512;
+
+__device__ __forceinline__ uint32_t ws_smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void ws_bar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(ws_smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void ws_bar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(ws_smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool ws_bar_wait(uint64_t* bar, uint32_t parity, long long limit,
+                                            volatile int* abort_flag) {
+  const uint32_t a = ws_smem_u32(bar);
+  for (long long it = 0; it < limit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((it & 1023) == 1023 && *abort_flag) return false;
+  }
+  return false;
+}
+// barrier among the 256 math threads only (hardware barrier 1)
+__device__ __forceinline__ void ws_math_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+// true on every one of the 256 threads of hardware barrier `id` iff `pred` is
+// true on all of them: the two roles take each decision to stop together
+__device__ __forceinline__ bool ws_all(int id, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, %2, 256, p;\n"
+      " selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(id)
+      : "memory");
+  return r != 0;
+}
+
+__global__ void __launch_bounds__(WS_THREADS, 1)
+    k_s_update_ws(float* __restrict__ S, int64_t ld, const float* __restrict__ P, int K1,
+                  const uint32_t* __restrict__ tiles, const int* __restrict__ ntiles,
+                  const uint64_t* __restrict__ mXi, const uint64_t* __restrict__ mEta, int k0g,
+                  int k1g, int use_masks, int n, long long wait_limit,
+                  unsigned long long* __restrict__ counters) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float* sXiI = reinterpret_cast<float*>(smem_raw);
+  float* sEtaI = sXiI + WS_KC * PT;
+  float* sXiJ = sEtaI + WS_KC * PT;
+  float* sEtaJ = sXiJ + WS_KC * PT;
+  float* sDbuf = sEtaJ + WS_KC * PT;  // 2 x [PT][DP]
+  __shared__ __align__(8) uint64_t bar_full[2], bar_empty[2];
+  __shared__ volatile int abort_flag;
+  const int tid = threadIdx.x;
+  const int nt = *ntiles;
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int b = 0; b < 2; ++b) {
+      ws_bar_init(&bar_full[b], 256);
+      ws_bar_init(&bar_empty[b], 256);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  bool ok = true;
+  if (tid < 256) {
+    // ---------------- math warps
+    const int tx = tid & 15, ty = tid >> 4;
+    int i = 0;
+    for (int t = blockIdx.x; t < nt; t += gridDim.x, ++i) {
+      const uint32_t pr = tiles[t];
+      const int I = (int)(pr >> 16), J = (int)(pr & 0xffffu);
+      const uint64_t a1 = use_masks ? (mXi[I] & mEta[J]) : ~0ull;
+      const uint64_t a2 = use_masks ? (mEta[I] & mXi[J]) : ~0ull;
+      float acc[8][8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+      for (int kb = k0g; kb < k1g; kb += WS_KC) {
+        const int kc = min(WS_KC, k1g - kb);
+        uint64_t chunk = 0;
+        for (int kk = 0; kk < kc; ++kk) chunk |= 1ull << ((kb + kk) & 63);
+        if (((a1 | a2) & chunk) == 0) continue;
+        ws_math_sync();
+        const int nvec = kc * PT / 4;
+        const float4* gXiI = reinterpret_cast<const float4*>(P + ((int64_t)I * 2 + 0) * K1 * PT + (int64_t)kb * PT);
+        const float4* gEtaI = reinterpret_cast<const float4*>(P + ((int64_t)I * 2 + 1) * K1 * PT + (int64_t)kb * PT);
+        const float4* gXiJ = reinterpret_cast<const float4*>(P + ((int64_t)J * 2 + 0) * K1 * PT + (int64_t)kb * PT);
+        const float4* gEtaJ = reinterpret_cast<const float4*>(P + ((int64_t)J * 2 + 1) * K1 * PT + (int64_t)kb * PT);
+        for (int e = tid; e < nvec; e += 256) {
+          reinterpret_cast<float4*>(sXiI)[e] = __ldg(gXiI + e);
+          reinterpret_cast<float4*>(sEtaI)[e] = __ldg(gEtaI + e);
+          reinterpret_cast<float4*>(sXiJ)[e] = __ldg(gXiJ + e);
+          reinterpret_cast<float4*>(sEtaJ)[e] = __ldg(gEtaJ + e);
+        }
+        ws_math_sync();
+        for (int kk = 0; kk < kc; ++kk) {
+          const uint64_t bit = 1ull << ((kb + kk) & 63);
+          const bool p1 = (a1 & bit) != 0, p2 = (a2 & bit) != 0;
+          if (!(p1 || p2)) continue;
+          float rx[8], re[8], cx[8], ce[8];
+          ld4p(sXiI + kk * PT + ty * 4, &rx[0]);
+          ld4p(sXiI + kk * PT + 64 + ty * 4, &rx[4]);
+          ld4p(sEtaI + kk * PT + ty * 4, &re[0]);
+          ld4p(sEtaI + kk * PT + 64 + ty * 4, &re[4]);
+          ld4p(sXiJ + kk * PT + tx * 4, &cx[0]);
+          ld4p(sXiJ + kk * PT + 64 + tx * 4, &cx[4]);
+          ld4p(sEtaJ + kk * PT + tx * 4, &ce[0]);
+          ld4p(sEtaJ + kk * PT + 64 + tx * 4, &ce[4]);
+          if (p1) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+              for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(rx[r], ce[c], acc[r][c]);
+          }
+          if (p2) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+              for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(re[r], cx[c], acc[r][c]);
+          }
+        }
+      }
+      const int b = i & 1;
+      const bool got = ws_bar_wait(&bar_empty[b], ((i >> 1) & 1) ^ 1u, wait_limit, &abort_flag);
+      if (!ws_all(1, got)) {
+        ok = false;
+        break;
+      }
+      float* sD = sDbuf + b * PT * DP;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int row = (r < 4) ? ty * 4 + r : 64 + ty * 4 + (r - 4);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int col = (c < 4) ? tx * 4 + c : 64 + tx * 4 + (c - 4);
+          sD[row * DP + col] = acc[r][c];
+        }
+      }
+      ws_bar_arrive(&bar_full[b]);
+    }
+  } else {
+    // ---------------- memory warps: 8 warps, one 512-byte row segment per access
+    const int mt = tid - 256;
+    const int lane = mt & 31, warp = mt >> 5;
+    int i = 0;
+    unsigned long long my_tiles = 0, my_bytes = 0;
+    for (int t = blockIdx.x; t < nt; t += gridDim.x, ++i) {
+      const uint32_t pr = tiles[t];
+      const int I = (int)(pr >> 16), J = (int)(pr & 0xffffu);
+      const int b = i & 1;
+      const bool got = ws_bar_wait(&bar_full[b], (i >> 1) & 1, wait_limit, &abort_flag);
+      if (!ws_all(2, got)) {
+        ok = false;
+        break;
+      }
+      const float* sD = sDbuf + b * PT * DP;
+      constexpr int NQ = PT / 8;  // 16 rows per warp
+      {
+        float v[NQ][4];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const int row = warp + 8 * q;
+          ld4p(S + (int64_t)(I * PT + row) * ld + (int64_t)J * PT + lane * 4, v[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const int row = warp + 8 * q;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) v[q][e] += sD[row * DP + lane * 4 + e];
+          st4(S + (int64_t)(I * PT + row) * ld + (int64_t)J * PT + lane * 4, v[q]);
+        }
+      }
+      if (I != J) {
+        float v[NQ][4];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const int c = warp + 8 * q;
+          ld4p(S + (int64_t)(J * PT + c) * ld + (int64_t)I * PT + lane * 4, v[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const int c = warp + 8 * q;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) v[q][e] += sD[(lane * 4 + e) * DP + c];
+          st4(S + (int64_t)(J * PT + c) * ld + (int64_t)I * PT + lane * 4, v[q]);
+        }
+      }
+      ws_bar_arrive(&bar_empty[b]);
+      if (mt == 0) {
+        const long long vr = max(0, min(PT, n - I * PT)), vc = max(0, min(PT, n - J * PT));
+        my_tiles += 1;
+        my_bytes += (unsigned long long)(vr * vc) * 8ull * (I == J ? 1ull : 2ull);
+      }
+    }
+    if (mt == 0 && my_tiles) {
+      atomicAdd(&counters[CNT_TILES_TOUCHED], my_tiles);
+      atomicAdd(&counters[CNT_S_BYTES], my_bytes);
+      atomicAdd(&counters[CNT_PANEL_BYTES],
+                my_tiles * 4ull * (unsigned long long)(k1g - k0g) * PT * sizeof(float));
+    }
+  }
+  if (!ok) abort_flag = 1;
+  __syncthreads();
+  if (tid == 0 && abort_flag)
+    atomicExch(&counters[CNT_STATUS], (unsigned long long)SR_ERR_TIMEOUT);
+}
+
 constexpr int KC_F32 = 16;
 constexpr int KC_F64 = 16;
 
 }  // namespace
 
-int s_update_grid(int s_prec, int num_sms) { return num_sms * (s_prec == 64 ? 1 : 2); }
+int s_update_grid(int s_prec, int num_sms, bool ws) {
+  return num_sms * ((s_prec == 64 || ws) ? 1 : 2);
+}
 
 void launch_s_update(void* S, int s_prec, int64_t ld, const void* P, int K1, const uint32_t* tiles,
                      const int* ntiles, const uint64_t* mXi, const uint64_t* mEta, int k0, int k1,
-                     int use_masks, int n, int64_t* counters, int grid, cudaStream_t st) {
+                     int use_masks, int n, int64_t* counters, int grid, cudaStream_t st,
+                     long long ws_wait_limit) {
   if (s_prec == 64) {
     const size_t smem = (4ull * KC_F64 * PT + (size_t)PT * DP) * sizeof(double);
     static bool attr64 = false;
@@ -215,6 +437,16 @@ void launch_s_update(void* S, int s_prec, int64_t ld, const void* P, int K1, con
     k_s_update<double, KC_F64, 1><<<grid, 256, smem, st>>>(
         (double*)S, ld, (const double*)P, K1, tiles, ntiles, mXi, mEta, k0, k1, use_masks, n,
         (unsigned long long*)counters);
+  } else if (ws_wait_limit > 0) {
+    const size_t smem = (4ull * WS_KC * PT + 2ull * PT * DP) * sizeof(float);
+    static bool attr_ws = false;
+    if (!attr_ws) {
+      cudaFuncSetAttribute(k_s_update_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr_ws = true;
+    }
+    k_s_update_ws<<<grid, WS_THREADS, smem, st>>>((float*)S, ld, (const float*)P, K1, tiles, ntiles,
+                                                  mXi, mEta, k0, k1, use_masks, n, ws_wait_limit,
+                                                  (unsigned long long*)counters);
   } else {
     const size_t smem = (4ull * KC_F32 * PT + (size_t)PT * DP) * sizeof(float);
     static bool attr32 = false;

@@ -101,11 +101,15 @@ void launch_tile_list(const uint64_t* mXi, const uint64_t* mEta, int nT, int aff
 // S[I,J] += sum_{k in [k0,k1)} xi_k[I] eta_k[J]^T + eta_k[I] xi_k[J]^T, and the
 // mirrored tile S[J,I], over the tile list.  n = current node count (for the
 // algorithmic byte counters).
+// With S in FP32 and ws_wait_limit > 0 the warp-specialised kernel runs (its
+// mbarrier waits are bounded by ws_wait_limit iterations); otherwise the
+// single-role kernel.
 void launch_s_update(void* S, int s_prec, int64_t ld, const void* P, int K1, const uint32_t* tiles,
                      const int* ntiles, const uint64_t* mXi, const uint64_t* mEta, int k0, int k1,
-                     int use_masks, int n, int64_t* counters, int grid, cudaStream_t st);
-// Largest useful persistent grid for launch_s_update on this device.
-int s_update_grid(int s_prec, int num_sms);
+                     int use_masks, int n, int64_t* counters, int grid, cudaStream_t st,
+                     long long ws_wait_limit = 0);
+// Persistent grid for launch_s_update on this device (ws: warp-specialised).
+int s_update_grid(int s_prec, int num_sms, bool ws = false);
 
 // Jacobi sweep pieces for Eq. 1 (init / re-anchor).
 // Y[a, :] = scale * sum_b Q[a, b] X[b, :] + diag * e_a (the diagonal term only

@@ -118,7 +118,8 @@ def test_unit_update_converged_vs_batch_recompute(P, case):
 
 # ------------------------------------------------------------ update streams
 
-@pytest.mark.parametrize("variant", ["fused_aff", "fused_aff_norelabel", "fused_noaff", "plain"])
+@pytest.mark.parametrize("variant", ["fused_aff", "fused_aff_norelabel", "fused_single_role",
+                                     "fused_noaff", "plain"])
 def test_stream_fp32_powerlaw(P, variant):
     n, m, C, K = 1500, 15000, 0.6, 20
     s, d = chung_lu_digraph(n, m, 2.1, 2.1, 4)
@@ -126,6 +127,8 @@ def test_stream_fp32_powerlaw(P, variant):
     kw = dict(aff=1, s_update=P.SUPDATE_FUSED)
     if variant == "fused_aff_norelabel":
         kw = dict(aff=1, relabel=0, s_update=P.SUPDATE_FUSED)
+    elif variant == "fused_single_role":
+        kw = dict(aff=1, s_kernel=1, s_update=P.SUPDATE_FUSED)
     elif variant == "fused_noaff":
         kw = dict(aff=0, s_update=P.SUPDATE_FUSED)
     elif variant == "plain":
