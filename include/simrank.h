@@ -89,7 +89,12 @@ typedef struct simrank_config {
   void* cuda_stream;      /* cudaStream_t for all work of this handle; NULL = default stream */
   int32_t s_kernel;       /* CUDA-core S update with S in FP32: 0 = warp-specialised (math and
                              memory warps overlap), 1 = single-role kernel */
-  int32_t reserved[7];
+  int32_t defer;          /* dense FP32 S, unit / sink-block apply, fused update: 0 or 1 = apply
+                             each rank-one update to S at once; G > 1 = keep up to G updates'
+                             panels pending (the rows of S an update reads are corrected by them)
+                             and apply them in one rank-2G(K+1) pass (tensor cores when tc = 1).
+                             Pending updates are always applied before apply_updates returns. */
+  int32_t reserved[6];
 } simrank_config;
 
 /* Fills *cfg with defaults: C = 0.6, K = 15, s_precision = 32, dense, aff = 1,

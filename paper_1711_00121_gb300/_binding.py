@@ -39,7 +39,8 @@ class Config(ctypes.Structure):
         ("init_max_sweeps", ctypes.c_int32), ("init_tol", ctypes.c_double),
         ("profile", ctypes.c_int32), ("relabel", ctypes.c_int32),
         ("timeout_iters", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
-        ("s_kernel", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7),
+        ("s_kernel", ctypes.c_int32), ("defer", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 6),
     ]
 
 

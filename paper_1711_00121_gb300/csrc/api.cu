@@ -68,11 +68,24 @@ struct simrank_ctx {
   int64_t ops_cap = 0;
   int32_t* d_cols = nullptr;
   int64_t cols_cap = 0;
+  // column mode (§7): snapshot of the initial graph and the stored updates
+  bool column = false;
+  int32_t* g0_in_col = nullptr;
+  int32_t* g0_out_col = nullptr;
+  int32_t* g0_in_len = nullptr;
+  ChunkList g0_fwd, g0_hor, cur_fwd, cur_hor;
+  int64_t cur_fwd_cap = 0, cur_hor_cap = 0;
+  std::vector<void*> hist;  // per-update panel snapshots (tile-blocked, S precision)
   // one-shot batch scratch (grow-only)
   struct Buf {
     void* p = nullptr;
     size_t bytes = 0;
-  } ob[12];
+  } ob[16];
+  // deferred S updates: pending panels [T][which][G*K1][128] (FP32), count, tile masks
+  float* Pp = nullptr;
+  int np = 0;
+  uint64_t* pXi = nullptr;
+  uint64_t* pEta = nullptr;
   // profiling
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
   size_t events_used = 0;
@@ -392,6 +405,59 @@ simrank_status s_update_launch(simrank_ctx* h, int k0, int k1, int use_masks) {
   return SR_OK;
 }
 
+simrank_status ob_ensure(simrank_ctx* h, int slot, size_t bytes);
+
+bool deferring(const simrank_ctx* h) {
+  return h->cfg.defer > 1 && h->cfg.s_precision == 32 && !h->column &&
+         h->cfg.s_update == SR_SUPDATE_FUSED;
+}
+
+// Applies the pending updates' panels to S in one pass (rank 2 * np * K1).
+simrank_status flush_pending(simrank_ctx* h) {
+  if (h->np == 0) return SR_OK;
+  const int nT = (h->n_cur + PT - 1) / PT;
+  const int GK1 = h->cfg.defer * h->K1;
+  const int nterms = h->np * h->K1;
+  CUDA_TRY(h, cudaMemsetAsync(h->ntiles, 0, sizeof(int), h->st));
+  launch_tile_list(h->pXi, h->pEta, nT, h->cfg.aff ? 1 : 0, h->tiles, h->ntiles, h->st);
+  std::pair<cudaEvent_t, cudaEvent_t>* ev = nullptr;
+  if (h->cfg.profile) {
+    ev = next_event_pair(h);
+    if (!ev) return fail(h, SR_ERR_CUDA, "cudaEventCreate failed");
+  }
+  simrank_status s;
+  if (h->cfg.tc) {
+    const int rg = (nterms + 31) / 32 * 32;
+    const int64_t kd = 2 * (int64_t)rg;
+    if ((s = ob_ensure(h, 12, (size_t)h->n_pad * kd * 4)) != SR_OK) return s;
+    if ((s = ob_ensure(h, 13, (size_t)h->n_pad * kd * 4)) != SR_OK) return s;
+    launch_pack_tc_tiles(h->Pp, GK1, nterms, rg, nT * PT, (float*)h->ob[12].p, (float*)h->ob[13].p,
+                         kd, h->st);
+    if (ev) CUDA_TRY(h, cudaEventRecord(ev->first, h->st));
+    const int rc = launch_s_update_tc((float*)h->S, h->ld, (const float*)h->ob[12].p,
+                                      (const float*)h->ob[13].p, h->n_pad, kd, h->tiles, h->ntiles,
+                                      h->n_cur, h->counters, h->num_sms, wait_limit(h), h->st);
+    if (rc != 0) return fail(h, SR_ERR_CUDA, "tensor-core S update: launch setup failed");
+    h->launches += 2;
+  } else {
+    if (ev) CUDA_TRY(h, cudaEventRecord(ev->first, h->st));
+    const bool ws = h->cfg.s_kernel == 0;
+    launch_s_update(h->S, 32, h->ld, h->Pp, GK1, h->tiles, h->ntiles, h->pXi, h->pEta, 0, nterms,
+                    0, h->n_cur, h->counters, s_update_grid(32, h->num_sms, ws), h->st,
+                    ws ? wait_limit(h) : 0);
+    h->launches += 1;
+  }
+  LAUNCH_CHECK(h);
+  if (ev) CUDA_TRY(h, cudaEventRecord(ev->second, h->st));
+  h->prof_launches += 1;
+  h->launches += 1;
+  h->stats.tiles_total += (int64_t)nT * (nT + 1) / 2;
+  CUDA_TRY(h, cudaMemsetAsync(h->pXi, 0, h->nT_cap * sizeof(uint64_t), h->st));
+  CUDA_TRY(h, cudaMemsetAsync(h->pEta, 0, h->nT_cap * sizeof(uint64_t), h->st));
+  h->np = 0;
+  return SR_OK;
+}
+
 // One rank-one update of the current S for the sink block (srcs at d_srcs +
 // src_off, delta of them) into sink j, op = +1/-1, old in-degree d_j; the
 // graph patch ops [op_begin, op_end) turn the old graph into the new one.
@@ -409,8 +475,26 @@ simrank_status run_rank_one(simrank_ctx* h, int64_t src_off, int delta, int j, i
     if (!pe) return fail(h, SR_ERR_CUDA, "cudaEventCreate failed");
     CUDA_TRY(h, cudaEventRecord(pe[0], h->st));
   }
-  launch_gather_rows(h->S, h->cfg.s_precision, h->ld, h->d_srcs + src_off, delta, j, nT * PT,
-                     h->din, h->sI, h->sJ, h->scal, h->st);
+  const bool defer = deferring(h);
+  if (defer) {
+    if (!h->Pp) {
+      const size_t pb = (size_t)h->nT_cap * 2 * h->cfg.defer * h->K1 * PT * sizeof(float);
+      CUDA_TRY(h, cudaMalloc(&h->Pp, pb));
+      CUDA_TRY(h, cudaMemsetAsync(h->Pp, 0, pb, h->st));
+      CUDA_TRY(h, dev_alloc(&h->pXi, (size_t)h->nT_cap));
+      CUDA_TRY(h, dev_alloc(&h->pEta, (size_t)h->nT_cap));
+      CUDA_TRY(h, cudaMemsetAsync(h->pXi, 0, h->nT_cap * sizeof(uint64_t), h->st));
+      CUDA_TRY(h, cudaMemsetAsync(h->pEta, 0, h->nT_cap * sizeof(uint64_t), h->st));
+    }
+    // rows i (summed over the block) and j of the current S = S + pending panels
+    launch_gather_rows_pending(h->S, 32, h->ld, h->d_srcs + src_off, delta, j, nT * PT, h->Pp,
+                               h->cfg.defer * h->K1, h->np * h->K1, h->sI, h->sJ, h->st);
+    launch_scalars_from_rows(h->din, h->sI, h->sJ, h->d_srcs + src_off, delta, j, h->scal, h->st);
+    h->launches += 1;
+  } else {
+    launch_gather_rows(h->S, h->cfg.s_precision, h->ld, h->d_srcs + src_off, delta, j, nT * PT,
+                       h->din, h->sI, h->sJ, h->scal, h->st);
+  }
   launch_gamma(h->din, h->sI, h->sJ, h->scal, j, delta, op, d_j, C, nT, h->K1, h->P64,
                h->cfg.s_precision == 64 ? nullptr : h->P32, h->mXi, h->mEta, h->st);
   if (pe) CUDA_TRY(h, cudaEventRecord(pe[1], h->st));
@@ -421,6 +505,23 @@ simrank_status run_rank_one(simrank_ctx* h, int64_t src_off, int delta, int j, i
   LAUNCH_CHECK(h);
   h->launches += 2 + (op_end > op_begin ? 1 : 0) + h->cfg.K;
   if (pe) CUDA_TRY(h, cudaEventRecord(pe[2], h->st));
+  if (defer) {
+    // append this update's panels as pending terms np*K1 .. np*K1 + K (FP32)
+    const size_t w = (size_t)h->K1 * PT * sizeof(float);
+    const size_t dpitch = (size_t)h->cfg.defer * w;
+    CUDA_TRY(h, cudaMemcpy2DAsync((unsigned char*)h->Pp + (size_t)h->np * w, dpitch, h->P32, w, w,
+                                  (size_t)nT * 2, cudaMemcpyDeviceToDevice, h->st));
+    launch_or_any(h->mXi, h->mEta, nT, h->pXi, h->pEta, h->st);
+    h->launches += 1;
+    h->np += 1;
+    if (pe) {
+      CUDA_TRY(h, cudaEventRecord(pe[3], h->st));
+      CUDA_TRY(h, cudaEventRecord(pe[4], h->st));
+    }
+    h->stats.rank_one_updates += 1;
+    if (h->np == h->cfg.defer) return flush_pending(h);
+    return SR_OK;
+  }
   CUDA_TRY(h, cudaMemsetAsync(h->ntiles, 0, sizeof(int), h->st));
   const bool plain = h->cfg.s_update == SR_SUPDATE_PLAIN;
   launch_tile_list(h->mXi, h->mEta, nT, (plain || !h->cfg.aff) ? 0 : 1, h->tiles, h->ntiles, h->st);
@@ -713,6 +814,123 @@ simrank_status run_one_shot(simrank_ctx* h, const std::map<int32_t, std::vector<
   return SR_OK;
 }
 
+// Row chunks (at most kChunk nonzeros each) of the adjacency rows [0, n_rows).
+void build_chunks(const HostAdj& A, int n_rows, std::vector<RowChunk>& out) {
+  out.clear();
+  for (int a = 0; a < n_rows; ++a)
+    for (int off = 0; off < A.len[a]; off += kChunk)
+      out.push_back({a, std::min(kChunk, A.len[a] - off), A.start[a] + off});
+}
+
+simrank_status upload_chunks(simrank_ctx* h, const std::vector<RowChunk>& v, ChunkList& L,
+                             int64_t* cap) {
+  if ((int64_t)v.size() > *cap) {
+    if (L.chunks) cudaFree(L.chunks);
+    L.chunks = nullptr;
+    *cap = std::max<int64_t>((int64_t)v.size(), 2 * *cap);
+    CUDA_TRY(h, dev_alloc(&L.chunks, (size_t)*cap));
+  }
+  L.count = (int64_t)v.size();
+  if (!v.empty())
+    CUDA_TRY(h, cudaMemcpyAsync(L.chunks, v.data(), v.size() * sizeof(RowChunk),
+                                cudaMemcpyHostToDevice, h->st));
+  return SR_OK;
+}
+
+// One update in column mode (Alg 7 with new nodes as isolated nodes): the
+// old columns S_{*,i}, S_{*,j} by Procedure 1 on the current graph, gamma,
+// the graph patch, the xi/eta recurrence, and a snapshot of the panels.
+simrank_status run_column_update(simrank_ctx* h, int i, int j, int op, int d_j, int64_t op_begin,
+                                 int64_t op_end, int32_t* d_cols2) {
+  const int K = h->cfg.K, n_pad = h->n_pad, nT = (h->n_cur + PT - 1) / PT;
+  simrank_status s;
+  const int32_t ij[2] = {i, j};
+  CUDA_TRY(h, cudaMemcpyAsync(d_cols2, ij, sizeof(ij), cudaMemcpyHostToDevice, h->st));
+  const size_t blk = (size_t)n_pad * 2 * sizeof(double);
+  if ((s = ob_ensure(h, 10, blk * (K + 1))) != SR_OK) return s;
+  if ((s = ob_ensure(h, 11, blk * 3)) != SR_OK) return s;
+  unsigned char* w = (unsigned char*)h->ob[11].p;
+  launch_partial_sim_block(h->cur_fwd, h->cur_hor, h->dout.col, h->din.col, h->din.len, d_cols2, 2,
+                           n_pad, K, h->cfg.C, 64, h->ob[10].p, w, w + blk, w + 2 * blk, h->st);
+  launch_col_extract(w + 2 * blk, 64, 2, 0, n_pad, h->sI, h->st);
+  launch_col_extract(w + 2 * blk, 64, 2, 1, n_pad, h->sJ, h->st);
+  launch_col_scalars(h->din, h->sI, h->sJ, i, j, h->scal, h->st);
+  const bool f32 = h->cfg.s_precision == 32;
+  launch_gamma(h->din, h->sI, h->sJ, h->scal, j, 1, op, d_j, h->cfg.C, nT, h->K1, h->P64,
+               f32 ? h->P32 : nullptr, h->mXi, h->mEta, h->st);
+  launch_patch(h->d_ops, op_begin, op_end, h->din, h->dout, h->st);
+  for (int k = 0; k < K; ++k)
+    launch_chain_step(h->din, k, h->cfg.C, nT, h->K1, h->P64, f32 ? h->P32 : nullptr, h->mXi,
+                      h->mEta, h->st);
+  LAUNCH_CHECK(h);
+  h->launches += 2 * K + 6 + K;
+  const size_t pbytes = (size_t)h->nT_cap * 2 * h->K1 * PT * (f32 ? 4 : 8);
+  void* snap = nullptr;
+  CUDA_TRY(h, cudaMalloc(&snap, pbytes));
+  h->hist.push_back(snap);
+  CUDA_TRY(h, cudaMemcpyAsync(snap, f32 ? (void*)h->P32 : (void*)h->P64, pbytes,
+                              cudaMemcpyDeviceToDevice, h->st));
+  // the chunk lists of this update must not change before its kernels ran
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  h->stats.rank_one_updates += 1;
+  return SR_OK;
+}
+
+// Columns in column mode: Procedure 1 on the initial graph plus, for every
+// stored update, Eq. 70-71's column of M_K + M_K^T.
+simrank_status column_mode_columns(simrank_ctx* h, const int32_t* cols, int ncols, void* out,
+                                   int out_on_device, int out_fp64) {
+  const int prec = h->cfg.s_precision, K = h->cfg.K, n_pad = h->n_pad;
+  const size_t eb = prec == 64 ? 8 : 4;
+  size_t free_b = 0, total_b = 0;
+  CUDA_TRY(h, cudaMemGetInfo(&free_b, &total_b));
+  const size_t per_col = (size_t)n_pad * eb * (K + 4);
+  int Bmax = (int)std::min<size_t>(1024, std::max<size_t>(1, (size_t)(0.6 * free_b) / per_col));
+  simrank_status s;
+  if ((s = ob_ensure(h, 10, per_col * Bmax)) != SR_OK) return s;
+  if (ncols > h->cols_cap) {
+    if (h->d_cols) cudaFree(h->d_cols);
+    h->d_cols = nullptr;
+    h->cols_cap = ncols;
+    CUDA_TRY(h, dev_alloc(&h->d_cols, (size_t)ncols));
+  }
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_cols, cols, ncols * sizeof(int32_t), cudaMemcpyHostToDevice,
+                              h->st));
+  const size_t ob = (size_t)h->n_cur * ncols * (out_fp64 ? 8 : 4);
+  void* dst = out;
+  void* tmp = nullptr;
+  if (!out_on_device) {
+    CUDA_TRY(h, cudaMalloc(&tmp, ob));
+    dst = tmp;
+  }
+  for (int c0 = 0; c0 < ncols; c0 += Bmax) {
+    const int B = std::min(Bmax, ncols - c0);
+    const int32_t* bc = h->d_cols + c0;
+    unsigned char* base = (unsigned char*)h->ob[10].p;
+    const size_t blkb = (size_t)n_pad * B * eb;
+    void* xs = base;
+    void* y0 = base + blkb * (K + 1);
+    void* y1 = base + blkb * (K + 2);
+    void* res = base + blkb * (K + 3);
+    launch_partial_sim_block(h->g0_fwd, h->g0_hor, h->g0_out_col, h->g0_in_col, h->g0_in_len, bc,
+                             B, n_pad, K, h->cfg.C, prec, xs, y0, y1, res, h->st);
+    for (void* P : h->hist) launch_col_apply(P, prec, h->K1, bc, B, n_pad, prec, res, h->st);
+    launch_col_out(res, prec, B, h->n_cur,
+                   (unsigned char*)dst + (size_t)c0 * h->n_cur * (out_fp64 ? 8 : 4), out_fp64, h->st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      if (tmp) cudaFree(tmp);
+      return fail(h, SR_ERR_CUDA, std::string("column mode: ") + cudaGetErrorString(e));
+    }
+  }
+  cudaError_t e = cudaSuccess;
+  if (!out_on_device) e = cudaMemcpyAsync(out, tmp, ob, cudaMemcpyDeviceToHost, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (tmp) cudaFree(tmp);
+  if (e != cudaSuccess) return fail(h, SR_ERR_CUDA, std::string("column mode: ") + cudaGetErrorString(e));
+  return SR_OK;
+}
+
 void free_ctx(simrank_ctx* h) {
   if (!h) return;
   void* ptrs[] = {h->din.start, h->din.len,  h->din.col,   h->dout.start, h->dout.len,
@@ -724,6 +942,15 @@ void free_ctx(simrank_ctx* h) {
     if (p) cudaFree(p);
   for (auto& b : h->ob)
     if (b.p) cudaFree(b.p);
+  if (h->Pp) cudaFree(h->Pp);
+  if (h->pXi) cudaFree(h->pXi);
+  if (h->pEta) cudaFree(h->pEta);
+  void* colptrs[] = {h->g0_in_col, h->g0_out_col, h->g0_in_len, h->g0_fwd.chunks,
+                     h->g0_hor.chunks, h->cur_fwd.chunks, h->cur_hor.chunks};
+  for (void* p : colptrs)
+    if (p) cudaFree(p);
+  for (void* p : h->hist)
+    if (p) cudaFree(p);
   for (auto& e : h->events) {
     cudaEventDestroy(e.first);
     cudaEventDestroy(e.second);
@@ -768,8 +995,15 @@ simrank_status simrank_init(const simrank_config* cfg_in, int32_t n, int64_t m, 
   if (cfg.K < 0 || cfg.K > 1023) return fail(nullptr, SR_ERR_ARG, "K must be in [0, 1023]");
   if (cfg.s_precision != 32 && cfg.s_precision != 64)
     return fail(nullptr, SR_ERR_ARG, "s_precision must be 32 or 64");
-  if (cfg.mode != SR_MODE_DENSE)
-    return fail(nullptr, SR_ERR_UNSUPPORTED, "only SR_MODE_DENSE is available in this build");
+  if (cfg.mode != SR_MODE_DENSE && cfg.mode != SR_MODE_COLUMN)
+    return fail(nullptr, SR_ERR_ARG, "mode must be SR_MODE_DENSE or SR_MODE_COLUMN");
+  if (cfg.mode == SR_MODE_COLUMN) {
+    if (S0) return fail(nullptr, SR_ERR_ARG, "column mode keeps no dense S: S0 must be NULL");
+    if (weight) return fail(nullptr, SR_ERR_UNSUPPORTED, "column mode on a weighted graph");
+    if (cfg.apply != SR_APPLY_UNIT)
+      return fail(nullptr, SR_ERR_UNSUPPORTED, "column mode applies unit updates (Alg 7)");
+    cfg.relabel = 0;
+  }
   if (n < 1 || m < 0) return fail(nullptr, SR_ERR_ARG, "need n >= 1 and m >= 0");
   if (m > 0 && (!src || !dst)) return fail(nullptr, SR_ERR_ARG, "null edge arrays");
   if (cfg.n_capacity == 0) cfg.n_capacity = n;
@@ -890,8 +1124,9 @@ simrank_status simrank_init(const simrank_config* cfg_in, int32_t n, int64_t m, 
   }
 
   // --- S, panels, masks
+  h->column = cfg.mode == SR_MODE_COLUMN;
   const size_t eb = (size_t)elem_bytes(h);
-  const size_t s_bytes = (size_t)h->n_pad * h->ld * eb;
+  const size_t s_bytes = h->column ? 256 : (size_t)h->n_pad * h->ld * eb;
   if (cudaMalloc(&h->S, s_bytes) != cudaSuccess)
     return bail(fail(h, SR_ERR_OOM, "cudaMalloc of S (" + std::to_string(s_bytes) + " bytes) failed"));
   const size_t panel_elems = (size_t)h->nT_cap * 2 * h->K1 * PT;
@@ -911,7 +1146,25 @@ simrank_status simrank_init(const simrank_config* cfg_in, int32_t n, int64_t m, 
   cudaMemsetAsync(h->counters, 0, CNT_N * sizeof(int64_t), h->st);
   cudaMemsetAsync(h->S, 0, s_bytes, h->st);
 
-  if (S0) {
+  if (h->column) {
+    // snapshot of the initial graph for the base columns (Procedure 1)
+    std::vector<RowChunk> ch;
+    if (dev_alloc(&h->g0_in_col, (size_t)h->din.pool_cap) != cudaSuccess ||
+        dev_alloc(&h->g0_out_col, (size_t)h->dout.pool_cap) != cudaSuccess ||
+        dev_alloc(&h->g0_in_len, (size_t)h->n_pad) != cudaSuccess)
+      return bail(fail(h, SR_ERR_OOM, "cudaMalloc of the graph snapshot failed"));
+    cudaMemcpyAsync(h->g0_in_col, h->din.col, h->din.pool_cap * 4, cudaMemcpyDeviceToDevice, h->st);
+    cudaMemcpyAsync(h->g0_out_col, h->dout.col, h->dout.pool_cap * 4, cudaMemcpyDeviceToDevice,
+                    h->st);
+    cudaMemcpyAsync(h->g0_in_len, h->din.len, (size_t)h->n_pad * 4, cudaMemcpyDeviceToDevice, h->st);
+    int64_t cap_f = 0, cap_h = 0;
+    build_chunks(h->hout, h->n_pad, ch);
+    if ((s = upload_chunks(h, ch, h->g0_fwd, &cap_f)) != SR_OK) return bail(s);
+    build_chunks(h->hin, h->n_pad, ch);
+    if ((s = upload_chunks(h, ch, h->g0_hor, &cap_h)) != SR_OK) return bail(s);
+    if (cudaStreamSynchronize(h->st) != cudaSuccess)
+      return bail(fail(h, SR_ERR_CUDA, "init synchronisation failed"));
+  } else if (S0) {
     const void* src_S = S0;
     std::vector<unsigned char> perm_S;
     if (h->relabeled) {
@@ -998,6 +1251,39 @@ simrank_status simrank_apply_updates(simrank_t h, const simrank_update* u, int64
     r.op_end = (int64_t)ops.size();
     plan.push_back(r);
   };
+  if (h->column) {
+    // Alg 7: one update at a time; the old columns come from the graph
+    // before that update, so each update is planned right before it runs
+    h->n_cur = n_after;
+    for (int64_t t = 0; t < count; ++t) {
+      const int32_t i = um[t].src, j = um[t].dst, op = um[t].op;
+      std::vector<RowChunk> ch;
+      build_chunks(h->hout, h->n_pad, ch);
+      if ((s = upload_chunks(h, ch, h->cur_fwd, &h->cur_fwd_cap)) != SR_OK) return s;
+      build_chunks(h->hin, h->n_pad, ch);
+      if ((s = upload_chunks(h, ch, h->cur_hor, &h->cur_hor_cap)) != SR_OK) return s;
+      std::vector<PatchOp> ops1;
+      const int d_j = h->hin.len[j];
+      if (op > 0) {
+        adj_append(h->hin, j, i, ops1, true);
+        adj_append(h->hout, i, j, ops1, false);
+        h->edges.insert(ekey(i, j));
+      } else {
+        adj_remove(h->hin, j, i, ops1, true);
+        adj_remove(h->hout, i, j, ops1, false);
+        h->edges.erase(ekey(i, j));
+      }
+      if ((s = grow_pool(h, h->din, h->hin)) != SR_OK) return s;
+      if ((s = grow_pool(h, h->dout, h->hout)) != SR_OK) return s;
+      if ((s = ensure_dev_capacity(h, 2, (int64_t)ops1.size())) != SR_OK) return s;
+      CUDA_TRY(h, cudaMemcpyAsync(h->d_ops, ops1.data(), ops1.size() * sizeof(PatchOp),
+                                  cudaMemcpyHostToDevice, h->st));
+      if ((s = run_column_update(h, i, j, op, d_j, 0, (int64_t)ops1.size(), h->d_srcs)) != SR_OK)
+        return s;
+    }
+    h->stats.updates += count;
+    return SR_OK;
+  }
   if (h->cfg.apply == SR_APPLY_ONE_SHOT) {
     // net update per sink, in storage ids; then one rank-2r update
     std::vector<Block> blocks;
@@ -1029,6 +1315,8 @@ simrank_status simrank_apply_updates(simrank_t h, const simrank_update* u, int64
   }
   if (h->cfg.apply == SR_APPLY_UNIT) {
     for (int64_t t = 0; t < count; ++t) add_r1(um[t].dst, um[t].op, {um[t].src});
+  } else if (h->column) {
+    return fail(h, SR_ERR_UNSUPPORTED, "column mode applies unit updates");
   } else {
     // the canonical block order is defined on caller ids
     std::vector<Block> blocks;
@@ -1042,7 +1330,7 @@ simrank_status simrank_apply_updates(simrank_t h, const simrank_update* u, int64
   h->n_cur = n_after;
   if ((s = grow_pool(h, h->din, h->hin)) != SR_OK) return s;
   if ((s = grow_pool(h, h->dout, h->hout)) != SR_OK) return s;
-  if ((s = ensure_dev_capacity(h, (int64_t)srcs.size(), (int64_t)ops.size())) != SR_OK) return s;
+  if ((s = ensure_dev_capacity(h, (int64_t)srcs.size() + 2, (int64_t)ops.size())) != SR_OK) return s;
   CUDA_TRY(h, cudaMemcpyAsync(h->d_srcs, srcs.data(), srcs.size() * sizeof(int32_t),
                               cudaMemcpyHostToDevice, h->st));
   if (!ops.empty())
@@ -1055,6 +1343,7 @@ simrank_status simrank_apply_updates(simrank_t h, const simrank_update* u, int64
         SR_OK)
       return s;
   }
+  if ((s = flush_pending(h)) != SR_OK) return s;
   h->stats.updates += count;
   return SR_OK;
 }
@@ -1066,6 +1355,7 @@ simrank_status simrank_columns(simrank_t h, const int32_t* cols, int32_t ncols, 
   for (int c = 0; c < ncols; ++c)
     if (cols[c] < 0 || cols[c] >= h->n_cur) return fail(h, SR_ERR_ARG, "column id out of range");
   if (ncols == 0) return SR_OK;
+  if (h->column) return column_mode_columns(h, cols, ncols, out, out_on_device, out_fp64);
   std::vector<int32_t> icols(cols, cols + ncols);
   for (int32_t& x : icols) x = h->ext2int[x];
   cols = icols.data();
@@ -1136,6 +1426,7 @@ simrank_status simrank_get_stats(simrank_t h, simrank_stats* out) {
 
 simrank_status simrank_reanchor(simrank_t h, int32_t sweeps, double* max_change) {
   if (!h) return fail(nullptr, SR_ERR_ARG, "null handle");
+  if (h->column) return fail(h, SR_ERR_UNSUPPORTED, "column mode keeps no dense S to re-anchor");
   if (sweeps <= 0) return fail(h, SR_ERR_ARG, "sweeps must be positive");
   double diff = 0.0;
   int done = 0;

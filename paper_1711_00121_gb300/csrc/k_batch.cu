@@ -170,6 +170,25 @@ __global__ void k_pack_tc(const double* __restrict__ X, int64_t ldx, int rh, int
   }
 }
 
+// Tensor-core operands from tile-blocked FP32 panels [T][which][GK1][128]:
+// row a of A gets xi terms at columns q < nterms and eta terms at rg + q; the
+// other columns of the row are zero.  x = hi + lo, hi = tf32(x), lo = tf32(x - hi).
+__global__ void k_pack_tc_tiles(const float* __restrict__ Pp, int GK1, int nterms, int rg,
+                                int n_rows, float* __restrict__ Ahi, float* __restrict__ Alo,
+                                int64_t kd) {
+  const int64_t a = blockIdx.x;
+  const int64_t ba = ((a / PT) * 2) * (int64_t)GK1 * PT + (a % PT);
+  for (int c = threadIdx.x; c < kd; c += blockDim.x) {
+    const int h = c >= rg ? 1 : 0;
+    const int q = c - h * rg;
+    float x = 0.f;
+    if (q < nterms) x = Pp[ba + (int64_t)(h * GK1 + q) * PT];
+    const float hi = tf32_round(x);
+    Ahi[a * kd + c] = hi;
+    Alo[a * kd + c] = tf32_round(x - hi);
+  }
+}
+
 }  // namespace
 
 void launch_signed_rows(const void* S, int s_prec, int64_t ld, const int32_t* src, const int8_t* sign,
@@ -223,6 +242,11 @@ void launch_pack_ffma(const double* X, int64_t ldx, int rh, int r, int slot, int
     k_pack_ffma<double><<<grid, 256, 0, st>>>(X, ldx, rh, r, slot, terms, nT, (double*)Pn, mXi, mEta);
   else
     k_pack_ffma<float><<<grid, 256, 0, st>>>(X, ldx, rh, r, slot, terms, nT, (float*)Pn, mXi, mEta);
+}
+
+void launch_pack_tc_tiles(const float* Pp, int GK1, int nterms, int rg, int n_rows, float* Ahi,
+                          float* Alo, int64_t kd, cudaStream_t st) {
+  k_pack_tc_tiles<<<n_rows, 256, 0, st>>>(Pp, GK1, nterms, rg, n_rows, Ahi, Alo, kd);
 }
 
 void launch_pack_tc(const double* X, int64_t ldx, int rh, int r, int slot, int rg, int n_rows,

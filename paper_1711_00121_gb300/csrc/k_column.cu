@@ -1,0 +1,220 @@
+// Column mode (§7): SimRank columns without a dense S, in O(Kn + m) memory
+// per column.
+//  - Procedure 1 (PartialSim) on a block of B columns: forward steps
+//    X_t = Q^T X_{t-1} over the out-lists (row b of Q^T X sums X[a,:] / d_a
+//    over the out-neighbours a of b), stored for t = 0..K, then the Horner
+//    steps Y <- X_{K-t} + C Q Y over the in-lists; result (1-C) Y.
+//  - The change of a column through the stored updates (Eq. 70-71):
+//    Y[a, c] += sum_k xi_k[a] eta_k[x_c] + eta_k[a] xi_k[x_c].
+// Blocks are row-major [node][B]; FP32 or FP64 storage, FP64 accumulation.
+#include "sr_internal.h"
+
+namespace sr {
+
+namespace {
+
+// X0[x_c][c] = 1 (the other entries are zero beforehand)
+template <typename T>
+__global__ void k_col_unit(const int32_t* __restrict__ cols, int B, T* __restrict__ X0) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < B) X0[(int64_t)cols[c] * B + c] = (T)1;
+}
+
+// Y[a][c] = s * X[a][c] (X may be null: Y = 0), a < n_rows, c < B
+template <typename T>
+__global__ void k_col_fill(const T* __restrict__ X, double s, T* __restrict__ Y, int64_t count) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x)
+    Y[e] = X ? (T)(s * (double)X[e]) : (T)0;
+}
+
+// One row chunk (at most CHUNK nonzeros of one adjacency row) per CTA and
+// 128 columns per thread block column:
+//   Y[row][c] += row_scale * sum_{e in chunk} w_e X[col_e][c]
+// forward (Q^T, out-lists): w_e = 1 / d_{col_e}, row_scale = 1
+// Horner  (Q,   in-lists):  w_e = 1,            row_scale = scale / d_row
+// Long rows are split over many chunks, whose partial sums meet in atomics.
+template <typename T, bool FORWARD>
+__global__ void k_col_chunk(const RowChunk* __restrict__ chunks, const int32_t* __restrict__ col,
+                            const int32_t* __restrict__ in_len, const T* __restrict__ X,
+                            T* __restrict__ Y, int B, double scale) {
+  const RowChunk ch = chunks[blockIdx.x];
+  const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  if (c >= B) return;
+  double acc = 0.0;
+#pragma unroll 8
+  for (int e = 0; e < ch.len; ++e) {
+    const int a = col[ch.start + e];
+    const double x = (double)X[(int64_t)a * B + c];
+    acc += FORWARD ? x / (double)in_len[a] : x;
+  }
+  const double rs = FORWARD ? 1.0 : scale / (double)in_len[ch.row];
+  atomicAdd(&Y[(int64_t)ch.row * B + c], (T)(rs * acc));
+}
+
+// Y[a][c] += sum_k xi_k[a] eta_k[x_c] + eta_k[a] xi_k[x_c] for one stored
+// update (tile-blocked panels P[T][which][k][128]); the panel values at the
+// block's columns are staged in shared memory.
+template <typename T, typename TP>
+__global__ void k_col_apply(const TP* __restrict__ P, int K1, const int32_t* __restrict__ cols,
+                            int B, int n_rows, T* __restrict__ Y) {
+  extern __shared__ double sg[];  // [B][2*K1]: xi_k[x_c], eta_k[x_c]
+  for (int e = threadIdx.x; e < B * K1; e += blockDim.x) {
+    const int c = e / K1, k = e % K1;
+    const int64_t x = cols[c];
+    const int64_t base = ((x / PT) * 2) * (int64_t)K1 * PT + (int64_t)k * PT + (x % PT);
+    sg[c * 2 * K1 + k] = (double)P[base];
+    sg[c * 2 * K1 + K1 + k] = (double)P[base + (int64_t)K1 * PT];
+  }
+  __syncthreads();
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n_rows) return;
+  const int64_t ba = ((a / PT) * 2) * (int64_t)K1 * PT + (a % PT);
+  for (int c = 0; c < B; ++c) {
+    const double* g = sg + c * 2 * K1;
+    double acc = 0.0;
+    for (int k = 0; k < K1; ++k)
+      acc += (double)P[ba + (int64_t)k * PT] * g[K1 + k] +
+             (double)P[ba + (int64_t)(K1 + k) * PT] * g[k];
+    Y[a * B + c] = (T)((double)Y[a * B + c] + acc);
+  }
+}
+
+// scal[0] = x_i[i], scal[1] = x_j[j], scal[2] = (1/d_j) sum_{b in I(j)} x_i[b]
+// (columns i and j of S as FP64 vectors, old graph)
+__global__ void k_col_scalars(DevAdj in, const double* __restrict__ si, const double* __restrict__ sj,
+                              int i, int j, double* __restrict__ scal) {
+  __shared__ double red[32];
+  const int64_t st = in.start[j];
+  const int len = in.len[j];
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < len; e += blockDim.x) acc += si[in.col[st + e]];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double w = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) w += red[q];
+    scal[0] = si[i];
+    scal[1] = sj[j];
+    scal[2] = len > 0 ? w / (double)len : 0.0;
+  }
+}
+
+// out[c * n + a] = Y[a][c] (column-major output, optional FP32)
+template <typename T, typename TO>
+__global__ void k_col_out(const T* __restrict__ Y, int B, int n, TO* __restrict__ out) {
+  const int c = blockIdx.y;
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a < n) out[(int64_t)c * n + a] = (TO)Y[(int64_t)a * B + c];
+}
+
+// column c of a row-major [n][B] block into a contiguous FP64 vector
+template <typename T>
+__global__ void k_col_extract(const T* __restrict__ Y, int B, int c, int n, double* __restrict__ v) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a < n) v[a] = (double)Y[(int64_t)a * B + c];
+}
+
+}  // namespace
+
+template <typename T>
+static void partial_sim_block_t(const ChunkList& fwd, const ChunkList& hor, const int32_t* out_col,
+                                const int32_t* in_col, const int32_t* in_len, const int32_t* cols,
+                                int B, int n_rows, int K, double C, T* xs, T* y0, T* y1, T* result,
+                                cudaStream_t st) {
+  const int64_t blk = (int64_t)n_rows * B;
+  const int fill_blocks = 4096;
+  k_col_fill<T><<<fill_blocks, 256, 0, st>>>(nullptr, 0.0, xs, blk);
+  k_col_unit<T><<<(B + 127) / 128, 128, 0, st>>>(cols, B, xs);
+  const int ygroups = (B + 127) / 128;
+  const int tpb = B >= 128 ? 128 : (B + 31) / 32 * 32;
+  for (int t = 1; t <= K; ++t) {
+    T* dst = xs + (int64_t)t * blk;
+    k_col_fill<T><<<fill_blocks, 256, 0, st>>>(nullptr, 0.0, dst, blk);
+    if (fwd.count > 0)
+      k_col_chunk<T, true><<<dim3((unsigned)fwd.count, ygroups), tpb, 0, st>>>(
+          fwd.chunks, out_col, in_len, xs + (int64_t)(t - 1) * blk, dst, B, 1.0);
+  }
+  // Horner: y = x_K; y <- x_{K-t} + C Q y; result (1-C) y (the last step folds the scale)
+  const T* y = xs + (int64_t)K * blk;
+  T* bufs[2] = {y0, y1};
+  if (K == 0) {
+    k_col_fill<T><<<fill_blocks, 256, 0, st>>>(xs, 1.0 - C, result, blk);
+    return;
+  }
+  for (int t = 1; t <= K; ++t) {
+    T* dst = (t == K) ? result : bufs[t & 1];
+    const double s = (t == K) ? 1.0 - C : 1.0;
+    k_col_fill<T><<<fill_blocks, 256, 0, st>>>(xs + (int64_t)(K - t) * blk, s, dst, blk);
+    if (hor.count > 0)
+      k_col_chunk<T, false><<<dim3((unsigned)hor.count, ygroups), tpb, 0, st>>>(
+          hor.chunks, in_col, in_len, y, dst, B, s * C);
+    y = dst;
+  }
+}
+
+void launch_partial_sim_block(const ChunkList& fwd, const ChunkList& hor, const int32_t* out_col,
+                              const int32_t* in_col, const int32_t* in_len, const int32_t* cols,
+                              int B, int n_rows, int K, double C, int prec, void* xs, void* y0,
+                              void* y1, void* result, cudaStream_t st) {
+  if (prec == 64)
+    partial_sim_block_t<double>(fwd, hor, out_col, in_col, in_len, cols, B, n_rows, K, C,
+                                (double*)xs, (double*)y0, (double*)y1, (double*)result, st);
+  else
+    partial_sim_block_t<float>(fwd, hor, out_col, in_col, in_len, cols, B, n_rows, K, C,
+                               (float*)xs, (float*)y0, (float*)y1, (float*)result, st);
+}
+
+void launch_col_apply(const void* P, int p_prec, int K1, const int32_t* cols, int B, int n_rows,
+                      int prec, void* Y, cudaStream_t st) {
+  const size_t smem = (size_t)B * 2 * K1 * sizeof(double);
+  const int threads = 128;
+  const int blocks = (n_rows + threads - 1) / threads;
+#define SR_COL_APPLY(T, TP)                                                                  \
+  do {                                                                                       \
+    cudaFuncSetAttribute(k_col_apply<T, TP>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                         (int)smem);                                                         \
+    k_col_apply<T, TP><<<blocks, threads, smem, st>>>((const TP*)P, K1, cols, B, n_rows, (T*)Y); \
+  } while (0)
+  if (prec == 64 && p_prec == 64)
+    SR_COL_APPLY(double, double);
+  else if (prec == 64)
+    SR_COL_APPLY(double, float);
+  else if (p_prec == 64)
+    SR_COL_APPLY(float, double);
+  else
+    SR_COL_APPLY(float, float);
+#undef SR_COL_APPLY
+}
+
+void launch_col_scalars(const DevAdj& in, const double* si, const double* sj, int i, int j,
+                        double* scal, cudaStream_t st) {
+  k_col_scalars<<<1, 256, 0, st>>>(in, si, sj, i, j, scal);
+}
+
+void launch_col_out(const void* Y, int prec, int B, int n, void* out, int out_fp64,
+                    cudaStream_t st) {
+  dim3 grid((n + 255) / 256, B);
+  if (prec == 64) {
+    if (out_fp64)
+      k_col_out<double, double><<<grid, 256, 0, st>>>((const double*)Y, B, n, (double*)out);
+    else
+      k_col_out<double, float><<<grid, 256, 0, st>>>((const double*)Y, B, n, (float*)out);
+  } else {
+    if (out_fp64)
+      k_col_out<float, double><<<grid, 256, 0, st>>>((const float*)Y, B, n, (double*)out);
+    else
+      k_col_out<float, float><<<grid, 256, 0, st>>>((const float*)Y, B, n, (float*)out);
+  }
+}
+
+void launch_col_extract(const void* Y, int prec, int B, int c, int n, double* v, cudaStream_t st) {
+  if (prec == 64)
+    k_col_extract<double><<<(n + 255) / 256, 256, 0, st>>>((const double*)Y, B, c, n, v);
+  else
+    k_col_extract<float><<<(n + 255) / 256, 256, 0, st>>>((const float*)Y, B, c, n, v);
+}
+
+}  // namespace sr

@@ -66,6 +66,105 @@ __global__ void k_gather_rows(const T* __restrict__ S, int64_t ld, const int32_t
   }
 }
 
+// Rows of the current S when G earlier updates are still pending (their
+// panels not yet added to S): for x in {I_0..I_{delta-1}} and j,
+//   S_cur[x, a] = S[x, a] + sum_{u < np} sum_k xi^u_k[x] eta^u_k[a] + eta^u_k[x] xi^u_k[a]
+// with the pending panels Pp stored tile-blocked [T][which][G*K1][128] (FP32,
+// term = u * K1 + k).  sI[a] = sum_t S_cur[I_t, a], sJ[a] = S_cur[j, a].
+template <typename T>
+__global__ void __launch_bounds__(256) k_gather_rows_pending(
+    const T* __restrict__ S, int64_t ld, const int32_t* __restrict__ I, int delta, int j, int n_pad,
+    const float* __restrict__ Pp, int GK1, int nterms, double* __restrict__ sI,
+    double* __restrict__ sJ) {
+  // coefficients: [2 vectors (I-sum, j)][2 (xi, eta)][nterms]
+  extern __shared__ double coef[];
+  __shared__ double red[8][32][2];
+  for (int q = threadIdx.x; q < nterms; q += blockDim.x) {
+    double cx = 0.0, ce = 0.0;
+    for (int t = 0; t < delta; ++t) {
+      const int64_t x = I[t];
+      const int64_t base = ((x / PT) * 2) * (int64_t)GK1 * PT + (int64_t)q * PT + (x % PT);
+      cx += (double)Pp[base];
+      ce += (double)Pp[base + (int64_t)GK1 * PT];
+    }
+    const int64_t base = ((int64_t)(j / PT) * 2) * GK1 * PT + (int64_t)q * PT + (j % PT);
+    coef[0 * nterms + q] = cx;
+    coef[1 * nterms + q] = ce;
+    coef[2 * nterms + q] = (double)Pp[base];
+    coef[3 * nterms + q] = (double)Pp[base + (int64_t)GK1 * PT];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int a = blockIdx.x * 32 + lane;  // 32 consecutive rows share one tile
+  double accI = 0.0, accJ = 0.0;
+  if (a < n_pad) {
+    const int64_t ba = ((int64_t)(a / PT) * 2) * GK1 * PT + (a % PT);
+    for (int q = warp; q < nterms; q += 8) {
+      const double xa = (double)Pp[ba + (int64_t)q * PT];
+      const double ea = (double)Pp[ba + (int64_t)(GK1 + q) * PT];
+      accI += coef[0 * nterms + q] * ea + coef[1 * nterms + q] * xa;
+      accJ += coef[2 * nterms + q] * ea + coef[3 * nterms + q] * xa;
+    }
+    if (warp == 0) {
+      for (int t = 0; t < delta; ++t) accI += ld_s(S + (int64_t)I[t] * ld + a);
+      accJ += ld_s(S + (int64_t)j * ld + a);
+    }
+  }
+  red[warp][lane][0] = accI;
+  red[warp][lane][1] = accJ;
+  __syncthreads();
+  if (warp == 0 && a < n_pad) {
+    double vI = 0.0, vJ = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      vI += red[w][lane][0];
+      vJ += red[w][lane][1];
+    }
+    sI[a] = vI;
+    sJ[a] = vJ;
+  }
+}
+
+// scal[0] = S_II = sum_t sI[I_t], scal[1] = S_jj = sJ[j],
+// scal[2] = w_j = (1/(delta d_j)) sum_{b in I(j)} sI[b] on the graph `in` (old)
+__global__ void k_scalars_from_rows(DevAdj in, const double* __restrict__ sI,
+                                    const double* __restrict__ sJ, const int32_t* __restrict__ I,
+                                    int delta, int j, double* __restrict__ scal) {
+  __shared__ double red[2][32];
+  const int64_t st = in.start[j];
+  const int len = in.len[j];
+  double w = 0.0, sii = 0.0;
+  for (int e = threadIdx.x; e < len; e += blockDim.x) w += sI[in.col[st + e]];
+  for (int t = threadIdx.x; t < delta; t += blockDim.x) sii += sI[I[t]];
+  w = warp_sum(w);
+  sii = warp_sum(sii);
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = w;
+    red[1][threadIdx.x >> 5] = sii;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ws = 0.0, ss = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+      ws += red[0][q];
+      ss += red[1][q];
+    }
+    scal[0] = ss;
+    scal[1] = sJ[j];
+    scal[2] = len > 0 ? ws / ((double)delta * (double)len) : 0.0;
+  }
+}
+
+// tile-level "any term non-zero" masks of the pending updates
+__global__ void k_or_any(const uint64_t* __restrict__ mXi, const uint64_t* __restrict__ mEta,
+                         int nT, uint64_t* __restrict__ pXi, uint64_t* __restrict__ pEta) {
+  const int T = blockIdx.x * blockDim.x + threadIdx.x;
+  if (T < nT) {
+    if (mXi[T]) pXi[T] = 1ull;
+    if (mEta[T]) pEta[T] = 1ull;
+  }
+}
+
 // Per-tile sparse gather used by the gamma and chain kernels.  One CTA owns
 // the 128 rows of tile T; the nonzeros of those rows are flattened (row
 // offsets by an exclusive scan in shared memory) and split into contiguous
@@ -389,6 +488,35 @@ void launch_gather_rows(const void* S, int s_prec, int64_t ld, const int32_t* I,
   else
     k_gather_rows<float><<<blocks, threads, 0, st>>>((const float*)S, ld, I, delta, j, n_pad, in,
                                                      sI, sJ, scal);
+}
+
+void launch_gather_rows_pending(const void* S, int s_prec, int64_t ld, const int32_t* I, int delta,
+                                int j, int n_pad, const float* Pp, int GK1, int nterms, double* sI,
+                                double* sJ, cudaStream_t st) {
+  const int threads = 256;
+  const int blocks = (n_pad + 31) / 32;
+  const size_t smem = (size_t)4 * nterms * sizeof(double);
+  if (s_prec == 64) {
+    cudaFuncSetAttribute(k_gather_rows_pending<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    k_gather_rows_pending<double><<<blocks, threads, smem, st>>>((const double*)S, ld, I, delta, j,
+                                                                 n_pad, Pp, GK1, nterms, sI, sJ);
+  } else {
+    cudaFuncSetAttribute(k_gather_rows_pending<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    k_gather_rows_pending<float><<<blocks, threads, smem, st>>>((const float*)S, ld, I, delta, j,
+                                                                n_pad, Pp, GK1, nterms, sI, sJ);
+  }
+}
+
+void launch_scalars_from_rows(const DevAdj& in, const double* sI, const double* sJ, const int32_t* I,
+                              int delta, int j, double* scal, cudaStream_t st) {
+  k_scalars_from_rows<<<1, 256, 0, st>>>(in, sI, sJ, I, delta, j, scal);
+}
+
+void launch_or_any(const uint64_t* mXi, const uint64_t* mEta, int nT, uint64_t* pXi, uint64_t* pEta,
+                   cudaStream_t st) {
+  k_or_any<<<(nT + 127) / 128, 128, 0, st>>>(mXi, mEta, nT, pXi, pEta);
 }
 
 void launch_gamma(const DevAdj& in, const double* sI, const double* sJ, const double* scal, int j,

@@ -85,6 +85,21 @@ void launch_gamma(const DevAdj& in, const double* sI, const double* sJ, const do
                   int delta, int op, int d_j, double C, int nT, int K1, double* P64, float* P32,
                   uint64_t* mXi, uint64_t* mEta, cudaStream_t st);
 
+// Deferred S updates: rows of the current S = S + the pending panels Pp
+// (tile-blocked FP32 [T][which][GK1][128], nterms used terms).
+void launch_gather_rows_pending(const void* S, int s_prec, int64_t ld, const int32_t* I, int delta,
+                                int j, int n_pad, const float* Pp, int GK1, int nterms, double* sI,
+                                double* sJ, cudaStream_t st);
+// scal[0] = sum_t sI[I_t], scal[1] = sJ[j], scal[2] = (1/(delta d_j)) sum_{b in I(j)} sI[b]
+void launch_scalars_from_rows(const DevAdj& in, const double* sI, const double* sJ, const int32_t* I,
+                              int delta, int j, double* scal, cudaStream_t st);
+// pXi[T] = 1 if mXi[T] != 0 (and the same for eta); other entries unchanged
+void launch_or_any(const uint64_t* mXi, const uint64_t* mEta, int nT, uint64_t* pXi, uint64_t* pEta,
+                   cudaStream_t st);
+// tensor-core operands (row-major hi/lo, kd columns) from tile-blocked FP32 panels
+void launch_pack_tc_tiles(const float* Pp, int GK1, int nterms, int rg, int n_rows, float* Ahi,
+                          float* Alo, int64_t kd, cudaStream_t st);
+
 // Apply patch ops [begin, end) to the device adjacency (one CTA, in order).
 void launch_patch(const PatchOp* ops, int64_t begin, int64_t end, DevAdj in, DevAdj out,
                   cudaStream_t st);
@@ -157,5 +172,34 @@ void launch_pack_tc(const double* X, int64_t ldx, int rh, int r, int slot, int r
 int launch_s_update_tc(float* S, int64_t ld, const float* Ahi, const float* Alo, int64_t n_rows,
                        int64_t kd, const uint32_t* tiles, const int* ntiles, int n,
                        int64_t* counters, int grid, long long wait_limit, cudaStream_t st);
+
+// ---- column mode (§7), k_column.cu
+// A piece of one adjacency row: row id, count (<= kChunk) and pool offset.
+struct RowChunk {
+  int32_t row;
+  int32_t len;
+  int64_t start;
+};
+constexpr int kChunk = 32;
+struct ChunkList {
+  RowChunk* chunks = nullptr;  // device
+  int64_t count = 0;
+};
+// Procedure 1 on B columns `cols` (device) of the graph whose out-lists
+// (fwd chunks over out_col) and in-lists (hor chunks over in_col) are given;
+// in_len = in-degrees.  xs holds (K+1) row-major [n_rows][B] blocks, y0 / y1
+// are scratch blocks, result receives (1-C) sum_k C^k Q^k (Q^T)^k e_cols.
+void launch_partial_sim_block(const ChunkList& fwd, const ChunkList& hor, const int32_t* out_col,
+                              const int32_t* in_col, const int32_t* in_len, const int32_t* cols,
+                              int B, int n_rows, int K, double C, int prec, void* xs, void* y0,
+                              void* y1, void* result, cudaStream_t st);
+// Y[a][c] += sum_k xi_k[a] eta_k[cols[c]] + eta_k[a] xi_k[cols[c]] (panels P, FP32/64)
+void launch_col_apply(const void* P, int p_prec, int K1, const int32_t* cols, int B, int n_rows,
+                      int prec, void* Y, cudaStream_t st);
+// scal[0] = si[i], scal[1] = sj[j], scal[2] = (1/d_j) sum_{b in I(j)} si[b]
+void launch_col_scalars(const DevAdj& in, const double* si, const double* sj, int i, int j,
+                        double* scal, cudaStream_t st);
+void launch_col_out(const void* Y, int prec, int B, int n, void* out, int out_fp64, cudaStream_t st);
+void launch_col_extract(const void* Y, int prec, int B, int c, int n, double* v, cudaStream_t st);
 
 }  // namespace sr

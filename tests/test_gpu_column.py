@@ -1,0 +1,76 @@
+"""Column mode (§7, Alg 7 Inc-SR-All-P with Procedure 1) against the oracle,
+through the C ABI."""
+import numpy as np
+import pytest
+
+from oracle import simrank_oracle as O
+from synth import er_graph, chung_lu_digraph, update_stream
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1711_00121_gb300 as P
+
+    return P
+
+
+def test_column_mode_base_columns_fp64(P):
+    n, m, C, K = 700, 3500, 0.6, 9
+    s, d = er_graph(n, m, 51)
+    sr = P.SimRank(n, s, d, C=C, K=K, s_precision=64, mode=P.MODE_COLUMN)
+    cols = np.array([0, 3, 129, 300, 699], np.int32)
+    Q = O.transition_matrix(n, s, d, sparse=True)
+    want = O.partial_sim_block(Q, cols, K, C)
+    assert np.max(np.abs(sr.columns(cols) - want)) < 1e-12
+
+
+def test_column_mode_updates_all_cases_fp64(P):
+    n, m, C, K = 500, 2500, 0.6, 8
+    s, d = er_graph(n, m, 52)
+    edges = set(zip(s.tolist(), d.tolist()))
+    deg = np.bincount(d, minlength=n)
+    j_big = int(np.argmax(deg))
+    i_new = next(x for x in range(n) if x != j_big and (x, j_big) not in edges)
+    e_del = next(e for e in sorted(edges) if deg[e[1]] > 1 and e[1] != j_big)
+    ups = [
+        (i_new, j_big, 1),   # C0 insert
+        (e_del[0], e_del[1], -1),  # C0 delete
+        (4, n, 1),           # C1: j new
+        (n + 1, j_big, 1),   # C2: i new
+        (n + 2, n + 3, 1),   # C3: both new
+        (9, n, 1),           # C0 into a node created above
+    ]
+    sr = P.SimRank(n, s, d, C=C, K=K, s_precision=64, mode=P.MODE_COLUMN, n_capacity=n + 4)
+    sr.apply_updates(ups)
+    assert sr.n == n + 4
+    cols = np.array([0, j_big, i_new, e_del[1], n, n + 1, n + 3, 257], np.int32)
+    got = sr.columns(cols)
+    Q0 = O.transition_matrix(n, s, d, sparse=True)
+    for c, x in enumerate(cols.tolist()):
+        col0 = O.partial_sim(Q0, x, K, C) if x < n else np.zeros(n)
+        want = O.inc_sr_all_p(n, s, d, col0, x, ups, C, K)
+        assert np.max(np.abs(got[:, c] - want)) < 1e-10, x
+
+
+def test_column_mode_stream_fp32(P):
+    n, m, C, K = 1200, 12000, 0.6, 10
+    s, d = chung_lu_digraph(n, m, 2.1, 2.1, 53)
+    st = update_stream(n, s, d, 12, 54)
+    sr = P.SimRank(n, s, d, C=C, K=K, s_precision=32, mode=P.MODE_COLUMN)
+    sr.apply_updates(st)
+    rng = np.random.default_rng(55)
+    cols = np.sort(rng.choice(n, size=40, replace=False)).astype(np.int32)
+    got = sr.columns(cols)
+    Q0 = O.transition_matrix(n, s, d, sparse=True)
+    base = O.partial_sim_block(Q0, cols, K, C)
+    for c, x in enumerate(cols.tolist()[:6]):
+        want = O.inc_sr_all_p(n, s, d, base[:, c], x, st.tolist(), C, K)
+        assert np.max(np.abs(got[:, c] - want)) < 1e-6, x
