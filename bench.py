@@ -182,8 +182,9 @@ def run_gpu(args, rank, world):
         arr = P.updates_array(st)
         t = torch.from_numpy(arr.view(np.uint8)).pin_memory()
         packed.append((t, arr.size))
+    form = dict(defer=args.defer, tc=args.tc)
     sr = P.SimRank(N, s, d, C=C, K=K, s_precision=32, aff=1, profile=1,
-                   stream=stream.cuda_stream)
+                   stream=stream.cuda_stream, **form)
     sr.sync()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -212,7 +213,8 @@ def run_gpu(args, rank, world):
     sr.close()
     del sr
     torch.cuda.empty_cache()
-    sr2 = P.SimRank(N, s_e, d_e, C=C, K=K, s_precision=32, aff=1, stream=stream.cuda_stream)
+    sr2 = P.SimRank(N, s_e, d_e, C=C, K=K, s_precision=32, aff=1, stream=stream.cuda_stream,
+                    **form)
     with torch.cuda.stream(stream):
         for t in range(args.warmup):
             sr2.apply_updates_ptr(packed[t][0].data_ptr(), packed[t][1])
@@ -253,7 +255,7 @@ def run_gpu(args, rank, world):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N, "m": M, "C": C, "K": K,
-                   "updates_per_step": per_step,
+                   "updates_per_step": per_step, "defer": args.defer, "tc": args.tc,
                    "l2": "inputs larger than L2 (S is 1.6 GB FP32)",
                    "aff_tile_fraction": tiles_touched / max(tiles_total, 1),
                    "hbm_gbs_step": alg_bytes / (ms / 1000.0) / 1e9,
@@ -384,6 +386,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--updates-per-step", type=int, default=UPDATES_PER_STEP,
                     help="batch size of one step (the benchmarked workload uses 1000)")
+    ap.add_argument("--defer", type=int, default=0,
+                    help="stream workload: rank-one updates kept pending per S pass (0 = apply each)")
+    ap.add_argument("--tc", type=int, default=0, help="S passes on tensor cores (with --defer)")
     ap.add_argument("--workload", default="stream", choices=["stream", "batched"],
                     help="stream: the benchmarked update stream; batched: one-shot vs per-edge")
     ap.add_argument("--batch", type=int, default=64, help="batched workload: edges per batch")

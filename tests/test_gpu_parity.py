@@ -119,7 +119,7 @@ def test_unit_update_converged_vs_batch_recompute(P, case):
 # ------------------------------------------------------------ update streams
 
 @pytest.mark.parametrize("variant", ["fused_aff", "fused_aff_norelabel", "fused_single_role",
-                                     "fused_noaff", "plain"])
+                                     "fused_noaff", "plain", "deferred_ffma", "deferred_tc"])
 def test_stream_fp32_powerlaw(P, variant):
     n, m, C, K = 1500, 15000, 0.6, 20
     s, d = chung_lu_digraph(n, m, 2.1, 2.1, 4)
@@ -129,6 +129,10 @@ def test_stream_fp32_powerlaw(P, variant):
         kw = dict(aff=1, relabel=0, s_update=P.SUPDATE_FUSED)
     elif variant == "fused_single_role":
         kw = dict(aff=1, s_kernel=1, s_update=P.SUPDATE_FUSED)
+    elif variant == "deferred_ffma":
+        kw = dict(aff=1, defer=7, tc=0)
+    elif variant == "deferred_tc":
+        kw = dict(aff=1, defer=16, tc=1)
     elif variant == "fused_noaff":
         kw = dict(aff=0, s_update=P.SUPDATE_FUSED)
     elif variant == "plain":
@@ -225,6 +229,19 @@ def test_c2_matches_alg4(P):
 
 
 # --------------------------------------------------------- batches (§8, Alg 6)
+
+@pytest.mark.parametrize("defer", [0, 5])
+def test_sink_blocks_fp32_deferred_vs_inc_bsr(P, defer):
+    n, m, C, K = 600, 3600, 0.6, 10
+    s, d = er_graph(n, m, 14)
+    ups, n_new = batch_with_new_nodes(n, s, d, 60, 14, frac_new=0.2, reuse_target=0.5)
+    S = oracle_S(n, s, d, C)
+    sr = P.SimRank(n, s, d, C=C, K=K, s_precision=32, n_capacity=n + n_new,
+                   apply=P.APPLY_SINK_BLOCKS, defer=defer, tc=1)
+    sr.apply_updates(ups)
+    want, _ = O.inc_bsr(n, s, d, S, ups.tolist(), C, K)
+    assert maxabs(sr.dense(), want) < TOL32
+
 
 @pytest.mark.parametrize("seed", [12, 13])
 def test_sink_blocks_fp64_vs_inc_bsr(P, seed):
