@@ -94,7 +94,9 @@ typedef struct simrank_config {
                              panels pending (the rows of S an update reads are corrected by them)
                              and apply them in one rank-2G(K+1) pass (tensor cores when tc = 1).
                              Pending updates are always applied before apply_updates returns. */
-  int32_t reserved[6];
+  int32_t chain;          /* xi/eta recurrence of a rank-one update: 0 = all K steps in one
+                             cooperative launch (bounded grid barrier), 1 = one launch per step */
+  int32_t reserved[5];
 } simrank_config;
 
 /* Fills *cfg with defaults: C = 0.6, K = 15, s_precision = 32, dense, aff = 1,
@@ -168,6 +170,20 @@ simrank_status simrank_get_stats(simrank_t h, simrank_stats* out);
  * long FP32 update streams).  *max_change (nullable) receives the max-abs
  * change of the last sweep.  Synchronises. */
 simrank_status simrank_reanchor(simrank_t h, int32_t sweeps, double* max_change);
+
+/* Loss and gradient for learning edge weights: for the K-truncated series
+ * S_K = (1-C) sum_{k=0}^{K} C^k Q^k (Q^T)^k (Eq. 17; the paper defines neither
+ * weights nor gradients: Q[a][b] = w_ba / sum_x w_xa with the weights given at
+ * init, 1 / in-degree without them),
+ *   *loss = sum_p (S_K[a_p, b_p] - target_p)^2,
+ *   grad_weight[e] = dL / d w_e for the init edges e < m, in the caller's init order.
+ * The gradient is the exact derivative of that truncated forward (an adjoint
+ * series with its terms recomputed per block of endpoints, then an SDDMM at
+ * the edges and the chain rule through the row normalisation).  Host arrays;
+ * npairs pairs a, b (node ids) and targets.  Needs a handle to which no
+ * updates have been applied (SR_ERR_UNSUPPORTED otherwise).  Synchronises. */
+simrank_status simrank_grad(simrank_t h, const int32_t* a, const int32_t* b, const double* target,
+                            int64_t npairs, double* loss, double* grad_weight);
 
 /* Host-only planning of one batch (no GPU work, usable without a device):
  * net update by edge counts, split by sign, similar-sink partition (§8,

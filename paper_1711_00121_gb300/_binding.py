@@ -39,8 +39,8 @@ class Config(ctypes.Structure):
         ("init_max_sweeps", ctypes.c_int32), ("init_tol", ctypes.c_double),
         ("profile", ctypes.c_int32), ("relabel", ctypes.c_int32),
         ("timeout_iters", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
-        ("s_kernel", ctypes.c_int32), ("defer", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 6),
+        ("s_kernel", ctypes.c_int32), ("defer", ctypes.c_int32), ("chain", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 5),
     ]
 
 
@@ -80,6 +80,7 @@ SIGNATURES = {
     "simrank_get_stats": (_I32, [_P, ctypes.POINTER(Stats)]),
     "simrank_reanchor": (_I32, [_P, _I32, ctypes.POINTER(ctypes.c_double)]),
     "simrank_plan_batch": (_I32, [_P, _I64, _I32, _I32, ctypes.POINTER(_I32), _P, _P, _P, _P]),
+    "simrank_grad": (_I32, [_P, _P, _P, _P, _I64, ctypes.POINTER(ctypes.c_double), _P]),
     "simrank_update_noalloc": (_I32, [_I32, _I64, _P, _I32, _P, _P, _P, _P, _I32, _I32, _I32, _I32,
                                       ctypes.c_double, _I32, _P]),
 }
@@ -210,6 +211,17 @@ class SimRank:
         out = {name: getattr(s, name) for name, _ in Stats._fields_ if name != "reserved"}
         out["phase_ms"] = list(s.phase_ms)
         return out
+
+    def grad(self, a, b, target, m):
+        """Pair loss and its gradient with respect to the m initial edge weights."""
+        a = np.ascontiguousarray(a, np.int32)
+        b = np.ascontiguousarray(b, np.int32)
+        t = np.ascontiguousarray(target, np.float64)
+        g = np.zeros(int(m), np.float64)
+        L = ctypes.c_double()
+        _check(lib().simrank_grad(self._h, _ptr(a), _ptr(b), _ptr(t), int(a.size), ctypes.byref(L),
+                                  _ptr(g)), self._h)
+        return L.value, g
 
     def reanchor(self, sweeps):
         d = ctypes.c_double()

@@ -47,7 +47,9 @@ struct simrank_ctx {
   // device graph
   DevAdj din, dout;
   float* d_in_w = nullptr;
+  float* d_out_w = nullptr;
   double* d_wsum = nullptr;
+  std::vector<int32_t> init_src, init_dst;  // initial edges in storage ids, caller order
   // dense S and panels
   void* S = nullptr;
   double* P64 = nullptr;
@@ -61,6 +63,7 @@ struct simrank_ctx {
   double* scal = nullptr;
   int64_t* counters = nullptr;
   unsigned long long* diffbits = nullptr;
+  unsigned int* gbar = nullptr;  // grid barrier state of the cooperative chain kernel
   // per-call staging
   int32_t* d_srcs = nullptr;
   int64_t srcs_cap = 0;
@@ -80,7 +83,7 @@ struct simrank_ctx {
   struct Buf {
     void* p = nullptr;
     size_t bytes = 0;
-  } ob[16];
+  } ob[24];
   // deferred S updates: pending panels [T][which][G*K1][128] (FP32), count, tile masks
   float* Pp = nullptr;
   int np = 0;
@@ -499,11 +502,17 @@ simrank_status run_rank_one(simrank_ctx* h, int64_t src_off, int delta, int j, i
                h->cfg.s_precision == 64 ? nullptr : h->P32, h->mXi, h->mEta, h->st);
   if (pe) CUDA_TRY(h, cudaEventRecord(pe[1], h->st));
   launch_patch(h->d_ops, op_begin, op_end, h->din, h->dout, h->st);
-  for (int k = 0; k < h->cfg.K; ++k)
-    launch_chain_step(h->din, k, C, nT, h->K1, h->P64,
-                      h->cfg.s_precision == 64 ? nullptr : h->P32, h->mXi, h->mEta, h->st);
+  float* p32 = h->cfg.s_precision == 64 ? nullptr : h->P32;
+  if (h->cfg.chain == 0) {
+    CUDA_TRY(h, launch_chain_all(h->din, h->cfg.K, C, nT, h->K1, h->P64, p32, h->mXi, h->mEta,
+                                 h->gbar, wait_limit(h), h->counters, h->st));
+    h->launches += 3 + (op_end > op_begin ? 1 : 0);
+  } else {
+    for (int k = 0; k < h->cfg.K; ++k)
+      launch_chain_step(h->din, k, C, nT, h->K1, h->P64, p32, h->mXi, h->mEta, h->st);
+    h->launches += 2 + (op_end > op_begin ? 1 : 0) + h->cfg.K;
+  }
   LAUNCH_CHECK(h);
-  h->launches += 2 + (op_end > op_begin ? 1 : 0) + h->cfg.K;
   if (pe) CUDA_TRY(h, cudaEventRecord(pe[2], h->st));
   if (defer) {
     // append this update's panels as pending terms np*K1 .. np*K1 + K (FP32)
@@ -933,10 +942,12 @@ simrank_status column_mode_columns(simrank_ctx* h, const int32_t* cols, int ncol
 
 void free_ctx(simrank_ctx* h) {
   if (!h) return;
+  if (h->d_out_w) cudaFree(h->d_out_w);
   void* ptrs[] = {h->din.start, h->din.len,  h->din.col,   h->dout.start, h->dout.len,
                   h->dout.col,  h->d_in_w,   h->d_wsum,    h->S,          h->P64,
                   h->P32,       h->mXi,      h->mEta,      h->tiles,      h->ntiles,
                   h->sI,        h->sJ,       h->scal,      h->counters,   h->diffbits,
+                  h->gbar,
                   h->d_srcs,    h->d_ops,    h->d_cols,     h->d_ext2int};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -999,7 +1010,6 @@ simrank_status simrank_init(const simrank_config* cfg_in, int32_t n, int64_t m, 
     return fail(nullptr, SR_ERR_ARG, "mode must be SR_MODE_DENSE or SR_MODE_COLUMN");
   if (cfg.mode == SR_MODE_COLUMN) {
     if (S0) return fail(nullptr, SR_ERR_ARG, "column mode keeps no dense S: S0 must be NULL");
-    if (weight) return fail(nullptr, SR_ERR_UNSUPPORTED, "column mode on a weighted graph");
     if (cfg.apply != SR_APPLY_UNIT)
       return fail(nullptr, SR_ERR_UNSUPPORTED, "column mode applies unit updates (Alg 7)");
     cfg.relabel = 0;
@@ -1063,7 +1073,7 @@ simrank_status simrank_init(const simrank_config* cfg_in, int32_t n, int64_t m, 
 
   // --- host graph (storage ids), validated
   std::vector<std::vector<int32_t>> in_rows(h->n_pad), out_rows(h->n_pad);
-  std::vector<std::vector<float>> in_w(h->weighted ? h->n_pad : 0);
+  std::vector<std::vector<float>> in_w(h->weighted ? h->n_pad : 0), out_w(h->weighted ? h->n_pad : 0);
   h->edges.reserve((size_t)m * 2 + 16);
   for (int64_t e = 0; e < m; ++e) {
     const int32_t s = src[e], d = dst[e];
@@ -1077,7 +1087,12 @@ simrank_status simrank_init(const simrank_config* cfg_in, int32_t n, int64_t m, 
     const int32_t si = h->ext2int[s], di = h->ext2int[d];
     in_rows[di].push_back(si);
     out_rows[si].push_back(di);
-    if (h->weighted) in_w[di].push_back(weight[e]);
+    if (h->weighted) {
+      in_w[di].push_back(weight[e]);
+      out_w[si].push_back(weight[e]);
+    }
+    h->init_src.push_back(si);
+    h->init_dst.push_back(di);
   }
   if (h->relabeled) {
     // the duplicate check above ran on caller ids; keep the edge set in storage ids
@@ -1108,18 +1123,21 @@ simrank_status simrank_init(const simrank_config* cfg_in, int32_t n, int64_t m, 
   if ((s = upload_adj(h->din, h->hin)) != SR_OK) return bail(s);
   if ((s = upload_adj(h->dout, h->hout)) != SR_OK) return bail(s);
   if (h->weighted) {
-    std::vector<float> wpool(h->hin.pool.size(), 0.f);
+    std::vector<float> wpool(h->hin.pool.size(), 0.f), opool(h->hout.pool.size(), 0.f);
     std::vector<double> wsum(h->n_pad, 0.0);
     for (int a = 0; a < h->n_pad; ++a) {
       for (size_t e = 0; e < in_w[a].size(); ++e) {
         wpool[h->hin.start[a] + e] = in_w[a][e];
         wsum[a] += in_w[a][e];
       }
+      for (size_t e = 0; e < out_w[a].size(); ++e) opool[h->hout.start[a] + e] = out_w[a][e];
     }
     if (cudaMalloc(&h->d_in_w, wpool.size() * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&h->d_out_w, opool.size() * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&h->d_wsum, wsum.size() * sizeof(double)) != cudaSuccess)
       return bail(fail(h, SR_ERR_OOM, "cudaMalloc of weights failed"));
     cudaMemcpy(h->d_in_w, wpool.data(), wpool.size() * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemcpy(h->d_out_w, opool.data(), opool.size() * sizeof(float), cudaMemcpyHostToDevice);
     cudaMemcpy(h->d_wsum, wsum.data(), wsum.size() * sizeof(double), cudaMemcpyHostToDevice);
   }
 
@@ -1137,13 +1155,15 @@ simrank_status simrank_init(const simrank_config* cfg_in, int32_t n, int64_t m, 
       dev_alloc(&h->tiles, (size_t)h->nT_cap * (h->nT_cap + 1) / 2) != cudaSuccess ||
       dev_alloc(&h->ntiles, 1) != cudaSuccess || dev_alloc(&h->sI, (size_t)h->n_pad) != cudaSuccess ||
       dev_alloc(&h->sJ, (size_t)h->n_pad) != cudaSuccess || dev_alloc(&h->scal, 8) != cudaSuccess ||
-      dev_alloc(&h->counters, CNT_N) != cudaSuccess || dev_alloc(&h->diffbits, 1) != cudaSuccess)
+      dev_alloc(&h->counters, CNT_N) != cudaSuccess || dev_alloc(&h->diffbits, 1) != cudaSuccess ||
+      dev_alloc(&h->gbar, 2) != cudaSuccess)
     return bail(fail(h, SR_ERR_OOM, "cudaMalloc of work buffers failed"));
   cudaMemsetAsync(h->P64, 0, panel_elems * sizeof(double), h->st);
   if (h->P32) cudaMemsetAsync(h->P32, 0, panel_elems * sizeof(float), h->st);
   cudaMemsetAsync(h->mXi, 0, h->nT_cap * sizeof(uint64_t), h->st);
   cudaMemsetAsync(h->mEta, 0, h->nT_cap * sizeof(uint64_t), h->st);
   cudaMemsetAsync(h->counters, 0, CNT_N * sizeof(int64_t), h->st);
+  cudaMemsetAsync(h->gbar, 0, 2 * sizeof(unsigned int), h->st);
   cudaMemsetAsync(h->S, 0, s_bytes, h->st);
 
   if (h->column) {
@@ -1435,6 +1455,188 @@ simrank_status simrank_reanchor(simrank_t h, int32_t sweeps, double* max_change)
   h->stats.init_residual = diff;
   h->stats.init_sweeps = done;
   if (max_change) *max_change = diff;
+  return SR_OK;
+}
+
+simrank_status simrank_grad(simrank_t h, const int32_t* pa, const int32_t* pb, const double* target,
+                            int64_t npairs, double* loss, double* grad_weight) {
+  if (!h) return fail(nullptr, SR_ERR_ARG, "null handle");
+  if (npairs < 0 || (npairs > 0 && (!pa || !pb || !target)) || !loss || !grad_weight)
+    return fail(h, SR_ERR_ARG, "bad pair arrays");
+  if (h->stats.updates > 0)
+    return fail(h, SR_ERR_UNSUPPORTED, "simrank_grad needs the graph as initialised (no updates)");
+  const int n_pad = h->n_pad, K = h->cfg.K;
+  const double C = h->cfg.C;
+  for (int64_t p = 0; p < npairs; ++p)
+    if (pa[p] < 0 || pb[p] < 0 || pa[p] >= h->n_cur || pb[p] >= h->n_cur)
+      return fail(h, SR_ERR_ARG, "pair id out of range");
+  simrank_status s;
+  std::vector<RowChunk> ch;
+  build_chunks(h->hout, n_pad, ch);
+  if ((s = upload_chunks(h, ch, h->cur_fwd, &h->cur_fwd_cap)) != SR_OK) return s;
+  build_chunks(h->hin, n_pad, ch);
+  if ((s = upload_chunks(h, ch, h->cur_hor, &h->cur_hor_cap)) != SR_OK) return s;
+  WeightView wv;
+  if (h->weighted) {
+    wv.in_w = h->d_in_w;
+    wv.out_w = h->d_out_w;
+    wv.wsum = h->d_wsum;
+  }
+  std::vector<int32_t> A(npairs), Bv(npairs);
+  for (int64_t p = 0; p < npairs; ++p) {
+    A[p] = h->ext2int[pa[p]];
+    Bv[p] = h->ext2int[pb[p]];
+  }
+  // endpoint block size from free memory: F and F_psi (K+1 blocks each), 2 y blocks
+  size_t free_b = 0, total_b = 0;
+  CUDA_TRY(h, cudaMemGetInfo(&free_b, &total_b));
+  const size_t per_col = (size_t)n_pad * 8 * (2 * (K + 1) + 2);
+  const int Eb = (int)std::max<size_t>(1, std::min<size_t>(1024, (size_t)(0.5 * free_b) / per_col));
+  const size_t blkb = (size_t)n_pad * Eb * 8;
+  if ((s = ob_ensure(h, 14, blkb * (K + 1))) != SR_OK) return s;
+  if ((s = ob_ensure(h, 15, blkb * (K + 1))) != SR_OK) return s;
+  if ((s = ob_ensure(h, 16, blkb)) != SR_OK) return s;
+  if ((s = ob_ensure(h, 17, blkb)) != SR_OK) return s;
+  const int64_t pool = h->din.pool_cap;
+  if ((s = ob_ensure(h, 18, (size_t)pool * 8 * 2)) != SR_OK) return s;
+  double* F = (double*)h->ob[14].p;
+  double* Fp = (double*)h->ob[15].p;
+  double* y0 = (double*)h->ob[16].p;
+  double* y1 = (double*)h->ob[17].p;
+  double* G = (double*)h->ob[18].p;
+  double* dW = G + pool;
+  auto upload_i32 = [&](int slot, const std::vector<int32_t>& v) -> simrank_status {
+    simrank_status r = ob_ensure(h, slot, std::max<size_t>(v.size(), 1) * 4);
+    if (r != SR_OK) return r;
+    if (!v.empty())
+      CUDA_TRY(h, cudaMemcpyAsync(h->ob[slot].p, v.data(), v.size() * 4, cudaMemcpyHostToDevice, h->st));
+    return SR_OK;
+  };
+  auto upload_f64 = [&](int slot, const std::vector<double>& v) -> simrank_status {
+    simrank_status r = ob_ensure(h, slot, std::max<size_t>(v.size(), 1) * 8);
+    if (r != SR_OK) return r;
+    if (!v.empty())
+      CUDA_TRY(h, cudaMemcpyAsync(h->ob[slot].p, v.data(), v.size() * 8, cudaMemcpyHostToDevice, h->st));
+    return SR_OK;
+  };
+
+  // ---- pass 1: S_K[a_p, b_p] from Procedure 1 on the distinct b's
+  std::vector<int32_t> bcols(Bv);
+  std::sort(bcols.begin(), bcols.end());
+  bcols.erase(std::unique(bcols.begin(), bcols.end()), bcols.end());
+  std::vector<double> sval(npairs, 0.0);
+  for (size_t c0 = 0; c0 < bcols.size(); c0 += Eb) {
+    const int B = (int)std::min<size_t>(Eb, bcols.size() - c0);
+    std::vector<int32_t> cols(bcols.begin() + c0, bcols.begin() + c0 + B);
+    std::vector<int32_t> rows, cidx;
+    std::vector<int64_t> who;
+    for (int64_t p = 0; p < npairs; ++p) {
+      auto it = std::lower_bound(cols.begin(), cols.end(), Bv[p]);
+      if (it != cols.end() && *it == Bv[p]) {
+        rows.push_back(A[p]);
+        cidx.push_back((int32_t)(it - cols.begin()));
+        who.push_back(p);
+      }
+    }
+    if ((s = upload_i32(19, cols)) != SR_OK) return s;
+    if ((s = upload_i32(20, rows)) != SR_OK) return s;
+    if ((s = upload_i32(21, cidx)) != SR_OK) return s;
+    if ((s = ob_ensure(h, 22, std::max<size_t>(rows.size(), 1) * 8)) != SR_OK) return s;
+    launch_partial_sim_block(h->cur_fwd, h->cur_hor, h->dout.col, h->din.col, h->din.len,
+                             (const int32_t*)h->ob[19].p, B, n_pad, K, C, 64, F, y0, y1, Fp, h->st,
+                             wv);
+    launch_adj_pairs(Fp, B, (const int32_t*)h->ob[20].p, (const int32_t*)h->ob[21].p,
+                     (int64_t)rows.size(), (double*)h->ob[22].p, h->st);
+    std::vector<double> got(rows.size());
+    if (!rows.empty())
+      CUDA_TRY(h, cudaMemcpyAsync(got.data(), h->ob[22].p, rows.size() * 8, cudaMemcpyDeviceToHost,
+                                  h->st));
+    CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    for (size_t q = 0; q < who.size(); ++q) sval[who[q]] = got[q];
+  }
+  double L = 0.0;
+  std::vector<double> g(npairs);
+  for (int64_t p = 0; p < npairs; ++p) {
+    const double r = sval[p] - target[p];
+    L += r * r;
+    g[p] = 2.0 * r;
+  }
+  *loss = L;
+
+  // ---- pass 2: dL/dQ at the edges, per block of endpoints
+  std::vector<int32_t> ends(A);
+  ends.insert(ends.end(), Bv.begin(), Bv.end());
+  std::sort(ends.begin(), ends.end());
+  ends.erase(std::unique(ends.begin(), ends.end()), ends.end());
+  std::vector<std::vector<std::pair<int32_t, double>>> psi(ends.size());
+  for (int64_t p = 0; p < npairs; ++p) {
+    const size_t ia = std::lower_bound(ends.begin(), ends.end(), A[p]) - ends.begin();
+    const size_t ib = std::lower_bound(ends.begin(), ends.end(), Bv[p]) - ends.begin();
+    psi[ia].push_back({Bv[p], g[p]});
+    psi[ib].push_back({A[p], g[p]});
+  }
+  CUDA_TRY(h, cudaMemsetAsync(G, 0, (size_t)pool * 8, h->st));
+  for (size_t c0 = 0; c0 < ends.size(); c0 += Eb) {
+    const int B = (int)std::min<size_t>(Eb, ends.size() - c0);
+    std::vector<int32_t> un, uc, pn, pc;
+    std::vector<double> ucoef, pcoef;
+    for (int c = 0; c < B; ++c) {
+      un.push_back(ends[c0 + c]);
+      uc.push_back(c);
+      ucoef.push_back(1.0);
+      for (auto& nv : psi[c0 + c]) {
+        pn.push_back(nv.first);
+        pc.push_back(c);
+        pcoef.push_back(nv.second);
+      }
+    }
+    if ((s = upload_i32(19, un)) != SR_OK) return s;
+    if ((s = upload_i32(20, uc)) != SR_OK) return s;
+    if ((s = upload_f64(22, ucoef)) != SR_OK) return s;
+    if ((s = upload_i32(21, pn)) != SR_OK) return s;
+    if ((s = upload_i32(23, pc)) != SR_OK) return s;
+    std::vector<double>* keep = &pcoef;
+    if ((s = ob_ensure(h, 13, std::max<size_t>(keep->size(), 1) * 8)) != SR_OK) return s;
+    if (!keep->empty())
+      CUDA_TRY(h, cudaMemcpyAsync(h->ob[13].p, keep->data(), keep->size() * 8,
+                                  cudaMemcpyHostToDevice, h->st));
+    const int64_t blk = (int64_t)n_pad * B;
+    CUDA_TRY(h, cudaMemsetAsync(F, 0, (size_t)blk * 8, h->st));
+    CUDA_TRY(h, cudaMemsetAsync(Fp, 0, (size_t)blk * 8, h->st));
+    launch_adj_scatter((const int32_t*)h->ob[19].p, (const int32_t*)h->ob[20].p,
+                       (const double*)h->ob[22].p, B, B, F, h->st);
+    launch_adj_scatter((const int32_t*)h->ob[21].p, (const int32_t*)h->ob[23].p,
+                       (const double*)h->ob[13].p, (int64_t)pn.size(), B, Fp, h->st);
+    for (int l = 1; l <= K; ++l) {
+      launch_col_forward64(h->cur_fwd, h->dout.col, wv, h->din.len, F + (l - 1) * blk, F + l * blk,
+                           B, n_pad, h->st);
+      launch_col_forward64(h->cur_fwd, h->dout.col, wv, h->din.len, Fp + (l - 1) * blk,
+                           Fp + l * blk, B, n_pad, h->st);
+    }
+    CUDA_TRY(h, cudaMemsetAsync(y0, 0, (size_t)blk * 8, h->st));
+    double* y = y0;
+    double* yn = y1;
+    for (int l = K - 1; l >= 0; --l) {
+      launch_col_horner64(h->cur_hor, h->din.col, wv, h->din.len, Fp + (l + 1) * blk,
+                          std::pow(C, l + 1), y, yn, B, n_pad, 1.0, h->st);
+      launch_adj_sddmm(h->cur_hor, h->din.col, F + l * blk, yn, B, 1.0 - C, G, h->st);
+      std::swap(y, yn);
+    }
+    LAUNCH_CHECK(h);
+    // the host vectors above must outlive their copies
+    CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  }
+  launch_adj_weights(h->din, wv, n_pad, G, dW, h->st);
+  LAUNCH_CHECK(h);
+  std::vector<double> dwh((size_t)pool);
+  CUDA_TRY(h, cudaMemcpyAsync(dwh.data(), dW, (size_t)pool * 8, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  // map the caller's edge order to pool positions (rows are as initialised)
+  std::vector<int32_t> cnt(n_pad, 0);
+  for (size_t e = 0; e < h->init_src.size(); ++e) {
+    const int32_t d = h->init_dst[e];
+    grad_weight[e] = dwh[(size_t)(h->hin.start[d] + cnt[d]++)];
+  }
   return SR_OK;
 }
 

@@ -36,8 +36,11 @@ __global__ void k_col_fill(const T* __restrict__ X, double s, T* __restrict__ Y,
 // Long rows are split over many chunks, whose partial sums meet in atomics.
 template <typename T, bool FORWARD>
 __global__ void k_col_chunk(const RowChunk* __restrict__ chunks, const int32_t* __restrict__ col,
-                            const int32_t* __restrict__ in_len, const T* __restrict__ X,
+                            const float* __restrict__ ew, const int32_t* __restrict__ in_len,
+                            const double* __restrict__ wsum, const T* __restrict__ X,
                             T* __restrict__ Y, int B, double scale) {
+  // weighted Q (wsum != null): Q[a][b] = w(b -> a) / wsum[a]; ew = weight of each
+  // adjacency entry (by pool position), null = 1
   const RowChunk ch = chunks[blockIdx.x];
   const int c = blockIdx.y * blockDim.x + threadIdx.x;
   if (c >= B) return;
@@ -45,10 +48,12 @@ __global__ void k_col_chunk(const RowChunk* __restrict__ chunks, const int32_t* 
 #pragma unroll 8
   for (int e = 0; e < ch.len; ++e) {
     const int a = col[ch.start + e];
-    const double x = (double)X[(int64_t)a * B + c];
-    acc += FORWARD ? x / (double)in_len[a] : x;
+    double x = (double)X[(int64_t)a * B + c];
+    if (ew) x *= (double)ew[ch.start + e];
+    if (FORWARD) x /= wsum ? wsum[a] : (double)in_len[a];
+    acc += x;
   }
-  const double rs = FORWARD ? 1.0 : scale / (double)in_len[ch.row];
+  const double rs = FORWARD ? 1.0 : scale / (wsum ? wsum[ch.row] : (double)in_len[ch.row]);
   atomicAdd(&Y[(int64_t)ch.row * B + c], (T)(rs * acc));
 }
 
@@ -121,9 +126,9 @@ __global__ void k_col_extract(const T* __restrict__ Y, int B, int c, int n, doub
 
 template <typename T>
 static void partial_sim_block_t(const ChunkList& fwd, const ChunkList& hor, const int32_t* out_col,
-                                const int32_t* in_col, const int32_t* in_len, const int32_t* cols,
-                                int B, int n_rows, int K, double C, T* xs, T* y0, T* y1, T* result,
-                                cudaStream_t st) {
+                                const int32_t* in_col, const WeightView& wv, const int32_t* in_len,
+                                const int32_t* cols, int B, int n_rows, int K, double C, T* xs, T* y0,
+                                T* y1, T* result, cudaStream_t st) {
   const int64_t blk = (int64_t)n_rows * B;
   const int fill_blocks = 4096;
   k_col_fill<T><<<fill_blocks, 256, 0, st>>>(nullptr, 0.0, xs, blk);
@@ -135,7 +140,7 @@ static void partial_sim_block_t(const ChunkList& fwd, const ChunkList& hor, cons
     k_col_fill<T><<<fill_blocks, 256, 0, st>>>(nullptr, 0.0, dst, blk);
     if (fwd.count > 0)
       k_col_chunk<T, true><<<dim3((unsigned)fwd.count, ygroups), tpb, 0, st>>>(
-          fwd.chunks, out_col, in_len, xs + (int64_t)(t - 1) * blk, dst, B, 1.0);
+          fwd.chunks, out_col, wv.out_w, in_len, wv.wsum, xs + (int64_t)(t - 1) * blk, dst, B, 1.0);
   }
   // Horner: y = x_K; y <- x_{K-t} + C Q y; result (1-C) y (the last step folds the scale)
   const T* y = xs + (int64_t)K * blk;
@@ -150,7 +155,7 @@ static void partial_sim_block_t(const ChunkList& fwd, const ChunkList& hor, cons
     k_col_fill<T><<<fill_blocks, 256, 0, st>>>(xs + (int64_t)(K - t) * blk, s, dst, blk);
     if (hor.count > 0)
       k_col_chunk<T, false><<<dim3((unsigned)hor.count, ygroups), tpb, 0, st>>>(
-          hor.chunks, in_col, in_len, y, dst, B, s * C);
+          hor.chunks, in_col, wv.in_w, in_len, wv.wsum, y, dst, B, s * C);
     y = dst;
   }
 }
@@ -158,13 +163,38 @@ static void partial_sim_block_t(const ChunkList& fwd, const ChunkList& hor, cons
 void launch_partial_sim_block(const ChunkList& fwd, const ChunkList& hor, const int32_t* out_col,
                               const int32_t* in_col, const int32_t* in_len, const int32_t* cols,
                               int B, int n_rows, int K, double C, int prec, void* xs, void* y0,
-                              void* y1, void* result, cudaStream_t st) {
+                              void* y1, void* result, cudaStream_t st, const WeightView& wv) {
   if (prec == 64)
-    partial_sim_block_t<double>(fwd, hor, out_col, in_col, in_len, cols, B, n_rows, K, C,
+    partial_sim_block_t<double>(fwd, hor, out_col, in_col, wv, in_len, cols, B, n_rows, K, C,
                                 (double*)xs, (double*)y0, (double*)y1, (double*)result, st);
   else
-    partial_sim_block_t<float>(fwd, hor, out_col, in_col, in_len, cols, B, n_rows, K, C,
+    partial_sim_block_t<float>(fwd, hor, out_col, in_col, wv, in_len, cols, B, n_rows, K, C,
                                (float*)xs, (float*)y0, (float*)y1, (float*)result, st);
+}
+
+// Y = Q^T X (FP64 blocks [n_rows][B])
+void launch_col_forward64(const ChunkList& fwd, const int32_t* out_col, const WeightView& wv,
+                          const int32_t* in_len, const double* X, double* Y, int B, int n_rows,
+                          cudaStream_t st) {
+  const int64_t blk = (int64_t)n_rows * B;
+  k_col_fill<double><<<4096, 256, 0, st>>>(nullptr, 0.0, Y, blk);
+  const int tpb = B >= 128 ? 128 : (B + 31) / 32 * 32;
+  if (fwd.count > 0)
+    k_col_chunk<double, true><<<dim3((unsigned)fwd.count, (B + 127) / 128), tpb, 0, st>>>(
+        fwd.chunks, out_col, wv.out_w, in_len, wv.wsum, X, Y, B, 1.0);
+}
+
+// Yn = add_scale * Xadd + scale * Q Y (FP64 blocks [n_rows][B])
+void launch_col_horner64(const ChunkList& hor, const int32_t* in_col, const WeightView& wv,
+                         const int32_t* in_len, const double* Xadd, double add_scale,
+                         const double* Y, double* Yn, int B, int n_rows, double scale,
+                         cudaStream_t st) {
+  const int64_t blk = (int64_t)n_rows * B;
+  k_col_fill<double><<<4096, 256, 0, st>>>(Xadd, add_scale, Yn, blk);
+  const int tpb = B >= 128 ? 128 : (B + 31) / 32 * 32;
+  if (hor.count > 0)
+    k_col_chunk<double, false><<<dim3((unsigned)hor.count, (B + 127) / 128), tpb, 0, st>>>(
+        hor.chunks, in_col, wv.in_w, in_len, wv.wsum, Y, Yn, B, scale);
 }
 
 void launch_col_apply(const void* P, int p_prec, int K1, const int32_t* cols, int B, int n_rows,

@@ -7,11 +7,14 @@
 //   D = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T,  accumulated in FP32 (TMEM).
 //
 // One CTA per SM, persistent over the tile-pair list.  Warp 0 issues TMA loads
-// (128 x 32 FP32 boxes, 128-byte swizzle) into a 3-stage ring; warp 1 owns the
-// TMEM accumulator (128 lanes x 128 columns) and issues tcgen05.mma (M = 128,
-// N = 128, K = 8); warps 2-5 read the accumulator with tcgen05.ld and update S
-// in HBM.  Every mbarrier wait is bounded: on timeout the kernel records a
-// status word, skips the remaining work and still frees its TMEM.
+// (128 x 32 FP32 boxes, 128-byte swizzle) into a 2-stage ring; warp 1 owns two
+// TMEM accumulators (128 lanes x 128 columns each) and issues tcgen05.mma
+// (M = 128, N = 128, K = 8) for tile t + 1 while warps 2-9 drain tile t: they
+// copy the accumulator (tcgen05.ld) into a padded shared tile and stream
+// S[I,J] and S[J,I] from it with coalesced 16-byte accesses.  Every mbarrier
+// wait is bounded and every stop decision of the epilogue warps is taken by
+// all of them: on timeout the kernel records a status word, skips the
+// remaining work and still frees its TMEM.
 #include <cuda.h>
 
 #include "sr_internal.h"
@@ -23,11 +26,12 @@ namespace {
 constexpr int TM = 128;            // rows of an S tile (M)
 constexpr int TN = 128;            // columns of an S tile (N)
 constexpr int KCH = 32;            // FP32 elements of K per stage (one 128-byte swizzle row)
-constexpr int STAGES = 3;
+constexpr int STAGES = 2;
 constexpr int OPB = TM * KCH * 4;  // bytes of one operand box: 16 KB
 constexpr int STAGE_BYTES = 4 * OPB;
-constexpr int TC_THREADS = 192;
-constexpr uint32_t TMEM_COLS = 128;
+constexpr int TC_THREADS = 320;       // 10 warps: TMA, MMA, 8 epilogue
+constexpr uint32_t TMEM_COLS = 256;   // two 128-column accumulators
+constexpr int EP = TN + 1;            // row pitch of the shared accumulator copy
 
 // tcgen05 instruction descriptor, kind::tf32: D = F32, A = B = TF32, both
 // K-major, N = 128, M = 128.
@@ -121,6 +125,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+// true on all 256 epilogue threads iff pred is true on all of them (barrier 1)
+__device__ __forceinline__ bool ep_all(bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, 256, p;\n"
+      " selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)pred)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void ep_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_s_update_tc(const __grid_constant__ CUtensorMap tm_hi,
                   const __grid_constant__ CUtensorMap tm_lo, float* __restrict__ S, int64_t ld,
@@ -128,12 +145,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                   long long wait_limit, int n, unsigned long long* __restrict__ counters) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES];
-  __shared__ __align__(8) uint64_t bar_acc_full, bar_acc_empty;
+  __shared__ __align__(8) uint64_t bar_acc_full[2], bar_acc_empty[2];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  float* sD = reinterpret_cast<float*>(smem_raw + (base - smem_u32(smem_raw)) +
+                                       (size_t)STAGES * STAGE_BYTES);
   const int nt = *ntiles;
   const int half = nkb / 2;  // B row = A row with its halves swapped
 
@@ -143,8 +162,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mbar_init(smem_u32(&bar_full[s]), 1);
       mbar_init(smem_u32(&bar_empty[s]), 1);
     }
-    mbar_init(smem_u32(&bar_acc_full), 1);
-    mbar_init(smem_u32(&bar_acc_empty), 128);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&bar_acc_full[b]), 1);
+      mbar_init(smem_u32(&bar_acc_empty[b]), 256);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -186,15 +207,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (!ok) abort_flag = 1;
     }
   } else if (warp == 1) {
-    // ---------------- MMA issuer
+    // ---------------- MMA issuer: tile tl accumulates in TMEM columns (tl & 1) * 128
     if (lane == 0) {
       uint32_t it = 0, tl = 0;
       for (int t = blockIdx.x; t < nt && ok; t += gridDim.x, ++tl) {
-        if (!mbar_wait(smem_u32(&bar_acc_empty), (tl & 1u) ^ 1u, wait_limit, &abort_flag)) {
+        const uint32_t b = tl & 1u;
+        if (!mbar_wait(smem_u32(&bar_acc_empty[b]), ((tl >> 1) & 1u) ^ 1u, wait_limit,
+                       &abort_flag)) {
           ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc = tmem + b * (uint32_t)TN;
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int s = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1u;
@@ -210,64 +234,94 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           for (int kk = 0; kk < KCH / 8; ++kk) {
             const uint64_t adv = (uint64_t)(kk * 32) >> 4;  // 8 TF32 = 32 bytes along K
             const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
-            mma_tf32(tmem, a_hi + adv, b_hi + adv, first);
-            mma_tf32(tmem, a_hi + adv, b_lo + adv, 1u);
-            mma_tf32(tmem, a_lo + adv, b_hi + adv, 1u);
+            mma_tf32(acc, a_hi + adv, b_hi + adv, first);
+            mma_tf32(acc, a_hi + adv, b_lo + adv, 1u);
+            mma_tf32(acc, a_lo + adv, b_hi + adv, 1u);
           }
           mma_commit(smem_u32(&bar_empty[s]));  // stage reusable once these MMAs finish
         }
         if (!ok) break;
-        mma_commit(smem_u32(&bar_acc_full));
+        mma_commit(smem_u32(&bar_acc_full[b]));
       }
       if (!ok) abort_flag = 1;
     }
   } else {
-    // ---------------- epilogue: warps 2..5, TMEM lanes 32 * (warp % 4) ..
-    const int quarter = warp & 3;
-    const int row = quarter * 32 + lane;
+    // ---------------- epilogue: warps 2..9 (256 threads)
+    const int et = threadIdx.x - 64;     // 0..255
+    const int ew = et >> 5;              // epilogue warp 0..7
+    const int quarter = warp & 3;        // TMEM lanes this warp may read
+    const int chalf = (ew >> 2) * 64;    // columns [chalf, chalf + 64) of the accumulator
     uint32_t tl = 0;
     unsigned long long my_tiles = 0, my_bytes = 0;
     for (int t = blockIdx.x; t < nt; t += gridDim.x, ++tl) {
-      if (!mbar_wait(smem_u32(&bar_acc_full), tl & 1u, wait_limit, &abort_flag)) {
+      const uint32_t b = tl & 1u;
+      const bool got = mbar_wait(smem_u32(&bar_acc_full[b]), (tl >> 1) & 1u, wait_limit, &abort_flag);
+      if (!ep_all(got)) {
         ok = false;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t pr = tiles[t];
       const int I = (int)(pr >> 16), J = (int)(pr & 0xffffu);
-      float* srow = S + (int64_t)(I * TM + row) * ld + (int64_t)J * TN;
+      // accumulator -> shared tile (row = TMEM lane)
+      const int row = quarter * 32 + lane;
 #pragma unroll 1
-      for (int c0 = 0; c0 < TN; c0 += 32) {
+      for (int c0 = chalf; c0 < chalf + 64; c0 += 32) {
         float v[32];
-        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
+        tmem_ld32(tmem + b * (uint32_t)TN + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
 #pragma unroll
-        for (int q = 0; q < 32; q += 4) {
-          float4 x = *reinterpret_cast<float4*>(srow + c0 + q);
-          x.x += v[q];
-          x.y += v[q + 1];
-          x.z += v[q + 2];
-          x.w += v[q + 3];
-          *reinterpret_cast<float4*>(srow + c0 + q) = x;
-        }
-        if (I != J) {
-          // S[J*128 + c][I*128 + row]: the warp's 32 lanes cover 128 contiguous bytes
-#pragma unroll
-          for (int q = 0; q < 32; ++q) {
-            float* p = S + (int64_t)(J * TN + c0 + q) * ld + (int64_t)I * TM + row;
-            *p += v[q];
-          }
-        }
+        for (int q = 0; q < 32; ++q) sD[row * EP + c0 + q] = v[q];
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      mbar_arrive(smem_u32(&bar_acc_empty));
-      if (threadIdx.x == 64) {
+      mbar_arrive(smem_u32(&bar_acc_empty[b]));  // the MMA warp may refill this accumulator
+      ep_sync();
+      // S[I, J] += D: a warp covers one 512-byte row segment per access
+      constexpr int NQ = TM / 8;
+      {
+        float4 v[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const int r = ew + 8 * q;
+          v[q] = *reinterpret_cast<const float4*>(S + (int64_t)(I * TM + r) * ld + (int64_t)J * TN + lane * 4);
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const int r = ew + 8 * q;
+          const float* d = sD + r * EP + lane * 4;
+          v[q].x += d[0];
+          v[q].y += d[1];
+          v[q].z += d[2];
+          v[q].w += d[3];
+          *reinterpret_cast<float4*>(S + (int64_t)(I * TM + r) * ld + (int64_t)J * TN + lane * 4) = v[q];
+        }
+      }
+      if (I != J) {
+        // S[J, I] += D^T
+        float4 v[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const int c = ew + 8 * q;
+          v[q] = *reinterpret_cast<const float4*>(S + (int64_t)(J * TN + c) * ld + (int64_t)I * TM + lane * 4);
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const int c = ew + 8 * q;
+          v[q].x += sD[(lane * 4 + 0) * EP + c];
+          v[q].y += sD[(lane * 4 + 1) * EP + c];
+          v[q].z += sD[(lane * 4 + 2) * EP + c];
+          v[q].w += sD[(lane * 4 + 3) * EP + c];
+          *reinterpret_cast<float4*>(S + (int64_t)(J * TN + c) * ld + (int64_t)I * TM + lane * 4) = v[q];
+        }
+      }
+      ep_sync();  // the shared tile is free for the next accumulator
+      if (et == 0) {
         const long long vr = max(0, min(TM, n - I * TM)), vc = max(0, min(TN, n - J * TN));
         my_tiles += 1;
         my_bytes += (unsigned long long)(vr * vc) * 8ull * (I == J ? 1ull : 2ull);
       }
     }
     if (!ok) abort_flag = 1;
-    if (threadIdx.x == 64 && my_tiles) {
+    if (et == 0 && my_tiles) {
       atomicAdd(&counters[CNT_TILES_TOUCHED], my_tiles);
       atomicAdd(&counters[CNT_S_BYTES], my_bytes);
     }
@@ -323,7 +377,7 @@ int launch_s_update_tc(float* S, int64_t ld, const float* Ahi, const float* Alo,
   CUtensorMap mhi, mlo;
   if (!make_map(&mhi, const_cast<float*>(Ahi), n_rows, kd)) return 2;
   if (!make_map(&mlo, const_cast<float*>(Alo), n_rows, kd)) return 2;
-  const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024;
+  const size_t smem = (size_t)STAGES * STAGE_BYTES + (size_t)TM * EP * 4 + 1024;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_s_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -109,6 +109,12 @@ void launch_patch(const PatchOp* ops, int64_t begin, int64_t end, DevAdj in, Dev
 void launch_chain_step(const DevAdj& in, int k, double C, int nT, int K1, double* P64, float* P32,
                        uint64_t* mXi, uint64_t* mEta, cudaStream_t st);
 
+// All K steps of the recurrence in one cooperative launch with a bounded grid
+// barrier (bar: two zeroed unsigned ints owned by the handle).
+cudaError_t launch_chain_all(const DevAdj& in, int K, double C, int nT, int K1, double* P64,
+                             float* P32, uint64_t* mXi, uint64_t* mEta, unsigned int* bar,
+                             long long limit, int64_t* counters, cudaStream_t st);
+
 // Affected tile pairs (I <= J) of Thm 4 at tile granularity.
 void launch_tile_list(const uint64_t* mXi, const uint64_t* mEta, int nT, int aff, uint32_t* tiles,
                       int* ntiles, cudaStream_t st);
@@ -185,6 +191,14 @@ struct ChunkList {
   RowChunk* chunks = nullptr;  // device
   int64_t count = 0;
 };
+// Edge weights of a weighted Q (all null: Q[a][b] = 1 / in-degree(a)):
+// out_w / in_w give the weight of each out-list / in-list entry by pool
+// position, wsum[a] the total in-weight of a.
+struct WeightView {
+  const float* out_w = nullptr;
+  const float* in_w = nullptr;
+  const double* wsum = nullptr;
+};
 // Procedure 1 on B columns `cols` (device) of the graph whose out-lists
 // (fwd chunks over out_col) and in-lists (hor chunks over in_col) are given;
 // in_len = in-degrees.  xs holds (K+1) row-major [n_rows][B] blocks, y0 / y1
@@ -192,7 +206,15 @@ struct ChunkList {
 void launch_partial_sim_block(const ChunkList& fwd, const ChunkList& hor, const int32_t* out_col,
                               const int32_t* in_col, const int32_t* in_len, const int32_t* cols,
                               int B, int n_rows, int K, double C, int prec, void* xs, void* y0,
-                              void* y1, void* result, cudaStream_t st);
+                              void* y1, void* result, cudaStream_t st,
+                              const WeightView& wv = WeightView());
+void launch_col_forward64(const ChunkList& fwd, const int32_t* out_col, const WeightView& wv,
+                          const int32_t* in_len, const double* X, double* Y, int B, int n_rows,
+                          cudaStream_t st);
+void launch_col_horner64(const ChunkList& hor, const int32_t* in_col, const WeightView& wv,
+                         const int32_t* in_len, const double* Xadd, double add_scale,
+                         const double* Y, double* Yn, int B, int n_rows, double scale,
+                         cudaStream_t st);
 // Y[a][c] += sum_k xi_k[a] eta_k[cols[c]] + eta_k[a] xi_k[cols[c]] (panels P, FP32/64)
 void launch_col_apply(const void* P, int p_prec, int K1, const int32_t* cols, int B, int n_rows,
                       int prec, void* Y, cudaStream_t st);
@@ -201,5 +223,20 @@ void launch_col_scalars(const DevAdj& in, const double* si, const double* sj, in
                         double* scal, cudaStream_t st);
 void launch_col_out(const void* Y, int prec, int B, int n, void* out, int out_fp64, cudaStream_t st);
 void launch_col_extract(const void* Y, int prec, int B, int c, int n, double* v, cudaStream_t st);
+
+// ---- adjoint (k_adjoint.cu)
+// G[e] += scale * sum_{x < B} F[u][x] Y[v][x] for every in-list entry e (row u,
+// in-neighbour v = col[e]) covered by the chunks
+void launch_adj_sddmm(const ChunkList& hor, const int32_t* in_col, const double* F, const double* Y,
+                      int B, double scale, double* G, cudaStream_t st);
+// X[node[t]][c[t]] += coef[t] for t < count (X zeroed before)
+void launch_adj_scatter(const int32_t* node, const int32_t* c, const double* coef, int64_t count,
+                        int B, double* X, cudaStream_t st);
+// out[t] = Y[row[t]][c[t]]
+void launch_adj_pairs(const double* Y, int B, const int32_t* row, const int32_t* c, int64_t count,
+                      double* out, cudaStream_t st);
+// chain rule Q[a][b] = w_ba / wsum_a: dW[e] = (G[e] - sum_{e' in row a} G[e'] Q[e']) / wsum_a
+void launch_adj_weights(const DevAdj& in, const WeightView& wv, int n_rows, const double* G,
+                        double* dW, cudaStream_t st);
 
 }  // namespace sr
