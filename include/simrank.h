@@ -73,7 +73,9 @@ enum { SR_SUPDATE_FUSED = 0,     /* one read-modify-write pass of S per update: 
 typedef struct simrank_config {
   double C;               /* damping factor, 0 < C < 1 (Eq. 1) */
   int32_t K;              /* iterations of the xi/eta recurrence (Eq. 16a); terms k = 0..K; 0 <= K <= 1023 */
-  int32_t s_precision;    /* 32: S stored in FP32; 64: S stored in FP64.  Vectors are FP64 in both. */
+  int32_t s_precision;    /* 32: S stored in FP32; 64: S stored in FP64.  With chain = 0 the
+                             xi/eta vectors and gamma are computed in the same precision
+                             (lambda and row j of gamma in FP64); with chain = 1 in FP64. */
   int32_t mode;           /* SR_MODE_DENSE or SR_MODE_COLUMN */
   int32_t n_capacity;     /* maximum number of nodes, including nodes added later; >= n at init */
   int32_t aff;            /* 1: skip S tiles outside the affected area of Thm 4; 0: touch every tile */
@@ -93,10 +95,17 @@ typedef struct simrank_config {
                              each rank-one update to S at once; G > 1 = keep up to G updates'
                              panels pending (the rows of S an update reads are corrected by them)
                              and apply them in one rank-2G(K+1) pass (tensor cores when tc = 1).
-                             Pending updates are always applied before apply_updates returns. */
-  int32_t chain;          /* xi/eta recurrence of a rank-one update: 0 = all K steps in one
-                             cooperative launch (bounded grid barrier), 1 = one launch per step */
-  int32_t reserved[5];
+                             Pending updates are always applied before apply_updates returns.
+                             G * (K + 1) <= 4096, else SR_ERR_ARG. */
+  int32_t chain;          /* work of a rank-one update before its S pass: 0 = one cooperative
+                             launch (graph patch, rows of S, gamma, all K recurrence steps, masks,
+                             tile list; bounded grid barriers), 1 = one launch per step with
+                             FP64 vectors.  Graphs with more than 8 tiles of 128 nodes per
+                             co-resident CTA take the per-step path. */
+  int32_t prep_ctas;      /* chain = 0: cap on the CTAs of the fused launch (0 = as many as fit) */
+  int32_t prep_cache;     /* chain = 0: column indices cached in shared memory per CTA, a
+                             multiple of 4 in [0, 16384] (0 = 8192); the rest are read from L2 */
+  int32_t reserved[3];
 } simrank_config;
 
 /* Fills *cfg with defaults: C = 0.6, K = 15, s_precision = 32, dense, aff = 1,
@@ -158,8 +167,10 @@ typedef struct simrank_stats {
   double s_update_ms;       /* summed CUDA-event time of S-update launches (profile = 1 only) */
   double init_residual;     /* max-abs change of the last Jacobi sweep at init / re-anchor */
   double phase_ms[4];       /* profile = 1 only: CUDA-event time of the phases of rank-one updates:
-                               [0] old-S rows + gamma, [1] graph patch + xi/eta recurrence,
-                               [2] affected tile list, [3] S update */
+                               [0] old-S rows + gamma (chain = 0: the whole fused launch before
+                               the S pass), [1] graph patch + xi/eta recurrence (chain = 1),
+                               [2] affected tile list (chain = 1) and deferred S passes,
+                               [3] per-update S pass */
   int32_t init_sweeps;
   int32_t reserved[7];
 } simrank_stats;

@@ -40,7 +40,8 @@ class Config(ctypes.Structure):
         ("profile", ctypes.c_int32), ("relabel", ctypes.c_int32),
         ("timeout_iters", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
         ("s_kernel", ctypes.c_int32), ("defer", ctypes.c_int32), ("chain", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 5),
+        ("prep_ctas", ctypes.c_int32), ("prep_cache", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
 

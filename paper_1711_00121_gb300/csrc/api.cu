@@ -419,6 +419,16 @@ bool deferring(const simrank_ctx* h) {
 simrank_status flush_pending(simrank_ctx* h) {
   if (h->np == 0) return SR_OK;
   const int nT = (h->n_cur + PT - 1) / PT;
+  cudaEvent_t* pe = nullptr;
+  if (h->cfg.profile) {
+    if (h->phase_used >= 2048) {
+      CUDA_TRY(h, cudaStreamSynchronize(h->st));
+      harvest_events(h);
+    }
+    pe = next_phase_events(h);
+    if (!pe) return fail(h, SR_ERR_CUDA, "cudaEventCreate failed");
+    for (int q = 0; q < 3; ++q) CUDA_TRY(h, cudaEventRecord(pe[q], h->st));
+  }
   const int GK1 = h->cfg.defer * h->K1;
   const int nterms = h->np * h->K1;
   CUDA_TRY(h, cudaMemsetAsync(h->ntiles, 0, sizeof(int), h->st));
@@ -457,6 +467,10 @@ simrank_status flush_pending(simrank_ctx* h) {
   h->stats.tiles_total += (int64_t)nT * (nT + 1) / 2;
   CUDA_TRY(h, cudaMemsetAsync(h->pXi, 0, h->nT_cap * sizeof(uint64_t), h->st));
   CUDA_TRY(h, cudaMemsetAsync(h->pEta, 0, h->nT_cap * sizeof(uint64_t), h->st));
+  if (pe) {
+    CUDA_TRY(h, cudaEventRecord(pe[3], h->st));
+    CUDA_TRY(h, cudaEventRecord(pe[4], h->st));
+  }
   h->np = 0;
   return SR_OK;
 }
@@ -464,6 +478,10 @@ simrank_status flush_pending(simrank_ctx* h) {
 // One rank-one update of the current S for the sink block (srcs at d_srcs +
 // src_off, delta of them) into sink j, op = +1/-1, old in-degree d_j; the
 // graph patch ops [op_begin, op_end) turn the old graph into the new one.
+// chain = 0 runs everything before the S pass in one cooperative launch
+// (k_prep.cu, arithmetic in the precision of S); chain = 1, or a graph with
+// more tiles than the co-resident CTAs can own, takes the per-step kernels
+// (FP64 vectors).
 simrank_status run_rank_one(simrank_ctx* h, int64_t src_off, int delta, int j, int op, int d_j,
                             int64_t op_begin, int64_t op_end) {
   const int nT = (h->n_cur + PT - 1) / PT;
@@ -479,64 +497,115 @@ simrank_status run_rank_one(simrank_ctx* h, int64_t src_off, int delta, int j, i
     CUDA_TRY(h, cudaEventRecord(pe[0], h->st));
   }
   const bool defer = deferring(h);
-  if (defer) {
-    if (!h->Pp) {
-      const size_t pb = (size_t)h->nT_cap * 2 * h->cfg.defer * h->K1 * PT * sizeof(float);
-      CUDA_TRY(h, cudaMalloc(&h->Pp, pb));
-      CUDA_TRY(h, cudaMemsetAsync(h->Pp, 0, pb, h->st));
-      CUDA_TRY(h, dev_alloc(&h->pXi, (size_t)h->nT_cap));
-      CUDA_TRY(h, dev_alloc(&h->pEta, (size_t)h->nT_cap));
-      CUDA_TRY(h, cudaMemsetAsync(h->pXi, 0, h->nT_cap * sizeof(uint64_t), h->st));
-      CUDA_TRY(h, cudaMemsetAsync(h->pEta, 0, h->nT_cap * sizeof(uint64_t), h->st));
-    }
-    // rows i (summed over the block) and j of the current S = S + pending panels
-    launch_gather_rows_pending(h->S, 32, h->ld, h->d_srcs + src_off, delta, j, nT * PT, h->Pp,
-                               h->cfg.defer * h->K1, h->np * h->K1, h->sI, h->sJ, h->st);
-    launch_scalars_from_rows(h->din, h->sI, h->sJ, h->d_srcs + src_off, delta, j, h->scal, h->st);
-    h->launches += 1;
-  } else {
-    launch_gather_rows(h->S, h->cfg.s_precision, h->ld, h->d_srcs + src_off, delta, j, nT * PT,
-                       h->din, h->sI, h->sJ, h->scal, h->st);
+  if (defer && !h->Pp) {
+    const size_t pb = (size_t)h->nT_cap * 2 * h->cfg.defer * h->K1 * PT * sizeof(float);
+    CUDA_TRY(h, cudaMalloc(&h->Pp, pb));
+    CUDA_TRY(h, cudaMemsetAsync(h->Pp, 0, pb, h->st));
+    CUDA_TRY(h, dev_alloc(&h->pXi, (size_t)h->nT_cap));
+    CUDA_TRY(h, dev_alloc(&h->pEta, (size_t)h->nT_cap));
+    CUDA_TRY(h, cudaMemsetAsync(h->pXi, 0, h->nT_cap * sizeof(uint64_t), h->st));
+    CUDA_TRY(h, cudaMemsetAsync(h->pEta, 0, h->nT_cap * sizeof(uint64_t), h->st));
   }
-  launch_gamma(h->din, h->sI, h->sJ, h->scal, j, delta, op, d_j, C, nT, h->K1, h->P64,
-               h->cfg.s_precision == 64 ? nullptr : h->P32, h->mXi, h->mEta, h->st);
-  if (pe) CUDA_TRY(h, cudaEventRecord(pe[1], h->st));
-  launch_patch(h->d_ops, op_begin, op_end, h->din, h->dout, h->st);
-  float* p32 = h->cfg.s_precision == 64 ? nullptr : h->P32;
+  const bool plain = h->cfg.s_update == SR_SUPDATE_PLAIN;
+  bool fused = false;
   if (h->cfg.chain == 0) {
-    CUDA_TRY(h, launch_chain_all(h->din, h->cfg.K, C, nT, h->K1, h->P64, p32, h->mXi, h->mEta,
-                                 h->gbar, wait_limit(h), h->counters, h->st));
-    h->launches += 3 + (op_end > op_begin ? 1 : 0);
-  } else {
+    PrepParams pp{};
+    pp.in = h->din;
+    pp.out = h->dout;
+    pp.ops = h->d_ops;
+    pp.op_begin = op_begin;
+    pp.op_end = op_end;
+    pp.S = h->S;
+    pp.ld = h->ld;
+    pp.I = h->d_srcs + src_off;
+    pp.delta = delta;
+    pp.j = j;
+    pp.op = op;
+    pp.d_j = d_j;
+    pp.C = C;
+    pp.K = h->cfg.K;
+    pp.nT = nT;
+    if (defer) {
+      pp.P = h->Pp;
+      pp.ldk = h->cfg.defer * h->K1;
+      pp.koff = h->np * h->K1;
+      pp.npend = h->np * h->K1;
+      pp.pXi = h->pXi;
+      pp.pEta = h->pEta;
+    } else {
+      pp.P = panel_for_s(h);
+      pp.ldk = h->K1;
+      pp.tiles = h->tiles;
+      pp.ntiles = h->ntiles;
+      pp.tile_mode = (plain || !h->cfg.aff) ? 0 : 1;
+    }
+    pp.sI = h->sI;
+    pp.sJ = h->sJ;
+    pp.mXi = h->mXi;
+    pp.mEta = h->mEta;
+    pp.cap = h->cfg.prep_cache > 0 ? h->cfg.prep_cache : 8192;
+    pp.bar = h->gbar + 2;
+    pp.limit = wait_limit(h);
+    pp.counters = (unsigned long long*)h->counters;
+    const int rc = launch_prep(pp, h->cfg.s_precision, defer ? h->cfg.defer * h->K1 : 0,
+                               h->num_sms, h->cfg.prep_ctas, h->st);
+    if (rc == 1) return fail(h, SR_ERR_CUDA, "fused pre-update launch failed");
+    fused = (rc == 0);
+    if (fused) {
+      LAUNCH_CHECK(h);
+      h->launches += 1;
+      if (pe) {
+        CUDA_TRY(h, cudaEventRecord(pe[1], h->st));
+        CUDA_TRY(h, cudaEventRecord(pe[2], h->st));
+        CUDA_TRY(h, cudaEventRecord(pe[3], h->st));
+      }
+    }
+  }
+  if (!fused) {
+    if (defer) {
+      // rows i (summed over the block) and j of the current S = S + pending panels
+      launch_gather_rows_pending(h->S, 32, h->ld, h->d_srcs + src_off, delta, j, nT * PT, h->Pp,
+                                 h->cfg.defer * h->K1, h->np * h->K1, h->sI, h->sJ, h->st);
+      launch_scalars_from_rows(h->din, h->sI, h->sJ, h->d_srcs + src_off, delta, j, h->scal, h->st);
+      h->launches += 1;
+    } else {
+      launch_gather_rows(h->S, h->cfg.s_precision, h->ld, h->d_srcs + src_off, delta, j, nT * PT,
+                         h->din, h->sI, h->sJ, h->scal, h->st);
+    }
+    launch_gamma(h->din, h->sI, h->sJ, h->scal, j, delta, op, d_j, C, nT, h->K1, h->P64,
+                 h->cfg.s_precision == 64 ? nullptr : h->P32, h->mXi, h->mEta, h->st);
+    if (pe) CUDA_TRY(h, cudaEventRecord(pe[1], h->st));
+    launch_patch(h->d_ops, op_begin, op_end, h->din, h->dout, h->st);
+    float* p32 = h->cfg.s_precision == 64 ? nullptr : h->P32;
     for (int k = 0; k < h->cfg.K; ++k)
       launch_chain_step(h->din, k, C, nT, h->K1, h->P64, p32, h->mXi, h->mEta, h->st);
     h->launches += 2 + (op_end > op_begin ? 1 : 0) + h->cfg.K;
-  }
-  LAUNCH_CHECK(h);
-  if (pe) CUDA_TRY(h, cudaEventRecord(pe[2], h->st));
-  if (defer) {
-    // append this update's panels as pending terms np*K1 .. np*K1 + K (FP32)
-    const size_t w = (size_t)h->K1 * PT * sizeof(float);
-    const size_t dpitch = (size_t)h->cfg.defer * w;
-    CUDA_TRY(h, cudaMemcpy2DAsync((unsigned char*)h->Pp + (size_t)h->np * w, dpitch, h->P32, w, w,
-                                  (size_t)nT * 2, cudaMemcpyDeviceToDevice, h->st));
-    launch_or_any(h->mXi, h->mEta, nT, h->pXi, h->pEta, h->st);
-    h->launches += 1;
-    h->np += 1;
-    if (pe) {
-      CUDA_TRY(h, cudaEventRecord(pe[3], h->st));
-      CUDA_TRY(h, cudaEventRecord(pe[4], h->st));
+    LAUNCH_CHECK(h);
+    if (pe) CUDA_TRY(h, cudaEventRecord(pe[2], h->st));
+    if (defer) {
+      // append this update's panels as pending terms np*K1 .. np*K1 + K (FP32)
+      const size_t w = (size_t)h->K1 * PT * sizeof(float);
+      const size_t dpitch = (size_t)h->cfg.defer * w;
+      CUDA_TRY(h, cudaMemcpy2DAsync((unsigned char*)h->Pp + (size_t)h->np * w, dpitch, h->P32, w,
+                                    w, (size_t)nT * 2, cudaMemcpyDeviceToDevice, h->st));
+      launch_or_any(h->mXi, h->mEta, nT, h->pXi, h->pEta, h->st);
+      h->launches += 1;
+    } else {
+      CUDA_TRY(h, cudaMemsetAsync(h->ntiles, 0, sizeof(int), h->st));
+      launch_tile_list(h->mXi, h->mEta, nT, (plain || !h->cfg.aff) ? 0 : 1, h->tiles, h->ntiles,
+                       h->st);
+      LAUNCH_CHECK(h);
+      h->launches += 1;
     }
+    if (pe) CUDA_TRY(h, cudaEventRecord(pe[3], h->st));
+  }
+  if (defer) {
+    h->np += 1;
+    if (pe) CUDA_TRY(h, cudaEventRecord(pe[4], h->st));
     h->stats.rank_one_updates += 1;
     if (h->np == h->cfg.defer) return flush_pending(h);
     return SR_OK;
   }
-  CUDA_TRY(h, cudaMemsetAsync(h->ntiles, 0, sizeof(int), h->st));
-  const bool plain = h->cfg.s_update == SR_SUPDATE_PLAIN;
-  launch_tile_list(h->mXi, h->mEta, nT, (plain || !h->cfg.aff) ? 0 : 1, h->tiles, h->ntiles, h->st);
-  LAUNCH_CHECK(h);
-  h->launches += 1;
-  if (pe) CUDA_TRY(h, cudaEventRecord(pe[3], h->st));
   simrank_status s;
   if (plain) {
     for (int k = 0; k < h->K1; ++k)
@@ -1021,6 +1090,10 @@ simrank_status simrank_init(const simrank_config* cfg_in, int32_t n, int64_t m, 
   if ((int64_t)cfg.n_capacity > (int64_t)65535 * PT)
     return fail(nullptr, SR_ERR_ARG, "n_capacity too large for 16-bit tile indices");
   if (cfg.apply < 0 || cfg.apply > 2) return fail(nullptr, SR_ERR_ARG, "bad apply mode");
+  if (cfg.prep_ctas < 0 || cfg.prep_cache < 0 || cfg.prep_cache > 16384 || cfg.prep_cache % 4)
+    return fail(nullptr, SR_ERR_ARG, "prep_ctas >= 0; prep_cache a multiple of 4 in [0, 16384]");
+  if (cfg.defer < 0 || (cfg.defer > 1 && (int64_t)cfg.defer * (cfg.K + 1) > 4096))
+    return fail(nullptr, SR_ERR_ARG, "defer * (K + 1) must be at most 4096");
   if (cfg.tc && cfg.s_precision != 32)
     return fail(nullptr, SR_ERR_ARG, "the tensor-core update needs s_precision = 32");
   if (cfg.init_tol <= 0.0) cfg.init_tol = 1e-13;
@@ -1156,14 +1229,14 @@ simrank_status simrank_init(const simrank_config* cfg_in, int32_t n, int64_t m, 
       dev_alloc(&h->ntiles, 1) != cudaSuccess || dev_alloc(&h->sI, (size_t)h->n_pad) != cudaSuccess ||
       dev_alloc(&h->sJ, (size_t)h->n_pad) != cudaSuccess || dev_alloc(&h->scal, 8) != cudaSuccess ||
       dev_alloc(&h->counters, CNT_N) != cudaSuccess || dev_alloc(&h->diffbits, 1) != cudaSuccess ||
-      dev_alloc(&h->gbar, 2) != cudaSuccess)
+      dev_alloc(&h->gbar, 4) != cudaSuccess)
     return bail(fail(h, SR_ERR_OOM, "cudaMalloc of work buffers failed"));
   cudaMemsetAsync(h->P64, 0, panel_elems * sizeof(double), h->st);
   if (h->P32) cudaMemsetAsync(h->P32, 0, panel_elems * sizeof(float), h->st);
   cudaMemsetAsync(h->mXi, 0, h->nT_cap * sizeof(uint64_t), h->st);
   cudaMemsetAsync(h->mEta, 0, h->nT_cap * sizeof(uint64_t), h->st);
   cudaMemsetAsync(h->counters, 0, CNT_N * sizeof(int64_t), h->st);
-  cudaMemsetAsync(h->gbar, 0, 2 * sizeof(unsigned int), h->st);
+  cudaMemsetAsync(h->gbar, 0, 4 * sizeof(unsigned int), h->st);
   cudaMemsetAsync(h->S, 0, s_bytes, h->st);
 
   if (h->column) {

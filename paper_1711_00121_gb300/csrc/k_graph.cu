@@ -458,100 +458,6 @@ __global__ void __launch_bounds__(GT) k_chain_step(DevAdj in, int k, double C, i
   }
 }
 
-// Grid-wide barrier for a cooperative launch (all CTAs co-resident).  The
-// wait is bounded: after `limit` polls the CTA gives up and returns false.
-__device__ bool grid_barrier(unsigned int* count, unsigned int* gen, unsigned int nblocks,
-                             long long limit) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    const unsigned int g = *((volatile unsigned int*)gen);
-    __threadfence();
-    const unsigned int arrived = atomicAdd(count, 1u) + 1u;
-    if (arrived == nblocks) {
-      *((volatile unsigned int*)count) = 0u;
-      __threadfence();
-      atomicAdd(gen, 1u);
-    } else {
-      long long it = 0;
-      while (*((volatile unsigned int*)gen) == g) {
-        if (++it > limit) {
-          ok = 0;
-          break;
-        }
-        __nanosleep(32);
-      }
-    }
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
-// All K steps of the xi/eta recurrence in one cooperative launch: each CTA
-// handles tiles blockIdx.x, blockIdx.x + gridDim.x, ... of every step, with a
-// grid barrier between steps.  On a barrier timeout the kernel records
-// SR_ERR_TIMEOUT in counters[CNT_STATUS] and stops.
-__global__ void __launch_bounds__(GT) k_chain_all(DevAdj in, int K, double C, int K1, int nT,
-                                                  double* __restrict__ P64,
-                                                  float* __restrict__ P32,
-                                                  uint64_t* __restrict__ mXi,
-                                                  uint64_t* __restrict__ mEta,
-                                                  unsigned int* __restrict__ bar,
-                                                  long long limit,
-                                                  unsigned long long* __restrict__ counters) {
-  __shared__ TileRows tr;
-  __shared__ double acc[2][PT];
-  __shared__ int any_x, any_e;
-  const int tid = threadIdx.x;
-  for (int k = 0; k < K; ++k) {
-    for (int T = blockIdx.x; T < nT; T += gridDim.x) {
-      if (tid == 0) {
-        any_x = 0;
-        any_e = 0;
-      }
-      tile_rows_load(in, T, tr);
-      // column k was written by other CTAs earlier in this launch: L2-coherent loads
-      const double* src = P64;
-      tile_gather<2>(in, tr,
-                     [&](int v, int b) {
-                       return __ldcg(src + (((int64_t)(b / PT) * 2 + v) * K1 + k) * PT + (b % PT));
-                     },
-                     acc);
-      if (tid < PT) {
-        const int r = tid;
-        const int len = tr.len[r];
-        const double inv = (len > 0) ? 1.0 / (double)len : 0.0;
-        const double x = C * acc[0][r] * inv;
-        const double y = acc[1][r] * inv;
-        const int64_t bx = ((int64_t)T * 2 + 0) * K1 * PT + (int64_t)(k + 1) * PT + r;
-        const int64_t be = bx + (int64_t)K1 * PT;
-        P64[bx] = x;
-        P64[be] = y;
-        if (P32) {
-          P32[bx] = (float)x;
-          P32[be] = (float)y;
-        }
-        if (x != 0.0) any_x = 1;
-        if (y != 0.0) any_e = 1;
-      }
-      __syncthreads();
-      if (tid == 0) {
-        const unsigned long long bit = 1ull << ((k + 1) & 63);
-        if (any_x) atomicOr((unsigned long long*)&mXi[T], bit);
-        if (any_e) atomicOr((unsigned long long*)&mEta[T], bit);
-      }
-      __syncthreads();
-    }
-    if (k + 1 < K && !grid_barrier(bar, bar + 1, gridDim.x, limit)) {
-      if (tid == 0) atomicExch(&counters[CNT_STATUS], (unsigned long long)SR_ERR_TIMEOUT);
-      return;
-    }
-  }
-}
-
 __global__ void k_tile_list(const uint64_t* __restrict__ mXi, const uint64_t* __restrict__ mEta,
                             int nT, int aff, uint32_t* __restrict__ tiles,
                             int* __restrict__ ntiles) {
@@ -629,30 +535,6 @@ void launch_patch(const PatchOp* ops, int64_t begin, int64_t end, DevAdj in, Dev
 void launch_chain_step(const DevAdj& in, int k, double C, int nT, int K1, double* P64, float* P32,
                        uint64_t* mXi, uint64_t* mEta, cudaStream_t st) {
   k_chain_step<<<nT, GT, 0, st>>>(in, k, C, K1, P64, P32, mXi, mEta);
-}
-
-int chain_all_grid(int nT) {
-  static int per_sm = -1, sms = 0;
-  if (per_sm < 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chain_all, GT, 0) != cudaSuccess)
-      per_sm = 0;
-  }
-  return std::min(nT, per_sm * sms);
-}
-
-cudaError_t launch_chain_all(const DevAdj& in, int K, double C, int nT, int K1, double* P64,
-                             float* P32, uint64_t* mXi, uint64_t* mEta, unsigned int* bar,
-                             long long limit, int64_t* counters, cudaStream_t st) {
-  if (K <= 0) return cudaSuccess;
-  const int grid = chain_all_grid(nT);
-  if (grid <= 0) return cudaErrorLaunchOutOfResources;
-  DevAdj a = in;
-  unsigned long long* cnt = (unsigned long long*)counters;
-  void* args[] = {&a, &K, &C, &K1, &nT, &P64, &P32, &mXi, &mEta, &bar, &limit, &cnt};
-  return cudaLaunchCooperativeKernel((const void*)k_chain_all, grid, GT, args, 0, st);
 }
 
 void launch_tile_list(const uint64_t* mXi, const uint64_t* mEta, int nT, int aff, uint32_t* tiles,

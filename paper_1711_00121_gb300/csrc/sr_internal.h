@@ -109,11 +109,43 @@ void launch_patch(const PatchOp* ops, int64_t begin, int64_t end, DevAdj in, Dev
 void launch_chain_step(const DevAdj& in, int k, double C, int nT, int K1, double* P64, float* P32,
                        uint64_t* mXi, uint64_t* mEta, cudaStream_t st);
 
-// All K steps of the recurrence in one cooperative launch with a bounded grid
-// barrier (bar: two zeroed unsigned ints owned by the handle).
-cudaError_t launch_chain_all(const DevAdj& in, int K, double C, int nT, int K1, double* P64,
-                             float* P32, uint64_t* mXi, uint64_t* mEta, unsigned int* bar,
-                             long long limit, int64_t* counters, cudaStream_t st);
+// Everything a rank-one update does before its S pass, in one cooperative
+// launch (k_prep.cu): patch ops [op_begin, op_end), the rows sI, sJ of the
+// current S (panel terms [0, npend) of P not yet in S are added in), gamma
+// into term koff of P, K recurrence steps into terms koff+1 .. koff+K, the
+// mask words mXi/mEta of tiles [0, nT) (ORed as 0/1 into pXi/pEta when
+// those are set) and, when `tiles` is set, the tile-pair list (tile_mode 0 =
+// all pairs, 1 = AFF-pruned).  P is tile-blocked [T][which][ldk][128] in the
+// precision of S; sI, sJ hold n_pad values of that precision.  bar: two
+// zeroed unsigned ints, left zeroed.  Returns 0 on launch, 2 when the graph
+// has more tiles than the co-resident CTAs can own (use the per-step path),
+// 1 on a launch error.
+struct PrepParams {
+  DevAdj in, out;
+  const PatchOp* ops;
+  int64_t op_begin, op_end;
+  const void* S;
+  int64_t ld;
+  const int32_t* I;
+  int delta, j, op, d_j;
+  double C;
+  int K;
+  int nT;
+  void* P;
+  int ldk, koff, npend;
+  void* sI;
+  void* sJ;
+  uint64_t *mXi, *mEta, *pXi, *pEta;
+  uint32_t* tiles;
+  int* ntiles;
+  int tile_mode;
+  int cap;  // column indices cached per CTA
+  unsigned int* bar;
+  long long limit;
+  unsigned long long* counters;
+};
+int launch_prep(const PrepParams& p, int s_prec, int npend_max, int num_sms, int max_ctas,
+                cudaStream_t st);
 
 // Affected tile pairs (I <= J) of Thm 4 at tile granularity.
 void launch_tile_list(const uint64_t* mXi, const uint64_t* mEta, int nT, int aff, uint32_t* tiles,

@@ -119,7 +119,8 @@ def test_unit_update_converged_vs_batch_recompute(P, case):
 # ------------------------------------------------------------ update streams
 
 @pytest.mark.parametrize("variant", ["fused_aff", "fused_aff_norelabel", "fused_single_role",
-                                     "fused_noaff", "plain", "deferred_ffma", "deferred_tc"])
+                                     "fused_noaff", "plain", "deferred_ffma", "deferred_tc",
+                                     "per_step_chain", "prep_multi_tile", "deferred_multi_tile"])
 def test_stream_fp32_powerlaw(P, variant):
     n, m, C, K = 1500, 15000, 0.6, 20
     s, d = chung_lu_digraph(n, m, 2.1, 2.1, 4)
@@ -137,6 +138,14 @@ def test_stream_fp32_powerlaw(P, variant):
         kw = dict(aff=0, s_update=P.SUPDATE_FUSED)
     elif variant == "plain":
         kw = dict(aff=0, s_update=P.SUPDATE_PLAIN)
+    elif variant == "per_step_chain":
+        kw = dict(aff=1, chain=1)
+    elif variant == "prep_multi_tile":
+        # 12 tiles on 2 CTAs (6 tiles each) and a 64-entry column cache: the
+        # multi-tile and uncached-column paths of the fused launch
+        kw = dict(aff=1, prep_ctas=2, prep_cache=64)
+    elif variant == "deferred_multi_tile":
+        kw = dict(aff=1, defer=7, tc=1, prep_ctas=3, prep_cache=128)
     sr = P.SimRank(n, s, d, C=C, K=K, s_precision=32, **kw)
     sr.apply_updates(st)
     S = oracle_S(n, s, d, C)
@@ -146,12 +155,14 @@ def test_stream_fp32_powerlaw(P, variant):
     assert maxabs(got, got.T) < 1e-7
 
 
-def test_stream_fp64_matches_oracle(P):
+@pytest.mark.parametrize("kw", [{}, {"chain": 1}, {"prep_ctas": 2, "prep_cache": 32}],
+                         ids=["fused", "per_step", "fused_multi_tile"])
+def test_stream_fp64_matches_oracle(P, kw):
     n, m, C, K = 700, 4200, 0.8, 12
     s, d = er_graph(n, m, 6)
     st = update_stream(n, s, d, 25, 7)
     S = oracle_S(n, s, d, C)
-    sr = P.SimRank(n, s, d, S0=S, C=C, K=K, s_precision=64)
+    sr = P.SimRank(n, s, d, S0=S, C=C, K=K, s_precision=64, **kw)
     sr.apply_updates(st)
     want, _ = O.sequential_unit_updates(n, s, d, S, st.tolist(), C, K)
     assert maxabs(sr.dense(), want) < TOL64
@@ -243,14 +254,14 @@ def test_sink_blocks_fp32_deferred_vs_inc_bsr(P, defer):
     assert maxabs(sr.dense(), want) < TOL32
 
 
-@pytest.mark.parametrize("seed", [12, 13])
-def test_sink_blocks_fp64_vs_inc_bsr(P, seed):
+@pytest.mark.parametrize("seed,chain", [(12, 0), (13, 0), (12, 1)])
+def test_sink_blocks_fp64_vs_inc_bsr(P, seed, chain):
     n, m, C, K = 500, 2500, 0.6, 10
     s, d = er_graph(n, m, seed)
     ups, n_new = batch_with_new_nodes(n, s, d, 60, seed, frac_new=0.2, reuse_target=0.5)
     S = oracle_S(n, s, d, C)
     sr = P.SimRank(n, s, d, S0=S, C=C, K=K, s_precision=64, n_capacity=n + n_new,
-                   apply=P.APPLY_SINK_BLOCKS)
+                   apply=P.APPLY_SINK_BLOCKS, chain=chain)
     sr.apply_updates(ups)
     want, _ = O.inc_bsr(n, s, d, S, ups.tolist(), C, K)
     assert maxabs(sr.dense(), want) < TOL64
