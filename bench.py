@@ -401,6 +401,98 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------
+# Many-graph workload: 512 directed Chung-Lu graphs (exponent 2.1), n uniform
+# in [500, 8000], mean degree 8, C = 0.6, K = 15, S in FP32 (46 GB in all);
+# each graph gets its own stream of 1-32 unit updates.  The batched form (one
+# prep launch over all graphs and one S pass over all their tiles per round,
+# replayed from a CUDA graph) and the per-graph-launch form run the same
+# kernels on two handles over statistically identical streams.
+# --------------------------------------------------------------------------
+MG, MN_LO, MN_HI, MDEG, MC, MK, M_SEED = 512, 500, 8000, 8, 0.6, 15, 4
+
+
+def run_multi(args):
+    import torch
+
+    import paper_1711_00121_gb300 as P
+    from synth.graphs import EdgeSet as ES
+
+    torch.cuda.set_device(0)
+    G = args.graphs
+    rng = np.random.default_rng(M_SEED)
+    sizes = rng.integers(MN_LO, MN_HI + 1, size=G)
+    counts = rng.integers(1, 33, size=G)
+    graphs = []
+    for g in range(G):
+        n = int(sizes[g])
+        s, d = chung_lu_digraph(n, MDEG * n, 2.1, 2.1, M_SEED * 100000 + g)
+        graphs.append((n, s, d))
+    res = {}
+    for form, launch in (("batched_cuda_graph", 0), ("per_graph_launches", 1)):
+        sets = [ES(n, s, d) for n, s, d in graphs]
+
+        def draw(tag):
+            return [update_stream(n, None, None, int(counts[g]), M_SEED * 7919 + 1000 * tag + g,
+                                  edge_set=sets[g]) for g, (n, _, _) in enumerate(graphs)]
+
+        warm = [draw(t) for t in range(args.warmup)]
+        timed = [draw(100 + t) for t in range(args.steps)]
+        t0 = time.time()
+        mh = P.MultiSimRank(graphs, C=MC, K=MK, s_precision=32, multi_launch=launch,
+                            init_tol=1e-9)
+        init_s = time.time() - t0
+        packed = []
+        for ups in warm + timed:
+            arrs = [P.updates_array(u) for u in ups]
+            off = np.zeros(G + 1, np.int64)
+            off[1:] = np.cumsum([a.size for a in arrs])
+            packed.append((np.ascontiguousarray(np.concatenate(arrs)), off))
+        for pk, off in packed[:args.warmup]:
+            mh.apply_packed(pk, off)
+        mh.sync()
+        st0 = mh.stats()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(0) as clk:
+            ev0.record()
+            h0 = time.time()
+            for pk, off in packed[args.warmup:]:
+                mh.apply_packed(pk, off)
+            mh.sync()
+            host_s = time.time() - h0
+            ev1.record()
+            torch.cuda.synchronize()
+        st1 = mh.stats()
+        n_upd = int(counts.sum()) * args.steps
+        res[form] = {"updates_per_s": n_upd / host_s, "s": host_s, "updates_timed": n_upd,
+                     "kernel_launches": st1["kernel_launches"] - st0["kernel_launches"],
+                     "s_bytes": st1["s_bytes"] - st0["s_bytes"],
+                     "hbm_gbs": (st1["s_bytes"] - st0["s_bytes"]) / host_s / 1e9,
+                     "init_s": init_s, "clocks": clk.summary()}
+        if form == "batched_cuda_graph":
+            # accuracy: the smallest graph's final S against the FP64 oracle
+            from oracle import simrank_oracle as O
+
+            g = int(np.argmin(sizes))
+            n, s0, d0 = graphs[g]
+            S = O.simrank_fixed_point(O.transition_matrix(n, s0, d0, sparse=True), MC, tol=1e-15)
+            allu = np.concatenate([w[g] for w in warm + timed])
+            want, _ = O.sequential_unit_updates(n, s0, d0, S, allu.tolist(), MC, MK)
+            res[form]["max_abs_vs_oracle_smallest_graph"] = float(np.max(np.abs(mh.dense(g) - want)))
+        mh.close()
+        del mh
+        torch.cuda.empty_cache()
+    one = res["batched_cuda_graph"]
+    line = {"workload": f"many graphs: {G} directed Chung-Lu graphs (exponent 2.1), n~U[{MN_LO},{MN_HI}], "
+                        f"mean degree {MDEG}, C={MC}, K={MK}, FP32 S, 1-32 unit updates per graph per call",
+            "sum_S_gb": float(sum(int(((n + 127) // 128 * 128)) ** 2 * 4 for n in sizes) / 1e9),
+            "updates_per_call": int(counts.sum()), "steps": args.steps, "warmup": args.warmup,
+            "forms": res,
+            "speedup_batched_vs_per_graph": one["updates_per_s"] / res["per_graph_launches"]["updates_per_s"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -413,8 +505,10 @@ def main():
     ap.add_argument("--defer", type=int, default=0,
                     help="stream workload: rank-one updates kept pending per S pass (0 = apply each)")
     ap.add_argument("--tc", type=int, default=0, help="S passes on tensor cores (with --defer)")
-    ap.add_argument("--workload", default="stream", choices=["stream", "batched"],
-                    help="stream: the benchmarked update stream; batched: one-shot vs per-edge")
+    ap.add_argument("--workload", default="stream", choices=["stream", "batched", "multi"],
+                    help="stream: the benchmarked update stream; batched: one-shot vs per-edge; "
+                         "multi: many graphs batched vs per-graph launches")
+    ap.add_argument("--graphs", type=int, default=MG, help="multi workload: number of graphs")
     ap.add_argument("--batch", type=int, default=64, help="batched workload: edges per batch")
     ap.add_argument("--per-edge-sample", type=int, default=256,
                     help="batched workload: per-edge updates timed per batch")
@@ -423,6 +517,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.workload == "batched":
         run_batched(args)
+        return
+    if args.workload == "multi":
+        run_multi(args)
         return
     if args.impl == "reference":
         run_reference(args, rank)

@@ -105,7 +105,11 @@ typedef struct simrank_config {
   int32_t prep_ctas;      /* chain = 0: cap on the CTAs of the fused launch (0 = as many as fit) */
   int32_t prep_cache;     /* chain = 0: column indices cached in shared memory per CTA, a
                              multiple of 4 in [0, 16384] (0 = 8192); the rest are read from L2 */
-  int32_t reserved[3];
+  int32_t multi_launch;   /* simrank_multi_apply: 0 = per round, one launch for the work of all
+                             graphs before their S passes and one S pass over all their tiles,
+                             replayed from a CUDA graph; 1 = the same kernels launched graph by
+                             graph (the per-graph-launch baseline) */
+  int32_t reserved[2];
 } simrank_config;
 
 /* Fills *cfg with defaults: C = 0.6, K = 15, s_precision = 32, dense, aff = 1,
@@ -208,6 +212,55 @@ simrank_status simrank_grad(simrank_t h, const int32_t* a, const int32_t* b, con
 simrank_status simrank_plan_batch(const simrank_update* u, int64_t count, int32_t n_old,
                                   int32_t max_blocks, int32_t* nblocks, int32_t* block_sink,
                                   int32_t* block_op, int64_t* block_off, int32_t* block_src);
+
+/* ---------------------------------------------------------------------------
+ * Many independent graphs advanced together.  Each graph has its own dense S
+ * (cfg->s_precision), adjacency and caller ids, exactly as a simrank_t of its
+ * own; all graphs share C, K and the stream.  simrank_multi_apply applies
+ * every graph's updates in order, one rank-one update (Alg 1, Thm 3 / Thm 9,
+ * new nodes as in simrank_apply_updates) per graph per round; a round is one
+ * launch for the work of all graphs before their S passes (one CTA per graph)
+ * and one S pass over the affected tiles of all graphs (cfg->multi_launch).
+ * This batching is not in the paper: the graphs are independent problems.
+ * ------------------------------------------------------------------------- */
+typedef struct simrank_multi* simrank_multi_t;
+
+/* Creates ngraphs graphs: graph g has n[g] nodes (n_capacity[g] >= n[g] with
+ * the nodes beyond n[g] pre-allocated as isolated nodes; n_capacity NULL
+ * means n) and the edges src[e] -> dst[e] for edge_offsets[g] <= e <
+ * edge_offsets[g+1] (host arrays; edge_offsets has ngraphs + 1 entries).
+ * Every S starts at the fixed point of Eq. 1 (Jacobi sweeps on the GPU to
+ * cfg->init_tol).  cfg: dense mode, SR_APPLY_UNIT, fused S update, defer
+ * 0 or 1, n_capacity ignored (per graph instead), at most 65536 nodes per
+ * graph.  Errors: SR_ERR_ARG, SR_ERR_EDGE_EXISTS, SR_ERR_OOM, SR_ERR_CUDA,
+ * SR_ERR_UNSUPPORTED; the message is simrank_last_error(NULL). */
+simrank_status simrank_multi_init(const simrank_config* cfg, int32_t ngraphs, const int32_t* n,
+                                  const int32_t* n_capacity, const int64_t* edge_offsets,
+                                  const int32_t* src, const int32_t* dst, simrank_multi_t* out);
+
+/* Applies the updates u[update_offsets[g] .. update_offsets[g+1]) to graph g,
+ * in order, for every g (host arrays).  Every graph's updates are validated
+ * first, as by simrank_apply_updates; if any is invalid nothing is applied
+ * and simrank_multi_last_error names the graph.  Asynchronous on the stream. */
+simrank_status simrank_multi_apply(simrank_multi_t h, const simrank_update* u,
+                                   const int64_t* update_offsets);
+
+/* simrank_columns for graph g (caller ids of that graph). */
+simrank_status simrank_multi_columns(simrank_multi_t h, int32_t g, const int32_t* cols,
+                                     int32_t ncols, void* out, int32_t out_on_device,
+                                     int32_t out_fp64);
+int32_t simrank_multi_num_graphs(simrank_multi_t h);
+int32_t simrank_multi_num_nodes(simrank_multi_t h, int32_t g);
+/* Waits for the stream; reports SR_ERR_TIMEOUT if a bounded device wait ran out. */
+simrank_status simrank_multi_sync(simrank_multi_t h);
+/* Totals over all graphs of the apply calls (updates, rank_one_updates,
+ * tiles_touched, s_bytes, panel_bytes, kernel_launches); with cfg->profile = 1
+ * also s_update_ms, s_update_launches and phase_ms[0] (work before the S
+ * passes) / phase_ms[3] (S passes), from CUDA events (profiled calls are
+ * launched directly, not from a CUDA graph). */
+simrank_status simrank_multi_get_stats(simrank_multi_t h, simrank_stats* out);
+const char* simrank_multi_last_error(simrank_multi_t h);
+void simrank_multi_destroy(simrank_multi_t h);
 
 /* One edge update of a caller-owned dense S and graph, allocating nothing.
  * The paper has no counterpart: this is for callers that cannot allocate

@@ -5,6 +5,7 @@ The computation lives in the CUDA library ``libsimrank.so`` (C ABI in
 """
 from ._binding import (  # noqa: F401
     SimRank,
+    MultiSimRank,
     SimrankError,
     Config,
     Update,

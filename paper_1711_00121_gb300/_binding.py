@@ -41,7 +41,7 @@ class Config(ctypes.Structure):
         ("timeout_iters", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
         ("s_kernel", ctypes.c_int32), ("defer", ctypes.c_int32), ("chain", ctypes.c_int32),
         ("prep_ctas", ctypes.c_int32), ("prep_cache", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("multi_launch", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2),
     ]
 
 
@@ -84,6 +84,15 @@ SIGNATURES = {
     "simrank_grad": (_I32, [_P, _P, _P, _P, _I64, ctypes.POINTER(ctypes.c_double), _P]),
     "simrank_update_noalloc": (_I32, [_I32, _I64, _P, _I32, _P, _P, _P, _P, _I32, _I32, _I32, _I32,
                                       ctypes.c_double, _I32, _P]),
+    "simrank_multi_init": (_I32, [ctypes.POINTER(Config), _I32, _P, _P, _P, _P, _P, ctypes.POINTER(_P)]),
+    "simrank_multi_apply": (_I32, [_P, _P, _P]),
+    "simrank_multi_columns": (_I32, [_P, _I32, _P, _I32, _P, _I32, _I32]),
+    "simrank_multi_num_graphs": (_I32, [_P]),
+    "simrank_multi_num_nodes": (_I32, [_P, _I32]),
+    "simrank_multi_sync": (_I32, [_P]),
+    "simrank_multi_get_stats": (_I32, [_P, ctypes.POINTER(Stats)]),
+    "simrank_multi_last_error": (ctypes.c_char_p, [_P]),
+    "simrank_multi_destroy": (None, [_P]),
 }
 
 _lib = None
@@ -228,6 +237,87 @@ class SimRank:
         d = ctypes.c_double()
         _check(lib().simrank_reanchor(self._h, int(sweeps), ctypes.byref(d)), self._h)
         return d.value
+
+
+def _mcheck(status, handle=None):
+    if status != SR_OK:
+        msg = lib().simrank_multi_last_error(handle)
+        raise SimrankError(status, msg.decode() if msg else "")
+
+
+class MultiSimRank:
+    """Many independent graphs in GPU memory, advanced together.
+
+    ``graphs`` is a list of (n, src, dst) or (n, src, dst, n_capacity).
+    """
+
+    def __init__(self, graphs, stream=None, **cfg_kw):
+        cfg = default_config(**cfg_kw)
+        if stream is not None:
+            cfg.cuda_stream = stream
+        n = np.array([int(gr[0]) for gr in graphs], np.int32)
+        cap = np.array([int(gr[3]) if len(gr) > 3 else int(gr[0]) for gr in graphs], np.int32)
+        m = [len(gr[1]) for gr in graphs]
+        off = np.zeros(len(graphs) + 1, np.int64)
+        off[1:] = np.cumsum(m)
+        src = np.ascontiguousarray(np.concatenate([np.asarray(gr[1], np.int32) for gr in graphs]))
+        dst = np.ascontiguousarray(np.concatenate([np.asarray(gr[2], np.int32) for gr in graphs]))
+        h = _P()
+        _mcheck(lib().simrank_multi_init(ctypes.byref(cfg), len(graphs), _ptr(n), _ptr(cap), _ptr(off),
+                                         _ptr(src), _ptr(dst), ctypes.byref(h)), None)
+        self._h = h
+        self.cfg = cfg
+
+    @property
+    def num_graphs(self):
+        return lib().simrank_multi_num_graphs(self._h)
+
+    def num_nodes(self, g):
+        return lib().simrank_multi_num_nodes(self._h, int(g))
+
+    def apply_updates(self, per_graph):
+        """per_graph[g]: (count, 3) array of (src, dst, op) for graph g."""
+        arrs = [updates_array(np.asarray(x).reshape(-1, 3)) for x in per_graph]
+        off = np.zeros(len(arrs) + 1, np.int64)
+        off[1:] = np.cumsum([a.size for a in arrs])
+        allu = np.ascontiguousarray(np.concatenate(arrs)) if arrs else np.zeros(0, UPDATE_DTYPE)
+        self.apply_packed(allu, off)
+
+    def apply_packed(self, packed, offsets):
+        """Packed simrank_update records (host) and their ngraphs + 1 offsets."""
+        _mcheck(lib().simrank_multi_apply(self._h, _ptr(packed), _ptr(offsets)), self._h)
+
+    def columns(self, g, cols, fp64=True):
+        cols = np.ascontiguousarray(cols, np.int32)
+        n = self.num_nodes(g)
+        out = np.zeros((cols.size, n), np.float64 if fp64 else np.float32)
+        _mcheck(lib().simrank_multi_columns(self._h, int(g), _ptr(cols), int(cols.size), _ptr(out), 0,
+                                            1 if fp64 else 0), self._h)
+        return out.T
+
+    def dense(self, g, fp64=True):
+        return self.columns(g, np.arange(self.num_nodes(g), dtype=np.int32), fp64=fp64)
+
+    def sync(self):
+        _mcheck(lib().simrank_multi_sync(self._h), self._h)
+
+    def stats(self) -> dict:
+        s = Stats()
+        _mcheck(lib().simrank_multi_get_stats(self._h, ctypes.byref(s)), self._h)
+        out = {name: getattr(s, name) for name, _ in Stats._fields_ if name != "reserved"}
+        out["phase_ms"] = list(s.phase_ms)
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().simrank_multi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def plan_batch(upd, n_old):

@@ -1738,3 +1738,429 @@ simrank_status simrank_plan_batch(const simrank_update* u, int64_t count, int32_
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Many independent graphs (simrank_multi_*).  Each graph is a simrank_ctx of
+// its own (S, adjacency, ids, validation and bookkeeping as for one graph);
+// the multi handle plans all graphs' updates on the host, uploads one step
+// table, and queues per launch l: one prep launch over the steps of l (one
+// CTA each) and one S pass over the tile pairs they list.  In the batched
+// form launch l is round l (every graph's l-th update); in the per-graph
+// form every step is a launch of its own, graph by graph.
+// ===========================================================================
+struct simrank_multi {
+  simrank_config cfg{};
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  int num_sms = 0;
+  std::vector<simrank_ctx*> g;
+  MultiGraphDesc* d_desc = nullptr;
+  MultiStep* d_steps = nullptr;
+  int64_t steps_cap = 0;
+  int* d_count = nullptr;  // [launch] number of steps
+  int* d_ntiles = nullptr; // [launch] tile pairs listed
+  int64_t launch_cap = 0;
+  uint64_t* d_tiles = nullptr;
+  int64_t tiles_cap = 0;
+  int32_t* d_srcs = nullptr;
+  int64_t srcs_cap = 0;
+  PatchOp* d_ops = nullptr;
+  int64_t ops_cap = 0;
+  int64_t* counters = nullptr;
+  // host staging of the last call (uploaded, then the stream is synchronised)
+  std::vector<MultiGraphDesc> h_desc;
+  std::vector<MultiStep> h_steps;
+  std::vector<int> h_count;
+  std::vector<int32_t> h_srcs;
+  std::vector<PatchOp> h_ops;
+  // CUDA graph of the last launch sequence, reused while its shape and
+  // buffers are unchanged
+  cudaGraphExec_t exec = nullptr;
+  std::vector<int> exec_count;
+  std::vector<const void*> exec_ptrs;
+  // stats
+  simrank_stats stats{};
+  std::vector<std::array<cudaEvent_t, 3>> ev;
+  size_t ev_used = 0;
+  double prep_ms = 0.0, sup_ms = 0.0;
+  int64_t sup_launches = 0, launches = 0;
+  std::string err;
+};
+
+namespace {
+
+simrank_status mfail(simrank_multi* h, simrank_status s, const std::string& msg) {
+  if (h)
+    h->err = msg;
+  else
+    g_init_error = msg;
+  return s;
+}
+
+#define MCUDA_TRY(h, call)                                                                 \
+  do {                                                                                     \
+    cudaError_t e__ = (call);                                                              \
+    if (e__ != cudaSuccess)                                                                \
+      return mfail((h), e__ == cudaErrorMemoryAllocation ? SR_ERR_OOM : SR_ERR_CUDA,       \
+                   std::string(#call) + ": " + cudaGetErrorString(e__));                   \
+  } while (0)
+
+template <typename T>
+cudaError_t grow_dev(T** p, int64_t* cap, int64_t need) {
+  if (need <= *cap) return cudaSuccess;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = std::max<int64_t>(need, 2 * *cap);
+  return dev_alloc(p, (size_t)*cap);
+}
+
+void multi_free(simrank_multi* h) {
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  for (void* p : {(void*)h->d_desc, (void*)h->d_steps, (void*)h->d_count, (void*)h->d_ntiles,
+                  (void*)h->d_tiles, (void*)h->d_srcs, (void*)h->d_ops, (void*)h->counters})
+    if (p) cudaFree(p);
+  for (auto& e : h->ev)
+    for (cudaEvent_t x : e) cudaEventDestroy(x);
+  for (simrank_ctx* c : h->g)
+    if (c) {
+      cudaStreamSynchronize(c->st);
+      free_ctx(c);
+    }
+  if (h->own_stream && h->st) cudaStreamDestroy(h->st);
+  delete h;
+}
+
+void multi_harvest(simrank_multi* h) {
+  for (size_t e = 0; e < h->ev_used; ++e) {
+    float a = 0.f, b = 0.f;
+    if (cudaEventElapsedTime(&a, h->ev[e][0], h->ev[e][1]) == cudaSuccess) h->prep_ms += a;
+    if (cudaEventElapsedTime(&b, h->ev[e][1], h->ev[e][2]) == cudaSuccess) h->sup_ms += b;
+  }
+  h->ev_used = 0;
+}
+
+// Queues launch l: the prep of steps [off, off + cnt) and the S pass.
+void multi_enqueue(simrank_multi* h, int l, int64_t off, int cnt) {
+  const int sp = h->cfg.s_precision;
+  const int sgrid = h->num_sms * (sp == 64 ? 1 : 2);
+  launch_multi_prep(sp, h->d_desc, h->d_steps + off, h->d_count + l, cnt, h->d_srcs, h->d_ops,
+                    h->cfg.C, h->cfg.K, h->cfg.aff ? 1 : 0, h->d_tiles, h->d_ntiles + l, h->st);
+  launch_s_update_multi(sp, h->d_desc, h->d_tiles, h->d_ntiles + l, h->cfg.K + 1, h->counters,
+                        sgrid, h->st);
+}
+
+}  // namespace
+
+extern "C" {
+
+simrank_status simrank_multi_init(const simrank_config* cfg_in, int32_t ngraphs, const int32_t* n,
+                                  const int32_t* n_capacity, const int64_t* edge_offsets,
+                                  const int32_t* src, const int32_t* dst, simrank_multi_t* out) {
+  if (!cfg_in || !out || !n || !edge_offsets) return mfail(nullptr, SR_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (ngraphs < 1) return mfail(nullptr, SR_ERR_ARG, "ngraphs must be >= 1");
+  const simrank_config& cfg = *cfg_in;
+  if (cfg.mode != SR_MODE_DENSE || cfg.apply != SR_APPLY_UNIT || cfg.defer > 1 ||
+      cfg.s_update != SR_SUPDATE_FUSED)
+    return mfail(nullptr, SR_ERR_UNSUPPORTED,
+                 "many graphs: dense mode, unit apply, fused S update, defer 0 or 1");
+  if (cfg.multi_launch != 0 && cfg.multi_launch != 1)
+    return mfail(nullptr, SR_ERR_ARG, "multi_launch must be 0 or 1");
+  for (int g = 0; g < ngraphs; ++g) {
+    const int cap = n_capacity ? n_capacity[g] : n[g];
+    if (n[g] < 1 || cap < n[g] || cap > 65536)
+      return mfail(nullptr, SR_ERR_ARG,
+                   "graph " + std::to_string(g) + ": need 1 <= n <= n_capacity <= 65536");
+    if (edge_offsets[g + 1] < edge_offsets[g])
+      return mfail(nullptr, SR_ERR_ARG, "edge_offsets must be non-decreasing");
+  }
+  simrank_multi* h = new (std::nothrow) simrank_multi();
+  if (!h) return mfail(nullptr, SR_ERR_OOM, "host allocation failed");
+  h->cfg = cfg;
+  h->st = (cudaStream_t)cfg.cuda_stream;
+  if (!h->st) {
+    // stream capture needs a stream other than the legacy default stream
+    if (cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking) != cudaSuccess) {
+      delete h;
+      return mfail(nullptr, SR_ERR_CUDA, "cudaStreamCreate failed");
+    }
+    h->own_stream = true;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  h->g.assign(ngraphs, nullptr);
+  for (int g = 0; g < ngraphs; ++g) {
+    simrank_config c = cfg;
+    c.n_capacity = n_capacity ? n_capacity[g] : n[g];
+    c.cuda_stream = h->st;
+    const int64_t e0 = edge_offsets[g], m = edge_offsets[g + 1] - edge_offsets[g];
+    simrank_t ctx = nullptr;
+    const simrank_status s = simrank_init(&c, n[g], m, src ? src + e0 : nullptr,
+                                          dst ? dst + e0 : nullptr, nullptr, nullptr, &ctx);
+    if (s != SR_OK) {
+      const std::string msg = "graph " + std::to_string(g) + ": " + g_init_error;
+      multi_free(h);
+      return mfail(nullptr, s, msg);
+    }
+    h->g[g] = ctx;
+  }
+  if (dev_alloc(&h->d_desc, (size_t)ngraphs) != cudaSuccess ||
+      dev_alloc(&h->counters, (size_t)CNT_N) != cudaSuccess) {
+    multi_free(h);
+    return mfail(nullptr, SR_ERR_OOM, "cudaMalloc failed");
+  }
+  cudaMemsetAsync(h->counters, 0, CNT_N * sizeof(int64_t), h->st);
+  h->h_desc.resize(ngraphs);
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) {
+    multi_free(h);
+    return mfail(nullptr, SR_ERR_CUDA, "initialisation failed on the GPU");
+  }
+  *out = h;
+  return SR_OK;
+}
+
+simrank_status simrank_multi_apply(simrank_multi_t h, const simrank_update* u,
+                                   const int64_t* update_offsets) {
+  if (!h) return mfail(nullptr, SR_ERR_ARG, "null handle");
+  if (!update_offsets) return mfail(h, SR_ERR_ARG, "null update_offsets");
+  const int G = (int)h->g.size();
+  // caller ids -> storage ids, then validation of every graph before any change
+  std::vector<std::vector<simrank_update>> um(G);
+  std::vector<int> n_after(G);
+  int64_t total = 0;
+  int R = 0;
+  for (int g = 0; g < G; ++g) {
+    const int64_t c = update_offsets[g + 1] - update_offsets[g];
+    if (c < 0) return mfail(h, SR_ERR_ARG, "update_offsets must be non-decreasing");
+    if (c > 0 && !u) return mfail(h, SR_ERR_ARG, "null update array");
+    simrank_ctx* x = h->g[g];
+    um[g].assign(u + update_offsets[g], u + update_offsets[g] + c);
+    if (x->relabeled)
+      for (auto& v : um[g]) {
+        if (v.src >= 0 && v.src < x->n_cap) v.src = x->ext2int[v.src];
+        if (v.dst >= 0 && v.dst < x->n_cap) v.dst = x->ext2int[v.dst];
+      }
+    n_after[g] = x->n_cur;
+    const simrank_status s = validate(x, um[g].data(), c, &n_after[g]);
+    if (s != SR_OK) return mfail(h, s, "graph " + std::to_string(g) + ": " + x->err);
+    total += c;
+    R = std::max<int>(R, (int)c);
+  }
+  if (total == 0) return SR_OK;
+  // plan: per graph its steps, in order (host mirrors and patch ops)
+  h->h_srcs.clear();
+  h->h_ops.clear();
+  std::vector<std::vector<MultiStep>> per(G);
+  for (int g = 0; g < G; ++g) {
+    simrank_ctx* x = h->g[g];
+    int n_run = x->n_cur;
+    for (const simrank_update& v : um[g]) {
+      const int32_t i = v.src, j = v.dst;
+      n_run = std::max(n_run, std::max(i, j) + 1);
+      MultiStep s{};
+      s.g = g;
+      s.j = j;
+      s.op = v.op;
+      s.d_j = x->hin.len[j];
+      s.delta = 1;
+      s.src_off = (int64_t)h->h_srcs.size();
+      h->h_srcs.push_back(i);
+      s.op_begin = (int64_t)h->h_ops.size();
+      if (v.op > 0) {
+        adj_append(x->hin, j, i, h->h_ops, true);
+        adj_append(x->hout, i, j, h->h_ops, false);
+        x->edges.insert(ekey(i, j));
+      } else {
+        adj_remove(x->hin, j, i, h->h_ops, true);
+        adj_remove(x->hout, i, j, h->h_ops, false);
+        x->edges.erase(ekey(i, j));
+      }
+      s.op_end = (int64_t)h->h_ops.size();
+      s.n_after = n_run;
+      per[g].push_back(s);
+    }
+    x->n_cur = n_after[g];
+    simrank_status s;
+    if ((s = grow_pool(x, x->din, x->hin)) != SR_OK || (s = grow_pool(x, x->dout, x->hout)) != SR_OK)
+      return mfail(h, s, "graph " + std::to_string(g) + ": " + x->err);
+    x->stats.updates += (int64_t)um[g].size();
+    x->stats.rank_one_updates += (int64_t)um[g].size();
+    MultiGraphDesc& d = h->h_desc[g];
+    d.S = x->S;
+    d.ld = x->ld;
+    d.P = x->cfg.s_precision == 64 ? (void*)x->P64 : (void*)x->P32;
+    d.mXi = x->mXi;
+    d.mEta = x->mEta;
+    d.in = x->din;
+    d.out = x->dout;
+    d.sI = x->sI;
+    d.sJ = x->sJ;
+    d.n = x->n_cur;
+  }
+  // launch table
+  h->h_steps.clear();
+  h->h_count.clear();
+  std::vector<int64_t> loff;
+  int64_t tiles_need = 0;
+  auto pairs = [](int n_after) {
+    const int64_t nT = (n_after + PT - 1) / PT;
+    return nT * (nT + 1) / 2;
+  };
+  if (h->cfg.multi_launch == 0) {
+    for (int r = 0; r < R; ++r) {
+      loff.push_back((int64_t)h->h_steps.size());
+      int64_t tp = 0;
+      for (int g = 0; g < G; ++g)
+        if ((int)per[g].size() > r) {
+          h->h_steps.push_back(per[g][r]);
+          tp += pairs(per[g][r].n_after);
+        }
+      h->h_count.push_back((int)(h->h_steps.size() - loff.back()));
+      tiles_need = std::max(tiles_need, tp);
+    }
+  } else {
+    for (int g = 0; g < G; ++g)
+      for (const MultiStep& s : per[g]) {
+        loff.push_back((int64_t)h->h_steps.size());
+        h->h_steps.push_back(s);
+        h->h_count.push_back(1);
+        tiles_need = std::max(tiles_need, pairs(s.n_after));
+      }
+  }
+  const int L = (int)h->h_count.size();
+  MCUDA_TRY(h, grow_dev(&h->d_steps, &h->steps_cap, (int64_t)h->h_steps.size()));
+  if (L > h->launch_cap) {
+    if (h->d_count) cudaFree(h->d_count);
+    if (h->d_ntiles) cudaFree(h->d_ntiles);
+    h->d_count = nullptr;
+    h->d_ntiles = nullptr;
+    h->launch_cap = std::max<int64_t>(L, 2 * h->launch_cap);
+    MCUDA_TRY(h, dev_alloc(&h->d_count, (size_t)h->launch_cap));
+    MCUDA_TRY(h, dev_alloc(&h->d_ntiles, (size_t)h->launch_cap));
+  }
+  MCUDA_TRY(h, grow_dev(&h->d_tiles, &h->tiles_cap, tiles_need));
+  MCUDA_TRY(h, grow_dev(&h->d_srcs, &h->srcs_cap, (int64_t)h->h_srcs.size()));
+  MCUDA_TRY(h, grow_dev(&h->d_ops, &h->ops_cap, (int64_t)h->h_ops.size()));
+  MCUDA_TRY(h, cudaMemcpyAsync(h->d_desc, h->h_desc.data(), G * sizeof(MultiGraphDesc),
+                               cudaMemcpyHostToDevice, h->st));
+  MCUDA_TRY(h, cudaMemcpyAsync(h->d_steps, h->h_steps.data(), h->h_steps.size() * sizeof(MultiStep),
+                               cudaMemcpyHostToDevice, h->st));
+  MCUDA_TRY(h, cudaMemcpyAsync(h->d_count, h->h_count.data(), L * sizeof(int),
+                               cudaMemcpyHostToDevice, h->st));
+  MCUDA_TRY(h, cudaMemcpyAsync(h->d_srcs, h->h_srcs.data(), h->h_srcs.size() * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, h->st));
+  if (!h->h_ops.empty())
+    MCUDA_TRY(h, cudaMemcpyAsync(h->d_ops, h->h_ops.data(), h->h_ops.size() * sizeof(PatchOp),
+                                 cudaMemcpyHostToDevice, h->st));
+  // the staging vectors may change once the copies are done
+  MCUDA_TRY(h, cudaStreamSynchronize(h->st));
+
+  if (h->cfg.profile) {
+    multi_harvest(h);
+    MCUDA_TRY(h, cudaMemsetAsync(h->d_ntiles, 0, L * sizeof(int), h->st));
+    for (int l = 0; l < L; ++l) {
+      if (h->ev_used == h->ev.size()) {
+        std::array<cudaEvent_t, 3> a{};
+        for (auto& x : a) MCUDA_TRY(h, cudaEventCreate(&x));
+        h->ev.push_back(a);
+      }
+      auto& e = h->ev[h->ev_used++];
+      const int sp = h->cfg.s_precision;
+      MCUDA_TRY(h, cudaEventRecord(e[0], h->st));
+      launch_multi_prep(sp, h->d_desc, h->d_steps + loff[l], h->d_count + l, h->h_count[l],
+                        h->d_srcs, h->d_ops, h->cfg.C, h->cfg.K, h->cfg.aff ? 1 : 0, h->d_tiles,
+                        h->d_ntiles + l, h->st);
+      MCUDA_TRY(h, cudaEventRecord(e[1], h->st));
+      launch_s_update_multi(sp, h->d_desc, h->d_tiles, h->d_ntiles + l, h->cfg.K + 1, h->counters,
+                            h->num_sms * (sp == 64 ? 1 : 2), h->st);
+      MCUDA_TRY(h, cudaEventRecord(e[2], h->st));
+    }
+  } else {
+    const std::vector<const void*> ptrs = {h->d_desc, h->d_steps, h->d_count, h->d_ntiles,
+                                           h->d_tiles, h->d_srcs, h->d_ops, h->counters};
+    if (!h->exec || h->exec_count != h->h_count || h->exec_ptrs != ptrs) {
+      if (h->exec) cudaGraphExecDestroy(h->exec);
+      h->exec = nullptr;
+      cudaGraph_t graph = nullptr;
+      MCUDA_TRY(h, cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
+      cudaMemsetAsync(h->d_ntiles, 0, L * sizeof(int), h->st);
+      for (int l = 0; l < L; ++l) multi_enqueue(h, l, loff[l], h->h_count[l]);
+      const cudaError_t ce = cudaStreamEndCapture(h->st, &graph);
+      if (ce != cudaSuccess) return mfail(h, SR_ERR_CUDA, std::string("stream capture: ") + cudaGetErrorString(ce));
+      const cudaError_t ie = cudaGraphInstantiate(&h->exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ie != cudaSuccess) {
+        h->exec = nullptr;
+        return mfail(h, SR_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+      }
+      h->exec_count = h->h_count;
+      h->exec_ptrs = ptrs;
+    }
+    MCUDA_TRY(h, cudaGraphLaunch(h->exec, h->st));
+  }
+  const cudaError_t le = cudaGetLastError();
+  if (le != cudaSuccess) return mfail(h, SR_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(le));
+  h->launches += 2 * (int64_t)L;
+  h->sup_launches += L;
+  h->stats.updates += total;
+  h->stats.rank_one_updates += total;
+  return SR_OK;
+}
+
+simrank_status simrank_multi_columns(simrank_multi_t h, int32_t g, const int32_t* cols,
+                                     int32_t ncols, void* out, int32_t out_on_device,
+                                     int32_t out_fp64) {
+  if (!h) return mfail(nullptr, SR_ERR_ARG, "null handle");
+  if (g < 0 || g >= (int)h->g.size()) return mfail(h, SR_ERR_ARG, "graph index out of range");
+  const simrank_status s = simrank_columns(h->g[g], cols, ncols, out, out_on_device, out_fp64);
+  if (s != SR_OK) return mfail(h, s, "graph " + std::to_string(g) + ": " + h->g[g]->err);
+  return SR_OK;
+}
+
+int32_t simrank_multi_num_graphs(simrank_multi_t h) { return h ? (int32_t)h->g.size() : -1; }
+
+int32_t simrank_multi_num_nodes(simrank_multi_t h, int32_t g) {
+  if (!h || g < 0 || g >= (int)h->g.size()) return -1;
+  return h->g[g]->n_cur;
+}
+
+simrank_status simrank_multi_sync(simrank_multi_t h) {
+  if (!h) return mfail(nullptr, SR_ERR_ARG, "null handle");
+  MCUDA_TRY(h, cudaStreamSynchronize(h->st));
+  int64_t status = 0;
+  MCUDA_TRY(h, cudaMemcpy(&status, h->counters + CNT_STATUS, sizeof(status), cudaMemcpyDeviceToHost));
+  if (status != 0) return mfail(h, (simrank_status)status, "a bounded device wait ran out");
+  return SR_OK;
+}
+
+simrank_status simrank_multi_get_stats(simrank_multi_t h, simrank_stats* out) {
+  if (!h || !out) return mfail(h, SR_ERR_ARG, "null argument");
+  MCUDA_TRY(h, cudaStreamSynchronize(h->st));
+  multi_harvest(h);
+  int64_t c[CNT_N];
+  MCUDA_TRY(h, cudaMemcpy(c, h->counters, sizeof(c), cudaMemcpyDeviceToHost));
+  simrank_stats r = h->stats;
+  r.tiles_touched = c[CNT_TILES_TOUCHED];
+  r.s_bytes = c[CNT_S_BYTES];
+  r.panel_bytes = c[CNT_PANEL_BYTES];
+  r.kernel_launches = h->launches;
+  r.s_update_launches = h->sup_launches;
+  r.s_update_ms = h->sup_ms;
+  r.phase_ms[0] = h->prep_ms;
+  r.phase_ms[3] = h->sup_ms;
+  *out = r;
+  return SR_OK;
+}
+
+const char* simrank_multi_last_error(simrank_multi_t h) {
+  return h ? h->err.c_str() : g_init_error.c_str();
+}
+
+void simrank_multi_destroy(simrank_multi_t h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->st);
+  multi_free(h);
+}
+
+}  // extern "C"

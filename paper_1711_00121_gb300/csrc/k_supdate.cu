@@ -54,12 +54,59 @@ __device__ __forceinline__ void st4(T* p, const T (&v)[4]) {
 // that both a row sweep and a column sweep of a warp hit 32 distinct banks.
 constexpr int DP = PT + 1;
 
-template <typename T, int KC, int MINB>
+// One affected tile pair of one graph: where its S and panels live, and the
+// AFF words of the two cross terms (bit k % 64: xi_k[I] eta_k[J]^T resp.
+// eta_k[I] xi_k[J]^T can be nonzero).
+template <typename T>
+struct TileRef {
+  T* S;
+  int64_t ld;
+  const T* P;
+  int I, J, n;
+  uint64_t a1, a2;
+};
+
+// Tile source of one graph: a list of (I << 16 | J) pairs.
+template <typename T>
+struct OneGraphTiles {
+  T* S;
+  int64_t ld;
+  const T* P;
+  const uint32_t* tiles;
+  const uint64_t* mXi;
+  const uint64_t* mEta;
+  int use_masks, n;
+  __device__ __forceinline__ TileRef<T> get(int t) const {
+    const uint32_t pr = tiles[t];
+    const int I = (int)(pr >> 16), J = (int)(pr & 0xffffu);
+    TileRef<T> r{S, ld, P, I, J, n, ~0ull, ~0ull};
+    if (use_masks) {
+      r.a1 = mXi[I] & mEta[J];
+      r.a2 = mEta[I] & mXi[J];
+    }
+    return r;
+  }
+};
+
+// Tile source of many graphs: (g << 32 | I << 16 | J) entries and one
+// descriptor per graph.
+template <typename T>
+struct ManyGraphTiles {
+  const MultiGraphDesc* d;
+  const uint64_t* tiles;
+  __device__ __forceinline__ TileRef<T> get(int t) const {
+    const uint64_t e = tiles[t];
+    const int g = (int)(e >> 32), I = (int)((e >> 16) & 0xffffu), J = (int)(e & 0xffffu);
+    const MultiGraphDesc& q = d[g];
+    return TileRef<T>{(T*)q.S, q.ld, (const T*)q.P, I, J, q.n, q.mXi[I] & q.mEta[J],
+                      q.mEta[I] & q.mXi[J]};
+  }
+};
+
+template <typename T, int KC, int MINB, typename Src>
 __global__ void __launch_bounds__(256, MINB)
-    k_s_update(T* __restrict__ S, int64_t ld, const T* __restrict__ P, int K1,
-               const uint32_t* __restrict__ tiles, const int* __restrict__ ntiles,
-               const uint64_t* __restrict__ mXi, const uint64_t* __restrict__ mEta, int k0g,
-               int k1g, int use_masks, int n, unsigned long long* __restrict__ counters) {
+    k_s_update(Src src, int K1, const int* __restrict__ ntiles, int k0g, int k1g,
+               unsigned long long* __restrict__ counters) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   T* sXiI = reinterpret_cast<T*>(smem_raw);
   T* sEtaI = sXiI + KC * PT;
@@ -71,10 +118,13 @@ __global__ void __launch_bounds__(256, MINB)
   const int nt = *ntiles;
   unsigned long long my_tiles = 0, my_bytes = 0;
   for (int t = blockIdx.x; t < nt; t += gridDim.x) {
-    const uint32_t pr = tiles[t];
-    const int I = (int)(pr >> 16), J = (int)(pr & 0xffffu);
-    const uint64_t a1 = use_masks ? (mXi[I] & mEta[J]) : ~0ull;  // xi_I eta_J^T
-    const uint64_t a2 = use_masks ? (mEta[I] & mXi[J]) : ~0ull;  // eta_I xi_J^T
+    const TileRef<T> tr = src.get(t);
+    T* __restrict__ S = tr.S;
+    const T* __restrict__ P = tr.P;
+    const int64_t ld = tr.ld;
+    const int I = tr.I, J = tr.J, n = tr.n;
+    const uint64_t a1 = tr.a1;  // xi_I eta_J^T
+    const uint64_t a2 = tr.a2;  // eta_I xi_J^T
     T acc[8][8];
 #pragma unroll
     for (int r = 0; r < 8; ++r)
@@ -430,13 +480,13 @@ void launch_s_update(void* S, int s_prec, int64_t ld, const void* P, int K1, con
     const size_t smem = (4ull * KC_F64 * PT + (size_t)PT * DP) * sizeof(double);
     static bool attr64 = false;
     if (!attr64) {
-      cudaFuncSetAttribute(k_s_update<double, KC_F64, 1>,
+      cudaFuncSetAttribute(k_s_update<double, KC_F64, 1, OneGraphTiles<double>>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       attr64 = true;
     }
-    k_s_update<double, KC_F64, 1><<<grid, 256, smem, st>>>(
-        (double*)S, ld, (const double*)P, K1, tiles, ntiles, mXi, mEta, k0, k1, use_masks, n,
-        (unsigned long long*)counters);
+    OneGraphTiles<double> src{(double*)S, ld, (const double*)P, tiles, mXi, mEta, use_masks, n};
+    k_s_update<double, KC_F64, 1><<<grid, 256, smem, st>>>(src, K1, ntiles, k0, k1,
+                                                             (unsigned long long*)counters);
   } else if (ws_wait_limit > 0) {
     const size_t smem = (4ull * WS_KC * PT + 2ull * PT * DP) * sizeof(float);
     static bool attr_ws = false;
@@ -451,13 +501,41 @@ void launch_s_update(void* S, int s_prec, int64_t ld, const void* P, int K1, con
     const size_t smem = (4ull * KC_F32 * PT + (size_t)PT * DP) * sizeof(float);
     static bool attr32 = false;
     if (!attr32) {
-      cudaFuncSetAttribute(k_s_update<float, KC_F32, 2>,
+      cudaFuncSetAttribute(k_s_update<float, KC_F32, 2, OneGraphTiles<float>>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       attr32 = true;
     }
-    k_s_update<float, KC_F32, 2><<<grid, 256, smem, st>>>(
-        (float*)S, ld, (const float*)P, K1, tiles, ntiles, mXi, mEta, k0, k1, use_masks, n,
-        (unsigned long long*)counters);
+    OneGraphTiles<float> src{(float*)S, ld, (const float*)P, tiles, mXi, mEta, use_masks, n};
+    k_s_update<float, KC_F32, 2><<<grid, 256, smem, st>>>(src, K1, ntiles, k0, k1,
+                                                            (unsigned long long*)counters);
+  }
+}
+
+void launch_s_update_multi(int s_prec, const MultiGraphDesc* descs, const uint64_t* tiles,
+                           const int* ntiles, int K1, int64_t* counters, int grid,
+                           cudaStream_t st) {
+  if (s_prec == 64) {
+    const size_t smem = (4ull * KC_F64 * PT + (size_t)PT * DP) * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_s_update<double, KC_F64, 1, ManyGraphTiles<double>>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr = true;
+    }
+    ManyGraphTiles<double> src{descs, tiles};
+    k_s_update<double, KC_F64, 1><<<grid, 256, smem, st>>>(src, K1, ntiles, 0, K1,
+                                                             (unsigned long long*)counters);
+  } else {
+    const size_t smem = (4ull * KC_F32 * PT + (size_t)PT * DP) * sizeof(float);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_s_update<float, KC_F32, 2, ManyGraphTiles<float>>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr = true;
+    }
+    ManyGraphTiles<float> src{descs, tiles};
+    k_s_update<float, KC_F32, 2><<<grid, 256, smem, st>>>(src, K1, ntiles, 0, K1,
+                                                            (unsigned long long*)counters);
   }
 }
 

@@ -147,6 +147,42 @@ struct PrepParams {
 int launch_prep(const PrepParams& p, int s_prec, int npend_max, int num_sms, int max_ctas,
                 cudaStream_t st);
 
+// ---------------------------------------------------------------------------
+// Many independent graphs advanced together (k_multi.cu).
+// ---------------------------------------------------------------------------
+// One graph: its dense S (precision of the handle), tile-blocked panels
+// [T][which][K1][128] in the same precision, AFF words, adjacency, and the
+// sI/sJ scratch rows (n_pad values each).
+struct MultiGraphDesc {
+  void* S;
+  int64_t ld;
+  void* P;
+  uint64_t* mXi;
+  uint64_t* mEta;
+  DevAdj in, out;
+  void* sI;
+  void* sJ;
+  int n;  // current node count (byte counters)
+  int pad_;
+};
+// One rank-one update of graph g in a round: sources srcs[src_off ..
+// src_off + delta) into sink j, op = +1/-1, old in-degree d_j, patch ops
+// [op_begin, op_end), node count after the update n_after.
+struct MultiStep {
+  int32_t g, j, op, d_j, delta, n_after;
+  int64_t src_off, op_begin, op_end;
+};
+// Rank-one work before the S pass for steps[0 .. *count) (one CTA each, grid
+// >= *count): patch, rows of S, gamma, K recurrence steps, masks, and the
+// tile pairs (g << 32 | I << 16 | J) appended to tiles / *ntiles.
+void launch_multi_prep(int s_prec, const MultiGraphDesc* descs, const MultiStep* steps,
+                       const int* count, int grid, const int32_t* srcs, const PatchOp* ops,
+                       double C, int K, int aff, uint64_t* tiles, int* ntiles, cudaStream_t st);
+// S pass over the tile pairs of many graphs (single-role CUDA-core kernel).
+void launch_s_update_multi(int s_prec, const MultiGraphDesc* descs, const uint64_t* tiles,
+                           const int* ntiles, int K1, int64_t* counters, int grid,
+                           cudaStream_t st);
+
 // Affected tile pairs (I <= J) of Thm 4 at tile granularity.
 void launch_tile_list(const uint64_t* mXi, const uint64_t* mEta, int nT, int aff, uint32_t* tiles,
                       int* ntiles, cudaStream_t st);
