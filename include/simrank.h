@@ -109,7 +109,9 @@ typedef struct simrank_config {
                              graphs before their S passes and one S pass over all their tiles,
                              replayed from a CUDA graph; 1 = the same kernels launched graph by
                              graph (the per-graph-launch baseline) */
-  int32_t reserved[2];
+  int32_t prep_item;      /* chain = 0: nonzeros per work item of the fused launch's gathers
+                             (0 = 1024); a tile with more nonzeros is split over several CTAs */
+  int32_t reserved[1];
 } simrank_config;
 
 /* Fills *cfg with defaults: C = 0.6, K = 15, s_precision = 32, dense, aff = 1,

@@ -41,7 +41,8 @@ class Config(ctypes.Structure):
         ("timeout_iters", ctypes.c_int64), ("cuda_stream", ctypes.c_void_p),
         ("s_kernel", ctypes.c_int32), ("defer", ctypes.c_int32), ("chain", ctypes.c_int32),
         ("prep_ctas", ctypes.c_int32), ("prep_cache", ctypes.c_int32),
-        ("multi_launch", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2),
+        ("multi_launch", ctypes.c_int32), ("prep_item", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 1),
     ]
 
 

@@ -63,7 +63,9 @@ struct simrank_ctx {
   double* scal = nullptr;
   int64_t* counters = nullptr;
   unsigned long long* diffbits = nullptr;
-  unsigned int* gbar = nullptr;  // grid barrier state of the cooperative chain kernel
+  unsigned int* gbar = nullptr;  // grid barrier state of the cooperative pre-update kernel
+  void* W = nullptr;             // (xi, eta) working columns of the pre-update kernel
+  int* tile_nnz = nullptr;
   // per-call staging
   int32_t* d_srcs = nullptr;
   int64_t srcs_cap = 0;
@@ -544,11 +546,21 @@ simrank_status run_rank_one(simrank_ctx* h, int64_t src_off, int delta, int j, i
     pp.mXi = h->mXi;
     pp.mEta = h->mEta;
     pp.cap = h->cfg.prep_cache > 0 ? h->cfg.prep_cache : 8192;
+    pp.item = h->cfg.prep_item > 0 ? h->cfg.prep_item : 1024;
+    pp.n_pad = h->n_pad;
+    pp.nT_cap = h->nT_cap;
+    if (!h->W) {
+      CUDA_TRY(h, cudaMalloc(&h->W, (size_t)h->K1 * h->n_pad * 2 * (h->cfg.s_precision / 8)));
+      CUDA_TRY(h, dev_alloc(&h->tile_nnz, (size_t)h->nT_cap));
+    }
+    pp.W = h->W;
+    pp.tile_nnz = h->tile_nnz;
     pp.bar = h->gbar + 2;
     pp.limit = wait_limit(h);
     pp.counters = (unsigned long long*)h->counters;
     const int rc = launch_prep(pp, h->cfg.s_precision, defer ? h->cfg.defer * h->K1 : 0,
-                               h->num_sms, h->cfg.prep_ctas, h->st);
+                               h->num_sms, h->cfg.prep_ctas, (int64_t)h->edges.size() + delta,
+                               h->st);
     if (rc == 1) return fail(h, SR_ERR_CUDA, "fused pre-update launch failed");
     fused = (rc == 0);
     if (fused) {
@@ -1016,7 +1028,7 @@ void free_ctx(simrank_ctx* h) {
                   h->dout.col,  h->d_in_w,   h->d_wsum,    h->S,          h->P64,
                   h->P32,       h->mXi,      h->mEta,      h->tiles,      h->ntiles,
                   h->sI,        h->sJ,       h->scal,      h->counters,   h->diffbits,
-                  h->gbar,
+                  h->gbar,      h->W,        h->tile_nnz,
                   h->d_srcs,    h->d_ops,    h->d_cols,     h->d_ext2int};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -1090,8 +1102,10 @@ simrank_status simrank_init(const simrank_config* cfg_in, int32_t n, int64_t m, 
   if ((int64_t)cfg.n_capacity > (int64_t)65535 * PT)
     return fail(nullptr, SR_ERR_ARG, "n_capacity too large for 16-bit tile indices");
   if (cfg.apply < 0 || cfg.apply > 2) return fail(nullptr, SR_ERR_ARG, "bad apply mode");
-  if (cfg.prep_ctas < 0 || cfg.prep_cache < 0 || cfg.prep_cache > 16384 || cfg.prep_cache % 4)
-    return fail(nullptr, SR_ERR_ARG, "prep_ctas >= 0; prep_cache a multiple of 4 in [0, 16384]");
+  if (cfg.prep_ctas < 0 || cfg.prep_cache < 0 || cfg.prep_cache > 16384 || cfg.prep_cache % 4 ||
+      cfg.prep_item < 0)
+    return fail(nullptr, SR_ERR_ARG,
+                "prep_ctas, prep_item >= 0; prep_cache a multiple of 4 in [0, 16384]");
   if (cfg.defer < 0 || (cfg.defer > 1 && (int64_t)cfg.defer * (cfg.K + 1) > 4096))
     return fail(nullptr, SR_ERR_ARG, "defer * (K + 1) must be at most 4096");
   if (cfg.tc && cfg.s_precision != 32)

@@ -1,25 +1,37 @@
 // Everything one rank-one (sink-block) update does before its S pass, in one
 // cooperative launch:
 //   phase 0  graph patch (Thm 1: row j of the in-adjacency gains / loses the
-//            sources I), and the rows of the current S that gamma reads,
+//            sources I); the rows of the current S that gamma reads,
 //            sI = sum_t S[I_t, *] and sJ = S[j, *], with the panels of updates
-//            whose S pass is still pending added in;
-//   phase 1  gamma (Thm 3 insert, Thm 9 delete, Table 2 sink blocks) written
-//            as eta_0, with xi_0 = C e_j;
+//            whose S pass is still pending added in; per-tile nonzero counts;
+//   phase 1  w = Q sI (the SpMV of Thm 3's preprocessing), then gamma (Thm 3
+//            insert, Thm 9 delete, Table 2 sink blocks) as eta_0, with
+//            xi_0 = C e_j;
 //   phase 2  the K steps of the recurrence on the new graph (Eq. 16a),
 //            xi_{k+1} = C Q xi_k, eta_{k+1} = Q eta_k;
 //   phase 3  the affected-area mask words of every tile (Thm 4) and the list
 //            of affected tile pairs of the S pass.
-// Phases are separated by a bounded grid barrier.  Each CTA owns the tiles
-// blockIdx.x + t * gridDim.x; their row extents and up to `cap` column
-// indices stay in shared memory for all K steps, so a step is one gather of
-// the previous column plus one barrier.  Arithmetic is in the precision of S:
-// FP64 work on GB300 runs at a small fraction of the FP32 rate, and the FP32
-// path stores S and the panels in FP32 anyway.
+// Phases and steps are separated by a bounded grid barrier.
 //
-// gamma needs w = (1/delta) Q_old S_{*,I}; only row j of Q changes, so the
-// kernel gathers on the patched graph and corrects row j by the sources it
-// gained or lost: sum over old in-neighbours = sum over new - op * S_II.
+// Work split.  A gather of one scattered vector element per nonzero is bound
+// by the L1 throughput of the SM that issues it, so the nonzeros, not the
+// rows, are spread evenly: every 128-row tile is cut into items of at most
+// `item` flattened nonzeros, and items go round-robin to the CTAs (a hub row
+// with thousands of in-neighbours spreads over many SMs).  Each CTA keeps the
+// row extents and column indices of its first items in shared memory for all
+// K steps.  Partial row sums are combined within a warp and added to the next
+// column with global atomics.  xi_k and eta_k are kept interleaved in the
+// working buffer W[k][a] (one 8- or 16-byte load per nonzero).  Row-wise work
+// (gamma, the copy of each finished column into the tile-blocked panels that
+// the S pass reads, the masks) goes by tiles, round-robin.
+//
+// gamma needs w on the OLD graph; only row j of Q changes, so the kernel
+// gathers on the patched graph and corrects row j: the sum over the old
+// in-neighbours = the sum over the new ones - op * S_II.
+//
+// Arithmetic is in the precision of S (lambda and row j of gamma in FP64).
+// The atomic accumulation makes the last bit of a result depend on the order
+// of the additions.
 #include <algorithm>
 
 #include "sr_internal.h"
@@ -29,17 +41,22 @@ namespace sr {
 namespace {
 
 constexpr int PG = 512;     // threads of a prep CTA
-constexpr int PREP_MT = 8;  // tiles one CTA may own
+constexpr int PREP_MT = 8;  // tiles one CTA may own for row-wise work
+constexpr int MAXI = 6;     // items whose row extents stay in shared memory
 
-struct alignas(16) PrepTile {
+template <typename V>
+struct V2 {
+  V x, y;
+};
+
+struct alignas(16) PrepItem {
   int64_t start[PT];
   int len[PT];
   int off[PT + 1];
-  int cbase;          // first cached column index of this tile in the CTA's cache
-  int clen;           // flattened nonzeros [0, clen) of the tile are cached
-  int pad_;
-  uint64_t mask[2];   // this update's AFF words: bit k % 64 set if xi_k / eta_k has a
-                      // nonzero in the tile
+  int T;       // tile
+  int e0, e1;  // flattened nonzeros [e0, e1) of the tile
+  int cbase;   // nonzeros [e0, e0 + clen) have their column index at cc[cbase ...]
+  int clen;
 };
 
 __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
@@ -73,60 +90,119 @@ __device__ __forceinline__ bool prep_barrier(unsigned int* count, unsigned int t
   return *s_ok != 0;
 }
 
-template <int NV, typename V>
-__device__ __forceinline__ void seg_flush(int key, V (&val)[NV], V (*acc)[PT]) {
+__device__ __forceinline__ void red_add(float* p, float v) { atomicAdd(p, v); }
+__device__ __forceinline__ void red_add(double* p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void red_add2(V2<float>* p, float x, float y) {
+  atomicAdd(reinterpret_cast<float2*>(p), make_float2(x, y));
+}
+__device__ __forceinline__ void red_add2(V2<double>* p, double x, double y) {
+  atomicAdd(&p->x, x);
+  atomicAdd(&p->y, y);
+}
+__device__ __forceinline__ V2<float> ld_v2(const V2<float>* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return V2<float>{v.x, v.y};
+}
+__device__ __forceinline__ V2<double> ld_v2(const V2<double>* p) {
+  const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return V2<double>{v.x, v.y};
+}
+
+// Row extents of tile T (after the patch) and the exclusive scan of their lengths.
+__device__ __forceinline__ void item_rows_load(const DevAdj& in, int T, PrepItem& it) {
+  const int tid = threadIdx.x;
+  if (tid < PT) {
+    it.start[tid] = __ldcg(in.start + (int64_t)T * PT + tid);
+    it.len[tid] = __ldcg(in.len + (int64_t)T * PT + tid);
+  }
+  __syncthreads();
+  if (tid < 32) {
+    int v[4], sum = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      v[q] = it.len[tid * 4 + q];
+      sum += v[q];
+    }
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (tid >= o) incl += y;
+    }
+    int run = incl - sum;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      it.off[tid * 4 + q] = run;
+      run += v[q];
+    }
+    if (tid == 31) it.off[PT] = incl;
+  }
+  __syncthreads();
+}
+
+// Item q of the launch: its tile (the last T with ioff[T] <= q) and range.
+__device__ __forceinline__ void item_locate(const DevAdj& in, const int* ioff, int nT, int q,
+                                            int item, PrepItem& it) {
+  int lo = 0, hi = nT;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (ioff[mid] <= q) lo = mid; else hi = mid;
+  }
+  item_rows_load(in, lo, it);
+  if (threadIdx.x == 0) {
+    it.T = lo;
+    it.e0 = (q - ioff[lo]) * item;
+    it.e1 = min(it.off[PT], it.e0 + item);
+    it.cbase = 0;
+    it.clen = 0;
+  }
+  __syncthreads();
+}
+
+// Combines per-lane partials of equal row keys across a warp (keys are
+// non-decreasing with the lane; key < 0 = nothing) and hands each segment's
+// nonzero total to emit(key, a, b) once.
+template <typename V, typename Emit>
+__device__ __forceinline__ void seg_emit(int key, V a, V b, Emit emit) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const int k2 = __shfl_down_sync(0xffffffffu, key, o);
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const V x = __shfl_down_sync(0xffffffffu, val[v], o);
-      if (lane + o < 32 && k2 == key) val[v] += x;
+    const V xa = __shfl_down_sync(0xffffffffu, a, o);
+    const V xb = __shfl_down_sync(0xffffffffu, b, o);
+    if (lane + o < 32 && k2 == key) {
+      a += xa;
+      b += xb;
     }
   }
   const int kprev = __shfl_up_sync(0xffffffffu, key, 1);
-  if (key >= 0 && (lane == 0 || kprev != key)) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v)
-      if (val[v] != V(0)) atomicAdd(&acc[v][key], val[v]);
-  }
+  if (key >= 0 && (lane == 0 || kprev != key) && (a != V(0) || b != V(0))) emit(key, a, b);
 }
 
-// acc[v][r] = sum over the in-neighbours b of row r of tile `tr` of gather(v, b).
-// The tile's nonzeros are flattened and split into one contiguous run per
-// thread (hub rows spread over the whole CTA); rows wholly inside a run are
-// stored directly, the first and last row of a run are combined across lanes
-// by seg_flush.  Column indices come from the shared cache where cached.
-template <int NV, typename V, typename Gf>
-__device__ __forceinline__ void prep_gather(const PrepTile& tr, const int* __restrict__ cc,
+// Sums gather(b) over the nonzeros [e0, e1) of the item's tile, per row, and
+// calls emit(r, a, b) with each row's (partial) sums.  The range is split into
+// one contiguous run per thread; a row wholly inside one run is emitted by
+// that thread, the first and last row of a run go through seg_emit.
+template <typename V, typename Gf, typename Emit>
+__device__ __forceinline__ void item_gather(const PrepItem& it, const int* __restrict__ cc,
                                             const int32_t* __restrict__ col, Gf gather,
-                                            V (*acc)[PT]) {
+                                            Emit emit) {
   const int tid = threadIdx.x;
-  if (tid < PT) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v][tid] = V(0);
-  }
-  __syncthreads();
-  const int total = tr.off[PT];
-  const int per = (total + PG - 1) / PG;
-  const int e0 = tid * per;
-  const int e1 = min(total, e0 + per);
+  const int n_e = it.e1 - it.e0;
+  const int per = (n_e + PG - 1) / PG;
+  const int e0 = it.e0 + tid * per;
+  const int e1 = min(it.e1, e0 + per);
   int r_first = -1, r_last = -1;
-  V pf[NV], pl[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) pf[v] = pl[v] = V(0);
+  V fa = V(0), fb = V(0), la = V(0), lb = V(0);
   if (e0 < e1) {
     int lo = 0, hi = PT;
     while (hi - lo > 1) {
       const int mid = (lo + hi) >> 1;
-      if (tr.off[mid] <= e0) lo = mid; else hi = mid;
+      if (it.off[mid] <= e0) lo = mid; else hi = mid;
     }
     int r = lo;
     r_first = r;
-    V part[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) part[v] = V(0);
+    V pa = V(0), pb = V(0);
     constexpr int B = 8;
     for (int e = e0; e < e1; e += B) {
       int rr[B], bb[B];
@@ -135,51 +211,47 @@ __device__ __forceinline__ void prep_gather(const PrepTile& tr, const int* __res
       for (int q = 0; q < B; ++q) {
         const int ee = e + q;
         if (ee < e1) {
-          while (ee >= tr.off[rc + 1]) ++rc;
+          while (ee >= it.off[rc + 1]) ++rc;
           rr[q] = rc;
-          bb[q] = (ee < tr.clen) ? cc[tr.cbase + ee]
-                                 : __ldcg(col + tr.start[rc] + (ee - tr.off[rc]));
+          const int ce = ee - it.e0;
+          bb[q] = (ce < it.clen) ? cc[it.cbase + ce]
+                                 : __ldcg(col + it.start[rc] + (ee - it.off[rc]));
         } else {
           rr[q] = -1;
           bb[q] = 0;
         }
       }
-      V xv[NV][B];
+      V2<V> xv[B];
 #pragma unroll
-      for (int q = 0; q < B; ++q)
-#pragma unroll
-        for (int v = 0; v < NV; ++v) xv[v][q] = (rr[q] >= 0) ? gather(v, bb[q]) : V(0);
+      for (int q = 0; q < B; ++q) xv[q] = (rr[q] >= 0) ? gather(bb[q]) : V2<V>{V(0), V(0)};
 #pragma unroll
       for (int q = 0; q < B; ++q) {
         if (rr[q] < 0) break;
         if (rr[q] != r) {
           if (r == r_first) {
-#pragma unroll
-            for (int v = 0; v < NV; ++v) pf[v] = part[v];
-          } else {
-#pragma unroll
-            for (int v = 0; v < NV; ++v) acc[v][r] = part[v];
+            fa = pa;
+            fb = pb;
+          } else if (pa != V(0) || pb != V(0)) {
+            emit(r, pa, pb);  // row wholly inside this run
           }
-#pragma unroll
-          for (int v = 0; v < NV; ++v) part[v] = V(0);
+          pa = pb = V(0);
           r = rr[q];
         }
-#pragma unroll
-        for (int v = 0; v < NV; ++v) part[v] += xv[v][q];
+        pa += xv[q].x;
+        pb += xv[q].y;
       }
     }
     if (r == r_first) {
-#pragma unroll
-      for (int v = 0; v < NV; ++v) pf[v] = part[v];
+      fa = pa;
+      fb = pb;
     } else {
       r_last = r;
-#pragma unroll
-      for (int v = 0; v < NV; ++v) pl[v] = part[v];
+      la = pa;
+      lb = pb;
     }
   }
-  seg_flush<NV, V>(r_first, pf, acc);
-  seg_flush<NV, V>(r_last, pl, acc);
-  __syncthreads();
+  seg_emit<V>(r_first, fa, fb, emit);
+  seg_emit<V>(r_last, la, lb, emit);
 }
 
 __device__ void prep_patch(const PatchOp* __restrict__ ops, int64_t begin, int64_t end,
@@ -208,22 +280,27 @@ __device__ void prep_patch(const PatchOp* __restrict__ ops, int64_t begin, int64
 }
 
 template <typename V>
-__global__ void __launch_bounds__(PG, 1) k_prep(PrepParams p) {
+__global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
   extern __shared__ __align__(16) unsigned char dsm[];
-  __shared__ V acc[2][PT];
   __shared__ V red[4][2][PT];
+  __shared__ unsigned long long mk[PREP_MT][2];
+  __shared__ int wsum[PG / 32];
   __shared__ int s_ok;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int G = gridDim.x;
   const int nT = p.nT;
   const int mt = (nT + G - 1) / G;
-  PrepTile* tr = reinterpret_cast<PrepTile*>(dsm);
-  int* cc = reinterpret_cast<int*>(tr + mt);
-  V* coef = reinterpret_cast<V*>(cc + p.cap);
+  // dynamic shared memory: item slots, column cache, item offsets, pending coefficients
+  PrepItem* items = reinterpret_cast<PrepItem*>(dsm);
+  int* cc = reinterpret_cast<int*>(items + (MAXI + 1));
+  int* ioff = cc + p.cap;  // [nT + 1]
+  V* coef = reinterpret_cast<V*>(ioff + ((p.nT_cap + 1 + 3) & ~3));
   const V* __restrict__ S = static_cast<const V*>(p.S);
   V* P = static_cast<V*>(p.P);
   V* sI = static_cast<V*>(p.sI);
   V* sJ = static_cast<V*>(p.sJ);
+  V2<V>* W = static_cast<V2<V>*>(p.W);
+  const int nrows = nT * PT;
   const int64_t ldk = p.ldk;
   auto pidx = [ldk](int64_t a, int which, int k) -> int64_t {
     return (((a / PT) * 2 + which) * ldk + k) * PT + (a % PT);
@@ -231,13 +308,20 @@ __global__ void __launch_bounds__(PG, 1) k_prep(PrepParams p) {
   const int np = p.npend;
   const int koff = p.koff;
   const V Cv = (V)p.C;
+  const int K = p.K;
+  const int new_len_j = p.d_j + p.op * p.delta;
   unsigned int nb = 0;
   bool alive = true;
 
-  // ---- phase 0: patch (CTA 0) and the rows sI, sJ of the current S
+  // ---- phase 0: patch (CTA 0), zero W, rows sI / sJ, tile nonzero counts
   if (blockIdx.x == 0) {
     if (p.op_end > p.op_begin) prep_patch(p.ops, p.op_begin, p.op_end, p.in, p.out);
     if (tid == 0 && p.tiles) *p.ntiles = 0;
+  }
+  {
+    const int64_t total = (int64_t)(K + 1) * nrows;
+    for (int64_t e = (int64_t)blockIdx.x * PG + tid; e < total; e += (int64_t)G * PG)
+      W[(e / nrows) * (int64_t)p.n_pad + (e % nrows)] = V2<V>{V(0), V(0)};
   }
   if (np > 0) {
     // c_x[q] = sum_t xi_q[I_t], c_e[q] = sum_t eta_q[I_t]; the same at j
@@ -255,90 +339,117 @@ __global__ void __launch_bounds__(PG, 1) k_prep(PrepParams p) {
     }
     __syncthreads();
   }
-  {
+  for (int t = 0; t < mt; ++t) {
+    const int T = blockIdx.x + t * G;
+    if (T >= nT) break;
     const int r = tid & (PT - 1), part = tid >> 7;
-    for (int t = 0; t < mt; ++t) {
-      const int T = blockIdx.x + t * G;
-      if (T >= nT) break;
-      const int64_t a = (int64_t)T * PT + r;
-      V vI = V(0), vJ = V(0);
-      for (int u = part; u < p.delta; u += 4) vI += S[(int64_t)p.I[u] * p.ld + a];
-      if (part == 3) vJ = S[(int64_t)p.j * p.ld + a];
-      // S_cur[x, a] = S[x, a] + sum_q xi_q[x] eta_q[a] + eta_q[x] xi_q[a]
-      for (int q = part; q < np; q += 4) {
-        const V xa = P[pidx(a, 0, q)];
-        const V ea = P[pidx(a, 1, q)];
-        vI += coef[q] * ea + coef[np + q] * xa;
-        vJ += coef[2 * np + q] * ea + coef[3 * np + q] * xa;
-      }
-      red[part][0][r] = vI;
-      red[part][1][r] = vJ;
-      __syncthreads();
-      if (tid < PT) {
-        sI[a] = (red[0][0][r] + red[1][0][r]) + (red[2][0][r] + red[3][0][r]);
-        sJ[a] = (red[0][1][r] + red[1][1][r]) + (red[2][1][r] + red[3][1][r]);
-      }
-      __syncthreads();
+    const int64_t a = (int64_t)T * PT + r;
+    V vI = V(0), vJ = V(0);
+    for (int u = part; u < p.delta; u += 4) vI += S[(int64_t)p.I[u] * p.ld + a];
+    if (part == 3) vJ = S[(int64_t)p.j * p.ld + a];
+    // S_cur[x, a] = S[x, a] + sum_q xi_q[x] eta_q[a] + eta_q[x] xi_q[a]
+    for (int q = part; q < np; q += 4) {
+      const V xa = P[pidx(a, 0, q)];
+      const V ea = P[pidx(a, 1, q)];
+      vI += coef[q] * ea + coef[np + q] * xa;
+      vJ += coef[2 * np + q] * ea + coef[3 * np + q] * xa;
     }
+    red[part][0][r] = vI;
+    red[part][1][r] = vJ;
+    // nonzeros of the tile after the patch (row j is being patched by CTA 0:
+    // it counts with its new length; no other row's length changes)
+    int L = 0;
+    if (part == 0) L = (a == p.j) ? new_len_j : p.in.len[a];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) L += __shfl_xor_sync(0xffffffffu, L, o);
+    if (lane == 0) wsum[warp] = L;
+    __syncthreads();
+    if (tid < PT) {
+      sI[a] = (red[0][0][r] + red[1][0][r]) + (red[2][0][r] + red[3][0][r]);
+      sJ[a] = (red[0][1][r] + red[1][1][r]) + (red[2][1][r] + red[3][1][r]);
+    }
+    if (tid == 0) p.tile_nnz[T] = (wsum[0] + wsum[1]) + (wsum[2] + wsum[3]);
+    __syncthreads();
   }
   alive = prep_barrier(p.bar, ++nb * G, p.limit, &s_ok);
 
-  // ---- phase 1: tile rows of the new graph, column cache, gamma
+  // ---- phase 1: item table; w = Q sI summed by atomics into W[0].x
+  int my_items = 0;
   if (alive) {
+    {
+      // ioff[T] = items of tiles before T (tile T has ceil(nnz_T / item) items)
+      const int per = (nT + PG - 1) / PG;
+      const int t0 = min(nT, tid * per), t1 = min(nT, t0 + per);
+      int s = 0;
+      for (int T = t0; T < t1; ++T) s += (__ldcg(p.tile_nnz + T) + p.item - 1) / p.item;
+      int incl = s;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      if (lane == 31) wsum[warp] = incl;
+      __syncthreads();
+      if (warp == 0) {
+        const int v = (lane < PG / 32) ? wsum[lane] : 0;
+        int w = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, w, o);
+          if (lane >= o) w += y;
+        }
+        if (lane < PG / 32) wsum[lane] = w - v;
+        if (lane == PG / 32 - 1) ioff[nT] = w;
+      }
+      __syncthreads();
+      int run = wsum[warp] + incl - s;
+      for (int T = t0; T < t1; ++T) {
+        ioff[T] = run;
+        run += (__ldcg(p.tile_nnz + T) + p.item - 1) / p.item;
+      }
+      __syncthreads();
+    }
+    const int n_items = ioff[nT];
+    my_items = (n_items > (int)blockIdx.x) ? (n_items - (int)blockIdx.x + G - 1) / G : 0;
     int cbase = 0;
+    for (int u = 0; u < my_items; ++u) {
+      PrepItem& it = items[min(u, MAXI)];
+      item_locate(p.in, ioff, nT, blockIdx.x + u * G, p.item, it);
+      if (u < MAXI) {
+        const int clen = max(0, min(it.e1 - it.e0, p.cap - cbase));
+        // cache the column indices of [e0, e0 + clen), one warp per row
+        for (int r = warp; r < PT; r += PG / 32) {
+          const int o = it.off[r];
+          const int s0 = max(o, it.e0), s1 = min(o + it.len[r], it.e0 + clen);
+          for (int e = s0 + lane; e < s1; e += 32)
+            cc[cbase + (e - it.e0)] = __ldcg(p.in.col + it.start[r] + (e - o));
+        }
+        __syncthreads();
+        if (tid == 0) {
+          it.cbase = cbase;
+          it.clen = clen;
+        }
+        cbase += clen;
+        __syncthreads();
+      }
+      const int64_t rb = (int64_t)it.T * PT;
+      item_gather<V>(it, cc, p.in.col, [&](int b) { return V2<V>{__ldcg(sI + b), V(0)}; },
+                     [&](int r, V a, V) { red_add(&W[rb + r].x, a); });
+      __syncthreads();
+    }
+    alive = prep_barrier(p.bar, ++nb * G, p.limit, &s_ok);
+  }
+
+  // ---- phase 1b: gamma per row (tiles round-robin); W[0] = (xi_0, eta_0)
+  if (alive) {
     for (int t = 0; t < mt; ++t) {
       const int T = blockIdx.x + t * G;
       if (T >= nT) break;
-      PrepTile& tt = tr[t];
-      if (tid < PT) {
-        tt.start[tid] = __ldcg(p.in.start + (int64_t)T * PT + tid);
-        tt.len[tid] = __ldcg(p.in.len + (int64_t)T * PT + tid);
-      }
-      __syncthreads();
-      if (tid < 32) {
-        int v[4], sum = 0;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          v[q] = tt.len[tid * 4 + q];
-          sum += v[q];
-        }
-        int incl = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(0xffffffffu, incl, o);
-          if (tid >= o) incl += y;
-        }
-        int run = incl - sum;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          tt.off[tid * 4 + q] = run;
-          run += v[q];
-        }
-        if (tid == 31) {
-          tt.off[PT] = incl;
-          tt.cbase = cbase;
-          tt.clen = max(0, min(incl, p.cap - cbase));
-          tt.mask[0] = tt.mask[1] = 0ull;
-        }
-      }
-      __syncthreads();
-      const int clen = tt.clen;
-      {
-        const int lane = tid & 31, warp = tid >> 5;
-        for (int r = warp; r < PT; r += PG / 32) {
-          const int o = tt.off[r];
-          if (o >= clen) break;
-          const int L = min(tt.len[r], clen - o);
-          for (int e = lane; e < L; e += 32) cc[cbase + o + e] = __ldcg(p.in.col + tt.start[r] + e);
-        }
-      }
-      cbase += clen;
-      __syncthreads();
-      prep_gather<1, V>(tt, cc, p.in.col, [&](int, int b) { return __ldcg(sI + b); }, acc);
       int pe = 0;
       if (tid < PT) {
         const int64_t a = (int64_t)T * PT + tid;
-        const int len = tt.len[tid];
+        const int len = __ldcg(p.in.len + a);
+        const V y = __ldcg(&W[a].x);
         const double dl = (double)p.delta;
         V g;
         if (a == p.j) {
@@ -348,8 +459,7 @@ __global__ void __launch_bounds__(PG, 1) k_prep(PrepParams p) {
           const double S_jj = (double)__ldcg(sJ + p.j);
           const double C = p.C;
           const double wj =
-              (p.d_j > 0) ? ((double)acc[0][tid] - (double)p.op * S_II) / (dl * (double)p.d_j)
-                          : 0.0;
+              (p.d_j > 0) ? ((double)y - (double)p.op * S_II) / (dl * (double)p.d_j) : 0.0;
           const double lam = S_II / (dl * dl) + S_jj / C - 2.0 * wj - 1.0 / C + 1.0;
           double gd;
           if (p.op > 0) {
@@ -369,67 +479,69 @@ __global__ void __launch_bounds__(PG, 1) k_prep(PrepParams p) {
           }
           g = (V)gd;
         } else {
-          const V w = (len > 0) ? acc[0][tid] / ((V)p.delta * (V)len) : V(0);
+          const V w = (len > 0) ? y / ((V)p.delta * (V)len) : V(0);
           const V sJa = __ldcg(sJ + a);
           if (p.op > 0) {
-            if (p.d_j == 0) {
-              g = w;
-            } else {
-              const V dd = (V)(p.d_j + p.delta);
-              g = ((V)p.delta / dd) * (w - sJa / Cv);
-            }
+            g = (p.d_j == 0) ? w : ((V)p.delta / (V)(p.d_j + p.delta)) * (w - sJa / Cv);
           } else {
-            if (p.d_j == p.delta) {
-              g = -w;
-            } else {
-              const V dd = (V)(p.d_j - p.delta);
-              g = ((V)p.delta / dd) * (sJa / Cv - w);
-            }
+            g = (p.d_j == p.delta) ? -w : ((V)p.delta / (V)(p.d_j - p.delta)) * (sJa / Cv - w);
           }
         }
-        P[pidx(a, 0, koff)] = (a == p.j) ? Cv : V(0);
+        const V x0 = (a == p.j) ? Cv : V(0);
+        W[a] = V2<V>{x0, g};
+        P[pidx(a, 0, koff)] = x0;
         P[pidx(a, 1, koff)] = g;
         pe = (g != V(0));
       }
       const int any_e = __syncthreads_or(pe);
       if (tid == 0) {
-        tt.mask[0] = (T == p.j / PT) ? 1ull : 0ull;
-        tt.mask[1] = any_e ? 1ull : 0ull;
+        mk[t][0] = (T == p.j / PT) ? 1ull : 0ull;
+        mk[t][1] = any_e ? 1ull : 0ull;
       }
     }
-    if (p.K > 0) alive = prep_barrier(p.bar, ++nb * G, p.limit, &s_ok);
+    if (K > 0) alive = prep_barrier(p.bar, ++nb * G, p.limit, &s_ok);
   }
 
-  // ---- phase 2: K steps of the recurrence on the new graph
-  for (int k = 0; alive && k < p.K; ++k) {
-    const int kc = koff + k;
-    for (int t = 0; t < mt; ++t) {
-      const int T = blockIdx.x + t * G;
-      if (T >= nT) break;
-      PrepTile& tt = tr[t];
-      prep_gather<2, V>(tt, cc, p.in.col,
-                        [&](int v, int b) { return __ldcg(P + pidx(b, v, kc)); }, acc);
-      int px = 0, pe = 0;
-      if (tid < PT) {
-        const int len = tt.len[tid];
-        const V inv = (len > 0) ? V(1) / (V)len : V(0);
-        const V x = Cv * acc[0][tid] * inv;
-        const V y = acc[1][tid] * inv;
-        const int64_t a = (int64_t)T * PT + tid;
-        P[pidx(a, 0, kc + 1)] = x;
-        P[pidx(a, 1, kc + 1)] = y;
-        px = (x != V(0));
-        pe = (y != V(0));
-      }
-      const int ax = __syncthreads_or(px);
-      const int ae = __syncthreads_or(pe);
-      if (tid == 0) {
-        const uint64_t bit = 1ull << ((k + 1) & 63);
-        if (ax) tt.mask[0] |= bit;
-        if (ae) tt.mask[1] |= bit;
+  // ---- phase 2: K steps; step k first copies the finished column k into P
+  for (int k = 0; alive && k <= K; ++k) {
+    if (k >= 1) {
+      const V2<V>* Wk = W + (int64_t)k * p.n_pad;
+      const unsigned long long bit = 1ull << (k & 63);
+      for (int t = 0; t < mt; ++t) {
+        const int T = blockIdx.x + t * G;
+        if (T >= nT) break;
+        int px = 0, pe = 0;
+        if (tid < PT) {
+          const int64_t a = (int64_t)T * PT + tid;
+          const V2<V> v = ld_v2(Wk + a);
+          P[pidx(a, 0, koff + k)] = v.x;
+          P[pidx(a, 1, koff + k)] = v.y;
+          px = (v.x != V(0));
+          pe = (v.y != V(0));
+        }
+        const int ax = __syncthreads_or(px);
+        const int ae = __syncthreads_or(pe);
+        if (tid == 0) {
+          if (ax) mk[t][0] |= bit;
+          if (ae) mk[t][1] |= bit;
+        }
       }
     }
-    if (k + 1 < p.K) alive = prep_barrier(p.bar, ++nb * G, p.limit, &s_ok);
+    if (k == K) break;
+    const V2<V>* Wk = W + (int64_t)k * p.n_pad;
+    V2<V>* Wn = W + (int64_t)(k + 1) * p.n_pad;
+    for (int u = 0; u < my_items; ++u) {
+      PrepItem& it = items[min(u, MAXI)];
+      if (u >= MAXI) item_locate(p.in, ioff, nT, blockIdx.x + u * G, p.item, it);
+      const int64_t rb = (int64_t)it.T * PT;
+      item_gather<V>(it, cc, p.in.col, [&](int b) { return ld_v2(Wk + b); },
+                     [&](int r, V a, V b) {
+                       const V inv = V(1) / (V)it.len[r];
+                       red_add2(Wn + rb + r, Cv * a * inv, b * inv);
+                     });
+      __syncthreads();
+    }
+    alive = prep_barrier(p.bar, ++nb * G, p.limit, &s_ok);
   }
 
   // ---- phase 3: mask words and the affected tile pairs
@@ -439,11 +551,11 @@ __global__ void __launch_bounds__(PG, 1) k_prep(PrepParams p) {
       for (int t = 0; t < mt; ++t) {
         const int T = blockIdx.x + t * G;
         if (T >= nT) break;
-        p.mXi[T] = tr[t].mask[0];
-        p.mEta[T] = tr[t].mask[1];
+        p.mXi[T] = mk[t][0];
+        p.mEta[T] = mk[t][1];
         if (p.pXi) {
-          if (tr[t].mask[0]) p.pXi[T] = 1ull;
-          if (tr[t].mask[1]) p.pEta[T] = 1ull;
+          if (mk[t][0]) p.pXi[T] = 1ull;
+          if (mk[t][1]) p.pEta[T] = 1ull;
         }
       }
     }
@@ -452,13 +564,14 @@ __global__ void __launch_bounds__(PG, 1) k_prep(PrepParams p) {
       if (alive) {
         const unsigned long long* mx = reinterpret_cast<const unsigned long long*>(p.mXi);
         const unsigned long long* me = reinterpret_cast<const unsigned long long*>(p.mEta);
-        const int lane = tid & 31;
         for (int I = blockIdx.x; I < nT; I += G) {
           const unsigned long long xi = __ldcg(mx + I), ei = __ldcg(me + I);
           for (int J0 = I; J0 < nT; J0 += PG) {
             const int J = J0 + tid;
             bool act = false;
-            if (J < nT) act = (p.tile_mode == 0) || (((xi & __ldcg(me + J)) | (ei & __ldcg(mx + J))) != 0ull);
+            if (J < nT)
+              act = (p.tile_mode == 0) ||
+                    (((xi & __ldcg(me + J)) | (ei & __ldcg(mx + J))) != 0ull);
             const unsigned mask = __ballot_sync(0xffffffffu, act);
             if (mask == 0) continue;
             const int leader = __ffs(mask) - 1;
@@ -466,7 +579,8 @@ __global__ void __launch_bounds__(PG, 1) k_prep(PrepParams p) {
             if (lane == leader) base = atomicAdd(p.ntiles, __popc(mask));
             base = __shfl_sync(0xffffffffu, base, leader);
             if (act)
-              p.tiles[base + __popc(mask & ((1u << lane) - 1u))] = ((uint32_t)I << 16) | (uint32_t)J;
+              p.tiles[base + __popc(mask & ((1u << lane) - 1u))] =
+                  ((uint32_t)I << 16) | (uint32_t)J;
           }
         }
       }
@@ -488,27 +602,30 @@ __global__ void __launch_bounds__(PG, 1) k_prep(PrepParams p) {
 }
 
 template <typename V>
-size_t prep_smem(int mt, int cap, int npend_max) {
-  return (size_t)mt * sizeof(PrepTile) + (size_t)cap * sizeof(int) +
-         (size_t)4 * npend_max * sizeof(V);
+size_t prep_smem(int cap, int nT_cap, int npend_max) {
+  return (size_t)(MAXI + 1) * sizeof(PrepItem) + (size_t)cap * sizeof(int) +
+         (size_t)((nT_cap + 1 + 3) & ~3) * sizeof(int) + (size_t)4 * npend_max * sizeof(V);
 }
 
 }  // namespace
 
 int launch_prep(const PrepParams& prm, int s_prec, int npend_max, int num_sms, int max_ctas,
-                cudaStream_t st) {
+                int64_t nnz_bound, cudaStream_t st) {
   if (prm.nT <= 0) return 0;
-  const size_t smem = (s_prec == 64) ? prep_smem<double>(PREP_MT, prm.cap, npend_max)
-                                     : prep_smem<float>(PREP_MT, prm.cap, npend_max);
+  if (prm.item <= 0 || prm.cap < 0 || (prm.cap & 3)) return 1;
+  const size_t smem = (s_prec == 64) ? prep_smem<double>(prm.cap, prm.nT_cap, npend_max)
+                                     : prep_smem<float>(prm.cap, prm.nT_cap, npend_max);
   const void* fn = (s_prec == 64) ? (const void*)k_prep<double> : (const void*)k_prep<float>;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 1;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PG, smem) != cudaSuccess ||
-      per_sm <= 0)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PG, smem) != cudaSuccess)
     return 1;
-  int grid = std::min(prm.nT, per_sm * num_sms);
+  if (per_sm <= 0) return 2;
+  // as many CTAs as there are items (at most all co-resident ones)
+  const int64_t items = (int64_t)prm.nT + nnz_bound / prm.item;
+  int grid = (int)std::min<int64_t>(std::max<int64_t>(items, prm.nT), (int64_t)per_sm * num_sms);
   if (max_ctas > 0) grid = std::min(grid, max_ctas);
   if ((prm.nT + grid - 1) / grid > PREP_MT) return 2;
   if (prm.npend > npend_max) return 1;

@@ -116,8 +116,12 @@ void launch_chain_step(const DevAdj& in, int k, double C, int nT, int K1, double
 // mask words mXi/mEta of tiles [0, nT) (ORed as 0/1 into pXi/pEta when
 // those are set) and, when `tiles` is set, the tile-pair list (tile_mode 0 =
 // all pairs, 1 = AFF-pruned).  P is tile-blocked [T][which][ldk][128] in the
-// precision of S; sI, sJ hold n_pad values of that precision.  bar: two
-// zeroed unsigned ints, left zeroed.  Returns 0 on launch, 2 when the graph
+// precision of S; sI, sJ hold n_pad values of that precision; W is the
+// working buffer [K+1][n_pad] of (xi, eta) pairs of that precision; tile_nnz
+// holds nT_cap ints.  Gathers are split into items of at most `item`
+// nonzeros; `cap` column indices are cached per CTA (a multiple of 4).
+// bar: two zeroed unsigned ints, left zeroed.  nnz_bound bounds the edges of
+// the new graph (it sizes the grid).  Returns 0 on launch, 2 when the graph
 // has more tiles than the co-resident CTAs can own (use the per-step path),
 // 1 on a launch error.
 struct PrepParams {
@@ -139,13 +143,17 @@ struct PrepParams {
   uint32_t* tiles;
   int* ntiles;
   int tile_mode;
-  int cap;  // column indices cached per CTA
+  int cap;
+  int item;
+  int n_pad, nT_cap;
+  void* W;
+  int* tile_nnz;
   unsigned int* bar;
   long long limit;
   unsigned long long* counters;
 };
 int launch_prep(const PrepParams& p, int s_prec, int npend_max, int num_sms, int max_ctas,
-                cudaStream_t st);
+                int64_t nnz_bound, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Many independent graphs advanced together (k_multi.cu).

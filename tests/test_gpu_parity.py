@@ -120,7 +120,8 @@ def test_unit_update_converged_vs_batch_recompute(P, case):
 
 @pytest.mark.parametrize("variant", ["fused_aff", "fused_aff_norelabel", "fused_single_role",
                                      "fused_noaff", "plain", "deferred_ffma", "deferred_tc",
-                                     "per_step_chain", "prep_multi_tile", "deferred_multi_tile"])
+                                     "per_step_chain", "prep_multi_tile", "prep_small_items",
+                                     "deferred_multi_tile"])
 def test_stream_fp32_powerlaw(P, variant):
     n, m, C, K = 1500, 15000, 0.6, 20
     s, d = chung_lu_digraph(n, m, 2.1, 2.1, 4)
@@ -144,6 +145,9 @@ def test_stream_fp32_powerlaw(P, variant):
         # 12 tiles on 2 CTAs (6 tiles each) and a 64-entry column cache: the
         # multi-tile and uncached-column paths of the fused launch
         kw = dict(aff=1, prep_ctas=2, prep_cache=64)
+    elif variant == "prep_small_items":
+        # 48-nonzero work items: every tile split over several CTAs
+        kw = dict(aff=1, prep_item=48, prep_ctas=40)
     elif variant == "deferred_multi_tile":
         kw = dict(aff=1, defer=7, tc=1, prep_ctas=3, prep_cache=128)
     sr = P.SimRank(n, s, d, C=C, K=K, s_precision=32, **kw)
@@ -155,8 +159,9 @@ def test_stream_fp32_powerlaw(P, variant):
     assert maxabs(got, got.T) < 1e-7
 
 
-@pytest.mark.parametrize("kw", [{}, {"chain": 1}, {"prep_ctas": 2, "prep_cache": 32}],
-                         ids=["fused", "per_step", "fused_multi_tile"])
+@pytest.mark.parametrize("kw", [{}, {"chain": 1}, {"prep_ctas": 2, "prep_cache": 32},
+                                {"prep_item": 40, "prep_ctas": 30}],
+                         ids=["fused", "per_step", "fused_multi_tile", "fused_small_items"])
 def test_stream_fp64_matches_oracle(P, kw):
     n, m, C, K = 700, 4200, 0.8, 12
     s, d = er_graph(n, m, 6)
