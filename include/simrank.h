@@ -110,7 +110,8 @@ typedef struct simrank_config {
                              replayed from a CUDA graph; 1 = the same kernels launched graph by
                              graph (the per-graph-launch baseline) */
   int32_t prep_item;      /* chain = 0: nonzeros per work item of the fused launch's gathers
-                             (0 = 1024); a tile with more nonzeros is split over several CTAs */
+                             (0 = sized so that the items fit one per CTA, at least 256); a tile
+                             with more nonzeros is split over several CTAs */
   int32_t reserved[1];
 } simrank_config;
 

@@ -139,7 +139,9 @@ cudaError_t dev_alloc(T** p, size_t count) {
   return cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T));
 }
 
-// Builds adjacency lists (rows indexed by `key`, entries `val`) with per-row slack.
+// Builds adjacency lists (rows indexed by `key`, entries `val`) with per-row
+// slack.  Row capacities are multiples of 4, so every row starts on a 16-byte
+// boundary of the pool (vector loads of whole rows).
 void build_adj(HostAdj& A, int n_rows, const std::vector<std::vector<int32_t>>& rows) {
   A.start.assign(n_rows, 0);
   A.len.assign(n_rows, 0);
@@ -147,7 +149,7 @@ void build_adj(HostAdj& A, int n_rows, const std::vector<std::vector<int32_t>>& 
   int64_t used = 0;
   for (int a = 0; a < n_rows; ++a) {
     const int len = (int)rows[a].size();
-    const int cap = len + std::max(4, len / 4);
+    const int cap = (len + std::max(4, len / 4) + 3) & ~3;
     A.start[a] = used;
     A.len[a] = len;
     A.cap[a] = cap;
@@ -162,7 +164,7 @@ void build_adj(HostAdj& A, int n_rows, const std::vector<std::vector<int32_t>>& 
 // Appends `v` to row r of the mirror, recording the device patch ops.
 void adj_append(HostAdj& A, int r, int32_t v, std::vector<PatchOp>& ops, bool is_in) {
   if (A.len[r] == A.cap[r]) {
-    const int new_cap = 2 * A.len[r] + 4;
+    const int new_cap = (2 * A.len[r] + 4 + 3) & ~3;
     const int64_t ns = A.used;
     if ((int64_t)A.pool.size() < ns + new_cap) A.pool.resize((size_t)(2 * (ns + new_cap)), 0);
     std::copy(A.pool.begin() + A.start[r], A.pool.begin() + A.start[r] + A.len[r],
@@ -546,7 +548,7 @@ simrank_status run_rank_one(simrank_ctx* h, int64_t src_off, int delta, int j, i
     pp.mXi = h->mXi;
     pp.mEta = h->mEta;
     pp.cap = h->cfg.prep_cache > 0 ? h->cfg.prep_cache : 8192;
-    pp.item = h->cfg.prep_item > 0 ? h->cfg.prep_item : 1024;
+    pp.item = h->cfg.prep_item;
     pp.n_pad = h->n_pad;
     pp.nT_cap = h->nT_cap;
     if (!h->W) {

@@ -612,7 +612,7 @@ size_t prep_smem(int cap, int nT_cap, int npend_max) {
 int launch_prep(const PrepParams& prm, int s_prec, int npend_max, int num_sms, int max_ctas,
                 int64_t nnz_bound, cudaStream_t st) {
   if (prm.nT <= 0) return 0;
-  if (prm.item <= 0 || prm.cap < 0 || (prm.cap & 3)) return 1;
+  if (prm.item < 0 || prm.cap < 0 || (prm.cap & 3)) return 1;
   const size_t smem = (s_prec == 64) ? prep_smem<double>(prm.cap, prm.nT_cap, npend_max)
                                      : prep_smem<float>(prm.cap, prm.nT_cap, npend_max);
   const void* fn = (s_prec == 64) ? (const void*)k_prep<double> : (const void*)k_prep<float>;
@@ -623,13 +623,24 @@ int launch_prep(const PrepParams& prm, int s_prec, int npend_max, int num_sms, i
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PG, smem) != cudaSuccess)
     return 1;
   if (per_sm <= 0) return 2;
-  // as many CTAs as there are items (at most all co-resident ones)
-  const int64_t items = (int64_t)prm.nT + nnz_bound / prm.item;
-  int grid = (int)std::min<int64_t>(std::max<int64_t>(items, prm.nT), (int64_t)per_sm * num_sms);
+  // all co-resident CTAs (fewer for small graphs); with item = 0 the item
+  // size is chosen so that the items (at most nT + nnz / item of them) fit
+  // one per CTA
+  const int full = per_sm * num_sms;
+  int grid = full;
+  if (prm.item > 0)
+    grid = (int)std::min<int64_t>((int64_t)prm.nT + nnz_bound / prm.item + 1, full);
+  else
+    grid = (int)std::min<int64_t>((int64_t)prm.nT + nnz_bound / 256 + 1, full);
   if (max_ctas > 0) grid = std::min(grid, max_ctas);
+  grid = std::max(grid, 1);
   if ((prm.nT + grid - 1) / grid > PREP_MT) return 2;
   if (prm.npend > npend_max) return 1;
   PrepParams a = prm;
+  if (a.item == 0) {
+    const int64_t spare = (int64_t)grid - prm.nT;
+    a.item = (int)std::max<int64_t>(256, spare > 0 ? (nnz_bound + spare - 1) / spare : nnz_bound);
+  }
   void* args[] = {&a};
   if (cudaLaunchCooperativeKernel(fn, grid, PG, args, smem, st) != cudaSuccess) return 1;
   return 0;

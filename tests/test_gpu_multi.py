@@ -147,3 +147,19 @@ def test_multi_invalid_update_changes_nothing(P):
     for g in range(4):
         assert maxabs(mh.dense(g), before[g]) == 0.0
     mh.close()
+
+
+def test_multi_large_graph_global_path(P):
+    """A graph too large for the shared-memory vectors (FP64, > 5120 rows)
+    next to a small one: both paths of the prep kernel in one round."""
+    C, K = 0.4, 6
+    big = (5200,) + er_graph(5200, 3 * 5200, 61)
+    small = (300,) + er_graph(300, 1200, 62)
+    graphs = [big, small]
+    ups = [update_stream(n, s, d, 3, 63 + g) for g, (n, s, d) in enumerate(graphs)]
+    mh = P.MultiSimRank(graphs, C=C, K=K, s_precision=64)
+    mh.apply_updates(ups)
+    for g, (n, s, d) in enumerate(graphs):
+        want, _ = O.sequential_unit_updates(n, s, d, oracle_S(n, s, d, C), ups[g].tolist(), C, K)
+        assert maxabs(mh.dense(g), want) < TOL64, g
+    mh.close()
