@@ -112,11 +112,16 @@ typedef struct simrank_config {
   int32_t prep_item;      /* chain = 0: nonzeros per work item of the fused launch's gathers
                              (0 = sized so that the items fit one per CTA, at least 256); a tile
                              with more nonzeros is split over several CTAs */
-  int32_t reserved[1];
+  int32_t upper_only;     /* dense mode: 1 = keep only the 128 x 128 tiles of S on or above the
+                             block diagonal current (S is symmetric; updates then read and write
+                             half the bytes, and reads of a lower tile take its mirror); 0 = keep
+                             both triangles.  Default 1. */
+  int32_t reserved[4];
 } simrank_config;
 
 /* Fills *cfg with defaults: C = 0.6, K = 15, s_precision = 32, dense, aff = 1,
- * relabel = 1, unit apply, fused update, init_tol = 1e-13, 400 init sweeps. */
+ * relabel = 1, upper_only = 1, unit apply, fused update, init_tol = 1e-13,
+ * 400 init sweeps. */
 simrank_status simrank_default_config(simrank_config* cfg);
 
 /* Creates a handle for the graph (src[e] -> dst[e]), e < m, on n nodes.

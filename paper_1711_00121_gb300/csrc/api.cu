@@ -385,6 +385,9 @@ cudaEvent_t* next_phase_events(simrank_ctx* h) {
   return h->phase_ev[h->phase_used++].data();
 }
 
+// 1 when only the tiles of S on or above the block diagonal are kept
+int upper(const simrank_ctx* h) { return (h->cfg.upper_only && !h->column) ? 1 : 0; }
+
 void* panel_for_s(simrank_ctx* h) {
   return h->cfg.s_precision == 64 ? (void*)h->P64 : (void*)h->P32;
 }
@@ -404,7 +407,7 @@ simrank_status s_update_launch(simrank_ctx* h, int k0, int k1, int use_masks) {
   launch_s_update(h->S, h->cfg.s_precision, h->ld, panel_for_s(h), h->K1, h->tiles, h->ntiles,
                   h->mXi, h->mEta, k0, k1, use_masks, h->n_cur, h->counters,
                   s_update_grid(h->cfg.s_precision, h->num_sms, ws), h->st,
-                  ws ? wait_limit(h) : 0);
+                  ws ? wait_limit(h) : 0, upper(h));
   LAUNCH_CHECK(h);
   if (ev) CUDA_TRY(h, cudaEventRecord(ev->second, h->st));
   h->prof_launches += 1;
@@ -453,7 +456,8 @@ simrank_status flush_pending(simrank_ctx* h) {
     if (ev) CUDA_TRY(h, cudaEventRecord(ev->first, h->st));
     const int rc = launch_s_update_tc((float*)h->S, h->ld, (const float*)h->ob[12].p,
                                       (const float*)h->ob[13].p, h->n_pad, kd, h->tiles, h->ntiles,
-                                      h->n_cur, h->counters, h->num_sms, wait_limit(h), h->st);
+                                      h->n_cur, h->counters, h->num_sms, wait_limit(h), h->st,
+                                      upper(h));
     if (rc != 0) return fail(h, SR_ERR_CUDA, "tensor-core S update: launch setup failed");
     h->launches += 2;
   } else {
@@ -461,7 +465,7 @@ simrank_status flush_pending(simrank_ctx* h) {
     const bool ws = h->cfg.s_kernel == 0;
     launch_s_update(h->S, 32, h->ld, h->Pp, GK1, h->tiles, h->ntiles, h->pXi, h->pEta, 0, nterms,
                     0, h->n_cur, h->counters, s_update_grid(32, h->num_sms, ws), h->st,
-                    ws ? wait_limit(h) : 0);
+                    ws ? wait_limit(h) : 0, upper(h));
     h->launches += 1;
   }
   LAUNCH_CHECK(h);
@@ -543,6 +547,7 @@ simrank_status run_rank_one(simrank_ctx* h, int64_t src_off, int delta, int j, i
       pp.ntiles = h->ntiles;
       pp.tile_mode = (plain || !h->cfg.aff) ? 0 : 1;
     }
+    pp.upper = upper(h);
     pp.sI = h->sI;
     pp.sJ = h->sJ;
     pp.mXi = h->mXi;
@@ -579,12 +584,13 @@ simrank_status run_rank_one(simrank_ctx* h, int64_t src_off, int delta, int j, i
     if (defer) {
       // rows i (summed over the block) and j of the current S = S + pending panels
       launch_gather_rows_pending(h->S, 32, h->ld, h->d_srcs + src_off, delta, j, nT * PT, h->Pp,
-                                 h->cfg.defer * h->K1, h->np * h->K1, h->sI, h->sJ, h->st);
+                                 h->cfg.defer * h->K1, h->np * h->K1, h->sI, h->sJ, h->st,
+                                 upper(h));
       launch_scalars_from_rows(h->din, h->sI, h->sJ, h->d_srcs + src_off, delta, j, h->scal, h->st);
       h->launches += 1;
     } else {
       launch_gather_rows(h->S, h->cfg.s_precision, h->ld, h->d_srcs + src_off, delta, j, nT * PT,
-                         h->din, h->sI, h->sJ, h->scal, h->st);
+                         h->din, h->sI, h->sJ, h->scal, h->st, upper(h));
     }
     launch_gamma(h->din, h->sI, h->sJ, h->scal, j, delta, op, d_j, C, nT, h->K1, h->P64,
                  h->cfg.s_precision == 64 ? nullptr : h->P32, h->mXi, h->mEta, h->st);
@@ -804,13 +810,14 @@ simrank_status run_one_shot(simrank_ctx* h, const std::map<int32_t, std::vector<
   CUDA_TRY(h, cudaMemsetAsync(Z, 0, (size_t)nr * 8, h->st));
   CUDA_TRY(h, cudaMemsetAsync(Y, 0, (size_t)nr * 8, h->st));
   // Z = sum of signed source rows, Y = Q Z on the OLD graph
-  launch_signed_rows(h->S, sp, h->ld, d_src, d_sign, d_off, r, n_pad, Zc, h->st);
+  launch_signed_rows(h->S, sp, h->ld, d_src, d_sign, d_off, r, n_pad, Zc, h->st, upper(h));
   launch_transpose_rect(Zc, n_pad, Z, rp, r, n_pad, h->st);
   launch_spmm_rows(h->din, nullptr, nullptr, Z, 64, rp, Y, 64, rp, n_pad, rp, 1.0, 0.0, 0, h->st);
   launch_transpose_rect(Y, rp, Zc, n_pad, n_pad, r, h->st);  // Yc into buffer 1
   launch_lambda(h->S, sp, h->ld, d_sinks, d_av, d_bv, Y, Z, rp, d_src, d_sign, d_off, r, C, Lam,
-                h->st);
-  launch_w_assemble(h->S, sp, h->ld, d_sinks, d_av, d_bv, Zc, Lam, r, n_pad, C, Wc, h->st);
+                h->st, upper(h));
+  launch_w_assemble(h->S, sp, h->ld, d_sinks, d_av, d_bv, Zc, Lam, r, n_pad, C, Wc, h->st,
+                    upper(h));
   LAUNCH_CHECK(h);
   h->launches += 7;
   // the graph becomes the new one
@@ -884,13 +891,15 @@ simrank_status run_one_shot(simrank_ctx* h, const std::map<int32_t, std::vector<
       if (tc) {
         const int rc = launch_s_update_tc((float*)h->S, h->ld, (const float*)h->ob[8].p,
                                           (const float*)h->ob[9].p, n_pad, kd, h->tiles, h->ntiles,
-                                          h->n_cur, h->counters, h->num_sms, wait_limit, h->st);
+                                          h->n_cur, h->counters, h->num_sms, wait_limit, h->st,
+                                          upper(h));
         if (rc != 0) return fail(h, SR_ERR_CUDA, "tensor-core S update: launch setup failed");
       } else {
         const bool ws = sp == 32 && h->cfg.s_kernel == 0;
         launch_s_update(h->S, sp, h->ld, h->ob[8].p, g * r, h->tiles, h->ntiles, h->mXi, h->mEta,
                         0, slot * r, h->cfg.aff ? 1 : 0, h->n_cur, h->counters,
-                        s_update_grid(sp, h->num_sms, ws), h->st, ws ? wait_limit : 0);
+                        s_update_grid(sp, h->num_sms, ws), h->st, ws ? wait_limit : 0,
+                        upper(h));
       }
       LAUNCH_CHECK(h);
       if (ev) CUDA_TRY(h, cudaEventRecord(ev->second, h->st));
@@ -1074,6 +1083,7 @@ simrank_status simrank_default_config(simrank_config* cfg) {
   cfg->init_tol = 0.0;  // 0 = precision default
   cfg->profile = 0;
   cfg->relabel = 1;
+  cfg->upper_only = 1;
   cfg->timeout_iters = 0;
   cfg->cuda_stream = nullptr;
   return SR_OK;
@@ -1479,7 +1489,7 @@ simrank_status simrank_columns(simrank_t h, const int32_t* cols, int32_t ncols, 
   const size_t ob = (size_t)h->n_cur * ncols * (out_fp64 ? 8 : 4);
   if (out_on_device) {
     launch_copy_cols(h->S, h->cfg.s_precision, h->ld, h->d_cols, perm, ncols, h->n_cur, out,
-                     out_fp64, h->st);
+                     out_fp64, h->st, upper(h));
     LAUNCH_CHECK(h);
     CUDA_TRY(h, cudaStreamSynchronize(h->st));  // cols staging reuse safety
     return SR_OK;
@@ -1487,7 +1497,7 @@ simrank_status simrank_columns(simrank_t h, const int32_t* cols, int32_t ncols, 
   void* tmp = nullptr;
   CUDA_TRY(h, cudaMalloc(&tmp, ob));
   launch_copy_cols(h->S, h->cfg.s_precision, h->ld, h->d_cols, perm, ncols, h->n_cur, tmp,
-                   out_fp64, h->st);
+                   out_fp64, h->st, upper(h));
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, ob, cudaMemcpyDeviceToHost, h->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
@@ -1539,6 +1549,12 @@ simrank_status simrank_reanchor(simrank_t h, int32_t sweeps, double* max_change)
   if (sweeps <= 0) return fail(h, SR_ERR_ARG, "sweeps must be positive");
   double diff = 0.0;
   int done = 0;
+  // the sweeps read all of S: restore the lower tiles from their mirrors
+  if (upper(h)) {
+    launch_mirror_lower(h->S, h->cfg.s_precision, h->n_pad, h->ld, h->st);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(h, SR_ERR_CUDA, cudaGetErrorString(e));
+  }
   simrank_status s = jacobi_sweeps(h, sweeps, 0.0, &diff, &done);
   if (s != SR_OK) return s;
   h->stats.init_residual = diff;
@@ -2013,6 +2029,7 @@ simrank_status simrank_multi_apply(simrank_multi_t h, const simrank_update* u,
     d.sI = x->sI;
     d.sJ = x->sJ;
     d.n = x->n_cur;
+    d.upper = upper(x);
   }
   // launch table
   h->h_steps.clear();

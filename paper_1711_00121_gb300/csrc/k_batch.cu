@@ -18,13 +18,13 @@ namespace {
 template <typename T>
 __global__ void k_signed_rows(const T* __restrict__ S, int64_t ld, const int32_t* __restrict__ src,
                               const int8_t* __restrict__ sign, const int64_t* __restrict__ off,
-                              int n_pad, double* __restrict__ Zc) {
+                              int n_pad, double* __restrict__ Zc, int upper) {
   const int t = blockIdx.y;
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= n_pad) return;
   double acc = 0.0;
   for (int64_t e = off[t]; e < off[t + 1]; ++e) {
-    const double v = (double)S[(int64_t)src[e] * ld + a];
+    const double v = (double)s_at(S, ld, src[e], a, upper != 0);
     acc += sign[e] > 0 ? v : -v;
   }
   Zc[(int64_t)t * n_pad + a] = acc;
@@ -56,13 +56,13 @@ __global__ void k_lambda(const T* __restrict__ S, int64_t ld, const int32_t* __r
                          const double* __restrict__ Y, const double* __restrict__ Z, int64_t ldz,
                          const int32_t* __restrict__ src, const int8_t* __restrict__ sign,
                          const int64_t* __restrict__ off, int r, double C,
-                         double* __restrict__ Lam) {
+                         double* __restrict__ Lam, int upper) {
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
   const int t = blockIdx.y;
   if (u >= r) return;
   const int jt = sinks[t], ju = sinks[u];
   const double at = av[t], au = av[u], bt = bv[t], bu = bv[u];
-  double v = at * au * ((double)S[(int64_t)jt * ld + ju] - (t == u ? 1.0 - C : 0.0)) / C;
+  double v = at * au * ((double)s_at(S, ld, jt, ju, upper != 0) - (t == u ? 1.0 - C : 0.0)) / C;
   v += at * bu * Y[(int64_t)jt * ldz + u] + bt * au * Y[(int64_t)ju * ldz + t];
   double d = 0.0;
   for (int64_t e = off[t]; e < off[t + 1]; ++e) {
@@ -78,12 +78,12 @@ template <typename T>
 __global__ void k_w_assemble(const T* __restrict__ S, int64_t ld, const int32_t* __restrict__ sinks,
                              const double* __restrict__ av, const double* __restrict__ bv,
                              const double* __restrict__ Yc, int n_pad, double C,
-                             double* __restrict__ Wc) {
+                             double* __restrict__ Wc, int upper) {
   const int t = blockIdx.y;
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= n_pad) return;
   const int jt = sinks[t];
-  const double s = (double)S[(int64_t)jt * ld + a] - (a == jt ? 1.0 - C : 0.0);
+  const double s = (double)s_at(S, ld, jt, a, upper != 0) - (a == jt ? 1.0 - C : 0.0);
   Wc[(int64_t)t * n_pad + a] = av[t] * s / C + bv[t] * Yc[(int64_t)t * n_pad + a];
 }
 
@@ -192,12 +192,13 @@ __global__ void k_pack_tc_tiles(const float* __restrict__ Pp, int GK1, int nterm
 }  // namespace
 
 void launch_signed_rows(const void* S, int s_prec, int64_t ld, const int32_t* src, const int8_t* sign,
-                        const int64_t* off, int r, int n_pad, double* Zc, cudaStream_t st) {
+                        const int64_t* off, int r, int n_pad, double* Zc, cudaStream_t st,
+                        int upper) {
   dim3 grid((n_pad + 255) / 256, r);
   if (s_prec == 64)
-    k_signed_rows<double><<<grid, 256, 0, st>>>((const double*)S, ld, src, sign, off, n_pad, Zc);
+    k_signed_rows<double><<<grid, 256, 0, st>>>((const double*)S, ld, src, sign, off, n_pad, Zc, upper);
   else
-    k_signed_rows<float><<<grid, 256, 0, st>>>((const float*)S, ld, src, sign, off, n_pad, Zc);
+    k_signed_rows<float><<<grid, 256, 0, st>>>((const float*)S, ld, src, sign, off, n_pad, Zc, upper);
 }
 
 void launch_transpose_rect(const double* A, int64_t lda, double* B, int64_t ldb, int rows, int cols,
@@ -209,24 +210,24 @@ void launch_transpose_rect(const double* A, int64_t lda, double* B, int64_t ldb,
 void launch_lambda(const void* S, int s_prec, int64_t ld, const int32_t* sinks, const double* av,
                    const double* bv, const double* Y, const double* Z, int64_t ldz,
                    const int32_t* src, const int8_t* sign, const int64_t* off, int r, double C,
-                   double* Lam, cudaStream_t st) {
+                   double* Lam, cudaStream_t st, int upper) {
   dim3 grid((r + 127) / 128, r);
   if (s_prec == 64)
     k_lambda<double><<<grid, 128, 0, st>>>((const double*)S, ld, sinks, av, bv, Y, Z, ldz, src, sign,
-                                          off, r, C, Lam);
+                                          off, r, C, Lam, upper);
   else
     k_lambda<float><<<grid, 128, 0, st>>>((const float*)S, ld, sinks, av, bv, Y, Z, ldz, src, sign,
-                                         off, r, C, Lam);
+                                         off, r, C, Lam, upper);
 }
 
 void launch_w_assemble(const void* S, int s_prec, int64_t ld, const int32_t* sinks, const double* av,
                        const double* bv, const double* Yc, const double* Lam, int r, int n_pad,
-                       double C, double* Wc, cudaStream_t st) {
+                       double C, double* Wc, cudaStream_t st, int upper) {
   dim3 grid((n_pad + 255) / 256, r);
   if (s_prec == 64)
-    k_w_assemble<double><<<grid, 256, 0, st>>>((const double*)S, ld, sinks, av, bv, Yc, n_pad, C, Wc);
+    k_w_assemble<double><<<grid, 256, 0, st>>>((const double*)S, ld, sinks, av, bv, Yc, n_pad, C, Wc, upper);
   else
-    k_w_assemble<float><<<grid, 256, 0, st>>>((const float*)S, ld, sinks, av, bv, Yc, n_pad, C, Wc);
+    k_w_assemble<float><<<grid, 256, 0, st>>>((const float*)S, ld, sinks, av, bv, Yc, n_pad, C, Wc, upper);
   dim3 g2((r + 127) / 128, r);
   k_w_lambda<<<g2, 128, 0, st>>>(sinks, Lam, r, n_pad, Wc);
 }

@@ -12,6 +12,12 @@ namespace {
 
 template <typename T>
 __device__ __forceinline__ double ld_s(const T* p) { return (double)__ldg(p); }
+// S[r, c] as a double, reading the mirror of a lower tile when upper != 0
+template <typename T>
+__device__ __forceinline__ double ld_sym(const T* S, int64_t ld, int64_t r, int64_t c, int upper) {
+  return (upper && (r / PT) > (c / PT)) ? (double)__ldg(S + c * ld + r)
+                                        : (double)__ldg(S + r * ld + c);
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -24,28 +30,26 @@ __device__ __forceinline__ double warp_sum(double v) {
 template <typename T>
 __global__ void k_gather_rows(const T* __restrict__ S, int64_t ld, const int32_t* __restrict__ I,
                               int delta, int j, int n_pad, DevAdj in, double* __restrict__ sI,
-                              double* __restrict__ sJ, double* __restrict__ scal) {
+                              double* __restrict__ sJ, double* __restrict__ scal, int upper) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a < n_pad) {
     double acc = 0.0;
-    for (int t = 0; t < delta; ++t) acc += ld_s(S + (int64_t)I[t] * ld + a);
+    for (int t = 0; t < delta; ++t) acc += ld_sym(S, ld, I[t], a, upper);
     sI[a] = acc;
-    sJ[a] = ld_s(S + (int64_t)j * ld + a);
+    sJ[a] = ld_sym(S, ld, j, a, upper);
   }
   if (blockIdx.x == 0) {
     __shared__ double red[2][32];
     double acc = 0.0;
-    for (int t = 0; t < delta; ++t) {
-      const T* row = S + (int64_t)I[t] * ld;
-      for (int u = threadIdx.x; u < delta; u += blockDim.x) acc += ld_s(row + I[u]);
-    }
+    for (int t = 0; t < delta; ++t)
+      for (int u = threadIdx.x; u < delta; u += blockDim.x) acc += ld_sym(S, ld, I[t], I[u], upper);
     const int64_t js = in.start[j];
     const int jl = in.len[j];
     double wj = 0.0;
     for (int t = 0; t < delta; ++t) {
-      const T* row = S + (int64_t)I[t] * ld;
 #pragma unroll 8
-      for (int u = threadIdx.x; u < jl; u += blockDim.x) wj += ld_s(row + in.col[js + u]);
+      for (int u = threadIdx.x; u < jl; u += blockDim.x)
+        wj += ld_sym(S, ld, I[t], in.col[js + u], upper);
     }
     acc = warp_sum(acc);
     wj = warp_sum(wj);
@@ -61,7 +65,7 @@ __global__ void k_gather_rows(const T* __restrict__ S, int64_t ld, const int32_t
       w = warp_sum(w);
       if (threadIdx.x == 0) {
         scal[0] = v;
-        scal[1] = ld_s(S + (int64_t)j * ld + j);
+        scal[1] = ld_sym(S, ld, j, j, upper);
         scal[2] = (jl > 0) ? w / ((double)delta * (double)jl) : 0.0;
       }
     }
@@ -77,7 +81,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_gather_rows_pending(
     const T* __restrict__ S, int64_t ld, const int32_t* __restrict__ I, int delta, int j, int n_pad,
     const float* __restrict__ Pp, int GK1, int nterms, double* __restrict__ sI,
-    double* __restrict__ sJ) {
+    double* __restrict__ sJ, int upper) {
   // coefficients: [2 vectors (I-sum, j)][2 (xi, eta)][nterms]
   extern __shared__ double coef[];
   __shared__ double red[8][32][2];
@@ -108,8 +112,8 @@ __global__ void __launch_bounds__(256) k_gather_rows_pending(
       accJ += coef[2 * nterms + q] * ea + coef[3 * nterms + q] * xa;
     }
     if (warp == 0) {
-      for (int t = 0; t < delta; ++t) accI += ld_s(S + (int64_t)I[t] * ld + a);
-      accJ += ld_s(S + (int64_t)j * ld + a);
+      for (int t = 0; t < delta; ++t) accI += ld_sym(S, ld, I[t], a, upper);
+      accJ += ld_sym(S, ld, j, a, upper);
     }
   }
   red[warp][lane][0] = accI;
@@ -481,20 +485,20 @@ __global__ void k_tile_list(const uint64_t* __restrict__ mXi, const uint64_t* __
 
 void launch_gather_rows(const void* S, int s_prec, int64_t ld, const int32_t* I, int delta, int j,
                         int n_pad, const DevAdj& in, double* sI, double* sJ, double* scal,
-                        cudaStream_t st) {
+                        cudaStream_t st, int upper) {
   const int threads = 256;
   const int blocks = (n_pad + threads - 1) / threads;
   if (s_prec == 64)
     k_gather_rows<double><<<blocks, threads, 0, st>>>((const double*)S, ld, I, delta, j, n_pad, in,
-                                                      sI, sJ, scal);
+                                                      sI, sJ, scal, upper);
   else
     k_gather_rows<float><<<blocks, threads, 0, st>>>((const float*)S, ld, I, delta, j, n_pad, in,
-                                                     sI, sJ, scal);
+                                                     sI, sJ, scal, upper);
 }
 
 void launch_gather_rows_pending(const void* S, int s_prec, int64_t ld, const int32_t* I, int delta,
                                 int j, int n_pad, const float* Pp, int GK1, int nterms, double* sI,
-                                double* sJ, cudaStream_t st) {
+                                double* sJ, cudaStream_t st, int upper) {
   const int threads = 256;
   const int blocks = (n_pad + 31) / 32;
   const size_t smem = (size_t)4 * nterms * sizeof(double);
@@ -502,12 +506,14 @@ void launch_gather_rows_pending(const void* S, int s_prec, int64_t ld, const int
     cudaFuncSetAttribute(k_gather_rows_pending<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     k_gather_rows_pending<double><<<blocks, threads, smem, st>>>((const double*)S, ld, I, delta, j,
-                                                                 n_pad, Pp, GK1, nterms, sI, sJ);
+                                                                 n_pad, Pp, GK1, nterms, sI, sJ,
+                                                                 upper);
   } else {
     cudaFuncSetAttribute(k_gather_rows_pending<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     k_gather_rows_pending<float><<<blocks, threads, smem, st>>>((const float*)S, ld, I, delta, j,
-                                                                n_pad, Pp, GK1, nterms, sI, sJ);
+                                                                n_pad, Pp, GK1, nterms, sI, sJ,
+                                                                 upper);
   }
 }
 

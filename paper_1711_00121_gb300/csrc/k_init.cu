@@ -152,13 +152,28 @@ __global__ void k_convert(const TA* __restrict__ A, TB* __restrict__ B, int64_t 
 // out[c * n + a] = S[cols[c], perm[a]] (perm = caller id -> storage id, or identity)
 template <typename TS, typename TO>
 __global__ void k_copy_cols(const TS* __restrict__ S, int64_t ld, const int32_t* __restrict__ cols,
-                            const int32_t* __restrict__ perm, int n, TO* __restrict__ out) {
+                            const int32_t* __restrict__ perm, int n, TO* __restrict__ out,
+                            int upper) {
   const int c = blockIdx.y;
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a < n) {
     const int p = perm ? perm[a] : a;
-    out[(int64_t)c * n + a] = (TO)S[(int64_t)cols[c] * ld + p];
+    out[(int64_t)c * n + a] = (TO)s_at(S, ld, cols[c], p, upper != 0);
   }
+}
+
+// Lower tiles := the transposes of their mirrors (S[J, I] = S[I, J]^T for
+// 128-tiles I < J), one CTA per 32 x 32 block of the upper triangle.
+template <typename T>
+__global__ void k_mirror_lower(T* __restrict__ A, int64_t ld) {
+  const int bi = blockIdx.y, bj = blockIdx.x;  // 32-blocks
+  if ((bi * 32) / PT >= (bj * 32) / PT) return;
+  __shared__ T t[32][33];
+  for (int r = threadIdx.y; r < 32; r += 8)
+    t[r][threadIdx.x] = A[(int64_t)(bi * 32 + r) * ld + bj * 32 + threadIdx.x];
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8)
+    A[(int64_t)(bj * 32 + r) * ld + bi * 32 + threadIdx.x] = t[threadIdx.x][r];
 }
 
 }  // namespace
@@ -206,6 +221,14 @@ void launch_symmetrize(void* A, int prec, int n_pad, int64_t ld, cudaStream_t st
     k_symmetrize<float><<<grid, block, 0, st>>>((float*)A, ld);
 }
 
+void launch_mirror_lower(void* A, int prec, int n_pad, int64_t ld, cudaStream_t st) {
+  dim3 grid(n_pad / 32, n_pad / 32), block(32, 8);
+  if (prec == 64)
+    k_mirror_lower<double><<<grid, block, 0, st>>>((double*)A, ld);
+  else
+    k_mirror_lower<float><<<grid, block, 0, st>>>((float*)A, ld);
+}
+
 void launch_set_diag(void* A, int prec, int from, int to, int64_t ld, double value,
                      cudaStream_t st) {
   if (to <= from) return;
@@ -229,19 +252,19 @@ void launch_convert(const void* A, int a_prec, void* B, int b_prec, int64_t coun
 }
 
 void launch_copy_cols(const void* S, int s_prec, int64_t ld, const int32_t* cols, const int32_t* perm,
-                      int ncols, int n, void* out, int out_fp64, cudaStream_t st) {
+                      int ncols, int n, void* out, int out_fp64, cudaStream_t st, int upper) {
   if (ncols <= 0 || n <= 0) return;
   dim3 grid((n + 255) / 256, ncols);
   if (s_prec == 64) {
     if (out_fp64)
-      k_copy_cols<double, double><<<grid, 256, 0, st>>>((const double*)S, ld, cols, perm, n, (double*)out);
+      k_copy_cols<double, double><<<grid, 256, 0, st>>>((const double*)S, ld, cols, perm, n, (double*)out, upper);
     else
-      k_copy_cols<double, float><<<grid, 256, 0, st>>>((const double*)S, ld, cols, perm, n, (float*)out);
+      k_copy_cols<double, float><<<grid, 256, 0, st>>>((const double*)S, ld, cols, perm, n, (float*)out, upper);
   } else {
     if (out_fp64)
-      k_copy_cols<float, double><<<grid, 256, 0, st>>>((const float*)S, ld, cols, perm, n, (double*)out);
+      k_copy_cols<float, double><<<grid, 256, 0, st>>>((const float*)S, ld, cols, perm, n, (double*)out, upper);
     else
-      k_copy_cols<float, float><<<grid, 256, 0, st>>>((const float*)S, ld, cols, perm, n, (float*)out);
+      k_copy_cols<float, float><<<grid, 256, 0, st>>>((const float*)S, ld, cols, perm, n, (float*)out, upper);
   }
 }
 

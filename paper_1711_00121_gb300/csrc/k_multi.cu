@@ -380,8 +380,8 @@ __global__ void __launch_bounds__(MT, 1)
       st32[a] = (int)__ldcg(q.in.start + a);
       ln[a] = __ldcg(q.in.len + a);
       V vI = V(0);
-      for (int t = 0; t < sc.delta; ++t) vI += S[(int64_t)I[t] * q.ld + a];
-      vA[a] = V2<V>{vI, S[(int64_t)sc.j * q.ld + a]};  // (sI, sJ)
+      for (int t = 0; t < sc.delta; ++t) vI += s_at(S, q.ld, I[t], a, q.upper != 0);
+      vA[a] = V2<V>{vI, s_at(S, q.ld, sc.j, a, q.upper != 0)};  // (sI, sJ)
     }
     __syncthreads();
     if (tid == 0) {
@@ -443,9 +443,9 @@ __global__ void __launch_bounds__(MT, 1)
     V* sJ = static_cast<V*>(q.sJ);
     for (int a = tid; a < nrows; a += MT) {
       V vI = V(0);
-      for (int t = 0; t < sc.delta; ++t) vI += S[(int64_t)I[t] * q.ld + a];
+      for (int t = 0; t < sc.delta; ++t) vI += s_at(S, q.ld, I[t], a, q.upper != 0);
       sI[a] = vI;
-      sJ[a] = S[(int64_t)sc.j * q.ld + a];
+      sJ[a] = s_at(S, q.ld, sc.j, a, q.upper != 0);
     }
     __syncthreads();
     double S_II = 0.0;

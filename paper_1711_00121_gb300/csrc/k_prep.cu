@@ -345,8 +345,8 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
     const int r = tid & (PT - 1), part = tid >> 7;
     const int64_t a = (int64_t)T * PT + r;
     V vI = V(0), vJ = V(0);
-    for (int u = part; u < p.delta; u += 4) vI += S[(int64_t)p.I[u] * p.ld + a];
-    if (part == 3) vJ = S[(int64_t)p.j * p.ld + a];
+    for (int u = part; u < p.delta; u += 4) vI += s_at(S, p.ld, p.I[u], a, p.upper != 0);
+    if (part == 3) vJ = s_at(S, p.ld, p.j, a, p.upper != 0);
     // S_cur[x, a] = S[x, a] + sum_q xi_q[x] eta_q[a] + eta_q[x] xi_q[a]
     for (int q = part; q < np; q += 4) {
       const V xa = P[pidx(a, 0, q)];

@@ -64,6 +64,7 @@ struct TileRef {
   const T* P;
   int I, J, n;
   uint64_t a1, a2;
+  bool mirror;  // also apply Delta^T to S[J, I] (both triangles kept)
 };
 
 // Tile source of one graph: a list of (I << 16 | J) pairs.
@@ -75,11 +76,11 @@ struct OneGraphTiles {
   const uint32_t* tiles;
   const uint64_t* mXi;
   const uint64_t* mEta;
-  int use_masks, n;
+  int use_masks, n, mirror;
   __device__ __forceinline__ TileRef<T> get(int t) const {
     const uint32_t pr = tiles[t];
     const int I = (int)(pr >> 16), J = (int)(pr & 0xffffu);
-    TileRef<T> r{S, ld, P, I, J, n, ~0ull, ~0ull};
+    TileRef<T> r{S, ld, P, I, J, n, ~0ull, ~0ull, mirror != 0};
     if (use_masks) {
       r.a1 = mXi[I] & mEta[J];
       r.a2 = mEta[I] & mXi[J];
@@ -98,8 +99,8 @@ struct ManyGraphTiles {
     const uint64_t e = tiles[t];
     const int g = (int)(e >> 32), I = (int)((e >> 16) & 0xffffu), J = (int)(e & 0xffffu);
     const MultiGraphDesc& q = d[g];
-    return TileRef<T>{(T*)q.S, q.ld, (const T*)q.P, I, J, q.n, q.mXi[I] & q.mEta[J],
-                      q.mEta[I] & q.mXi[J]};
+    return TileRef<T>{(T*)q.S,         q.ld, (const T*)q.P, I, J, q.n, q.mXi[I] & q.mEta[J],
+                      q.mEta[I] & q.mXi[J], q.upper == 0};
   }
 };
 
@@ -213,7 +214,7 @@ __global__ void __launch_bounds__(256, MINB)
     }
     // ---- phase 4: S[J, I] += Delta^T; a warp covers one 512-byte row segment
     // (lane -> 4 consecutive columns), 16 vector loads in flight per thread
-    if (I != J) {
+    if (I != J && tr.mirror) {
       constexpr int NQ = PT * PT / 4 / 256;
       const int lane = tid & 31, warp = tid >> 5;
       T v[NQ][4];
@@ -233,7 +234,8 @@ __global__ void __launch_bounds__(256, MINB)
     if (tid == 0) {
       const long long vr = max(0, min(PT, n - I * PT)), vc = max(0, min(PT, n - J * PT));
       my_tiles += 1;
-      my_bytes += (unsigned long long)(vr * vc) * 2ull * sizeof(T) * (I == J ? 1ull : 2ull);
+      my_bytes += (unsigned long long)(vr * vc) * 2ull * sizeof(T) *
+                  ((I == J || !tr.mirror) ? 1ull : 2ull);
     }
   }
   if (tid == 0 && my_tiles) {
@@ -297,7 +299,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
     k_s_update_ws(float* __restrict__ S, int64_t ld, const float* __restrict__ P, int K1,
                   const uint32_t* __restrict__ tiles, const int* __restrict__ ntiles,
                   const uint64_t* __restrict__ mXi, const uint64_t* __restrict__ mEta, int k0g,
-                  int k1g, int use_masks, int n, long long wait_limit,
+                  int k1g, int use_masks, int n, int mirror, long long wait_limit,
                   unsigned long long* __restrict__ counters) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* sXiI = reinterpret_cast<float*>(smem_raw);
@@ -428,7 +430,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
           st4(S + (int64_t)(I * PT + row) * ld + (int64_t)J * PT + lane * 4, v[q]);
         }
       }
-      if (I != J) {
+      if (I != J && mirror) {
         float v[NQ][4];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
@@ -447,7 +449,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
       if (mt == 0) {
         const long long vr = max(0, min(PT, n - I * PT)), vc = max(0, min(PT, n - J * PT));
         my_tiles += 1;
-        my_bytes += (unsigned long long)(vr * vc) * 8ull * (I == J ? 1ull : 2ull);
+        my_bytes += (unsigned long long)(vr * vc) * 8ull * ((I == J || !mirror) ? 1ull : 2ull);
       }
     }
     if (mt == 0 && my_tiles) {
@@ -475,7 +477,8 @@ int s_update_grid(int s_prec, int num_sms, bool ws) {
 void launch_s_update(void* S, int s_prec, int64_t ld, const void* P, int K1, const uint32_t* tiles,
                      const int* ntiles, const uint64_t* mXi, const uint64_t* mEta, int k0, int k1,
                      int use_masks, int n, int64_t* counters, int grid, cudaStream_t st,
-                     long long ws_wait_limit) {
+                     long long ws_wait_limit, int upper) {
+  const int mirror = upper ? 0 : 1;
   if (s_prec == 64) {
     const size_t smem = (4ull * KC_F64 * PT + (size_t)PT * DP) * sizeof(double);
     static bool attr64 = false;
@@ -484,7 +487,8 @@ void launch_s_update(void* S, int s_prec, int64_t ld, const void* P, int K1, con
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       attr64 = true;
     }
-    OneGraphTiles<double> src{(double*)S, ld, (const double*)P, tiles, mXi, mEta, use_masks, n};
+    OneGraphTiles<double> src{(double*)S, ld,        (const double*)P, tiles, mXi,
+                              mEta,       use_masks, n,                mirror};
     k_s_update<double, KC_F64, 1><<<grid, 256, smem, st>>>(src, K1, ntiles, k0, k1,
                                                              (unsigned long long*)counters);
   } else if (ws_wait_limit > 0) {
@@ -495,7 +499,8 @@ void launch_s_update(void* S, int s_prec, int64_t ld, const void* P, int K1, con
       attr_ws = true;
     }
     k_s_update_ws<<<grid, WS_THREADS, smem, st>>>((float*)S, ld, (const float*)P, K1, tiles, ntiles,
-                                                  mXi, mEta, k0, k1, use_masks, n, ws_wait_limit,
+                                                  mXi, mEta, k0, k1, use_masks, n, mirror,
+                                                  ws_wait_limit,
                                                   (unsigned long long*)counters);
   } else {
     const size_t smem = (4ull * KC_F32 * PT + (size_t)PT * DP) * sizeof(float);
@@ -505,7 +510,7 @@ void launch_s_update(void* S, int s_prec, int64_t ld, const void* P, int K1, con
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       attr32 = true;
     }
-    OneGraphTiles<float> src{(float*)S, ld, (const float*)P, tiles, mXi, mEta, use_masks, n};
+    OneGraphTiles<float> src{(float*)S, ld, (const float*)P, tiles, mXi, mEta, use_masks, n, mirror};
     k_s_update<float, KC_F32, 2><<<grid, 256, smem, st>>>(src, K1, ntiles, k0, k1,
                                                             (unsigned long long*)counters);
   }

@@ -142,7 +142,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     k_s_update_tc(const __grid_constant__ CUtensorMap tm_hi,
                   const __grid_constant__ CUtensorMap tm_lo, float* __restrict__ S, int64_t ld,
                   const uint32_t* __restrict__ tiles, const int* __restrict__ ntiles, int nkb,
-                  long long wait_limit, int n, unsigned long long* __restrict__ counters) {
+                  long long wait_limit, int n, int mirror,
+                  unsigned long long* __restrict__ counters) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES];
   __shared__ __align__(8) uint64_t bar_acc_full[2], bar_acc_empty[2];
@@ -295,7 +296,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           *reinterpret_cast<float4*>(S + (int64_t)(I * TM + r) * ld + (int64_t)J * TN + lane * 4) = v[q];
         }
       }
-      if (I != J) {
+      if (I != J && mirror) {
         // S[J, I] += D^T
         float4 v[NQ];
 #pragma unroll
@@ -317,7 +318,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (et == 0) {
         const long long vr = max(0, min(TM, n - I * TM)), vc = max(0, min(TN, n - J * TN));
         my_tiles += 1;
-        my_bytes += (unsigned long long)(vr * vc) * 8ull * (I == J ? 1ull : 2ull);
+        my_bytes += (unsigned long long)(vr * vc) * 8ull * ((I == J || !mirror) ? 1ull : 2ull);
       }
     }
     if (!ok) abort_flag = 1;
@@ -372,7 +373,8 @@ bool make_map(CUtensorMap* m, float* ptr, int64_t rows, int64_t kd) {
 // 2 * 32; the B operand is A with its two column halves swapped.
 int launch_s_update_tc(float* S, int64_t ld, const float* Ahi, const float* Alo, int64_t n_rows,
                        int64_t kd, const uint32_t* tiles, const int* ntiles, int n,
-                       int64_t* counters, int grid, long long wait_limit, cudaStream_t st) {
+                       int64_t* counters, int grid, long long wait_limit, cudaStream_t st,
+                       int upper) {
   if (kd % (2 * KCH) != 0 || n_rows % TM != 0) return 1;
   CUtensorMap mhi, mlo;
   if (!make_map(&mhi, const_cast<float*>(Ahi), n_rows, kd)) return 2;
@@ -384,7 +386,8 @@ int launch_s_update_tc(float* S, int64_t ld, const float* Ahi, const float* Alo,
     attr = true;
   }
   k_s_update_tc<<<grid, TC_THREADS, smem, st>>>(mhi, mlo, S, ld, tiles, ntiles, (int)(kd / KCH),
-                                                wait_limit, n, (unsigned long long*)counters);
+                                                wait_limit, n, upper ? 0 : 1,
+                                                (unsigned long long*)counters);
   return 0;
 }
 

@@ -18,6 +18,15 @@ namespace sr {
 // which = 0 for xi_k, 1 for eta_k, k = 0..K (K1 = K + 1 terms).
 constexpr int PT = 128;
 
+// Element (r, c) of S when only the tiles on or above the block diagonal are
+// kept (upper = true): an element of a lower tile is read from its mirror.
+#ifdef __CUDACC__
+template <typename T>
+__device__ __forceinline__ T s_at(const T* S, int64_t ld, int64_t r, int64_t c, bool upper) {
+  return (upper && (r / PT) > (c / PT)) ? S[c * ld + r] : S[r * ld + c];
+}
+#endif
+
 inline int64_t panel_index(int64_t node, int which, int k, int K1) {
   return (((node / PT) * 2 + which) * (int64_t)K1 + k) * PT + (node % PT);
 }
@@ -76,7 +85,7 @@ void set_global_error(const std::string& msg);
 // scal[2] = w_j = (1/delta) [Q]_{j,*} S_{*,I} on the graph `in` (the old one).
 void launch_gather_rows(const void* S, int s_prec, int64_t ld, const int32_t* I, int delta, int j,
                         int n_pad, const DevAdj& in, double* sI, double* sJ, double* scal,
-                        cudaStream_t st);
+                        cudaStream_t st, int upper = 0);
 
 // gamma of Thm 3 / Thm 9 / Table 2 on the OLD graph; writes xi_0 = C e_j and
 // eta_0 = gamma into the panels (FP64 and, for FP32 S, FP32) and writes the
@@ -89,7 +98,7 @@ void launch_gamma(const DevAdj& in, const double* sI, const double* sJ, const do
 // (tile-blocked FP32 [T][which][GK1][128], nterms used terms).
 void launch_gather_rows_pending(const void* S, int s_prec, int64_t ld, const int32_t* I, int delta,
                                 int j, int n_pad, const float* Pp, int GK1, int nterms, double* sI,
-                                double* sJ, cudaStream_t st);
+                                double* sJ, cudaStream_t st, int upper = 0);
 // scal[0] = sum_t sI[I_t], scal[1] = sJ[j], scal[2] = (1/(delta d_j)) sum_{b in I(j)} sI[b]
 void launch_scalars_from_rows(const DevAdj& in, const double* sI, const double* sJ, const int32_t* I,
                               int delta, int j, double* scal, cudaStream_t st);
@@ -143,6 +152,7 @@ struct PrepParams {
   uint32_t* tiles;
   int* ntiles;
   int tile_mode;
+  int upper;  // 1: only tiles on or above the block diagonal of S are kept
   int cap;
   int item;
   int n_pad, nT_cap;
@@ -170,8 +180,8 @@ struct MultiGraphDesc {
   DevAdj in, out;
   void* sI;
   void* sJ;
-  int n;  // current node count (byte counters)
-  int pad_;
+  int n;      // current node count (byte counters)
+  int upper;  // 1: only tiles on or above the block diagonal are kept
 };
 // One rank-one update of graph g in a round: sources srcs[src_off ..
 // src_off + delta) into sink j, op = +1/-1, old in-degree d_j, patch ops
@@ -204,7 +214,7 @@ void launch_tile_list(const uint64_t* mXi, const uint64_t* mEta, int nT, int aff
 void launch_s_update(void* S, int s_prec, int64_t ld, const void* P, int K1, const uint32_t* tiles,
                      const int* ntiles, const uint64_t* mXi, const uint64_t* mEta, int k0, int k1,
                      int use_masks, int n, int64_t* counters, int grid, cudaStream_t st,
-                     long long ws_wait_limit = 0);
+                     long long ws_wait_limit = 0, int upper = 0);
 // Persistent grid for launch_s_update on this device (ws: warp-specialised).
 int s_update_grid(int s_prec, int num_sms, bool ws = false);
 
@@ -218,6 +228,8 @@ void launch_transpose(const void* A, void* B, int prec, int n_pad, int64_t ld, c
 // *out_bits = max(*out_bits, max |A - B|) over the n x n block (as double bits)
 void launch_maxdiff(const void* A, const void* B, int prec, int n, int64_t ld,
                     unsigned long long* out_bits, cudaStream_t st);
+// S[J, I] = S[I, J]^T for all 128-tiles I < J (restores the lower triangle)
+void launch_mirror_lower(void* A, int prec, int n_pad, int64_t ld, cudaStream_t st);
 void launch_symmetrize(void* A, int prec, int n_pad, int64_t ld, cudaStream_t st);
 // B[e] = A[e] for e < count, converting between FP32 and FP64.
 void launch_convert(const void* A, int a_prec, void* B, int b_prec, int64_t count, cudaStream_t st);
@@ -226,12 +238,12 @@ void launch_set_diag(void* A, int prec, int from, int to, int64_t ld, double val
 // out[c * n + a] = S[cols[c], perm[a]]  (column c of the symmetric S in caller
 // order; perm maps caller ids to storage ids, nullptr = identity)
 void launch_copy_cols(const void* S, int s_prec, int64_t ld, const int32_t* cols, const int32_t* perm,
-                      int ncols, int n, void* out, int out_fp64, cudaStream_t st);
+                      int ncols, int n, void* out, int out_fp64, cudaStream_t st, int upper = 0);
 
 // ---- one-shot batch (rank-2r) pieces, k_batch.cu
 // Zc[t][a] = sum_{e in block t} sign[e] * S[src[e], a], a < n_pad
 void launch_signed_rows(const void* S, int s_prec, int64_t ld, const int32_t* src, const int8_t* sign,
-                        const int64_t* off, int r, int n_pad, double* Zc, cudaStream_t st);
+                        const int64_t* off, int r, int n_pad, double* Zc, cudaStream_t st, int upper = 0);
 // B[c * ldb + r] = A[r * lda + c]
 void launch_transpose_rect(const double* A, int64_t lda, double* B, int64_t ldb, int rows, int cols,
                            cudaStream_t st);
@@ -239,11 +251,11 @@ void launch_transpose_rect(const double* A, int64_t lda, double* B, int64_t ldb,
 void launch_lambda(const void* S, int s_prec, int64_t ld, const int32_t* sinks, const double* av,
                    const double* bv, const double* Y, const double* Z, int64_t ldz,
                    const int32_t* src, const int8_t* sign, const int64_t* off, int r, double C,
-                   double* Lam, cudaStream_t st);
+                   double* Lam, cudaStream_t st, int upper = 0);
 // Wc[t][a] = a_t (S[j_t,a] - (1-C)[a==j_t]) / C + b_t Yc[t][a] + Lambda[u][t]/2 [a == j_u]
 void launch_w_assemble(const void* S, int s_prec, int64_t ld, const int32_t* sinks, const double* av,
                        const double* bv, const double* Yc, const double* Lam, int r, int n_pad,
-                       double C, double* Wc, cudaStream_t st);
+                       double C, double* Wc, cudaStream_t st, int upper = 0);
 void launch_xi0(const int32_t* sinks, int r, double C, double* X0, int64_t ldx, cudaStream_t st);
 void launch_pack_ffma(const double* X, int64_t ldx, int rh, int r, int slot, int terms, int nT,
                       void* Pn, int p_prec, uint64_t* mXi, uint64_t* mEta, cudaStream_t st);
@@ -253,7 +265,8 @@ void launch_pack_tc(const double* X, int64_t ldx, int rh, int r, int slot, int r
 // 0 on launch, 1 for a bad shape, 2 if no tensor map could be encoded.
 int launch_s_update_tc(float* S, int64_t ld, const float* Ahi, const float* Alo, int64_t n_rows,
                        int64_t kd, const uint32_t* tiles, const int* ntiles, int n,
-                       int64_t* counters, int grid, long long wait_limit, cudaStream_t st);
+                       int64_t* counters, int grid, long long wait_limit, cudaStream_t st,
+                       int upper = 0);
 
 // ---- column mode (§7), k_column.cu
 // A piece of one adjacency row: row id, count (<= kChunk) and pool offset.

@@ -34,12 +34,33 @@ def test_library_exports_every_declared_symbol():
     assert decl == set(P.SIGNATURES), decl ^ set(P.SIGNATURES)
 
 
-def test_struct_sizes_match_header():
-    # simrank_update is 16 bytes; config / stats layouts are fixed by the header
+def test_struct_layouts_match_header(tmp_path):
+    """Size and field offsets of the ctypes structs equal the C compiler's
+    layout of include/simrank.h (a small C program prints them)."""
     import ctypes
-    assert ctypes.sizeof(P.Update) == 16
-    assert ctypes.sizeof(P.Config) == 8 + 4 * 10 + 8 + 4 + 4 + 8 + 8 + 32
-    assert ctypes.sizeof(P.Stats) == 8 * 8 + 8 + 8 + 32 + 4 + 28
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"simrank_update": P.Update, "simrank_config": P.Config, "simrank_stats": P.Stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "simrank.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                       text=True).stdout.splitlines())
+    for cname, cls in structs.items():
+        assert int(got[cname]) == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert int(got[f"{cname}.{fname}"]) == getattr(cls, fname).offset, (cname, fname)
 
 
 def _expand_oracle(ups, n_old):

@@ -121,7 +121,7 @@ def test_unit_update_converged_vs_batch_recompute(P, case):
 @pytest.mark.parametrize("variant", ["fused_aff", "fused_aff_norelabel", "fused_single_role",
                                      "fused_noaff", "plain", "deferred_ffma", "deferred_tc",
                                      "per_step_chain", "prep_multi_tile", "prep_small_items",
-                                     "deferred_multi_tile"])
+                                     "deferred_multi_tile", "full_storage", "deferred_tc_full"])
 def test_stream_fp32_powerlaw(P, variant):
     n, m, C, K = 1500, 15000, 0.6, 20
     s, d = chung_lu_digraph(n, m, 2.1, 2.1, 4)
@@ -148,6 +148,10 @@ def test_stream_fp32_powerlaw(P, variant):
     elif variant == "prep_small_items":
         # 48-nonzero work items: every tile split over several CTAs
         kw = dict(aff=1, prep_item=48, prep_ctas=40)
+    elif variant == "full_storage":
+        kw = dict(aff=1, upper_only=0)
+    elif variant == "deferred_tc_full":
+        kw = dict(aff=1, defer=16, tc=1, upper_only=0)
     elif variant == "deferred_multi_tile":
         kw = dict(aff=1, defer=7, tc=1, prep_ctas=3, prep_cache=128)
     sr = P.SimRank(n, s, d, C=C, K=K, s_precision=32, **kw)
@@ -160,8 +164,10 @@ def test_stream_fp32_powerlaw(P, variant):
 
 
 @pytest.mark.parametrize("kw", [{}, {"chain": 1}, {"prep_ctas": 2, "prep_cache": 32},
-                                {"prep_item": 40, "prep_ctas": 30}],
-                         ids=["fused", "per_step", "fused_multi_tile", "fused_small_items"])
+                                {"prep_item": 40, "prep_ctas": 30}, {"upper_only": 0},
+                                {"upper_only": 0, "chain": 1}],
+                         ids=["fused", "per_step", "fused_multi_tile", "fused_small_items",
+                              "full_storage", "full_storage_per_step"])
 def test_stream_fp64_matches_oracle(P, kw):
     n, m, C, K = 700, 4200, 0.8, 12
     s, d = er_graph(n, m, 6)
