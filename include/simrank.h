@@ -81,7 +81,9 @@ typedef struct simrank_config {
   int32_t aff;            /* 1: skip S tiles outside the affected area of Thm 4; 0: touch every tile */
   int32_t apply;          /* SR_APPLY_* */
   int32_t s_update;       /* SR_SUPDATE_* */
-  int32_t tc;             /* one-shot batch form: 0 = CUDA-core FFMA update, 1 = tensor cores (3xTF32 split) */
+  int32_t tc;             /* S passes on the tensor cores (3xTF32 split): 1 = the one-shot batch
+                             form's pass, and with FP32 S the pass of every unit / sink-block
+                             update (or of every group of `defer` pending updates); 0 = CUDA cores */
   int32_t init_max_sweeps;/* cap on Jacobi sweeps of Eq. 1 at init / re-anchor */
   double init_tol;        /* init stops when a sweep changes S by less than this (max-abs) */
   int32_t profile;        /* 1: time every S-update launch with CUDA events (simrank_get_stats) */

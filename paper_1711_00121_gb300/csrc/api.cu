@@ -64,8 +64,7 @@ struct simrank_ctx {
   int64_t* counters = nullptr;
   unsigned long long* diffbits = nullptr;
   unsigned int* gbar = nullptr;  // grid barrier state of the cooperative pre-update kernel
-  void* W = nullptr;             // (xi, eta) working columns of the pre-update kernel
-  int* tile_nnz = nullptr;
+  int* tile_nnz = nullptr;       // per-tile nonzeros (scratch of the pre-update kernel)
   // per-call staging
   int32_t* d_srcs = nullptr;
   int64_t srcs_cap = 0;
@@ -417,10 +416,14 @@ simrank_status s_update_launch(simrank_ctx* h, int k0, int k1, int use_masks) {
 
 simrank_status ob_ensure(simrank_ctx* h, int slot, size_t bytes);
 
+// Updates go through the pending-panel buffer: G > 1 pending updates share
+// one S pass, or (tc = 1) each update's S pass runs on the tensor cores.
 bool deferring(const simrank_ctx* h) {
-  return h->cfg.defer > 1 && h->cfg.s_precision == 32 && !h->column &&
-         h->cfg.s_update == SR_SUPDATE_FUSED;
+  return (h->cfg.defer > 1 || h->cfg.tc) && h->cfg.s_precision == 32 && !h->column &&
+         h->cfg.s_update == SR_SUPDATE_FUSED && h->cfg.apply != SR_APPLY_ONE_SHOT;
 }
+// Updates per pending group (1 when tensor cores apply each update at once).
+int group(const simrank_ctx* h) { return std::max(1, (int)h->cfg.defer); }
 
 // Applies the pending updates' panels to S in one pass (rank 2 * np * K1).
 simrank_status flush_pending(simrank_ctx* h) {
@@ -436,7 +439,7 @@ simrank_status flush_pending(simrank_ctx* h) {
     if (!pe) return fail(h, SR_ERR_CUDA, "cudaEventCreate failed");
     for (int q = 0; q < 3; ++q) CUDA_TRY(h, cudaEventRecord(pe[q], h->st));
   }
-  const int GK1 = h->cfg.defer * h->K1;
+  const int GK1 = group(h) * h->K1;
   const int nterms = h->np * h->K1;
   CUDA_TRY(h, cudaMemsetAsync(h->ntiles, 0, sizeof(int), h->st));
   launch_tile_list(h->pXi, h->pEta, nT, h->cfg.aff ? 1 : 0, h->tiles, h->ntiles, h->st);
@@ -506,7 +509,7 @@ simrank_status run_rank_one(simrank_ctx* h, int64_t src_off, int delta, int j, i
   }
   const bool defer = deferring(h);
   if (defer && !h->Pp) {
-    const size_t pb = (size_t)h->nT_cap * 2 * h->cfg.defer * h->K1 * PT * sizeof(float);
+    const size_t pb = (size_t)h->nT_cap * 2 * group(h) * h->K1 * PT * sizeof(float);
     CUDA_TRY(h, cudaMalloc(&h->Pp, pb));
     CUDA_TRY(h, cudaMemsetAsync(h->Pp, 0, pb, h->st));
     CUDA_TRY(h, dev_alloc(&h->pXi, (size_t)h->nT_cap));
@@ -535,7 +538,7 @@ simrank_status run_rank_one(simrank_ctx* h, int64_t src_off, int delta, int j, i
     pp.nT = nT;
     if (defer) {
       pp.P = h->Pp;
-      pp.ldk = h->cfg.defer * h->K1;
+      pp.ldk = group(h) * h->K1;
       pp.koff = h->np * h->K1;
       pp.npend = h->np * h->K1;
       pp.pXi = h->pXi;
@@ -556,16 +559,12 @@ simrank_status run_rank_one(simrank_ctx* h, int64_t src_off, int delta, int j, i
     pp.item = h->cfg.prep_item;
     pp.n_pad = h->n_pad;
     pp.nT_cap = h->nT_cap;
-    if (!h->W) {
-      CUDA_TRY(h, cudaMalloc(&h->W, (size_t)h->K1 * h->n_pad * 2 * (h->cfg.s_precision / 8)));
-      CUDA_TRY(h, dev_alloc(&h->tile_nnz, (size_t)h->nT_cap));
-    }
-    pp.W = h->W;
+    if (!h->tile_nnz) CUDA_TRY(h, dev_alloc(&h->tile_nnz, (size_t)h->nT_cap));
     pp.tile_nnz = h->tile_nnz;
     pp.bar = h->gbar + 2;
     pp.limit = wait_limit(h);
     pp.counters = (unsigned long long*)h->counters;
-    const int rc = launch_prep(pp, h->cfg.s_precision, defer ? h->cfg.defer * h->K1 : 0,
+    const int rc = launch_prep(pp, h->cfg.s_precision, defer ? group(h) * h->K1 : 0,
                                h->num_sms, h->cfg.prep_ctas, (int64_t)h->edges.size() + delta,
                                h->st);
     if (rc == 1) return fail(h, SR_ERR_CUDA, "fused pre-update launch failed");
@@ -584,7 +583,7 @@ simrank_status run_rank_one(simrank_ctx* h, int64_t src_off, int delta, int j, i
     if (defer) {
       // rows i (summed over the block) and j of the current S = S + pending panels
       launch_gather_rows_pending(h->S, 32, h->ld, h->d_srcs + src_off, delta, j, nT * PT, h->Pp,
-                                 h->cfg.defer * h->K1, h->np * h->K1, h->sI, h->sJ, h->st,
+                                 group(h) * h->K1, h->np * h->K1, h->sI, h->sJ, h->st,
                                  upper(h));
       launch_scalars_from_rows(h->din, h->sI, h->sJ, h->d_srcs + src_off, delta, j, h->scal, h->st);
       h->launches += 1;
@@ -605,7 +604,7 @@ simrank_status run_rank_one(simrank_ctx* h, int64_t src_off, int delta, int j, i
     if (defer) {
       // append this update's panels as pending terms np*K1 .. np*K1 + K (FP32)
       const size_t w = (size_t)h->K1 * PT * sizeof(float);
-      const size_t dpitch = (size_t)h->cfg.defer * w;
+      const size_t dpitch = (size_t)group(h) * w;
       CUDA_TRY(h, cudaMemcpy2DAsync((unsigned char*)h->Pp + (size_t)h->np * w, dpitch, h->P32, w,
                                     w, (size_t)nT * 2, cudaMemcpyDeviceToDevice, h->st));
       launch_or_any(h->mXi, h->mEta, nT, h->pXi, h->pEta, h->st);
@@ -623,7 +622,7 @@ simrank_status run_rank_one(simrank_ctx* h, int64_t src_off, int delta, int j, i
     h->np += 1;
     if (pe) CUDA_TRY(h, cudaEventRecord(pe[4], h->st));
     h->stats.rank_one_updates += 1;
-    if (h->np == h->cfg.defer) return flush_pending(h);
+    if (h->np == group(h)) return flush_pending(h);
     return SR_OK;
   }
   simrank_status s;
@@ -1039,7 +1038,7 @@ void free_ctx(simrank_ctx* h) {
                   h->dout.col,  h->d_in_w,   h->d_wsum,    h->S,          h->P64,
                   h->P32,       h->mXi,      h->mEta,      h->tiles,      h->ntiles,
                   h->sI,        h->sJ,       h->scal,      h->counters,   h->diffbits,
-                  h->gbar,      h->W,        h->tile_nnz,
+                  h->gbar,      h->tile_nnz,
                   h->d_srcs,    h->d_ops,    h->d_cols,     h->d_ext2int};
   for (void* p : ptrs)
     if (p) cudaFree(p);

@@ -125,9 +125,9 @@ void launch_chain_step(const DevAdj& in, int k, double C, int nT, int K1, double
 // mask words mXi/mEta of tiles [0, nT) (ORed as 0/1 into pXi/pEta when
 // those are set) and, when `tiles` is set, the tile-pair list (tile_mode 0 =
 // all pairs, 1 = AFF-pruned).  P is tile-blocked [T][which][ldk][128] in the
-// precision of S; sI, sJ hold n_pad values of that precision; W is the
-// working buffer [K+1][n_pad] of (xi, eta) pairs of that precision; tile_nnz
-// holds nT_cap ints.  Gathers are split into items of at most `item`
+// precision of S (columns koff .. koff+K are zeroed and accumulated by
+// atomics); sI, sJ hold n_pad values of that precision; tile_nnz holds
+// nT_cap ints.  Gathers are split into items of at most `item`
 // nonzeros; `cap` column indices are cached per CTA (a multiple of 4).
 // bar: two zeroed unsigned ints, left zeroed.  nnz_bound bounds the edges of
 // the new graph (it sizes the grid).  Returns 0 on launch, 2 when the graph
@@ -156,7 +156,6 @@ struct PrepParams {
   int cap;
   int item;
   int n_pad, nT_cap;
-  void* W;
   int* tile_nnz;
   unsigned int* bar;
   long long limit;

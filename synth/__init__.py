@@ -10,6 +10,7 @@ from .graphs import (  # noqa: F401
     chung_lu_digraph,
     random_arborescence,
     update_stream,
+    keyed_update_stream,
     batch_with_new_nodes,
     edge_weights,
     query_pairs,

@@ -169,6 +169,57 @@ def update_stream(n: int, src, dst, count: int, seed: int, frac_insert: float = 
     return out
 
 
+def keyed_update_stream(n: int, src, dst, count: int, seed: int, frac_insert: float = 0.8):
+    """Same distribution as :func:`update_stream`, for graphs too large for a
+    Python edge set: membership tests use the sorted int64 keys src * n + dst.
+
+    Insertions draw the source proportional to (out-degree + 1) and the
+    target proportional to (in-degree + 1) of the initial graph; deletions
+    pick a uniformly random edge among those present (initial edges not yet
+    deleted and edges inserted earlier in the stream).  Returns an int32
+    array of shape (count, 3).
+    """
+    rng = np.random.default_rng(seed)
+    src = np.asarray(src, np.int64)
+    dst = np.asarray(dst, np.int64)
+    keys = np.sort(src * n + dst)
+    draw_src = _Sampler(np.bincount(src, minlength=n) + 1.0, rng)
+    draw_dst = _Sampler(np.bincount(dst, minlength=n) + 1.0, rng)
+    added, removed = set(), set()
+
+    def present(k):
+        if k in added:
+            return True
+        if k in removed:
+            return False
+        p = np.searchsorted(keys, k)
+        return p < keys.size and keys[p] == k
+
+    out = np.empty((count, 3), np.int32)
+    for t in range(count):
+        if rng.random() < frac_insert:
+            while True:
+                i, j = draw_src(), draw_dst()
+                k = i * n + j
+                if i != j and not present(k):
+                    break
+            added.add(k)
+            removed.discard(k)
+            out[t] = (i, j, UPDATE_INSERT)
+        else:
+            while True:
+                if added and rng.random() < len(added) / (len(added) + keys.size):
+                    k = sorted(added)[int(rng.integers(0, len(added)))]
+                else:
+                    k = int(keys[int(rng.integers(0, keys.size))])
+                if present(k):
+                    break
+            added.discard(k)
+            removed.add(k)
+            out[t] = (k // n, k % n, UPDATE_DELETE)
+    return out
+
+
 def batch_with_new_nodes(n: int, src, dst, b: int, seed: int, frac_new: float = 0.10,
                          frac_insert: float = 0.8, reuse_target: float = 0.25,
                          edge_set: EdgeSet | None = None):
