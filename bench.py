@@ -493,6 +493,66 @@ def run_multi(args):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------
+# Column-block workload (§7, Alg 7): directed Chung-Lu n = 2,000,000,
+# m = 20,000,000 (exponent 2.1), C = 0.6, K = 15, S never stored densely;
+# a stream of 32 unit updates is applied (each: Procedure 1 for its two old
+# columns on the current graph, gamma, the recurrence, a panel snapshot),
+# then blocks of 1024 columns are queried (Procedure 1 on the initial graph
+# plus the change through every stored update).  Metric: columns/s.
+# --------------------------------------------------------------------------
+CN, CDEG, CC, CK, CB, CU = 2000000, 10, 0.6, 15, 1024, 32
+
+
+def run_column(args):
+    import torch
+
+    import paper_1711_00121_gb300 as P
+    from synth import keyed_update_stream
+
+    torch.cuda.set_device(0)
+    n = args.column_n
+    m = CDEG * n
+    s, d = chung_lu_digraph(n, m, 2.1, 2.1, 5)
+    ups = keyed_update_stream(n, s, d, CU, 6)
+    stream = torch.cuda.Stream()
+    t0 = time.time()
+    sr = P.SimRank(n, s, d, C=CC, K=CK, s_precision=32, mode=P.MODE_COLUMN,
+                   stream=stream.cuda_stream)
+    init_s = time.time() - t0
+    with torch.cuda.stream(stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sr.apply_updates(ups)
+        e1.record(stream)
+        sr.sync()
+        apply_ms = e0.elapsed_time(e1)
+        rng = np.random.default_rng(8)
+        out = torch.empty((CB, n), dtype=torch.float32, device="cuda")
+        warm = np.sort(rng.choice(n, size=64, replace=False)).astype(np.int32)
+        sr.columns_device(warm, out[:64])
+        sr.sync()
+        times = []
+        with ClockSampler(0) as clk:
+            for t in range(args.steps):
+                cols = np.sort(rng.choice(n, size=CB, replace=False)).astype(np.int32)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                sr.columns_device(cols, out)
+                b.record(stream)
+                sr.sync()
+                times.append(a.elapsed_time(b))
+    ms = sum(times) / len(times)
+    line = {"workload": f"column block: directed Chung-Lu n={n} m={m} exponent 2.1, C={CC}, K={CK}, "
+                        f"{CU} stored unit updates, blocks of {CB} columns, FP32",
+            "metric": "columns/s", "value": CB / (ms / 1000.0), "unit": "columns/s",
+            "ms_per_block": ms, "steps": args.steps, "init_s": init_s,
+            "apply_ms_per_update": apply_ms / CU,
+            "s_per_column_per_update": (ms / 1000.0) / CB / CU, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    sr.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -502,12 +562,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--updates-per-step", type=int, default=UPDATES_PER_STEP,
                     help="batch size of one step (the benchmarked workload uses 1000)")
-    ap.add_argument("--defer", type=int, default=0,
+    ap.add_argument("--defer", type=int, default=16,
                     help="stream workload: rank-one updates kept pending per S pass (0 = apply each)")
-    ap.add_argument("--tc", type=int, default=0, help="S passes on tensor cores (with --defer)")
-    ap.add_argument("--workload", default="stream", choices=["stream", "batched", "multi"],
+    ap.add_argument("--tc", type=int, default=1, help="S passes on the tensor cores (3xTF32)")
+    ap.add_argument("--workload", default="stream",
+                    choices=["stream", "batched", "multi", "column"],
                     help="stream: the benchmarked update stream; batched: one-shot vs per-edge; "
-                         "multi: many graphs batched vs per-graph launches")
+                         "multi: many graphs batched vs per-graph launches; column: column-block "
+                         "mode queries")
+    ap.add_argument("--column-n", type=int, default=CN, help="column workload: node count")
     ap.add_argument("--graphs", type=int, default=MG, help="multi workload: number of graphs")
     ap.add_argument("--batch", type=int, default=64, help="batched workload: edges per batch")
     ap.add_argument("--per-edge-sample", type=int, default=256,
@@ -520,6 +583,9 @@ def main():
         return
     if args.workload == "multi":
         run_multi(args)
+        return
+    if args.workload == "column":
+        run_column(args)
         return
     if args.impl == "reference":
         run_reference(args, rank)

@@ -112,8 +112,7 @@ typedef struct simrank_config {
                              replayed from a CUDA graph; 1 = the same kernels launched graph by
                              graph (the per-graph-launch baseline) */
   int32_t prep_item;      /* chain = 0: nonzeros per work item of the fused launch's gathers
-                             (0 = sized so that the items fit one per CTA, at least 256); a tile
-                             with more nonzeros is split over several CTAs */
+                             (0 = 1024); a tile with more nonzeros is split over several CTAs */
   int32_t upper_only;     /* dense mode: 1 = keep only the 128 x 128 tiles of S on or above the
                              block diagonal current (S is symmetric; updates then read and write
                              half the bytes, and reads of a lower tile take its mirror); 0 = keep

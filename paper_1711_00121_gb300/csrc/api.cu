@@ -64,6 +64,7 @@ struct simrank_ctx {
   int64_t* counters = nullptr;
   unsigned long long* diffbits = nullptr;
   unsigned int* gbar = nullptr;  // grid barrier state of the cooperative pre-update kernel
+  void* W = nullptr;             // (xi, eta) working columns of the pre-update kernel
   int* tile_nnz = nullptr;       // per-tile nonzeros (scratch of the pre-update kernel)
   // per-call staging
   int32_t* d_srcs = nullptr;
@@ -559,7 +560,11 @@ simrank_status run_rank_one(simrank_ctx* h, int64_t src_off, int delta, int j, i
     pp.item = h->cfg.prep_item;
     pp.n_pad = h->n_pad;
     pp.nT_cap = h->nT_cap;
-    if (!h->tile_nnz) CUDA_TRY(h, dev_alloc(&h->tile_nnz, (size_t)h->nT_cap));
+    if (!h->W) {
+      CUDA_TRY(h, cudaMalloc(&h->W, (size_t)h->K1 * h->n_pad * 2 * (h->cfg.s_precision / 8)));
+      CUDA_TRY(h, dev_alloc(&h->tile_nnz, (size_t)h->nT_cap));
+    }
+    pp.W = h->W;
     pp.tile_nnz = h->tile_nnz;
     pp.bar = h->gbar + 2;
     pp.limit = wait_limit(h);
@@ -1014,7 +1019,19 @@ simrank_status column_mode_columns(simrank_ctx* h, const int32_t* cols, int ncol
     void* res = base + blkb * (K + 3);
     launch_partial_sim_block(h->g0_fwd, h->g0_hor, h->g0_out_col, h->g0_in_col, h->g0_in_len, bc,
                              B, n_pad, K, h->cfg.C, prec, xs, y0, y1, res, h->st);
-    for (void* P : h->hist) launch_col_apply(P, prec, h->K1, bc, B, n_pad, prec, res, h->st);
+    if (prec == 32 && !h->hist.empty()) {
+      // all stored updates in one FP32 product
+      const int U = (int)h->hist.size();
+      const size_t gbytes = (size_t)U * 2 * h->K1 * ((B + 3) / 4 * 4) * sizeof(float);
+      if ((s = ob_ensure(h, 17, U * sizeof(void*))) != SR_OK) return s;
+      if ((s = ob_ensure(h, 18, gbytes)) != SR_OK) return s;
+      CUDA_TRY(h, cudaMemcpyAsync(h->ob[17].p, h->hist.data(), U * sizeof(void*),
+                                  cudaMemcpyHostToDevice, h->st));
+      launch_col_corr((const float* const*)h->ob[17].p, U, h->K1, bc, B, n_pad,
+                      (float*)h->ob[18].p, (float*)res, h->st);
+    } else {
+      for (void* P : h->hist) launch_col_apply(P, prec, h->K1, bc, B, n_pad, prec, res, h->st);
+    }
     launch_col_out(res, prec, B, h->n_cur,
                    (unsigned char*)dst + (size_t)c0 * h->n_cur * (out_fp64 ? 8 : 4), out_fp64, h->st);
     cudaError_t e = cudaGetLastError();
@@ -1038,7 +1055,7 @@ void free_ctx(simrank_ctx* h) {
                   h->dout.col,  h->d_in_w,   h->d_wsum,    h->S,          h->P64,
                   h->P32,       h->mXi,      h->mEta,      h->tiles,      h->ntiles,
                   h->sI,        h->sJ,       h->scal,      h->counters,   h->diffbits,
-                  h->gbar,      h->tile_nnz,
+                  h->gbar,      h->W,        h->tile_nnz,
                   h->d_srcs,    h->d_ops,    h->d_cols,     h->d_ext2int};
   for (void* p : ptrs)
     if (p) cudaFree(p);

@@ -6,7 +6,11 @@
 //    steps Y <- X_{K-t} + C Q Y over the in-lists; result (1-C) Y.
 //  - The change of a column through the stored updates (Eq. 70-71):
 //    Y[a, c] += sum_k xi_k[a] eta_k[x_c] + eta_k[a] xi_k[x_c].
-// Blocks are row-major [node][B]; FP32 or FP64 storage, FP64 accumulation.
+// Blocks are row-major [node][B]; the arithmetic is in the storage
+// precision (FP32 or FP64).  With FP32 the change through the stored updates
+// is one dense product per block: Y += A G with A = [xi_k, eta_k of every
+// update] (n x 2 U (K+1), straight from the tile-blocked panels) and G the
+// matching values at the block's columns.
 #include "sr_internal.h"
 
 namespace sr {
@@ -23,9 +27,10 @@ __global__ void k_col_unit(const int32_t* __restrict__ cols, int B, T* __restric
 // Y[a][c] = s * X[a][c] (X may be null: Y = 0), a < n_rows, c < B
 template <typename T>
 __global__ void k_col_fill(const T* __restrict__ X, double s, T* __restrict__ Y, int64_t count) {
+  const T sv = (T)s;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
        e += (int64_t)gridDim.x * blockDim.x)
-    Y[e] = X ? (T)(s * (double)X[e]) : (T)0;
+    Y[e] = X ? sv * X[e] : (T)0;
 }
 
 // One row chunk (at most CHUNK nonzeros of one adjacency row) per CTA and
@@ -44,17 +49,17 @@ __global__ void k_col_chunk(const RowChunk* __restrict__ chunks, const int32_t* 
   const RowChunk ch = chunks[blockIdx.x];
   const int c = blockIdx.y * blockDim.x + threadIdx.x;
   if (c >= B) return;
-  double acc = 0.0;
+  T acc = T(0);
 #pragma unroll 8
   for (int e = 0; e < ch.len; ++e) {
     const int a = col[ch.start + e];
-    double x = (double)X[(int64_t)a * B + c];
-    if (ew) x *= (double)ew[ch.start + e];
-    if (FORWARD) x /= wsum ? wsum[a] : (double)in_len[a];
+    T x = X[(int64_t)a * B + c];
+    if (ew) x *= (T)ew[ch.start + e];
+    if (FORWARD) x /= wsum ? (T)wsum[a] : (T)in_len[a];
     acc += x;
   }
-  const double rs = FORWARD ? 1.0 : scale / (wsum ? wsum[ch.row] : (double)in_len[ch.row]);
-  atomicAdd(&Y[(int64_t)ch.row * B + c], (T)(rs * acc));
+  const T rs = FORWARD ? T(1) : (T)scale / (wsum ? (T)wsum[ch.row] : (T)in_len[ch.row]);
+  atomicAdd(&Y[(int64_t)ch.row * B + c], rs * acc);
 }
 
 // Y[a][c] += sum_k xi_k[a] eta_k[x_c] + eta_k[a] xi_k[x_c] for one stored
@@ -82,6 +87,89 @@ __global__ void k_col_apply(const TP* __restrict__ P, int K1, const int32_t* __r
       acc += (double)P[ba + (int64_t)k * PT] * g[K1 + k] +
              (double)P[ba + (int64_t)(K1 + k) * PT] * g[k];
     Y[a * B + c] = (T)((double)Y[a * B + c] + acc);
+  }
+}
+
+// G[u][r][c] for the FP32 product: r = which * K1 + k, the value of the
+// OTHER vector of term k of update u at column x_c (eta_k[x_c] pairs with
+// xi_k[a], xi_k[x_c] with eta_k[a]); c < B, zero for c in [B, Bp).
+__global__ void k_col_gvals(const float* const* __restrict__ hist, int K1,
+                            const int32_t* __restrict__ cols, int B, int Bp,
+                            float* __restrict__ G) {
+  const int u = blockIdx.y;
+  const float* P = hist[u];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 2 * K1 * Bp; e += gridDim.x * blockDim.x) {
+    const int r = e / Bp, c = e % Bp;
+    const int which = r / K1, k = r % K1;
+    float v = 0.f;
+    if (c < B) {
+      const int64_t x = cols[c];
+      v = P[(((x / PT) * 2 + (1 - which)) * (int64_t)K1 + k) * PT + (x % PT)];
+    }
+    G[((int64_t)u * 2 * K1 + r) * Bp + c] = v;
+  }
+}
+
+// Y[a][c] += sum_u sum_r A_u[a][r] G[u][r][c] for the 128 rows of tile
+// blockIdx.x and the 128 columns of group blockIdx.y (256 threads, an 8 x 8
+// block of outputs each; the r-chunks of A and G are staged in shared memory:
+// A_u's tile-blocked panel slice [r][128 rows] is already in that layout).
+constexpr int CG_KC = 16;
+__global__ void __launch_bounds__(256) k_col_corr(const float* const* __restrict__ hist, int U,
+                                                  int K1, const float* __restrict__ G, int Bp,
+                                                  int B, int n_rows, float* __restrict__ Y) {
+  __shared__ __align__(16) float sA[CG_KC][PT];
+  __shared__ __align__(16) float sG[CG_KC][PT];
+  const int T = blockIdx.x, c0 = blockIdx.y * PT;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float acc[8][8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+  const int R = 2 * K1;
+  for (int u = 0; u < U; ++u) {
+    const float* Pt = hist[u] + (int64_t)T * 2 * K1 * PT;  // [r][128], r = which * K1 + k
+    const float* Gu = G + (int64_t)u * R * Bp;
+    for (int r0 = 0; r0 < R; r0 += CG_KC) {
+      const int kc = min(CG_KC, R - r0);
+      __syncthreads();
+      for (int e = tid; e < kc * PT / 4; e += 256) {
+        const int rr = e / (PT / 4), q = e % (PT / 4);
+        reinterpret_cast<float4*>(sA[rr])[q] =
+            reinterpret_cast<const float4*>(Pt + (int64_t)(r0 + rr) * PT)[q];
+        float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int cc = c0 + 4 * q;
+        if (cc < Bp) g = *reinterpret_cast<const float4*>(Gu + (int64_t)(r0 + rr) * Bp + cc);
+        reinterpret_cast<float4*>(sG[rr])[q] = g;
+      }
+      __syncthreads();
+      for (int rr = 0; rr < kc; ++rr) {
+        float a[8], g[8];
+        const float4 a0 = reinterpret_cast<const float4*>(sA[rr])[ty];
+        const float4 a1 = reinterpret_cast<const float4*>(sA[rr])[16 + ty];
+        const float4 g0 = reinterpret_cast<const float4*>(sG[rr])[tx];
+        const float4 g1 = reinterpret_cast<const float4*>(sG[rr])[16 + tx];
+        a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w;
+        a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
+        g[0] = g0.x; g[1] = g0.y; g[2] = g0.z; g[3] = g0.w;
+        g[4] = g1.x; g[5] = g1.y; g[6] = g1.z; g[7] = g1.w;
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+          for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(a[r], g[c], acc[r][c]);
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int64_t row = (int64_t)T * PT + ((r < 4) ? ty * 4 + r : 64 + ty * 4 + (r - 4));
+    if (row >= n_rows) continue;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int col = c0 + ((c < 4) ? tx * 4 + c : 64 + tx * 4 + (c - 4));
+      if (col < B) Y[row * B + col] += acc[r][c];
+    }
   }
 }
 
@@ -217,6 +305,15 @@ void launch_col_apply(const void* P, int p_prec, int K1, const int32_t* cols, in
   else
     SR_COL_APPLY(float, float);
 #undef SR_COL_APPLY
+}
+
+void launch_col_corr(const float* const* hist, int U, int K1, const int32_t* cols, int B,
+                     int n_rows, float* G, float* Y, cudaStream_t st) {
+  if (U <= 0 || B <= 0) return;
+  const int Bp = (B + 3) / 4 * 4;
+  k_col_gvals<<<dim3((2 * K1 * Bp + 255) / 256, U), 256, 0, st>>>(hist, K1, cols, B, Bp, G);
+  k_col_corr<<<dim3(n_rows / PT, (B + PT - 1) / PT), 256, 0, st>>>(hist, U, K1, G, Bp, B, n_rows,
+                                                                   Y);
 }
 
 void launch_col_scalars(const DevAdj& in, const double* si, const double* sj, int i, int j,

@@ -20,9 +20,10 @@
 // with thousands of in-neighbours spreads over many SMs).  Each CTA keeps the
 // row extents and column indices of its first items in shared memory for all
 // K steps.  Partial row sums are combined within a warp and added to the next
-// column of the tile-blocked panels (the ones the S pass reads) with global
-// atomics.  Row-wise work (gamma, the masks) goes by tiles, round-robin; the
-// masks are read off the finished panels at the end.
+// column with global atomics.  xi_k and eta_k are kept interleaved in the
+// working buffer W[k][a] (one 8- or 16-byte load per nonzero).  Row-wise work
+// (gamma; after the last step, the copy of the columns into the tile-blocked
+// panels that the S pass reads, with the masks) goes by tiles, round-robin.
 //
 // gamma needs w on the OLD graph; only row j of Q changes, so the kernel
 // gathers on the patched graph and corrects row j: the sum over the old
@@ -91,6 +92,22 @@ __device__ __forceinline__ bool prep_barrier(unsigned int* count, unsigned int t
 
 __device__ __forceinline__ void red_add(float* p, float v) { atomicAdd(p, v); }
 __device__ __forceinline__ void red_add(double* p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void red_add2(V2<float>* p, float x, float y) {
+  atomicAdd(reinterpret_cast<float2*>(p), make_float2(x, y));
+}
+__device__ __forceinline__ void red_add2(V2<double>* p, double x, double y) {
+  atomicAdd(&p->x, x);
+  atomicAdd(&p->y, y);
+}
+__device__ __forceinline__ V2<float> ld_v2(const V2<float>* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return V2<float>{v.x, v.y};
+}
+__device__ __forceinline__ V2<double> ld_v2(const V2<double>* p) {
+  const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return V2<double>{v.x, v.y};
+}
+
 // Row extents of tile T (after the patch) and the exclusive scan of their lengths.
 __device__ __forceinline__ void item_rows_load(const DevAdj& in, int T, PrepItem& it) {
   const int tid = threadIdx.x;
@@ -282,6 +299,7 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
   V* P = static_cast<V*>(p.P);
   V* sI = static_cast<V*>(p.sI);
   V* sJ = static_cast<V*>(p.sJ);
+  V2<V>* W = static_cast<V2<V>*>(p.W);
   const int nrows = nT * PT;
   const int64_t ldk = p.ldk;
   auto pidx = [ldk](int64_t a, int which, int k) -> int64_t {
@@ -295,21 +313,15 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
   unsigned int nb = 0;
   bool alive = true;
 
-  // ---- phase 0: patch (CTA 0), zero this update's panel columns, rows sI /
-  // sJ, tile nonzero counts
+  // ---- phase 0: patch (CTA 0), zero W, rows sI / sJ, tile nonzero counts
   if (blockIdx.x == 0) {
     if (p.op_end > p.op_begin) prep_patch(p.ops, p.op_begin, p.op_end, p.in, p.out);
     if (tid == 0 && p.tiles) *p.ntiles = 0;
   }
   {
-    // columns koff .. koff + K of both panels: nT * 2 * (K + 1) runs of 128
-    const int64_t runs = (int64_t)nT * 2 * (K + 1);
-    for (int64_t e = (int64_t)blockIdx.x * PG + tid; e < runs * PT; e += (int64_t)G * PG) {
-      const int64_t run = e / PT;
-      const int64_t tw = run / (K + 1);  // T * 2 + which
-      const int k = (int)(run % (K + 1));
-      P[(tw * ldk + koff + k) * PT + (e % PT)] = V(0);
-    }
+    const int64_t total = (int64_t)(K + 1) * nrows;
+    for (int64_t e = (int64_t)blockIdx.x * PG + tid; e < total; e += (int64_t)G * PG)
+      W[(e / nrows) * (int64_t)p.n_pad + (e % nrows)] = V2<V>{V(0), V(0)};
   }
   if (np > 0) {
     // c_x[q] = sum_t xi_q[I_t], c_e[q] = sum_t eta_q[I_t]; the same at j
@@ -361,7 +373,7 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
   }
   alive = prep_barrier(p.bar, ++nb * G, p.limit, &s_ok);
 
-  // ---- phase 1: item table; w = Q sI summed by atomics into eta_0's slot
+  // ---- phase 1: item table; w = Q sI summed by atomics into W[0].x
   int my_items = 0;
   if (alive) {
     {
@@ -422,13 +434,13 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
       }
       const int64_t rb = (int64_t)it.T * PT;
       item_gather<V>(it, cc, p.in.col, [&](int b) { return V2<V>{__ldcg(sI + b), V(0)}; },
-                     [&](int r, V a, V) { red_add(P + pidx(rb + r, 1, koff), a); });
+                     [&](int r, V a, V) { red_add(&W[rb + r].x, a); });
       __syncthreads();
     }
     alive = prep_barrier(p.bar, ++nb * G, p.limit, &s_ok);
   }
 
-  // ---- phase 1b: gamma per row (tiles round-robin): (xi_0, eta_0)
+  // ---- phase 1b: gamma per row (tiles round-robin); W[0] = (xi_0, eta_0)
   if (alive) {
     for (int t = 0; t < mt; ++t) {
       const int T = blockIdx.x + t * G;
@@ -437,7 +449,7 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
       if (tid < PT) {
         const int64_t a = (int64_t)T * PT + tid;
         const int len = __ldcg(p.in.len + a);
-        const V y = __ldcg(P + pidx(a, 1, koff));
+        const V y = __ldcg(&W[a].x);
         const double dl = (double)p.delta;
         V g;
         if (a == p.j) {
@@ -476,6 +488,7 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
           }
         }
         const V x0 = (a == p.j) ? Cv : V(0);
+        W[a] = V2<V>{x0, g};
         P[pidx(a, 0, koff)] = x0;
         P[pidx(a, 1, koff)] = g;
         pe = (g != V(0));
@@ -491,38 +504,39 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
 
   // ---- phase 2: K steps
   for (int k = 0; alive && k < K; ++k) {
-    const int kc = koff + k;
+    const V2<V>* Wk = W + (int64_t)k * p.n_pad;
+    V2<V>* Wn = W + (int64_t)(k + 1) * p.n_pad;
     for (int u = 0; u < my_items; ++u) {
       PrepItem& it = items[min(u, MAXI)];
       if (u >= MAXI) item_locate(p.in, ioff, nT, blockIdx.x + u * G, p.item, it);
       const int64_t rb = (int64_t)it.T * PT;
-      item_gather<V>(it, cc, p.in.col,
-                     [&](int b) {
-                       return V2<V>{__ldcg(P + pidx(b, 0, kc)), __ldcg(P + pidx(b, 1, kc))};
-                     },
+      item_gather<V>(it, cc, p.in.col, [&](int b) { return ld_v2(Wk + b); },
                      [&](int r, V a, V b) {
                        const V inv = V(1) / (V)it.len[r];
-                       if (a != V(0)) red_add(P + pidx(rb + r, 0, kc + 1), Cv * a * inv);
-                       if (b != V(0)) red_add(P + pidx(rb + r, 1, kc + 1), b * inv);
+                       red_add2(Wn + rb + r, Cv * a * inv, b * inv);
                      });
       __syncthreads();
     }
     alive = prep_barrier(p.bar, ++nb * G, p.limit, &s_ok);
   }
 
-  // ---- masks of the owned tiles, read off the finished columns (exact)
+  // ---- columns 1..K of the owned tiles into the panels, with their mask bits
   if (alive && K > 0) {
     for (int t = 0; t < mt; ++t) {
       const int T = blockIdx.x + t * G;
       if (T >= nT) break;
-      // warp w looks at columns k = w, w + 16, ... of xi and eta
+      // warp w copies columns k = 1 + w, 1 + w + 16, ...
       for (int k = 1 + warp; k <= K; k += PG / 32) {
+        const V2<V>* Wk = W + (int64_t)k * p.n_pad;
         bool nx = false, ne = false;
 #pragma unroll
         for (int q = 0; q < PT / 32; ++q) {
           const int64_t a = (int64_t)T * PT + q * 32 + lane;
-          nx |= (__ldcg(P + pidx(a, 0, koff + k)) != V(0));
-          ne |= (__ldcg(P + pidx(a, 1, koff + k)) != V(0));
+          const V2<V> v = ld_v2(Wk + a);
+          P[pidx(a, 0, koff + k)] = v.x;
+          P[pidx(a, 1, koff + k)] = v.y;
+          nx |= (v.x != V(0));
+          ne |= (v.y != V(0));
         }
         const unsigned bx = __ballot_sync(0xffffffffu, nx), be = __ballot_sync(0xffffffffu, ne);
         const unsigned long long bit = 1ull << (k & 63);
@@ -613,24 +627,18 @@ int launch_prep(const PrepParams& prm, int s_prec, int npend_max, int num_sms, i
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PG, smem) != cudaSuccess)
     return 1;
   if (per_sm <= 0) return 2;
-  // all co-resident CTAs (fewer for small graphs); with item = 0 the item
-  // size is chosen so that the items (at most nT + nnz / item of them) fit
-  // one per CTA
+  // one CTA per item (at most nT + nnz / item of them), at most all
+  // co-resident CTAs
   const int full = per_sm * num_sms;
   int grid = full;
-  if (prm.item > 0)
-    grid = (int)std::min<int64_t>((int64_t)prm.nT + nnz_bound / prm.item + 1, full);
-  else
-    grid = (int)std::min<int64_t>((int64_t)prm.nT + nnz_bound / 256 + 1, full);
+  const int item = prm.item > 0 ? prm.item : 1024;
+  grid = (int)std::min<int64_t>((int64_t)prm.nT + nnz_bound / item + 1, full);
   if (max_ctas > 0) grid = std::min(grid, max_ctas);
   grid = std::max(grid, 1);
   if ((prm.nT + grid - 1) / grid > PREP_MT) return 2;
   if (prm.npend > npend_max) return 1;
   PrepParams a = prm;
-  if (a.item == 0) {
-    const int64_t spare = (int64_t)grid - prm.nT;
-    a.item = (int)std::max<int64_t>(256, spare > 0 ? (nnz_bound + spare - 1) / spare : nnz_bound);
-  }
+  if (a.item == 0) a.item = 1024;
   void* args[] = {&a};
   if (cudaLaunchCooperativeKernel(fn, grid, PG, args, smem, st) != cudaSuccess) return 1;
   return 0;

@@ -125,9 +125,9 @@ void launch_chain_step(const DevAdj& in, int k, double C, int nT, int K1, double
 // mask words mXi/mEta of tiles [0, nT) (ORed as 0/1 into pXi/pEta when
 // those are set) and, when `tiles` is set, the tile-pair list (tile_mode 0 =
 // all pairs, 1 = AFF-pruned).  P is tile-blocked [T][which][ldk][128] in the
-// precision of S (columns koff .. koff+K are zeroed and accumulated by
-// atomics); sI, sJ hold n_pad values of that precision; tile_nnz holds
-// nT_cap ints.  Gathers are split into items of at most `item`
+// precision of S; sI, sJ hold n_pad values of that precision; W is the
+// working buffer [K+1][n_pad] of (xi, eta) pairs of that precision; tile_nnz
+// holds nT_cap ints.  Gathers are split into items of at most `item`
 // nonzeros; `cap` column indices are cached per CTA (a multiple of 4).
 // bar: two zeroed unsigned ints, left zeroed.  nnz_bound bounds the edges of
 // the new graph (it sizes the grid).  Returns 0 on launch, 2 when the graph
@@ -156,6 +156,7 @@ struct PrepParams {
   int cap;
   int item;
   int n_pad, nT_cap;
+  void* W;
   int* tile_nnz;
   unsigned int* bar;
   long long limit;
@@ -304,6 +305,12 @@ void launch_col_horner64(const ChunkList& hor, const int32_t* in_col, const Weig
                          const double* Y, double* Yn, int B, int n_rows, double scale,
                          cudaStream_t st);
 // Y[a][c] += sum_k xi_k[a] eta_k[cols[c]] + eta_k[a] xi_k[cols[c]] (panels P, FP32/64)
+// FP32 blocks: Y[a][c] += sum over the U stored updates (device array of
+// their panel pointers, tile-blocked FP32) of xi_k[a] eta_k[x_c] +
+// eta_k[a] xi_k[x_c], as one product; G: scratch of U * 2 * K1 * round4(B)
+// floats.  n_rows is a multiple of 128.
+void launch_col_corr(const float* const* hist, int U, int K1, const int32_t* cols, int B,
+                     int n_rows, float* G, float* Y, cudaStream_t st);
 void launch_col_apply(const void* P, int p_prec, int K1, const int32_t* cols, int B, int n_rows,
                       int prec, void* Y, cudaStream_t st);
 // scal[0] = si[i], scal[1] = sj[j], scal[2] = (1/d_j) sum_{b in I(j)} si[b]
