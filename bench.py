@@ -2,16 +2,19 @@
 
 Workload (the power-law update stream): directed Chung-Lu graph, n = 20,000,
 in/out-degree exponent 2.1, mean degree 10 (m = 200,000), C = 0.6, K = 20,
-S in FP32 (1.6 GB, larger than L2), xi/eta vectors in FP64, affected-area
-pruning on.  One step applies a batch of 1,000 sequential unit updates (80%
-insertions with degree-biased endpoints, 20% deletions of uniform existing
-edges), each through the fused rank-2(K+1) S update.  Steps continue one
-valid stream, so every step changes the graph.
+S in FP32 (1.6 GB, larger than L2; upper tiles kept), xi/eta vectors in FP64,
+affected-area pruning on.  One step applies a batch of 1,000 sequential unit
+updates (80% insertions with degree-biased endpoints, 20% deletions of
+uniform existing edges); each update runs Alg 1 (one cooperative launch for
+its recurrence) and its rank-2(K+1) S change is applied by the tensor-core S
+pass, 16 pending updates per pass by default (--defer / --tc select the other
+forms).  Steps continue one valid stream, so every step changes the graph.
 
 Prints one JSON line (see the keys below).  ``--impl reference`` times the
 FP64 CPU oracle (Alg 1 as printed, dense) on a bounded sample instead.
 Under torchrun each rank runs an independent replica of the workload (the
 update stream is sequential and has no data-parallel split).
+Other workloads (--workload batched / multi / column) print their own line.
 """
 from __future__ import annotations
 
@@ -38,7 +41,15 @@ METRIC = "edge updates/sec & HBM GB/s: fused rank-2K ΔS vs plain Inc-uSR at 1e-
 UNIT = "edge updates/s"
 WORKLOAD = ("power-law update stream: directed Chung-Lu n=20000, exponent 2.1, mean degree 10, "
             "C=0.6, K=20, FP32 S, FP64 vectors, AFF pruning, 1000 sequential unit updates per step "
-            "(80% insert / 20% delete)")
+            "(80% insert / 20% delete), rank-2(K+1) S changes applied by the tensor-core S pass")
+
+
+def read_bf16_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f)["bf16_tflops"])
+    return 1900.0
 
 
 def read_peaks():
@@ -182,15 +193,24 @@ def run_gpu(args, rank, world):
         arr = P.updates_array(st)
         t = torch.from_numpy(arr.view(np.uint8)).pin_memory()
         packed.append((t, arr.size))
-    form = dict(defer=args.defer, tc=args.tc)
-    sr = P.SimRank(N, s, d, C=C, K=K, s_precision=32, aff=1, profile=1,
-                   stream=stream.cuda_stream, **form)
-    sr.sync()
+    form = dict(defer=args.defer, tc=args.tc, vec_fp32=args.vec_fp32)
+
+    def handle(profile):
+        h = P.SimRank(N, s, d, C=C, K=K, s_precision=32, aff=1, profile=profile,
+                      stream=stream.cuda_stream, **form)
+        h.sync()
+        return h
+
+    def apply(h, t):
+        h.apply_updates_ptr(packed[t][0].data_ptr(), packed[t][1])
+
+    # ---- value: device-timed steps (no per-launch profiling on this handle)
+    sr = handle(0)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
         for t in range(args.warmup):
-            sr.apply_updates_ptr(packed[t][0].data_ptr(), packed[t][1])
+            apply(sr, t)
         sr.sync()
         st0 = sr.stats()
         if dist:
@@ -199,37 +219,48 @@ def run_gpu(args, rank, world):
         with ClockSampler(local) as clk:
             ev0.record(stream)
             for t in range(args.warmup, total):
-                sr.apply_updates_ptr(packed[t][0].data_ptr(), packed[t][1])
+                apply(sr, t)
             ev1.record(stream)
             torch.cuda.synchronize()
         if dist:
             dist.barrier()
         ms = ev0.elapsed_time(ev1)
         st1 = sr.stats()
-    # e2e: the same metric with a host result read back every step (two S
-    # columns of the last update), on a second identical replica
-    e2e_val, d2h = None, 0
-    s_e, d_e, streams_e = s, d, streams
     sr.close()
     del sr
     torch.cuda.empty_cache()
-    sr2 = P.SimRank(N, s_e, d_e, C=C, K=K, s_precision=32, aff=1, stream=stream.cuda_stream,
-                    **form)
+    # ---- e2e: the public call with host buffers, a host read-back of two S
+    # columns of the last update every step, on a second identical replica
+    d2h = 0
+    sr2 = handle(0)
     with torch.cuda.stream(stream):
         for t in range(args.warmup):
-            sr2.apply_updates_ptr(packed[t][0].data_ptr(), packed[t][1])
+            apply(sr2, t)
         sr2.sync()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for t in range(args.warmup, total):
-            sr2.apply_updates_ptr(packed[t][0].data_ptr(), packed[t][1])
-            last = streams_e[t][-1]
+            apply(sr2, t)
+            last = streams[t][-1]
             cols = sr2.columns(np.array([last[0], last[1]], np.int32), fp64=False)
             d2h = cols.nbytes
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
     sr2.close()
-    e2e_val = args.steps * per_step / e2e_s
+    del sr2
+    torch.cuda.empty_cache()
+    # ---- per-kernel times: a third replica with CUDA events around every
+    # launch, over the first timed step (kernel times, phase split, roofline)
+    sr3 = handle(1)
+    with torch.cuda.stream(stream):
+        for t in range(args.warmup):
+            apply(sr3, t)
+        sr3.sync()
+        pst0 = sr3.stats()
+        apply(sr3, args.warmup)
+        sr3.sync()
+        pst1 = sr3.stats()
+    sr3.close()
     # max over ranks
     ms_t = torch.tensor([ms], device="cuda")
     e2e_t = torch.tensor([e2e_s], device="cuda")
@@ -241,13 +272,52 @@ def run_gpu(args, rank, world):
     updates = args.steps * per_step * world
     value = updates / (ms / 1000.0)
     e2e_val = updates / e2e_s
-    launches = st1["s_update_launches"] - st0["s_update_launches"]
-    s_bytes = st1["s_bytes"] - st0["s_bytes"]
-    kern_ms = st1["s_update_ms"] - st0["s_update_ms"]
-    alg_bytes = s_bytes + launches * 2 * (K + 1) * N * 4
     peak, peak_kind = read_peaks()
-    achieved = (alg_bytes / launches) / (kern_ms / launches / 1000.0) / 1e9 if launches else 0.0
-    phase = [b - a for a, b in zip(st0["phase_ms"], st1["phase_ms"])]
+    tf32_peak = read_bf16_peak() * 1.1 / 2.25
+    # profiled step: the two kernels of the path
+    pd = {k: pst1[k] - pst0[k] for k in ("s_update_launches", "s_bytes", "s_update_ms",
+                                        "tiles_touched", "tiles_total")}
+    phase = [b - a for a, b in zip(pst0["phase_ms"], pst1["phase_ms"])]
+    launches = pd["s_update_launches"]
+    sp_ms = pd["s_update_ms"]
+    G = max(1, args.defer)
+    terms = G * (K + 1)
+    rg = (terms + 31) // 32 * 32
+    n_pad = (N + 127) // 128 * 128
+    if args.tc:
+        operand_bytes = launches * n_pad * (2 * rg) * 4 * 2  # hi and lo operands
+        flops = pd["tiles_touched"] * 128 * 128 * (2 * rg) * 2 * 3
+    else:
+        operand_bytes = launches * 2 * terms * n_pad * 4
+        flops = pd["tiles_touched"] * 128 * 128 * 2 * terms * 2
+    sp_bytes = pd["s_bytes"] + operand_bytes
+    sp_gbs = sp_bytes / (sp_ms / 1000.0) / 1e9 if sp_ms > 0 else 0.0
+    sp_tflops = flops / (sp_ms / 1000.0) / 1e12 if sp_ms > 0 else 0.0
+    sp_name = "k_s_update_tc (tcgen05 3xTF32 S pass)" if args.tc else "k_s_update_ws (CUDA-core S pass)"
+    if args.tc and sp_tflops / tf32_peak > sp_gbs / peak:
+        s_pass = {"kernel": sp_name, "bound": "tensor", "achieved": sp_tflops, "peak": tf32_peak,
+                  "unit": "TFLOP/s", "frac": sp_tflops / tf32_peak,
+                  "peak_kind": "measured bf16 burst x 1.1/2.25 (nominal TF32/BF16)",
+                  "hbm_gbs": sp_gbs}
+    else:
+        s_pass = {"kernel": sp_name, "bound": "hbm", "achieved": sp_gbs, "peak": peak,
+                  "unit": "GB/s", "frac": sp_gbs / peak, "peak_kind": peak_kind,
+                  "tflops": sp_tflops}
+    s_pass.update({"traffic": None, "bytes_per_launch": sp_bytes / max(launches, 1),
+                   "ms_per_launch": sp_ms / max(launches, 1), "launches": launches})
+    # k_prep: one launch per update; algorithmic bytes = the graph read K+1
+    # times, the gathered (xi, eta) pairs, the two S rows and the panel writes
+    prep_ms = phase[0]
+    prep_bytes_1 = ((K + 1) * (M * 4 + n_pad * 12) + K * M * 16 + 2 * N * 4
+                    + 2 * (K + 1) * n_pad * 4)
+    prep_gbs = prep_bytes_1 * per_step / (prep_ms / 1000.0) / 1e9 if prep_ms > 0 else 0.0
+    prep = {"kernel": "k_prep (cooperative: patch, rows of S, gamma, K recurrence steps, masks, "
+                      "tile list)", "bound": "hbm", "achieved": prep_gbs, "peak": peak,
+            "unit": "GB/s", "frac": prep_gbs / peak, "peak_kind": peak_kind, "traffic": None,
+            "bytes_per_launch": prep_bytes_1, "ms_per_launch": prep_ms / per_step,
+            "launches": per_step,
+            "note": "latency-bound (L2-resident working set, K+4 grid barriers per launch)"}
+    dominant = s_pass if sp_ms >= prep_ms else prep
     tiles_touched = st1["tiles_touched"] - st0["tiles_touched"]
     tiles_total = st1["tiles_total"] - st0["tiles_total"]
     line = {
@@ -256,19 +326,17 @@ def run_gpu(args, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N, "m": M, "C": C, "K": K,
                    "updates_per_step": per_step, "defer": args.defer, "tc": args.tc,
+                   "vectors": "f32" if args.vec_fp32 else "f64", "storage": "upper tiles",
                    "l2": "inputs larger than L2 (S is 1.6 GB FP32)",
                    "aff_tile_fraction": tiles_touched / max(tiles_total, 1),
-                   "hbm_gbs_step": alg_bytes / (ms / 1000.0) / 1e9,
+                   "s_bytes_gbs_step": (st1["s_bytes"] - st0["s_bytes"]) / (ms / 1000.0) / 1e9,
                    "phase_us_per_update": {
-                       name: 1000.0 * v / max(args.steps * per_step, 1)
-                       for name, v in zip(["prep", "patch_chain_per_step", "tiles_and_deferred_passes",
-                                          "s_update"], phase)},
+                       name: 1000.0 * v / per_step
+                       for name, v in zip(["prep", "patch_chain_per_step", "deferred_passes",
+                                          "s_pass"], phase)},
                    "parallelism": "replicas" if world > 1 else "single"},
-        "roofline": {"kernel": "k_s_update (fused AFF-pruned rank-2(K+1) S update)",
-                     "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": peak_kind,
-                     "traffic": None, "bytes_per_launch": alg_bytes / max(launches, 1),
-                     "ms_per_launch": kern_ms / max(launches, 1), "launches": launches},
+        "roofline": dominant,
+        "kernels": {"s_pass": s_pass, "prep": prep},
         "e2e": {"value": e2e_val, "unit": UNIT,
                 "h2d_bytes_per_step": int(packed[0][1] * 16), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(st1["kernel_launches"] - st0["kernel_launches"]),
@@ -565,6 +633,7 @@ def main():
     ap.add_argument("--defer", type=int, default=16,
                     help="stream workload: rank-one updates kept pending per S pass (0 = apply each)")
     ap.add_argument("--tc", type=int, default=1, help="S passes on the tensor cores (3xTF32)")
+    ap.add_argument("--vec-fp32", type=int, default=0, help="xi/eta vectors in FP32 (default FP64)")
     ap.add_argument("--workload", default="stream",
                     choices=["stream", "batched", "multi", "column"],
                     help="stream: the benchmarked update stream; batched: one-shot vs per-edge; "

@@ -73,9 +73,9 @@ enum { SR_SUPDATE_FUSED = 0,     /* one read-modify-write pass of S per update: 
 typedef struct simrank_config {
   double C;               /* damping factor, 0 < C < 1 (Eq. 1) */
   int32_t K;              /* iterations of the xi/eta recurrence (Eq. 16a); terms k = 0..K; 0 <= K <= 1023 */
-  int32_t s_precision;    /* 32: S stored in FP32; 64: S stored in FP64.  With chain = 0 the
-                             xi/eta vectors and gamma are computed in the same precision
-                             (lambda and row j of gamma in FP64); with chain = 1 in FP64. */
+  int32_t s_precision;    /* 32: S stored in FP32; 64: S stored in FP64.  The xi/eta vectors
+                             are FP64 unless vec_fp32 = 1; the panels the S pass reads have
+                             the precision of S. */
   int32_t mode;           /* SR_MODE_DENSE or SR_MODE_COLUMN */
   int32_t n_capacity;     /* maximum number of nodes, including nodes added later; >= n at init */
   int32_t aff;            /* 1: skip S tiles outside the affected area of Thm 4; 0: touch every tile */
@@ -101,8 +101,8 @@ typedef struct simrank_config {
                              G * (K + 1) <= 4096, else SR_ERR_ARG. */
   int32_t chain;          /* work of a rank-one update before its S pass: 0 = one cooperative
                              launch (graph patch, rows of S, gamma, all K recurrence steps, masks,
-                             tile list; bounded grid barriers), 1 = one launch per step with
-                             FP64 vectors.  Graphs with more than 8 tiles of 128 nodes per
+                             tile list; bounded grid barriers), 1 = one launch per step (FP64
+                             vectors).  Graphs with more than 8 tiles of 128 nodes per
                              co-resident CTA take the per-step path. */
   int32_t prep_ctas;      /* chain = 0: cap on the CTAs of the fused launch (0 = as many as fit) */
   int32_t prep_cache;     /* chain = 0: column indices cached in shared memory per CTA, a
@@ -117,7 +117,9 @@ typedef struct simrank_config {
                              block diagonal current (S is symmetric; updates then read and write
                              half the bytes, and reads of a lower tile take its mirror); 0 = keep
                              both triangles.  Default 1. */
-  int32_t reserved[4];
+  int32_t vec_fp32;       /* chain = 0 with S in FP32: 0 = xi/eta vectors, gamma and the
+                             recurrence in FP64 (default); 1 = in FP32 */
+  int32_t reserved[3];
 } simrank_config;
 
 /* Fills *cfg with defaults: C = 0.6, K = 15, s_precision = 32, dense, aff = 1,

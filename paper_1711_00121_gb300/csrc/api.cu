@@ -561,7 +561,7 @@ simrank_status run_rank_one(simrank_ctx* h, int64_t src_off, int delta, int j, i
     pp.n_pad = h->n_pad;
     pp.nT_cap = h->nT_cap;
     if (!h->W) {
-      CUDA_TRY(h, cudaMalloc(&h->W, (size_t)h->K1 * h->n_pad * 2 * (h->cfg.s_precision / 8)));
+      CUDA_TRY(h, cudaMalloc(&h->W, (size_t)h->K1 * h->n_pad * 2 * sizeof(double)));
       CUDA_TRY(h, dev_alloc(&h->tile_nnz, (size_t)h->nT_cap));
     }
     pp.W = h->W;
@@ -569,7 +569,8 @@ simrank_status run_rank_one(simrank_ctx* h, int64_t src_off, int delta, int j, i
     pp.bar = h->gbar + 2;
     pp.limit = wait_limit(h);
     pp.counters = (unsigned long long*)h->counters;
-    const int rc = launch_prep(pp, h->cfg.s_precision, defer ? group(h) * h->K1 : 0,
+    const int rc = launch_prep(pp, h->cfg.s_precision, h->cfg.vec_fp32 ? 0 : 1,
+                               defer ? group(h) * h->K1 : 0,
                                h->num_sms, h->cfg.prep_ctas, (int64_t)h->edges.size() + delta,
                                h->st);
     if (rc == 1) return fail(h, SR_ERR_CUDA, "fused pre-update launch failed");

@@ -29,9 +29,10 @@
 // gathers on the patched graph and corrects row j: the sum over the old
 // in-neighbours = the sum over the new ones - op * S_II.
 //
-// Arithmetic is in the precision of S (lambda and row j of gamma in FP64).
-// The atomic accumulation makes the last bit of a result depend on the order
-// of the additions.
+// The vectors and the arithmetic are FP64 (vec64 = 1, or S in FP64) or FP32;
+// the panels the S pass reads have the precision of S, and lambda and row j
+// of gamma are always FP64.  The atomic accumulation makes the last bit of a
+// result depend on the order of the additions.
 #include <algorithm>
 
 #include "sr_internal.h"
@@ -279,7 +280,8 @@ __device__ void prep_patch(const PatchOp* __restrict__ ops, int64_t begin, int64
   }
 }
 
-template <typename V>
+// V: arithmetic and vector precision; TS: storage precision of S and the panels
+template <typename V, typename TS>
 __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ V red[4][2][PT];
@@ -295,8 +297,8 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
   int* cc = reinterpret_cast<int*>(items + (MAXI + 1));
   int* ioff = cc + p.cap;  // [nT + 1]
   V* coef = reinterpret_cast<V*>(ioff + ((p.nT_cap + 1 + 3) & ~3));
-  const V* __restrict__ S = static_cast<const V*>(p.S);
-  V* P = static_cast<V*>(p.P);
+  const TS* __restrict__ S = static_cast<const TS*>(p.S);
+  TS* P = static_cast<TS*>(p.P);
   V* sI = static_cast<V*>(p.sI);
   V* sJ = static_cast<V*>(p.sJ);
   V2<V>* W = static_cast<V2<V>*>(p.W);
@@ -329,13 +331,13 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
       V cx = V(0), ce = V(0);
       for (int t = 0; t < p.delta; ++t) {
         const int64_t x = p.I[t];
-        cx += P[pidx(x, 0, q)];
-        ce += P[pidx(x, 1, q)];
+        cx += (V)P[pidx(x, 0, q)];
+        ce += (V)P[pidx(x, 1, q)];
       }
       coef[q] = cx;
       coef[np + q] = ce;
-      coef[2 * np + q] = P[pidx(p.j, 0, q)];
-      coef[3 * np + q] = P[pidx(p.j, 1, q)];
+      coef[2 * np + q] = (V)P[pidx(p.j, 0, q)];
+      coef[3 * np + q] = (V)P[pidx(p.j, 1, q)];
     }
     __syncthreads();
   }
@@ -345,12 +347,12 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
     const int r = tid & (PT - 1), part = tid >> 7;
     const int64_t a = (int64_t)T * PT + r;
     V vI = V(0), vJ = V(0);
-    for (int u = part; u < p.delta; u += 4) vI += s_at(S, p.ld, p.I[u], a, p.upper != 0);
-    if (part == 3) vJ = s_at(S, p.ld, p.j, a, p.upper != 0);
+    for (int u = part; u < p.delta; u += 4) vI += (V)s_at(S, p.ld, p.I[u], a, p.upper != 0);
+    if (part == 3) vJ = (V)s_at(S, p.ld, p.j, a, p.upper != 0);
     // S_cur[x, a] = S[x, a] + sum_q xi_q[x] eta_q[a] + eta_q[x] xi_q[a]
     for (int q = part; q < np; q += 4) {
-      const V xa = P[pidx(a, 0, q)];
-      const V ea = P[pidx(a, 1, q)];
+      const V xa = (V)P[pidx(a, 0, q)];
+      const V ea = (V)P[pidx(a, 1, q)];
       vI += coef[q] * ea + coef[np + q] * xa;
       vJ += coef[2 * np + q] * ea + coef[3 * np + q] * xa;
     }
@@ -489,8 +491,8 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
         }
         const V x0 = (a == p.j) ? Cv : V(0);
         W[a] = V2<V>{x0, g};
-        P[pidx(a, 0, koff)] = x0;
-        P[pidx(a, 1, koff)] = g;
+        P[pidx(a, 0, koff)] = (TS)x0;
+        P[pidx(a, 1, koff)] = (TS)g;
         pe = (g != V(0));
       }
       const int any_e = __syncthreads_or(pe);
@@ -533,8 +535,8 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
         for (int q = 0; q < PT / 32; ++q) {
           const int64_t a = (int64_t)T * PT + q * 32 + lane;
           const V2<V> v = ld_v2(Wk + a);
-          P[pidx(a, 0, koff + k)] = v.x;
-          P[pidx(a, 1, koff + k)] = v.y;
+          P[pidx(a, 0, koff + k)] = (TS)v.x;
+          P[pidx(a, 1, koff + k)] = (TS)v.y;
           nx |= (v.x != V(0));
           ne |= (v.y != V(0));
         }
@@ -613,13 +615,16 @@ size_t prep_smem(int cap, int nT_cap, int npend_max) {
 
 }  // namespace
 
-int launch_prep(const PrepParams& prm, int s_prec, int npend_max, int num_sms, int max_ctas,
-                int64_t nnz_bound, cudaStream_t st) {
+int launch_prep(const PrepParams& prm, int s_prec, int vec64, int npend_max, int num_sms,
+                int max_ctas, int64_t nnz_bound, cudaStream_t st) {
   if (prm.nT <= 0) return 0;
   if (prm.item < 0 || prm.cap < 0 || (prm.cap & 3)) return 1;
-  const size_t smem = (s_prec == 64) ? prep_smem<double>(prm.cap, prm.nT_cap, npend_max)
-                                     : prep_smem<float>(prm.cap, prm.nT_cap, npend_max);
-  const void* fn = (s_prec == 64) ? (const void*)k_prep<double> : (const void*)k_prep<float>;
+  const bool v64 = (s_prec == 64) || vec64;
+  const size_t smem = v64 ? prep_smem<double>(prm.cap, prm.nT_cap, npend_max)
+                          : prep_smem<float>(prm.cap, prm.nT_cap, npend_max);
+  const void* fn = (s_prec == 64) ? (const void*)k_prep<double, double>
+                   : vec64        ? (const void*)k_prep<double, float>
+                                  : (const void*)k_prep<float, float>;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 1;

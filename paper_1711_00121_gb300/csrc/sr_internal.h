@@ -125,9 +125,9 @@ void launch_chain_step(const DevAdj& in, int k, double C, int nT, int K1, double
 // mask words mXi/mEta of tiles [0, nT) (ORed as 0/1 into pXi/pEta when
 // those are set) and, when `tiles` is set, the tile-pair list (tile_mode 0 =
 // all pairs, 1 = AFF-pruned).  P is tile-blocked [T][which][ldk][128] in the
-// precision of S; sI, sJ hold n_pad values of that precision; W is the
-// working buffer [K+1][n_pad] of (xi, eta) pairs of that precision; tile_nnz
-// holds nT_cap ints.  Gathers are split into items of at most `item`
+// precision of S; sI, sJ hold n_pad values of the vector precision (FP64 when
+// vec64 or S is FP64, else FP32); W is the working buffer [K+1][n_pad] of
+// (xi, eta) pairs of the vector precision; tile_nnz holds nT_cap ints.  Gathers are split into items of at most `item`
 // nonzeros; `cap` column indices are cached per CTA (a multiple of 4).
 // bar: two zeroed unsigned ints, left zeroed.  nnz_bound bounds the edges of
 // the new graph (it sizes the grid).  Returns 0 on launch, 2 when the graph
@@ -162,8 +162,8 @@ struct PrepParams {
   long long limit;
   unsigned long long* counters;
 };
-int launch_prep(const PrepParams& p, int s_prec, int npend_max, int num_sms, int max_ctas,
-                int64_t nnz_bound, cudaStream_t st);
+int launch_prep(const PrepParams& p, int s_prec, int vec64, int npend_max, int num_sms,
+                int max_ctas, int64_t nnz_bound, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Many independent graphs advanced together (k_multi.cu).
