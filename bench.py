@@ -193,7 +193,7 @@ def run_gpu(args, rank, world):
         arr = P.updates_array(st)
         t = torch.from_numpy(arr.view(np.uint8)).pin_memory()
         packed.append((t, arr.size))
-    form = dict(defer=args.defer, tc=args.tc, vec_fp32=args.vec_fp32)
+    form = dict(defer=args.defer, tc=args.tc, vec_fp64=args.vec_fp64)
 
     def handle(profile):
         h = P.SimRank(N, s, d, C=C, K=K, s_precision=32, aff=1, profile=profile,
@@ -261,6 +261,25 @@ def run_gpu(args, rank, world):
         sr3.sync()
         pst1 = sr3.stats()
     sr3.close()
+    del sr3
+    torch.cuda.empty_cache()
+    # ---- the same stream with FP64 xi/eta vectors (one step after one warm-up
+    # step), the precision form with FP64 recurrence vectors
+    v64 = None
+    if not args.vec_fp64 and total >= 2:
+        form64 = dict(form, vec_fp64=1)
+        sr4 = P.SimRank(N, s, d, C=C, K=K, s_precision=32, aff=1, stream=stream.cuda_stream,
+                        **form64)
+        with torch.cuda.stream(stream):
+            apply(sr4, 0)
+            sr4.sync()
+            a4, b4 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a4.record(stream)
+            apply(sr4, 1)
+            b4.record(stream)
+            sr4.sync()
+            v64 = per_step / (a4.elapsed_time(b4) / 1000.0)
+        sr4.close()
     # max over ranks
     ms_t = torch.tensor([ms], device="cuda")
     e2e_t = torch.tensor([e2e_s], device="cuda")
@@ -326,7 +345,7 @@ def run_gpu(args, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N, "m": M, "C": C, "K": K,
                    "updates_per_step": per_step, "defer": args.defer, "tc": args.tc,
-                   "vectors": "f32" if args.vec_fp32 else "f64", "storage": "upper tiles",
+                   "vectors": "f64" if args.vec_fp64 else "f32", "storage": "upper tiles",
                    "l2": "inputs larger than L2 (S is 1.6 GB FP32)",
                    "aff_tile_fraction": tiles_touched / max(tiles_total, 1),
                    "s_bytes_gbs_step": (st1["s_bytes"] - st0["s_bytes"]) / (ms / 1000.0) / 1e9,
@@ -337,6 +356,8 @@ def run_gpu(args, rank, world):
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": dominant,
         "kernels": {"s_pass": s_pass, "prep": prep},
+        "fp64_vectors": {"value": v64, "unit": UNIT, "steps": 1,
+                         "note": "same stream, xi/eta vectors and recurrence in FP64"},
         "e2e": {"value": e2e_val, "unit": UNIT,
                 "h2d_bytes_per_step": int(packed[0][1] * 16), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(st1["kernel_launches"] - st0["kernel_launches"]),
@@ -621,6 +642,63 @@ def run_column(args):
     sr.close()
 
 
+# --------------------------------------------------------------------------
+# Gradient workload (the adjoint): weighted directed Chung-Lu n = 50,000,
+# m = 500,000 (exponent 2.1), weights U(0.1, 1], C = 0.6, K = 20; loss over
+# 10,000 random pairs with targets U[0, 0.3]; dL/d(edge weights) by
+# simrank_grad (column mode, FP64).  Central differences of the library's own
+# loss on a few edges check the gradient at full size.
+# --------------------------------------------------------------------------
+GN, GM, GC, GK, GP = 50000, 500000, 0.6, 20, 10000
+
+
+def run_grad(args):
+    import torch
+
+    import paper_1711_00121_gb300 as P
+    from synth import edge_weights, query_pairs
+
+    torch.cuda.set_device(0)
+    s, d = chung_lu_digraph(GN, GM, 2.1, 2.1, 5)
+    w = edge_weights(GM, 5)
+    a, b, t = query_pairs(GN, GP, 5)
+    kw = dict(C=GC, K=GK, s_precision=64, mode=P.MODE_COLUMN)
+    sr = P.SimRank(GN, s, d, weight=w, **kw)
+    L, g = sr.grad(a, b, t, GM)  # warm-up
+    times = []
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            L, g = sr.grad(a, b, t, GM)
+            times.append(time.perf_counter() - t0)
+    sr.close()
+    # central differences on a few edges of largest |gradient|
+    rng = np.random.default_rng(9)
+    idx = np.argsort(-np.abs(g))[: args.fd_edges]
+    fd = []
+    for e in idx.tolist():
+        h = 1e-4 * float(w[e])
+        vals = []
+        for sign in (1.0, -1.0):
+            w2 = w.astype(np.float64).copy()
+            w2[e] += sign * h
+            sr2 = P.SimRank(GN, s, d, weight=w2.astype(np.float32), **kw)
+            # the loss at the float32-rounded weights, and the step actually taken
+            Lp, _ = sr2.grad(a, b, t, GM)
+            sr2.close()
+            vals.append((Lp, float(np.float32(w2[e]))))
+        (lp, wp), (lm, wm) = vals
+        fd.append({"edge": int(e), "grad": float(g[e]), "fd": (lp - lm) / (wp - wm)})
+    rel = max(abs(x["grad"] - x["fd"]) / max(abs(x["grad"]), 1e-300) for x in fd) if fd else None
+    sec = sum(times) / len(times)
+    line = {"workload": f"gradient: weighted directed Chung-Lu n={GN} m={GM} exponent 2.1, "
+                        f"weights U(0.1,1], C={GC}, K={GK}, {GP} pairs, FP64 adjoint",
+            "metric": "gradient evaluations/s", "value": 1.0 / sec, "unit": "evals/s",
+            "s_per_eval": sec, "steps": args.steps, "loss": L,
+            "fd_check": fd, "fd_max_rel_err": rel, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -633,13 +711,14 @@ def main():
     ap.add_argument("--defer", type=int, default=16,
                     help="stream workload: rank-one updates kept pending per S pass (0 = apply each)")
     ap.add_argument("--tc", type=int, default=1, help="S passes on the tensor cores (3xTF32)")
-    ap.add_argument("--vec-fp32", type=int, default=0, help="xi/eta vectors in FP32 (default FP64)")
+    ap.add_argument("--vec-fp64", type=int, default=0, help="xi/eta vectors in FP64 (default FP32)")
     ap.add_argument("--workload", default="stream",
-                    choices=["stream", "batched", "multi", "column"],
+                    choices=["stream", "batched", "multi", "column", "grad"],
                     help="stream: the benchmarked update stream; batched: one-shot vs per-edge; "
                          "multi: many graphs batched vs per-graph launches; column: column-block "
                          "mode queries")
     ap.add_argument("--column-n", type=int, default=CN, help="column workload: node count")
+    ap.add_argument("--fd-edges", type=int, default=3, help="grad workload: edges checked by FD")
     ap.add_argument("--graphs", type=int, default=MG, help="multi workload: number of graphs")
     ap.add_argument("--batch", type=int, default=64, help="batched workload: edges per batch")
     ap.add_argument("--per-edge-sample", type=int, default=256,
@@ -655,6 +734,9 @@ def main():
         return
     if args.workload == "column":
         run_column(args)
+        return
+    if args.workload == "grad":
+        run_grad(args)
         return
     if args.impl == "reference":
         run_reference(args, rank)

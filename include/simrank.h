@@ -74,16 +74,19 @@ typedef struct simrank_config {
   double C;               /* damping factor, 0 < C < 1 (Eq. 1) */
   int32_t K;              /* iterations of the xi/eta recurrence (Eq. 16a); terms k = 0..K; 0 <= K <= 1023 */
   int32_t s_precision;    /* 32: S stored in FP32; 64: S stored in FP64.  The xi/eta vectors
-                             are FP64 unless vec_fp32 = 1; the panels the S pass reads have
-                             the precision of S. */
+                             have the precision of S (FP64 also with FP32 S when vec_fp64 = 1,
+                             or with chain = 1); the panels the S pass reads have the precision
+                             of S. */
   int32_t mode;           /* SR_MODE_DENSE or SR_MODE_COLUMN */
   int32_t n_capacity;     /* maximum number of nodes, including nodes added later; >= n at init */
   int32_t aff;            /* 1: skip S tiles outside the affected area of Thm 4; 0: touch every tile */
   int32_t apply;          /* SR_APPLY_* */
   int32_t s_update;       /* SR_SUPDATE_* */
-  int32_t tc;             /* S passes on the tensor cores (3xTF32 split): 1 = the one-shot batch
-                             form's pass, and with FP32 S the pass of every unit / sink-block
-                             update (or of every group of `defer` pending updates); 0 = CUDA cores */
+  int32_t tc;             /* S passes on the tensor cores: 1 = 3xTF32 split, 2 = 3xFP16 split with
+                             an exact power-of-two balancing of each term (twice the tensor rate;
+                             the one-shot form keeps TF32); used for the one-shot batch form's
+                             pass and, with FP32 S, for the pass of every unit / sink-block update
+                             (or of every group of `defer` pending updates); 0 = CUDA cores */
   int32_t init_max_sweeps;/* cap on Jacobi sweeps of Eq. 1 at init / re-anchor */
   double init_tol;        /* init stops when a sweep changes S by less than this (max-abs) */
   int32_t profile;        /* 1: time every S-update launch with CUDA events (simrank_get_stats) */
@@ -117,8 +120,9 @@ typedef struct simrank_config {
                              block diagonal current (S is symmetric; updates then read and write
                              half the bytes, and reads of a lower tile take its mirror); 0 = keep
                              both triangles.  Default 1. */
-  int32_t vec_fp32;       /* chain = 0 with S in FP32: 0 = xi/eta vectors, gamma and the
-                             recurrence in FP64 (default); 1 = in FP32 */
+  int32_t vec_fp64;       /* chain = 0 with S in FP32: 1 = xi/eta vectors, gamma and the
+                             recurrence in FP64; 0 (default) = in FP32.  On GB300 the FP64 form
+                             makes the pre-update launch about 3.5x slower. */
   int32_t reserved[3];
 } simrank_config;
 

@@ -42,7 +42,7 @@ class Config(ctypes.Structure):
         ("s_kernel", ctypes.c_int32), ("defer", ctypes.c_int32), ("chain", ctypes.c_int32),
         ("prep_ctas", ctypes.c_int32), ("prep_cache", ctypes.c_int32),
         ("multi_launch", ctypes.c_int32), ("prep_item", ctypes.c_int32),
-        ("upper_only", ctypes.c_int32), ("vec_fp32", ctypes.c_int32),
+        ("upper_only", ctypes.c_int32), ("vec_fp64", ctypes.c_int32),
         ("reserved", ctypes.c_int32 * 3),
     ]
 

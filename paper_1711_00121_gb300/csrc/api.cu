@@ -451,17 +451,26 @@ simrank_status flush_pending(simrank_ctx* h) {
   }
   simrank_status s;
   if (h->cfg.tc) {
-    const int rg = (nterms + 31) / 32 * 32;
+    // tc = 2: FP16 operands (terms rounded up to 64), else TF32 (rounded up to 32)
+    const bool f16 = h->cfg.tc == 2;
+    const int rg = f16 ? (nterms + 63) / 64 * 64 : (nterms + 31) / 32 * 32;
     const int64_t kd = 2 * (int64_t)rg;
-    if ((s = ob_ensure(h, 12, (size_t)h->n_pad * kd * 4)) != SR_OK) return s;
-    if ((s = ob_ensure(h, 13, (size_t)h->n_pad * kd * 4)) != SR_OK) return s;
-    launch_pack_tc_tiles(h->Pp, GK1, nterms, rg, nT * PT, (float*)h->ob[12].p, (float*)h->ob[13].p,
-                         kd, h->st);
+    const size_t eb = f16 ? 2 : 4;
+    if ((s = ob_ensure(h, 12, (size_t)h->n_pad * kd * eb)) != SR_OK) return s;
+    if ((s = ob_ensure(h, 13, (size_t)h->n_pad * kd * eb)) != SR_OK) return s;
+    if (f16) {
+      if ((s = ob_ensure(h, 19, 2 * (size_t)nterms * sizeof(unsigned int))) != SR_OK) return s;
+      launch_pack_f16_tiles(h->Pp, GK1, nterms, rg, nT * PT, (unsigned int*)h->ob[19].p,
+                            h->ob[12].p, h->ob[13].p, kd, h->st);
+      h->launches += 2;
+    } else {
+      launch_pack_tc_tiles(h->Pp, GK1, nterms, rg, nT * PT, (float*)h->ob[12].p,
+                           (float*)h->ob[13].p, kd, h->st);
+    }
     if (ev) CUDA_TRY(h, cudaEventRecord(ev->first, h->st));
-    const int rc = launch_s_update_tc((float*)h->S, h->ld, (const float*)h->ob[12].p,
-                                      (const float*)h->ob[13].p, h->n_pad, kd, h->tiles, h->ntiles,
-                                      h->n_cur, h->counters, h->num_sms, wait_limit(h), h->st,
-                                      upper(h));
+    const int rc = launch_s_update_tc((float*)h->S, h->ld, h->ob[12].p, h->ob[13].p, h->n_pad,
+                                      kd, h->tiles, h->ntiles, h->n_cur, h->counters, h->num_sms,
+                                      wait_limit(h), h->st, upper(h), f16 ? 1 : 0);
     if (rc != 0) return fail(h, SR_ERR_CUDA, "tensor-core S update: launch setup failed");
     h->launches += 2;
   } else {
@@ -569,7 +578,7 @@ simrank_status run_rank_one(simrank_ctx* h, int64_t src_off, int delta, int j, i
     pp.bar = h->gbar + 2;
     pp.limit = wait_limit(h);
     pp.counters = (unsigned long long*)h->counters;
-    const int rc = launch_prep(pp, h->cfg.s_precision, h->cfg.vec_fp32 ? 0 : 1,
+    const int rc = launch_prep(pp, h->cfg.s_precision, h->cfg.vec_fp64 ? 1 : 0,
                                defer ? group(h) * h->K1 : 0,
                                h->num_sms, h->cfg.prep_ctas, (int64_t)h->edges.size() + delta,
                                h->st);
@@ -894,8 +903,8 @@ simrank_status run_one_shot(simrank_ctx* h, const std::map<int32_t, std::vector<
         CUDA_TRY(h, cudaEventRecord(ev->first, h->st));
       }
       if (tc) {
-        const int rc = launch_s_update_tc((float*)h->S, h->ld, (const float*)h->ob[8].p,
-                                          (const float*)h->ob[9].p, n_pad, kd, h->tiles, h->ntiles,
+        const int rc = launch_s_update_tc((float*)h->S, h->ld, h->ob[8].p,
+                                          h->ob[9].p, n_pad, kd, h->tiles, h->ntiles,
                                           h->n_cur, h->counters, h->num_sms, wait_limit, h->st,
                                           upper(h));
         if (rc != 0) return fail(h, SR_ERR_CUDA, "tensor-core S update: launch setup failed");
@@ -1137,6 +1146,7 @@ simrank_status simrank_init(const simrank_config* cfg_in, int32_t n, int64_t m, 
                 "prep_ctas, prep_item >= 0; prep_cache a multiple of 4 in [0, 16384]");
   if (cfg.defer < 0 || (cfg.defer > 1 && (int64_t)cfg.defer * (cfg.K + 1) > 4096))
     return fail(nullptr, SR_ERR_ARG, "defer * (K + 1) must be at most 4096");
+  if (cfg.tc < 0 || cfg.tc > 2) return fail(nullptr, SR_ERR_ARG, "tc must be 0, 1 or 2");
   if (cfg.tc && cfg.s_precision != 32)
     return fail(nullptr, SR_ERR_ARG, "the tensor-core update needs s_precision = 32");
   if (cfg.init_tol <= 0.0) cfg.init_tol = 1e-13;

@@ -8,6 +8,8 @@
 // Lambda need only the S rows of the batch's endpoints.  These kernels build
 // W and Lambda, the panels Xi_k = C^{k+1} Q_new^k U, H_k = Q_new^k W, and the
 // operand layouts of the two S-update kernels.
+#include <cuda_fp16.h>
+
 #include "sr_internal.h"
 
 namespace sr {
@@ -189,6 +191,51 @@ __global__ void k_pack_tc_tiles(const float* __restrict__ Pp, int GK1, int nterm
   }
 }
 
+// Largest |value| of each pending term: maxes[which][q] over all rows (the
+// bits of a non-negative float order like the float), one warp per term.
+__global__ void k_term_max(const float* __restrict__ Pp, int GK1, int nterms,
+                           unsigned int* __restrict__ maxes) {
+  const int T = blockIdx.x, which = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int q = warp; q < nterms; q += blockDim.x >> 5) {
+    const float4 v = reinterpret_cast<const float4*>(
+        Pp + (((int64_t)T * 2 + which) * GK1 + q) * PT)[lane];
+    float m = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0 && m > 0.f) atomicMax(&maxes[which * nterms + q], __float_as_uint(m));
+  }
+}
+
+// FP16 tensor-core operands from tile-blocked FP32 panels: as k_pack_tc_tiles,
+// after scaling term q's xi column by 2^e_q and its eta column by 2^-e_q,
+// e_q = (exponent of max|eta_q| - exponent of max|xi_q|) / 2.  The product
+// xi_q eta_q^T is unchanged by the scaling (powers of two are exact) and both
+// scaled columns share one magnitude, which keeps them in FP16's normal range.
+// x = hi + lo, hi = fp16(x), lo = fp16(x - hi).
+__global__ void k_pack_f16_tiles(const float* __restrict__ Pp, int GK1, int nterms, int rg,
+                                 int n_rows, const unsigned int* __restrict__ maxes,
+                                 __half* __restrict__ Ahi, __half* __restrict__ Alo, int64_t kd) {
+  const int64_t a = blockIdx.x;
+  const int64_t ba = ((a / PT) * 2) * (int64_t)GK1 * PT + (a % PT);
+  for (int c = threadIdx.x; c < kd; c += blockDim.x) {
+    const int h = c >= rg ? 1 : 0;
+    const int q = c - h * rg;
+    float x = 0.f;
+    if (q < nterms) {
+      x = Pp[ba + (int64_t)(h * GK1 + q) * PT];
+      const float mx = __uint_as_float(maxes[q]), me = __uint_as_float(maxes[nterms + q]);
+      if (mx > 0.f && me > 0.f && x != 0.f) {
+        const int e = (ilogbf(me) - ilogbf(mx)) / 2;
+        x = ldexpf(x, h ? -e : e);
+      }
+    }
+    const __half hi = __float2half_rn(x);
+    Ahi[a * kd + c] = hi;
+    Alo[a * kd + c] = __float2half_rn(x - __half2float(hi));
+  }
+}
+
 }  // namespace
 
 void launch_signed_rows(const void* S, int s_prec, int64_t ld, const int32_t* src, const int8_t* sign,
@@ -248,6 +295,15 @@ void launch_pack_ffma(const double* X, int64_t ldx, int rh, int r, int slot, int
 void launch_pack_tc_tiles(const float* Pp, int GK1, int nterms, int rg, int n_rows, float* Ahi,
                           float* Alo, int64_t kd, cudaStream_t st) {
   k_pack_tc_tiles<<<n_rows, 256, 0, st>>>(Pp, GK1, nterms, rg, n_rows, Ahi, Alo, kd);
+}
+
+void launch_pack_f16_tiles(const float* Pp, int GK1, int nterms, int rg, int n_rows,
+                           unsigned int* maxes, void* Ahi, void* Alo, int64_t kd, cudaStream_t st) {
+  const int nT = n_rows / PT;
+  cudaMemsetAsync(maxes, 0, 2 * (size_t)nterms * sizeof(unsigned int), st);
+  k_term_max<<<dim3(nT, 2), 256, 0, st>>>(Pp, GK1, nterms, maxes);
+  k_pack_f16_tiles<<<n_rows, 256, 0, st>>>(Pp, GK1, nterms, rg, n_rows, maxes, (__half*)Ahi,
+                                           (__half*)Alo, kd);
 }
 
 void launch_pack_tc(const double* X, int64_t ldx, int rh, int r, int slot, int rg, int n_rows,

@@ -2,14 +2,17 @@
 //   S[I,J] += D_IJ,  S[J,I] += D_IJ^T  (I <= J),   D = A B^T,
 // where row a of A is [xi terms | eta terms] and row a of B is the same row
 // with its two halves swapped, so A B^T = Xi H^T + H Xi^T (proof of Thm 2,
-// Eq. 23-28, applied to all sinks of a batch).  FP32 accuracy from the TF32
-// tensor pipe with the 3-term split x = hi + lo:
-//   D = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T,  accumulated in FP32 (TMEM).
+// Eq. 23-28, applied to all sinks of a batch).  FP32 accuracy from a 3-term
+// split x = hi + lo of the operands:
+//   D = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T,  accumulated in FP32 (TMEM),
+// with hi and lo in TF32 (kind::tf32) or, at twice the tensor rate, in FP16
+// (kind::f16) after a power-of-two scaling of each term (exact, see the pack).
 //
 // One CTA per SM, persistent over the tile-pair list.  Warp 0 issues TMA loads
-// (128 x 32 FP32 boxes, 128-byte swizzle) into a 2-stage ring; warp 1 owns two
-// TMEM accumulators (128 lanes x 128 columns each) and issues tcgen05.mma
-// (M = 128, N = 128, K = 8) for tile t + 1 while warps 2-9 drain tile t: they
+// (128 rows x 128 bytes boxes, 128-byte swizzle) into a 2-stage ring; warp 1
+// owns two TMEM accumulators (128 lanes x 128 columns each) and issues
+// tcgen05.mma (M = 128, N = 128, K = 32 bytes) for tile t + 1 while warps 2-9
+// drain tile t: they
 // copy the accumulator (tcgen05.ld) into a padded shared tile and stream
 // S[I,J] and S[J,I] from it with coalesced 16-byte accesses.  Every mbarrier
 // wait is bounded and every stop decision of the epilogue warps is taken by
@@ -23,20 +26,22 @@ namespace sr {
 
 namespace {
 
-constexpr int TM = 128;            // rows of an S tile (M)
-constexpr int TN = 128;            // columns of an S tile (N)
-constexpr int KCH = 32;            // FP32 elements of K per stage (one 128-byte swizzle row)
+constexpr int TM = 128;             // rows of an S tile (M)
+constexpr int TN = 128;             // columns of an S tile (N)
+constexpr int KB = 128;             // bytes of K per stage (one 128-byte swizzle row)
 constexpr int STAGES = 2;
-constexpr int OPB = TM * KCH * 4;  // bytes of one operand box: 16 KB
+constexpr int OPB = TM * KB;        // bytes of one operand box: 16 KB
 constexpr int STAGE_BYTES = 4 * OPB;
 constexpr int TC_THREADS = 320;       // 10 warps: TMA, MMA, 8 epilogue
 constexpr uint32_t TMEM_COLS = 256;   // two 128-column accumulators
 constexpr int EP = TN + 1;            // row pitch of the shared accumulator copy
 
-// tcgen05 instruction descriptor, kind::tf32: D = F32, A = B = TF32, both
-// K-major, N = 128, M = 128.
-constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) |
-                           ((uint32_t)(TM >> 4) << 24);
+// tcgen05 instruction descriptors: D = F32, A and B of the same type, both
+// K-major, N = 128, M = 128; kind::tf32 (type code 2) or kind::f16 (F16 = 0).
+constexpr uint32_t IDESC_TF32 = (1u << 4) | (2u << 7) | (2u << 10) |
+                                ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+constexpr uint32_t IDESC_F16 = (1u << 4) | (0u << 7) | (0u << 10) |
+                               ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -93,13 +98,22 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return d;
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+template <bool F16>
+__device__ __forceinline__ void mma_k32b(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
                                          uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
-      : "memory");
+  if (F16) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(IDESC_F16), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(IDESC_TF32), "r"(accumulate)
+        : "memory");
+  }
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -138,6 +152,7 @@ __device__ __forceinline__ bool ep_all(bool pred) {
 }
 __device__ __forceinline__ void ep_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
+template <bool F16>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_s_update_tc(const __grid_constant__ CUtensorMap tm_hi,
                   const __grid_constant__ CUtensorMap tm_lo, float* __restrict__ S, int64_t ld,
@@ -199,6 +214,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const uint32_t fb = smem_u32(&bar_full[s]);
           mbar_expect_tx(fb, STAGE_BYTES);
           const int kb_b = kb < half ? kb + half : kb - half;
+          constexpr int KCH = F16 ? KB / 2 : KB / 4;  // elements of K per stage
           tma_load_2d(st + 0 * OPB, &tm_hi, kb * KCH, I * TM, fb);
           tma_load_2d(st + 1 * OPB, &tm_lo, kb * KCH, I * TM, fb);
           tma_load_2d(st + 2 * OPB, &tm_hi, kb_b * KCH, J * TN, fb);
@@ -232,12 +248,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const uint64_t a_hi = smem_desc(st + 0 * OPB), a_lo = smem_desc(st + 1 * OPB);
           const uint64_t b_hi = smem_desc(st + 2 * OPB), b_lo = smem_desc(st + 3 * OPB);
 #pragma unroll
-          for (int kk = 0; kk < KCH / 8; ++kk) {
-            const uint64_t adv = (uint64_t)(kk * 32) >> 4;  // 8 TF32 = 32 bytes along K
+          for (int kk = 0; kk < KB / 32; ++kk) {
+            // one MMA covers 32 bytes of K: 8 TF32 or 16 FP16 elements
+            const uint64_t adv = (uint64_t)(kk * 32) >> 4;
             const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
-            mma_tf32(acc, a_hi + adv, b_hi + adv, first);
-            mma_tf32(acc, a_hi + adv, b_lo + adv, 1u);
-            mma_tf32(acc, a_lo + adv, b_hi + adv, 1u);
+            mma_k32b<F16>(acc, a_hi + adv, b_hi + adv, first);
+            mma_k32b<F16>(acc, a_hi + adv, b_lo + adv, 1u);
+            mma_k32b<F16>(acc, a_lo + adv, b_hi + adv, 1u);
           }
           mma_commit(smem_u32(&bar_empty[s]));  // stage reusable once these MMAs finish
         }
@@ -355,39 +372,52 @@ EncodeFn encode_fn() {
   return fn;
 }
 
-bool make_map(CUtensorMap* m, float* ptr, int64_t rows, int64_t kd) {
+// Row-major [rows][kd] operand of 4-byte (FP32/TF32) or 2-byte (FP16)
+// elements; boxes of 128 rows x 128 bytes.
+bool make_map(CUtensorMap* m, const void* ptr, int64_t rows, int64_t kd, int eb) {
   EncodeFn f = encode_fn();
   if (!f) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)kd, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)kd * 4};
-  const cuuint32_t box[2] = {(cuuint32_t)KCH, (cuuint32_t)TM};
+  const cuuint64_t strides[1] = {(cuuint64_t)kd * eb};
+  const cuuint32_t box[2] = {(cuuint32_t)(KB / eb), (cuuint32_t)TM};
   const cuuint32_t estr[2] = {1, 1};
-  return f(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, ptr, dims, strides, box, estr,
-           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return f(m, eb == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+           const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace
 
-// A_hi / A_lo: row-major [n_rows][kd] FP32 (TF32 values), kd a multiple of
-// 2 * 32; the B operand is A with its two column halves swapped.
-int launch_s_update_tc(float* S, int64_t ld, const float* Ahi, const float* Alo, int64_t n_rows,
+// A_hi / A_lo: row-major [n_rows][kd], FP32 holding TF32 values (f16 = 0) or
+// FP16 (f16 = 1); kd a multiple of 2 * (128 bytes / element size); the B
+// operand is A with its two column halves swapped.
+int launch_s_update_tc(float* S, int64_t ld, const void* Ahi, const void* Alo, int64_t n_rows,
                        int64_t kd, const uint32_t* tiles, const int* ntiles, int n,
                        int64_t* counters, int grid, long long wait_limit, cudaStream_t st,
-                       int upper) {
-  if (kd % (2 * KCH) != 0 || n_rows % TM != 0) return 1;
+                       int upper, int f16) {
+  const int eb = f16 ? 2 : 4;
+  const int kch = KB / eb;
+  if (kd % (2 * kch) != 0 || n_rows % TM != 0) return 1;
   CUtensorMap mhi, mlo;
-  if (!make_map(&mhi, const_cast<float*>(Ahi), n_rows, kd)) return 2;
-  if (!make_map(&mlo, const_cast<float*>(Alo), n_rows, kd)) return 2;
+  if (!make_map(&mhi, Ahi, n_rows, kd, eb)) return 2;
+  if (!make_map(&mlo, Alo, n_rows, kd, eb)) return 2;
   const size_t smem = (size_t)STAGES * STAGE_BYTES + (size_t)TM * EP * 4 + 1024;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_s_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
+  static bool attr[2] = {false, false};
+  const void* fn = f16 ? (const void*)k_s_update_tc<true> : (const void*)k_s_update_tc<false>;
+  if (!attr[f16 ? 1 : 0]) {
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr[f16 ? 1 : 0] = true;
   }
-  k_s_update_tc<<<grid, TC_THREADS, smem, st>>>(mhi, mlo, S, ld, tiles, ntiles, (int)(kd / KCH),
-                                                wait_limit, n, upper ? 0 : 1,
-                                                (unsigned long long*)counters);
+  const int nkb = (int)(kd / kch);
+  const int mirror = upper ? 0 : 1;
+  unsigned long long* cnt = (unsigned long long*)counters;
+  if (f16)
+    k_s_update_tc<true><<<grid, TC_THREADS, smem, st>>>(mhi, mlo, S, ld, tiles, ntiles, nkb,
+                                                        wait_limit, n, mirror, cnt);
+  else
+    k_s_update_tc<false><<<grid, TC_THREADS, smem, st>>>(mhi, mlo, S, ld, tiles, ntiles, nkb,
+                                                         wait_limit, n, mirror, cnt);
   return 0;
 }
 

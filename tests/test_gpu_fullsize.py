@@ -78,13 +78,14 @@ def test_fullsize_stream_properties(P, graph):
     assert stats["rank_one_updates"] == 1000
 
 
-@pytest.mark.parametrize("defer", [0, 16])
-def test_fullsize_stream_converged_vs_batch(P, graph, defer):
+@pytest.mark.parametrize("defer,tc", [(0, 0), (16, 1), (16, 2)])
+def test_fullsize_stream_converged_vs_batch(P, graph, defer, tc):
     """The same 1,000-update stream at K_CONV: sampled columns equal an FP64
     batch recomputation (Procedure 1 to convergence) on the final graph, with
-    S updated per edge or 16 updates at a time on the tensor cores."""
+    S updated per edge on the CUDA cores, or 16 updates at a time on the
+    tensor cores (TF32 or FP16 split)."""
     s, d = graph
-    sr = P.SimRank(N, s, d, C=C, K=K_CONV, s_precision=32, defer=defer, tc=1)
+    sr = P.SimRank(N, s, d, C=C, K=K_CONV, s_precision=32, defer=defer, tc=tc)
     es = EdgeSet(N, s, d)
     st = update_stream(N, s, d, 1000, 3, edge_set=es)
     sr.apply_updates(st)

@@ -122,7 +122,8 @@ def test_unit_update_converged_vs_batch_recompute(P, case):
                                      "fused_noaff", "plain", "deferred_ffma", "deferred_tc",
                                      "per_step_chain", "prep_multi_tile", "prep_small_items",
                                      "deferred_multi_tile", "full_storage", "deferred_tc_full",
-                                     "tc_each", "fp32_vectors", "deferred_fp32_vectors"])
+                                     "tc_each", "fp64_vectors", "deferred_fp64_vectors",
+                                     "deferred_tc_f16", "tc_each_f16"])
 def test_stream_fp32_powerlaw(P, variant):
     n, m, C, K = 1500, 15000, 0.6, 20
     s, d = chung_lu_digraph(n, m, 2.1, 2.1, 4)
@@ -149,10 +150,14 @@ def test_stream_fp32_powerlaw(P, variant):
     elif variant == "prep_small_items":
         # 48-nonzero work items: every tile split over several CTAs
         kw = dict(aff=1, prep_item=48, prep_ctas=40)
-    elif variant == "fp32_vectors":
-        kw = dict(aff=1, vec_fp32=1)
-    elif variant == "deferred_fp32_vectors":
-        kw = dict(aff=1, defer=16, tc=1, vec_fp32=1)
+    elif variant == "fp64_vectors":
+        kw = dict(aff=1, vec_fp64=1)
+    elif variant == "deferred_fp64_vectors":
+        kw = dict(aff=1, defer=16, tc=1, vec_fp64=1)
+    elif variant == "deferred_tc_f16":
+        kw = dict(aff=1, defer=16, tc=2)
+    elif variant == "tc_each_f16":
+        kw = dict(aff=1, defer=0, tc=2)
     elif variant == "tc_each":
         kw = dict(aff=1, defer=0, tc=1)
     elif variant == "full_storage":
