@@ -7,8 +7,8 @@ affected-area pruning on.  One step applies a batch of 1,000 sequential unit
 updates (80% insertions with degree-biased endpoints, 20% deletions of
 uniform existing edges); each update runs Alg 1 (one cooperative launch for
 its recurrence) and its rank-2(K+1) S change is applied by the tensor-core S
-pass, 16 pending updates per pass by default (--defer / --tc select the other
-forms).  Steps continue one valid stream, so every step changes the graph.
+pass (3-term FP16 split), 16 pending updates per pass by default (--defer /
+--tc / --vec-fp64 select the other forms).  Steps continue one valid stream, so every step changes the graph.
 
 Prints one JSON line (see the keys below).  ``--impl reference`` times the
 FP64 CPU oracle (Alg 1 as printed, dense) on a bounded sample instead.
@@ -226,6 +226,11 @@ def run_gpu(args, rank, world):
             dist.barrier()
         ms = ev0.elapsed_time(ev1)
         st1 = sr.stats()
+        # drift re-anchor (FP64 Jacobi sweeps of Eq. 1 from the current S)
+        ra0 = time.perf_counter()
+        ra_change = sr.reanchor(2)
+        sr.sync()
+        reanchor_ms = (time.perf_counter() - ra0) * 1000.0 / 2
     sr.close()
     del sr
     torch.cuda.empty_cache()
@@ -292,7 +297,11 @@ def run_gpu(args, rank, world):
     value = updates / (ms / 1000.0)
     e2e_val = updates / e2e_s
     peak, peak_kind = read_peaks()
-    tf32_peak = read_bf16_peak() * 1.1 / 2.25
+    # tensor peak of the operand type: FP16 = the measured bf16 burst (same
+    # nominal rate); TF32 = that x 1.1/2.25 (the nominal TF32/BF16 ratio)
+    tc_peak = read_bf16_peak() * (1.0 if args.tc == 2 else 1.1 / 2.25)
+    tc_peak_kind = ("measured bf16 burst (FP16 has the same nominal dense rate)" if args.tc == 2
+                    else "measured bf16 burst x 1.1/2.25 (nominal TF32/BF16)")
     # profiled step: the two kernels of the path
     pd = {k: pst1[k] - pst0[k] for k in ("s_update_launches", "s_bytes", "s_update_ms",
                                         "tiles_touched", "tiles_total")}
@@ -301,10 +310,11 @@ def run_gpu(args, rank, world):
     sp_ms = pd["s_update_ms"]
     G = max(1, args.defer)
     terms = G * (K + 1)
-    rg = (terms + 31) // 32 * 32
+    rg = (terms + 63) // 64 * 64 if args.tc == 2 else (terms + 31) // 32 * 32
     n_pad = (N + 127) // 128 * 128
     if args.tc:
-        operand_bytes = launches * n_pad * (2 * rg) * 4 * 2  # hi and lo operands
+        eb = 2 if args.tc == 2 else 4
+        operand_bytes = launches * n_pad * (2 * rg) * eb * 2  # hi and lo operands
         flops = pd["tiles_touched"] * 128 * 128 * (2 * rg) * 2 * 3
     else:
         operand_bytes = launches * 2 * terms * n_pad * 4
@@ -312,11 +322,11 @@ def run_gpu(args, rank, world):
     sp_bytes = pd["s_bytes"] + operand_bytes
     sp_gbs = sp_bytes / (sp_ms / 1000.0) / 1e9 if sp_ms > 0 else 0.0
     sp_tflops = flops / (sp_ms / 1000.0) / 1e12 if sp_ms > 0 else 0.0
-    sp_name = "k_s_update_tc (tcgen05 3xTF32 S pass)" if args.tc else "k_s_update_ws (CUDA-core S pass)"
-    if args.tc and sp_tflops / tf32_peak > sp_gbs / peak:
-        s_pass = {"kernel": sp_name, "bound": "tensor", "achieved": sp_tflops, "peak": tf32_peak,
-                  "unit": "TFLOP/s", "frac": sp_tflops / tf32_peak,
-                  "peak_kind": "measured bf16 burst x 1.1/2.25 (nominal TF32/BF16)",
+    sp_name = ("k_s_update_tc (tcgen05, 3-term " + ("FP16" if args.tc == 2 else "TF32") +
+               " split, S pass)") if args.tc else "k_s_update_ws (CUDA-core S pass)"
+    if args.tc and sp_tflops / tc_peak > sp_gbs / peak:
+        s_pass = {"kernel": sp_name, "bound": "tensor", "achieved": sp_tflops, "peak": tc_peak,
+                  "unit": "TFLOP/s", "frac": sp_tflops / tc_peak, "peak_kind": tc_peak_kind,
                   "hbm_gbs": sp_gbs}
     else:
         s_pass = {"kernel": sp_name, "bound": "hbm", "achieved": sp_gbs, "peak": peak,
@@ -356,6 +366,8 @@ def run_gpu(args, rank, world):
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": dominant,
         "kernels": {"s_pass": s_pass, "prep": prep},
+        "reanchor": {"ms_per_sweep": reanchor_ms, "max_change_last_sweep": ra_change,
+                     "note": "FP64 Jacobi sweep of Eq. 1 on the n=20000 S after the timed steps"},
         "fp64_vectors": {"value": v64, "unit": UNIT, "steps": 1,
                          "note": "same stream, xi/eta vectors and recurrence in FP64"},
         "e2e": {"value": e2e_val, "unit": UNIT,
@@ -710,7 +722,8 @@ def main():
                     help="batch size of one step (the benchmarked workload uses 1000)")
     ap.add_argument("--defer", type=int, default=16,
                     help="stream workload: rank-one updates kept pending per S pass (0 = apply each)")
-    ap.add_argument("--tc", type=int, default=1, help="S passes on the tensor cores (3xTF32)")
+    ap.add_argument("--tc", type=int, default=2,
+                    help="S passes on the tensor cores: 1 = 3xTF32 split, 2 = 3xFP16 split")
     ap.add_argument("--vec-fp64", type=int, default=0, help="xi/eta vectors in FP64 (default FP32)")
     ap.add_argument("--workload", default="stream",
                     choices=["stream", "batched", "multi", "column", "grad"],

@@ -64,6 +64,9 @@ struct simrank_ctx {
   int64_t* counters = nullptr;
   unsigned long long* diffbits = nullptr;
   unsigned int* gbar = nullptr;  // grid barrier state of the cooperative pre-update kernel
+  uint32_t* d_order = nullptr;   // all tile pairs I <= J in band order (tensor-core S pass)
+  int order_nT = -1;
+  int order_n = 0;
   void* W = nullptr;             // (xi, eta) working columns of the pre-update kernel
   int* tile_nnz = nullptr;       // per-tile nonzeros (scratch of the pre-update kernel)
   // per-call staging
@@ -426,6 +429,29 @@ bool deferring(const simrank_ctx* h) {
 // Updates per pending group (1 when tensor cores apply each update at once).
 int group(const simrank_ctx* h) { return std::max(1, (int)h->cfg.defer); }
 
+// All tile pairs (I <= J) of nT tiles, in the order the tensor-core S pass
+// takes them: bands of 8 tile rows; within a band, J ascending and, for each
+// J, the band's rows I <= J.  Concurrent CTAs then work on a few row bands
+// and a few column tiles, so their operand rows are shared through L2.
+simrank_status ensure_order(simrank_ctx* h, int nT) {
+  if (h->order_nT == nT) return SR_OK;
+  std::vector<uint32_t> v;
+  v.reserve((size_t)nT * (nT + 1) / 2);
+  constexpr int BAND = 8;
+  for (int b0 = 0; b0 < nT; b0 += BAND)
+    for (int J = b0; J < nT; ++J)
+      for (int I = b0; I < std::min(b0 + BAND, J + 1); ++I)
+        v.push_back(((uint32_t)I << 16) | (uint32_t)J);
+  if (h->d_order) cudaFree(h->d_order);
+  h->d_order = nullptr;
+  CUDA_TRY(h, dev_alloc(&h->d_order, v.size()));
+  CUDA_TRY(h, cudaMemcpy(h->d_order, v.data(), v.size() * sizeof(uint32_t),
+                         cudaMemcpyHostToDevice));
+  h->order_nT = nT;
+  h->order_n = (int)v.size();
+  return SR_OK;
+}
+
 // Applies the pending updates' panels to S in one pass (rank 2 * np * K1).
 simrank_status flush_pending(simrank_ctx* h) {
   if (h->np == 0) return SR_OK;
@@ -442,14 +468,18 @@ simrank_status flush_pending(simrank_ctx* h) {
   }
   const int GK1 = group(h) * h->K1;
   const int nterms = h->np * h->K1;
-  CUDA_TRY(h, cudaMemsetAsync(h->ntiles, 0, sizeof(int), h->st));
-  launch_tile_list(h->pXi, h->pEta, nT, h->cfg.aff ? 1 : 0, h->tiles, h->ntiles, h->st);
+  simrank_status s;
+  if (h->cfg.tc) {
+    if ((s = ensure_order(h, nT)) != SR_OK) return s;
+  } else {
+    CUDA_TRY(h, cudaMemsetAsync(h->ntiles, 0, sizeof(int), h->st));
+    launch_tile_list(h->pXi, h->pEta, nT, h->cfg.aff ? 1 : 0, h->tiles, h->ntiles, h->st);
+  }
   std::pair<cudaEvent_t, cudaEvent_t>* ev = nullptr;
   if (h->cfg.profile) {
     ev = next_event_pair(h);
     if (!ev) return fail(h, SR_ERR_CUDA, "cudaEventCreate failed");
   }
-  simrank_status s;
   if (h->cfg.tc) {
     // tc = 2: FP16 operands (terms rounded up to 64), else TF32 (rounded up to 32)
     const bool f16 = h->cfg.tc == 2;
@@ -469,7 +499,8 @@ simrank_status flush_pending(simrank_ctx* h) {
     }
     if (ev) CUDA_TRY(h, cudaEventRecord(ev->first, h->st));
     const int rc = launch_s_update_tc((float*)h->S, h->ld, h->ob[12].p, h->ob[13].p, h->n_pad,
-                                      kd, h->tiles, h->ntiles, h->n_cur, h->counters, h->num_sms,
+                                      kd, h->d_order, h->order_n, h->pXi, h->pEta,
+                                      h->cfg.aff ? 1 : 0, h->n_cur, h->counters, h->num_sms,
                                       wait_limit(h), h->st, upper(h), f16 ? 1 : 0);
     if (rc != 0) return fail(h, SR_ERR_CUDA, "tensor-core S update: launch setup failed");
     h->launches += 2;
@@ -892,10 +923,13 @@ simrank_status run_one_shot(simrank_ctx* h, const std::map<int32_t, std::vector<
     h->launches += 1;
     ++slot;
     if (slot == g || k == h->cfg.K) {
-      CUDA_TRY(h, cudaMemsetAsync(h->ntiles, 0, sizeof(int), h->st));
-      launch_tile_list(h->mXi, h->mEta, nT, tc ? 0 : (h->cfg.aff ? 1 : 0), h->tiles, h->ntiles,
-                       h->st);
-      h->launches += 1;
+      if (tc) {
+        if ((s = ensure_order(h, nT)) != SR_OK) return s;
+      } else {
+        CUDA_TRY(h, cudaMemsetAsync(h->ntiles, 0, sizeof(int), h->st));
+        launch_tile_list(h->mXi, h->mEta, nT, h->cfg.aff ? 1 : 0, h->tiles, h->ntiles, h->st);
+        h->launches += 1;
+      }
       std::pair<cudaEvent_t, cudaEvent_t>* ev = nullptr;
       if (h->cfg.profile) {
         ev = next_event_pair(h);
@@ -903,8 +937,8 @@ simrank_status run_one_shot(simrank_ctx* h, const std::map<int32_t, std::vector<
         CUDA_TRY(h, cudaEventRecord(ev->first, h->st));
       }
       if (tc) {
-        const int rc = launch_s_update_tc((float*)h->S, h->ld, h->ob[8].p,
-                                          h->ob[9].p, n_pad, kd, h->tiles, h->ntiles,
+        const int rc = launch_s_update_tc((float*)h->S, h->ld, h->ob[8].p, h->ob[9].p, n_pad,
+                                          kd, h->d_order, h->order_n, h->mXi, h->mEta, 0,
                                           h->n_cur, h->counters, h->num_sms, wait_limit, h->st,
                                           upper(h));
         if (rc != 0) return fail(h, SR_ERR_CUDA, "tensor-core S update: launch setup failed");
@@ -1065,7 +1099,7 @@ void free_ctx(simrank_ctx* h) {
                   h->dout.col,  h->d_in_w,   h->d_wsum,    h->S,          h->P64,
                   h->P32,       h->mXi,      h->mEta,      h->tiles,      h->ntiles,
                   h->sI,        h->sJ,       h->scal,      h->counters,   h->diffbits,
-                  h->gbar,      h->W,        h->tile_nnz,
+                  h->gbar,      h->W,        h->tile_nnz,  h->d_order,
                   h->d_srcs,    h->d_ops,    h->d_cols,     h->d_ext2int};
   for (void* p : ptrs)
     if (p) cudaFree(p);

@@ -152,11 +152,24 @@ __device__ __forceinline__ bool ep_all(bool pred) {
 }
 __device__ __forceinline__ void ep_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
+// Tile pair t of the (band-ordered) list; false when the masks show no
+// active cross term there.  Every role of the CTA takes the same decision.
+__device__ __forceinline__ bool tile_active(const uint32_t* __restrict__ tiles, int t,
+                                            const uint64_t* __restrict__ mX,
+                                            const uint64_t* __restrict__ mE, int use_masks,
+                                            int& I, int& J) {
+  const uint32_t pr = tiles[t];
+  I = (int)(pr >> 16);
+  J = (int)(pr & 0xffffu);
+  return !use_masks || (((mX[I] & mE[J]) | (mE[I] & mX[J])) != 0ull);
+}
+
 template <bool F16>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_s_update_tc(const __grid_constant__ CUtensorMap tm_hi,
                   const __grid_constant__ CUtensorMap tm_lo, float* __restrict__ S, int64_t ld,
-                  const uint32_t* __restrict__ tiles, const int* __restrict__ ntiles, int nkb,
+                  const uint32_t* __restrict__ tiles, int nt, const uint64_t* __restrict__ mX,
+                  const uint64_t* __restrict__ mE, int use_masks, int nkb,
                   long long wait_limit, int n, int mirror,
                   unsigned long long* __restrict__ counters) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -169,7 +182,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   float* sD = reinterpret_cast<float*>(smem_raw + (base - smem_u32(smem_raw)) +
                                        (size_t)STAGES * STAGE_BYTES);
-  const int nt = *ntiles;
   const int half = nkb / 2;  // B row = A row with its halves swapped
 
   if (threadIdx.x == 0) {
@@ -201,8 +213,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (lane == 0) {
       uint32_t it = 0;
       for (int t = blockIdx.x; t < nt && ok; t += gridDim.x) {
-        const uint32_t pr = tiles[t];
-        const int I = (int)(pr >> 16), J = (int)(pr & 0xffffu);
+        int I, J;
+        if (!tile_active(tiles, t, mX, mE, use_masks, I, J)) continue;
         for (int kb = 0; kb < nkb && ok; ++kb, ++it) {
           const int s = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1u;
@@ -227,10 +239,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // ---------------- MMA issuer: tile tl accumulates in TMEM columns (tl & 1) * 128
     if (lane == 0) {
       uint32_t it = 0, tl = 0;
-      for (int t = blockIdx.x; t < nt && ok; t += gridDim.x, ++tl) {
+      for (int t = blockIdx.x; t < nt && ok; t += gridDim.x) {
+        int I, J;
+        if (!tile_active(tiles, t, mX, mE, use_masks, I, J)) continue;
         const uint32_t b = tl & 1u;
-        if (!mbar_wait(smem_u32(&bar_acc_empty[b]), ((tl >> 1) & 1u) ^ 1u, wait_limit,
-                       &abort_flag)) {
+        const uint32_t eph = ((tl >> 1) & 1u) ^ 1u;
+        ++tl;
+        if (!mbar_wait(smem_u32(&bar_acc_empty[b]), eph, wait_limit, &abort_flag)) {
           ok = false;
           break;
         }
@@ -271,16 +286,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int chalf = (ew >> 2) * 64;    // columns [chalf, chalf + 64) of the accumulator
     uint32_t tl = 0;
     unsigned long long my_tiles = 0, my_bytes = 0;
-    for (int t = blockIdx.x; t < nt; t += gridDim.x, ++tl) {
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+      int I, J;
+      if (!tile_active(tiles, t, mX, mE, use_masks, I, J)) continue;
       const uint32_t b = tl & 1u;
-      const bool got = mbar_wait(smem_u32(&bar_acc_full[b]), (tl >> 1) & 1u, wait_limit, &abort_flag);
+      const uint32_t tph = (tl >> 1) & 1u;
+      ++tl;
+      const bool got = mbar_wait(smem_u32(&bar_acc_full[b]), tph, wait_limit, &abort_flag);
       if (!ep_all(got)) {
         ok = false;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t pr = tiles[t];
-      const int I = (int)(pr >> 16), J = (int)(pr & 0xffffu);
       // accumulator -> shared tile (row = TMEM lane)
       const int row = quarter * 32 + lane;
 #pragma unroll 1
@@ -393,9 +410,9 @@ bool make_map(CUtensorMap* m, const void* ptr, int64_t rows, int64_t kd, int eb)
 // FP16 (f16 = 1); kd a multiple of 2 * (128 bytes / element size); the B
 // operand is A with its two column halves swapped.
 int launch_s_update_tc(float* S, int64_t ld, const void* Ahi, const void* Alo, int64_t n_rows,
-                       int64_t kd, const uint32_t* tiles, const int* ntiles, int n,
-                       int64_t* counters, int grid, long long wait_limit, cudaStream_t st,
-                       int upper, int f16) {
+                       int64_t kd, const uint32_t* tiles, int nt, const uint64_t* mX,
+                       const uint64_t* mE, int use_masks, int n, int64_t* counters, int grid,
+                       long long wait_limit, cudaStream_t st, int upper, int f16) {
   const int eb = f16 ? 2 : 4;
   const int kch = KB / eb;
   if (kd % (2 * kch) != 0 || n_rows % TM != 0) return 1;
@@ -413,11 +430,13 @@ int launch_s_update_tc(float* S, int64_t ld, const void* Ahi, const void* Alo, i
   const int mirror = upper ? 0 : 1;
   unsigned long long* cnt = (unsigned long long*)counters;
   if (f16)
-    k_s_update_tc<true><<<grid, TC_THREADS, smem, st>>>(mhi, mlo, S, ld, tiles, ntiles, nkb,
-                                                        wait_limit, n, mirror, cnt);
+    k_s_update_tc<true><<<grid, TC_THREADS, smem, st>>>(mhi, mlo, S, ld, tiles, nt, mX, mE,
+                                                        use_masks, nkb, wait_limit, n, mirror,
+                                                        cnt);
   else
-    k_s_update_tc<false><<<grid, TC_THREADS, smem, st>>>(mhi, mlo, S, ld, tiles, ntiles, nkb,
-                                                         wait_limit, n, mirror, cnt);
+    k_s_update_tc<false><<<grid, TC_THREADS, smem, st>>>(mhi, mlo, S, ld, tiles, nt, mX, mE,
+                                                         use_masks, nkb, wait_limit, n, mirror,
+                                                         cnt);
   return 0;
 }
 

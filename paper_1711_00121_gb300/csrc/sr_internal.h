@@ -263,10 +263,12 @@ void launch_pack_tc(const double* X, int64_t ldx, int rh, int r, int slot, int r
                     float* Ahi, float* Alo, int64_t kd, cudaStream_t st);
 // tcgen05 symmetric update S += A B^T (B = A with halves swapped), 3xTF32; returns
 // 0 on launch, 1 for a bad shape, 2 if no tensor map could be encoded.
+// tiles[0 .. nt): tile pairs (I << 16 | J) in the order CTAs take them; a
+// pair is skipped when use_masks and (mX[I] & mE[J]) | (mE[I] & mX[J]) == 0.
 int launch_s_update_tc(float* S, int64_t ld, const void* Ahi, const void* Alo, int64_t n_rows,
-                       int64_t kd, const uint32_t* tiles, const int* ntiles, int n,
-                       int64_t* counters, int grid, long long wait_limit, cudaStream_t st,
-                       int upper = 0, int f16 = 0);
+                       int64_t kd, const uint32_t* tiles, int nt, const uint64_t* mX,
+                       const uint64_t* mE, int use_masks, int n, int64_t* counters, int grid,
+                       long long wait_limit, cudaStream_t st, int upper = 0, int f16 = 0);
 // FP16 operands (row-major [n_rows][kd] hi/lo) from tile-blocked FP32 pending
 // panels, each term scaled by 2^(+-e_q) (exact); maxes: 2 * nterms scratch uints.
 void launch_pack_f16_tiles(const float* Pp, int GK1, int nterms, int rg, int n_rows,
