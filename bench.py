@@ -2,7 +2,7 @@
 
 Workload (the power-law update stream): directed Chung-Lu graph, n = 20,000,
 in/out-degree exponent 2.1, mean degree 10 (m = 200,000), C = 0.6, K = 20,
-S in FP32 (1.6 GB, larger than L2; upper tiles kept), xi/eta vectors in FP64,
+S in FP32 (1.6 GB, larger than L2; upper tiles kept), xi/eta vectors in FP32,
 affected-area pruning on.  One step applies a batch of 1,000 sequential unit
 updates (80% insertions with degree-biased endpoints, 20% deletions of
 uniform existing edges); each update runs Alg 1 (one cooperative launch for
@@ -40,7 +40,7 @@ SEED_GRAPH, SEED_STREAM = 2, 3
 METRIC = "edge updates/sec & HBM GB/s: fused rank-2K ΔS vs plain Inc-uSR at 1e-6 error"
 UNIT = "edge updates/s"
 WORKLOAD = ("power-law update stream: directed Chung-Lu n=20000, exponent 2.1, mean degree 10, "
-            "C=0.6, K=20, FP32 S, FP64 vectors, AFF pruning, 1000 sequential unit updates per step "
+            "C=0.6, K=20, FP32 S, FP32 vectors, AFF pruning, 1000 sequential unit updates per step "
             "(80% insert / 20% delete), rank-2(K+1) S changes applied by the tensor-core S pass")
 
 
@@ -541,7 +541,7 @@ def run_multi(args):
         timed = [draw(100 + t) for t in range(args.steps)]
         t0 = time.time()
         mh = P.MultiSimRank(graphs, C=MC, K=MK, s_precision=32, multi_launch=launch,
-                            init_tol=1e-9)
+                            init_tol=1e-9, tc=args.multi_tc)
         init_s = time.time() - t0
         packed = []
         for ups in warm + timed:
@@ -586,7 +586,8 @@ def run_multi(args):
         torch.cuda.empty_cache()
     one = res["batched_cuda_graph"]
     line = {"workload": f"many graphs: {G} directed Chung-Lu graphs (exponent 2.1), n~U[{MN_LO},{MN_HI}], "
-                        f"mean degree {MDEG}, C={MC}, K={MK}, FP32 S, 1-32 unit updates per graph per call",
+                        f"mean degree {MDEG}, C={MC}, K={MK}, FP32 S, 1-32 unit updates per graph per call, "
+                        f"S pass on " + ("tensor cores (TF32 split)" if args.multi_tc else "CUDA cores"),
             "sum_S_gb": float(sum(int(((n + 127) // 128 * 128)) ** 2 * 4 for n in sizes) / 1e9),
             "updates_per_call": int(counts.sum()), "steps": args.steps, "warmup": args.warmup,
             "forms": res,
@@ -733,6 +734,8 @@ def main():
     ap.add_argument("--column-n", type=int, default=CN, help="column workload: node count")
     ap.add_argument("--fd-edges", type=int, default=3, help="grad workload: edges checked by FD")
     ap.add_argument("--graphs", type=int, default=MG, help="multi workload: number of graphs")
+    ap.add_argument("--multi-tc", type=int, default=1,
+                    help="multi workload: S passes on the tensor cores (TF32 split)")
     ap.add_argument("--batch", type=int, default=64, help="batched workload: edges per batch")
     ap.add_argument("--per-edge-sample", type=int, default=256,
                     help="batched workload: per-edge updates timed per batch")

@@ -247,7 +247,8 @@ typedef struct simrank_multi* simrank_multi_t;
  * Every S starts at the fixed point of Eq. 1 (Jacobi sweeps on the GPU to
  * cfg->init_tol).  cfg: dense mode, SR_APPLY_UNIT, fused S update, defer
  * 0 or 1, n_capacity ignored (per graph instead), at most 65536 nodes per
- * graph.  Errors: SR_ERR_ARG, SR_ERR_EDGE_EXISTS, SR_ERR_OOM, SR_ERR_CUDA,
+ * graph.  With cfg->tc != 0 and FP32 S each round's S pass runs on the tensor
+ * cores (TF32 split), the operands of all graphs in one shared pair of arrays.  Errors: SR_ERR_ARG, SR_ERR_EDGE_EXISTS, SR_ERR_OOM, SR_ERR_CUDA,
  * SR_ERR_UNSUPPORTED; the message is simrank_last_error(NULL). */
 simrank_status simrank_multi_init(const simrank_config* cfg, int32_t ngraphs, const int32_t* n,
                                   const int32_t* n_capacity, const int64_t* edge_offsets,

@@ -1860,6 +1860,13 @@ struct simrank_multi {
   PatchOp* d_ops = nullptr;
   int64_t ops_cap = 0;
   int64_t* counters = nullptr;
+  // tensor-core S pass (cfg.tc != 0, FP32 S): all graphs' operands in one
+  // row-major pair [op_rows][kd], graph g from row row_off[g]
+  float* Ahi = nullptr;
+  float* Alo = nullptr;
+  int64_t op_rows = 0, kd = 0;
+  int rg = 0, max_tiles = 0;
+  std::vector<int64_t> row_off;
   // host staging of the last call (uploaded, then the stream is synchronised)
   std::vector<MultiGraphDesc> h_desc;
   std::vector<MultiStep> h_steps;
@@ -1910,7 +1917,8 @@ cudaError_t grow_dev(T** p, int64_t* cap, int64_t need) {
 void multi_free(simrank_multi* h) {
   if (h->exec) cudaGraphExecDestroy(h->exec);
   for (void* p : {(void*)h->d_desc, (void*)h->d_steps, (void*)h->d_count, (void*)h->d_ntiles,
-                  (void*)h->d_tiles, (void*)h->d_srcs, (void*)h->d_ops, (void*)h->counters})
+                  (void*)h->d_tiles, (void*)h->d_srcs, (void*)h->d_ops, (void*)h->counters,
+                  (void*)h->Ahi, (void*)h->Alo})
     if (p) cudaFree(p);
   for (auto& e : h->ev)
     for (cudaEvent_t x : e) cudaEventDestroy(x);
@@ -1932,14 +1940,28 @@ void multi_harvest(simrank_multi* h) {
   h->ev_used = 0;
 }
 
+// The S pass of launch l: on the tensor cores (operands packed from the
+// panels of this launch's graphs) or on the CUDA cores.
+void multi_s_pass(simrank_multi* h, int l, int64_t off, int cnt) {
+  const int sp = h->cfg.s_precision;
+  if (h->Ahi) {
+    launch_multi_pack_tc(h->d_desc, h->d_steps + off, h->d_count + l, cnt, h->max_tiles,
+                         h->cfg.K + 1, h->rg, h->Ahi, h->Alo, h->kd, h->st);
+    const long long lim = h->cfg.timeout_iters > 0 ? h->cfg.timeout_iters : (1ll << 24);
+    launch_s_update_tc_multi(h->Ahi, h->Alo, h->op_rows, h->kd, h->d_desc, h->d_tiles,
+                             h->d_ntiles + l, h->counters, h->num_sms, lim, h->st, 0);
+  } else {
+    launch_s_update_multi(sp, h->d_desc, h->d_tiles, h->d_ntiles + l, h->cfg.K + 1, h->counters,
+                          h->num_sms * (sp == 64 ? 1 : 2), h->st);
+  }
+}
+
 // Queues launch l: the prep of steps [off, off + cnt) and the S pass.
 void multi_enqueue(simrank_multi* h, int l, int64_t off, int cnt) {
   const int sp = h->cfg.s_precision;
-  const int sgrid = h->num_sms * (sp == 64 ? 1 : 2);
   launch_multi_prep(sp, h->d_desc, h->d_steps + off, h->d_count + l, cnt, h->d_srcs, h->d_ops,
                     h->cfg.C, h->cfg.K, h->cfg.aff ? 1 : 0, h->d_tiles, h->d_ntiles + l, h->st);
-  launch_s_update_multi(sp, h->d_desc, h->d_tiles, h->d_ntiles + l, h->cfg.K + 1, h->counters,
-                        sgrid, h->st);
+  multi_s_pass(h, l, off, cnt);
 }
 
 }  // namespace
@@ -2002,6 +2024,22 @@ simrank_status simrank_multi_init(const simrank_config* cfg_in, int32_t ngraphs,
       dev_alloc(&h->counters, (size_t)CNT_N) != cudaSuccess) {
     multi_free(h);
     return mfail(nullptr, SR_ERR_OOM, "cudaMalloc failed");
+  }
+  h->row_off.resize(ngraphs);
+  for (int g = 0; g < ngraphs; ++g) {
+    h->row_off[g] = h->op_rows;
+    h->op_rows += h->g[g]->n_pad;
+    h->max_tiles = std::max(h->max_tiles, h->g[g]->n_pad / PT);
+  }
+  if (cfg.tc && cfg.s_precision == 32) {
+    h->rg = (cfg.K + 1 + 31) / 32 * 32;
+    h->kd = 2 * (int64_t)h->rg;
+    if (h->op_rows >= ((int64_t)1 << 31) ||
+        dev_alloc(&h->Ahi, (size_t)(h->op_rows * h->kd)) != cudaSuccess ||
+        dev_alloc(&h->Alo, (size_t)(h->op_rows * h->kd)) != cudaSuccess) {
+      multi_free(h);
+      return mfail(nullptr, SR_ERR_OOM, "tensor-core operand allocation failed");
+    }
   }
   cudaMemsetAsync(h->counters, 0, CNT_N * sizeof(int64_t), h->st);
   h->h_desc.resize(ngraphs);
@@ -2091,6 +2129,7 @@ simrank_status simrank_multi_apply(simrank_multi_t h, const simrank_update* u,
     d.sJ = x->sJ;
     d.n = x->n_cur;
     d.upper = upper(x);
+    d.row_off = h->row_off[g];
   }
   // launch table
   h->h_steps.clear();
@@ -2166,8 +2205,7 @@ simrank_status simrank_multi_apply(simrank_multi_t h, const simrank_update* u,
                         h->d_srcs, h->d_ops, h->cfg.C, h->cfg.K, h->cfg.aff ? 1 : 0, h->d_tiles,
                         h->d_ntiles + l, h->st);
       MCUDA_TRY(h, cudaEventRecord(e[1], h->st));
-      launch_s_update_multi(sp, h->d_desc, h->d_tiles, h->d_ntiles + l, h->cfg.K + 1, h->counters,
-                            h->num_sms * (sp == 64 ? 1 : 2), h->st);
+      multi_s_pass(h, l, loff[l], h->h_count[l]);
       MCUDA_TRY(h, cudaEventRecord(e[2], h->st));
     }
   } else {

@@ -514,7 +514,40 @@ __global__ void __launch_bounds__(MT, 1)
   }
 }
 
+// Tensor-core operands of one 128-row tile of a graph of this round: row a
+// of the graph is row row_off + a of A_hi / A_lo, with xi terms in columns
+// [0, K1) and eta terms in [rg, rg + K1), split as x = hi + lo in TF32.
+__global__ void k_multi_pack_tc(const MultiGraphDesc* __restrict__ descs,
+                                const MultiStep* __restrict__ steps,
+                                const int* __restrict__ count, int K1, int rg,
+                                float* __restrict__ Ahi, float* __restrict__ Alo, int64_t kd) {
+  if ((int)blockIdx.x >= *count) return;
+  const MultiStep stp = steps[blockIdx.x];
+  const int T = blockIdx.y;
+  if (T >= (stp.n_after + PT - 1) / PT) return;
+  const MultiGraphDesc& q = descs[stp.g];
+  const float* __restrict__ P = static_cast<const float*>(q.P);
+  const int64_t row0 = q.row_off + (int64_t)T * PT;
+  for (int64_t e = threadIdx.x; e < (int64_t)PT * kd; e += blockDim.x) {
+    const int r = (int)(e / kd), c = (int)(e % kd);
+    const int h = c >= rg ? 1 : 0;
+    const int k = c - h * rg;
+    const float x = (k < K1) ? P[((int64_t)(T * 2 + h) * K1 + k) * PT + r] : 0.f;
+    const float hi = tf32_rne(x);
+    Ahi[(row0 + r) * kd + c] = hi;
+    Alo[(row0 + r) * kd + c] = tf32_rne(x - hi);
+  }
+}
+
 }  // namespace
+
+void launch_multi_pack_tc(const MultiGraphDesc* descs, const MultiStep* steps, const int* count,
+                          int grid, int max_tiles, int K1, int rg, float* Ahi, float* Alo,
+                          int64_t kd, cudaStream_t st) {
+  if (grid <= 0 || max_tiles <= 0) return;
+  k_multi_pack_tc<<<dim3(grid, max_tiles), 256, 0, st>>>(descs, steps, count, K1, rg, Ahi, Alo,
+                                                         kd);
+}
 
 void launch_multi_prep(int s_prec, const MultiGraphDesc* descs, const MultiStep* steps,
                        const int* count, int grid, const int32_t* srcs, const PatchOp* ops,

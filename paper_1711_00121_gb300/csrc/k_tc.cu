@@ -152,26 +152,69 @@ __device__ __forceinline__ bool ep_all(bool pred) {
 }
 __device__ __forceinline__ void ep_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
-// Tile pair t of the (band-ordered) list; false when the masks show no
-// active cross term there.  Every role of the CTA takes the same decision.
-__device__ __forceinline__ bool tile_active(const uint32_t* __restrict__ tiles, int t,
-                                            const uint64_t* __restrict__ mX,
-                                            const uint64_t* __restrict__ mE, int use_masks,
-                                            int& I, int& J) {
-  const uint32_t pr = tiles[t];
-  I = (int)(pr >> 16);
-  J = (int)(pr & 0xffffu);
-  return !use_masks || (((mX[I] & mE[J]) | (mE[I] & mX[J])) != 0ull);
-}
+// One tile pair of the pass: where its S lives, the rows of its two operand
+// tiles, and whether S[J, I] is kept as well.
+struct TcRef {
+  float* S;
+  int64_t ld;
+  int I, J, rowI, rowJ, n;
+  bool mirror;
+};
 
-template <bool F16>
+// Tile pairs of one graph: tiles[t] = I << 16 | J (band order); a pair is
+// skipped when use_masks and its mask words show no active cross term.
+struct TcOneGraph {
+  const uint32_t* tiles;
+  int nt;
+  const uint64_t* mX;
+  const uint64_t* mE;
+  int use_masks;
+  float* S;
+  int64_t ld;
+  int n, mirror;
+  __device__ __forceinline__ int count() const { return nt; }
+  __device__ __forceinline__ bool get(int t, TcRef& r) const {
+    const uint32_t pr = tiles[t];
+    r.I = (int)(pr >> 16);
+    r.J = (int)(pr & 0xffffu);
+    if (use_masks && ((mX[r.I] & mE[r.J]) | (mE[r.I] & mX[r.J])) == 0ull) return false;
+    r.S = S;
+    r.ld = ld;
+    r.rowI = r.I * TM;
+    r.rowJ = r.J * TN;
+    r.n = n;
+    r.mirror = mirror != 0;
+    return true;
+  }
+};
+
+// Tile pairs of many graphs: tiles[t] = g << 32 | I << 16 | J, *ntiles of
+// them; graph g's operand rows start at descs[g].row_off.
+struct TcManyGraphs {
+  const uint64_t* tiles;
+  const int* ntiles;
+  const MultiGraphDesc* d;
+  __device__ __forceinline__ int count() const { return *ntiles; }
+  __device__ __forceinline__ bool get(int t, TcRef& r) const {
+    const uint64_t e = tiles[t];
+    const MultiGraphDesc& q = d[(int)(e >> 32)];
+    r.I = (int)((e >> 16) & 0xffffu);
+    r.J = (int)(e & 0xffffu);
+    r.S = (float*)q.S;
+    r.ld = q.ld;
+    r.rowI = (int)q.row_off + r.I * TM;
+    r.rowJ = (int)q.row_off + r.J * TN;
+    r.n = q.n;
+    r.mirror = q.upper == 0;
+    return true;
+  }
+};
+
+template <bool F16, typename Src>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_s_update_tc(const __grid_constant__ CUtensorMap tm_hi,
-                  const __grid_constant__ CUtensorMap tm_lo, float* __restrict__ S, int64_t ld,
-                  const uint32_t* __restrict__ tiles, int nt, const uint64_t* __restrict__ mX,
-                  const uint64_t* __restrict__ mE, int use_masks, int nkb,
-                  long long wait_limit, int n, int mirror,
-                  unsigned long long* __restrict__ counters) {
+                  const __grid_constant__ CUtensorMap tm_lo, Src src, int nkb,
+                  long long wait_limit, unsigned long long* __restrict__ counters) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES];
   __shared__ __align__(8) uint64_t bar_acc_full[2], bar_acc_empty[2];
@@ -183,6 +226,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   float* sD = reinterpret_cast<float*>(smem_raw + (base - smem_u32(smem_raw)) +
                                        (size_t)STAGES * STAGE_BYTES);
   const int half = nkb / 2;  // B row = A row with its halves swapped
+  const int nt = src.count();
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
@@ -213,8 +257,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (lane == 0) {
       uint32_t it = 0;
       for (int t = blockIdx.x; t < nt && ok; t += gridDim.x) {
-        int I, J;
-        if (!tile_active(tiles, t, mX, mE, use_masks, I, J)) continue;
+        TcRef r;
+        if (!src.get(t, r)) continue;
         for (int kb = 0; kb < nkb && ok; ++kb, ++it) {
           const int s = it % STAGES;
           const uint32_t ph = (it / STAGES) & 1u;
@@ -227,10 +271,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           mbar_expect_tx(fb, STAGE_BYTES);
           const int kb_b = kb < half ? kb + half : kb - half;
           constexpr int KCH = F16 ? KB / 2 : KB / 4;  // elements of K per stage
-          tma_load_2d(st + 0 * OPB, &tm_hi, kb * KCH, I * TM, fb);
-          tma_load_2d(st + 1 * OPB, &tm_lo, kb * KCH, I * TM, fb);
-          tma_load_2d(st + 2 * OPB, &tm_hi, kb_b * KCH, J * TN, fb);
-          tma_load_2d(st + 3 * OPB, &tm_lo, kb_b * KCH, J * TN, fb);
+          tma_load_2d(st + 0 * OPB, &tm_hi, kb * KCH, r.rowI, fb);
+          tma_load_2d(st + 1 * OPB, &tm_lo, kb * KCH, r.rowI, fb);
+          tma_load_2d(st + 2 * OPB, &tm_hi, kb_b * KCH, r.rowJ, fb);
+          tma_load_2d(st + 3 * OPB, &tm_lo, kb_b * KCH, r.rowJ, fb);
         }
       }
       if (!ok) abort_flag = 1;
@@ -240,8 +284,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (lane == 0) {
       uint32_t it = 0, tl = 0;
       for (int t = blockIdx.x; t < nt && ok; t += gridDim.x) {
-        int I, J;
-        if (!tile_active(tiles, t, mX, mE, use_masks, I, J)) continue;
+        TcRef r;
+        if (!src.get(t, r)) continue;
         const uint32_t b = tl & 1u;
         const uint32_t eph = ((tl >> 1) & 1u) ^ 1u;
         ++tl;
@@ -287,8 +331,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint32_t tl = 0;
     unsigned long long my_tiles = 0, my_bytes = 0;
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
-      int I, J;
-      if (!tile_active(tiles, t, mX, mE, use_masks, I, J)) continue;
+      TcRef r;
+      if (!src.get(t, r)) continue;
+      float* __restrict__ S = r.S;
+      const int64_t ld = r.ld;
+      const int I = r.I, J = r.J, n = r.n;
+      const bool mirror = r.mirror;
       const uint32_t b = tl & 1u;
       const uint32_t tph = (tl >> 1) & 1u;
       ++tl;
@@ -409,10 +457,9 @@ bool make_map(CUtensorMap* m, const void* ptr, int64_t rows, int64_t kd, int eb)
 // A_hi / A_lo: row-major [n_rows][kd], FP32 holding TF32 values (f16 = 0) or
 // FP16 (f16 = 1); kd a multiple of 2 * (128 bytes / element size); the B
 // operand is A with its two column halves swapped.
-int launch_s_update_tc(float* S, int64_t ld, const void* Ahi, const void* Alo, int64_t n_rows,
-                       int64_t kd, const uint32_t* tiles, int nt, const uint64_t* mX,
-                       const uint64_t* mE, int use_masks, int n, int64_t* counters, int grid,
-                       long long wait_limit, cudaStream_t st, int upper, int f16) {
+template <typename Src>
+int launch_tc(const void* Ahi, const void* Alo, int64_t n_rows, int64_t kd, const Src& src,
+              int grid, long long wait_limit, cudaStream_t st, int f16, int64_t* counters) {
   const int eb = f16 ? 2 : 4;
   const int kch = KB / eb;
   if (kd % (2 * kch) != 0 || n_rows % TM != 0) return 1;
@@ -420,24 +467,36 @@ int launch_s_update_tc(float* S, int64_t ld, const void* Ahi, const void* Alo, i
   if (!make_map(&mhi, Ahi, n_rows, kd, eb)) return 2;
   if (!make_map(&mlo, Alo, n_rows, kd, eb)) return 2;
   const size_t smem = (size_t)STAGES * STAGE_BYTES + (size_t)TM * EP * 4 + 1024;
-  static bool attr[2] = {false, false};
-  const void* fn = f16 ? (const void*)k_s_update_tc<true> : (const void*)k_s_update_tc<false>;
-  if (!attr[f16 ? 1 : 0]) {
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr[f16 ? 1 : 0] = true;
-  }
+  const void* fn = f16 ? (const void*)k_s_update_tc<true, Src> : (const void*)k_s_update_tc<false, Src>;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return 1;
   const int nkb = (int)(kd / kch);
-  const int mirror = upper ? 0 : 1;
   unsigned long long* cnt = (unsigned long long*)counters;
   if (f16)
-    k_s_update_tc<true><<<grid, TC_THREADS, smem, st>>>(mhi, mlo, S, ld, tiles, nt, mX, mE,
-                                                        use_masks, nkb, wait_limit, n, mirror,
-                                                        cnt);
+    k_s_update_tc<true, Src><<<grid, TC_THREADS, smem, st>>>(mhi, mlo, src, nkb, wait_limit, cnt);
   else
-    k_s_update_tc<false><<<grid, TC_THREADS, smem, st>>>(mhi, mlo, S, ld, tiles, nt, mX, mE,
-                                                         use_masks, nkb, wait_limit, n, mirror,
-                                                         cnt);
+    k_s_update_tc<false, Src><<<grid, TC_THREADS, smem, st>>>(mhi, mlo, src, nkb, wait_limit, cnt);
   return 0;
+}
+
+// A_hi / A_lo: row-major [n_rows][kd], FP32 holding TF32 values (f16 = 0) or
+// FP16 (f16 = 1); kd a multiple of 2 * (128 bytes / element size); the B
+// operand is A with its two column halves swapped.
+int launch_s_update_tc(float* S, int64_t ld, const void* Ahi, const void* Alo, int64_t n_rows,
+                       int64_t kd, const uint32_t* tiles, int nt, const uint64_t* mX,
+                       const uint64_t* mE, int use_masks, int n, int64_t* counters, int grid,
+                       long long wait_limit, cudaStream_t st, int upper, int f16) {
+  TcOneGraph src{tiles, nt, mX, mE, use_masks, S, ld, n, upper ? 0 : 1};
+  return launch_tc(Ahi, Alo, n_rows, kd, src, grid, wait_limit, st, f16, counters);
+}
+
+int launch_s_update_tc_multi(const void* Ahi, const void* Alo, int64_t rows, int64_t kd,
+                             const MultiGraphDesc* descs, const uint64_t* tiles, const int* ntiles,
+                             int64_t* counters, int grid, long long wait_limit, cudaStream_t st,
+                             int f16) {
+  TcManyGraphs src{tiles, ntiles, descs};
+  return launch_tc(Ahi, Alo, rows, kd, src, grid, wait_limit, st, f16, counters);
 }
 
 }  // namespace sr

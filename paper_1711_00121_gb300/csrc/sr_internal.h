@@ -27,6 +27,16 @@ __device__ __forceinline__ T s_at(const T* S, int64_t ld, int64_t r, int64_t c, 
 }
 #endif
 
+#ifdef __CUDACC__
+// x rounded to TF32 (10 explicit mantissa bits), to nearest, ties to even
+__device__ __forceinline__ float tf32_rne(float x) {
+  uint32_t u = __float_as_uint(x);
+  if ((u & 0x7f800000u) == 0x7f800000u) return x;  // inf / nan unchanged
+  u += 0x0fffu + ((u >> 13) & 1u);
+  return __uint_as_float(u & 0xffffe000u);
+}
+#endif
+
 inline int64_t panel_index(int64_t node, int which, int k, int K1) {
   return (((node / PT) * 2 + which) * (int64_t)K1 + k) * PT + (node % PT);
 }
@@ -182,6 +192,7 @@ struct MultiGraphDesc {
   void* sJ;
   int n;      // current node count (byte counters)
   int upper;  // 1: only tiles on or above the block diagonal are kept
+  int64_t row_off;  // first row of this graph in the shared tensor-core operands
 };
 // One rank-one update of graph g in a round: sources srcs[src_off ..
 // src_off + delta) into sink j, op = +1/-1, old in-degree d_j, patch ops
@@ -269,6 +280,19 @@ int launch_s_update_tc(float* S, int64_t ld, const void* Ahi, const void* Alo, i
                        int64_t kd, const uint32_t* tiles, int nt, const uint64_t* mX,
                        const uint64_t* mE, int use_masks, int n, int64_t* counters, int grid,
                        long long wait_limit, cudaStream_t st, int upper = 0, int f16 = 0);
+// The same pass over the tile pairs (g << 32 | I << 16 | J) of many graphs,
+// *ntiles of them; graph g's operand rows start at descs[g].row_off of the
+// shared operands A_hi / A_lo ([rows][kd]).
+int launch_s_update_tc_multi(const void* Ahi, const void* Alo, int64_t rows, int64_t kd,
+                             const MultiGraphDesc* descs, const uint64_t* tiles, const int* ntiles,
+                             int64_t* counters, int grid, long long wait_limit, cudaStream_t st,
+                             int f16);
+// Tensor-core operands of the graphs of steps[0 .. *count) from their
+// tile-blocked panels (K1 terms, TF32 split, rg columns per half): rows
+// descs[g].row_off + a for a < nT_g * 128.  max_tiles bounds nT_g.
+void launch_multi_pack_tc(const MultiGraphDesc* descs, const MultiStep* steps, const int* count,
+                          int grid, int max_tiles, int K1, int rg, float* Ahi, float* Alo,
+                          int64_t kd, cudaStream_t st);
 // FP16 operands (row-major [n_rows][kd] hi/lo) from tile-blocked FP32 pending
 // panels, each term scaled by 2^(+-e_q) (exact); maxes: 2 * nterms scratch uints.
 void launch_pack_f16_tiles(const float* Pp, int GK1, int nterms, int rg, int n_rows,

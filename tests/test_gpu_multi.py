@@ -68,12 +68,13 @@ def streams(graphs, seed, max_len):
     return ups
 
 
-@pytest.mark.parametrize("prec,launch", [(64, 0), (64, 1), (32, 0), (32, 1)])
-def test_multi_streams_match_oracle(P, prec, launch):
+@pytest.mark.parametrize("prec,launch,tc", [(64, 0, 0), (64, 1, 0), (32, 0, 0), (32, 1, 0),
+                                            (32, 0, 1), (32, 1, 1)])
+def test_multi_streams_match_oracle(P, prec, launch, tc):
     C, K = 0.6, 10
     graphs = make_graphs(9, 21)
     ups = streams(graphs, 22, 7)
-    mh = P.MultiSimRank(graphs, C=C, K=K, s_precision=prec, multi_launch=launch)
+    mh = P.MultiSimRank(graphs, C=C, K=K, s_precision=prec, multi_launch=launch, tc=tc)
     mh.apply_updates(ups)
     mh.sync()
     tol = TOL64 if prec == 64 else TOL32
