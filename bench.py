@@ -441,6 +441,9 @@ def run_batched(args):
         kw = dict(C=BC, K=BK, s_precision=32, n_capacity=cap, profile=1, stream=stream.cuda_stream)
         if form == "one_shot_tc":
             kw.update(apply=P.APPLY_ONE_SHOT, tc=1)
+        else:
+            # each edge its own rank-2(K+1) S pass, on the tensor cores (FP16 split)
+            kw.update(apply=P.APPLY_UNIT, defer=0, tc=2)
         sr = P.SimRank(BN, s, d, **kw)
         with torch.cuda.stream(stream):
             for t in range(args.warmup):
