@@ -437,12 +437,15 @@ def run_batched(args):
     stream = torch.cuda.Stream()
     res = {}
     per_edge_sample = min(b, args.per_edge_sample)
-    for form in ("one_shot_tc", "per_edge"):
+    for form in ("one_shot_tc", "per_edge", "per_edge_tc"):
         kw = dict(C=BC, K=BK, s_precision=32, n_capacity=cap, profile=1, stream=stream.cuda_stream)
         if form == "one_shot_tc":
             kw.update(apply=P.APPLY_ONE_SHOT, tc=1)
+        elif form == "per_edge":
+            # the plain per-edge form: each edge its own fused S pass on the CUDA cores
+            kw.update(apply=P.APPLY_UNIT, defer=0, tc=0)
         else:
-            # each edge its own rank-2(K+1) S pass, on the tensor cores (FP16 split)
+            # each edge its own S pass on the tensor cores (FP16 split)
             kw.update(apply=P.APPLY_UNIT, defer=0, tc=2)
         sr = P.SimRank(BN, s, d, **kw)
         with torch.cuda.stream(stream):
@@ -450,7 +453,7 @@ def run_batched(args):
                 sr.apply_updates(batches[t])
             sr.sync()
             st0 = sr.stats()
-            sampled = form == "per_edge" and per_edge_sample < b
+            sampled = form.startswith("per_edge") and per_edge_sample < b
             pairs = []
             n_upd = 0
             with ClockSampler(0) as clk:
@@ -501,7 +504,8 @@ def run_batched(args):
     line = {"workload": f"batched: Chung-Lu n={BN} m={BM} exponent {BGAMMA}, C={BC}, K={BK}, "
                         f"FP32 S, batches of b={b} with 10% new nodes",
             "batch": b, "steps": args.steps, "warmup": args.warmup, "forms": res,
-            "speedup_one_shot_vs_per_edge": one["updates_per_s"] / res["per_edge"]["updates_per_s"]}
+            "speedup_one_shot_vs_per_edge": one["updates_per_s"] / res["per_edge"]["updates_per_s"],
+            "speedup_one_shot_vs_per_edge_tc": one["updates_per_s"] / res["per_edge_tc"]["updates_per_s"]}
     print(json.dumps(line), flush=True)
 
 

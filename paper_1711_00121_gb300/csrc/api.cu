@@ -1949,7 +1949,8 @@ void multi_s_pass(simrank_multi* h, int l, int64_t off, int cnt) {
                          h->cfg.K + 1, h->rg, h->Ahi, h->Alo, h->kd, h->st);
     const long long lim = h->cfg.timeout_iters > 0 ? h->cfg.timeout_iters : (1ll << 24);
     launch_s_update_tc_multi(h->Ahi, h->Alo, h->op_rows, h->kd, h->d_desc, h->d_tiles,
-                             h->d_ntiles + l, h->counters, h->num_sms, lim, h->st, 0);
+                             h->d_ntiles + l, h->counters, h->num_sms, lim, h->st, 0,
+                             h->cfg.upper_only ? 1 : 0);
   } else {
     launch_s_update_multi(sp, h->d_desc, h->d_tiles, h->d_ntiles + l, h->cfg.K + 1, h->counters,
                           h->num_sms * (sp == 64 ? 1 : 2), h->st);

@@ -255,45 +255,6 @@ __device__ __forceinline__ void item_gather(const PrepItem& it, const int* __res
   seg_emit<V>(r_last, la, lb, emit);
 }
 
-// gamma_a (Thm 3 insert, Thm 9 delete, Table 2) from y = the sum of sI over
-// the NEW in-neighbours of a, len = the new in-degree of a and sJa = S[j, a];
-// row j in FP64 with lambda (Eq. 29b) and w_j on its old in-list (the new
-// sum - op * S_II).
-template <typename V>
-__device__ __forceinline__ V gamma_of(const PrepParams& p, int64_t a, V y, int len, V sJa,
-                                      double S_II) {
-  const double dl = (double)p.delta;
-  if (a == p.j) {
-    const double S_jj = (double)sJa;
-    const double C = p.C;
-    const double wj =
-        (p.d_j > 0) ? ((double)y - (double)p.op * S_II) / (dl * (double)p.d_j) : 0.0;
-    const double lam = S_II / (dl * dl) + S_jj / C - 2.0 * wj - 1.0 / C + 1.0;
-    double gd;
-    if (p.op > 0) {
-      if (p.d_j == 0) {
-        gd = wj + S_II / (2.0 * dl * dl);
-      } else {
-        const double dd = (double)p.d_j + dl;
-        gd = (dl / dd) * (wj - S_jj / C + lam * dl / (2.0 * dd) + 1.0 / C - 1.0);
-      }
-    } else {
-      if (p.d_j == p.delta) {
-        gd = -wj + S_II / (2.0 * dl * dl);
-      } else {
-        const double dd = (double)p.d_j - dl;
-        gd = (dl / dd) * (S_jj / C - wj + lam * dl / (2.0 * dd) - 1.0 / C + 1.0);
-      }
-    }
-    return (V)gd;
-  }
-  const V Cv = (V)p.C;
-  const V w = (len > 0) ? y / ((V)p.delta * (V)len) : V(0);
-  if (p.op > 0)
-    return (p.d_j == 0) ? w : ((V)p.delta / (V)(p.d_j + p.delta)) * (w - sJa / Cv);
-  return (p.d_j == p.delta) ? -w : ((V)p.delta / (V)(p.d_j - p.delta)) * (sJa / Cv - w);
-}
-
 __device__ void prep_patch(const PatchOp* __restrict__ ops, int64_t begin, int64_t end,
                            const DevAdj& in, const DevAdj& out) {
   for (int64_t o = begin; o < end; ++o) {
@@ -481,20 +442,56 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
     alive = prep_barrier(p.bar, ++nb * G, p.limit, &s_ok);
   }
 
-  // ---- phase 1b: gamma of the owned rows into panel column 0 and the k = 0
-  // mask bits.  W[0] keeps the sums y (step 0 forms (xi_0, eta_0) from them
-  // as it gathers), so no barrier is needed before step 0.
-  double S_II = 0.0;
+  // ---- phase 1b: gamma per row (tiles round-robin); W[0] = (xi_0, eta_0)
   if (alive) {
-    for (int u = 0; u < p.delta; ++u) S_II += (double)__ldcg(sI + p.I[u]);
     for (int t = 0; t < mt; ++t) {
       const int T = blockIdx.x + t * G;
       if (T >= nT) break;
       int pe = 0;
       if (tid < PT) {
         const int64_t a = (int64_t)T * PT + tid;
-        const V g = gamma_of<V>(p, a, __ldcg(&W[a].x), __ldcg(p.in.len + a), __ldcg(sJ + a), S_II);
-        P[pidx(a, 0, koff)] = (TS)((a == p.j) ? Cv : V(0));
+        const int len = __ldcg(p.in.len + a);
+        const V y = __ldcg(&W[a].x);
+        const double dl = (double)p.delta;
+        V g;
+        if (a == p.j) {
+          // row j: lambda (Eq. 29b) and w_j on the old row j, in FP64
+          double S_II = 0.0;
+          for (int u = 0; u < p.delta; ++u) S_II += (double)__ldcg(sI + p.I[u]);
+          const double S_jj = (double)__ldcg(sJ + p.j);
+          const double C = p.C;
+          const double wj =
+              (p.d_j > 0) ? ((double)y - (double)p.op * S_II) / (dl * (double)p.d_j) : 0.0;
+          const double lam = S_II / (dl * dl) + S_jj / C - 2.0 * wj - 1.0 / C + 1.0;
+          double gd;
+          if (p.op > 0) {
+            if (p.d_j == 0) {
+              gd = wj + S_II / (2.0 * dl * dl);
+            } else {
+              const double dd = (double)p.d_j + dl;
+              gd = (dl / dd) * (wj - S_jj / C + lam * dl / (2.0 * dd) + 1.0 / C - 1.0);
+            }
+          } else {
+            if (p.d_j == p.delta) {
+              gd = -wj + S_II / (2.0 * dl * dl);
+            } else {
+              const double dd = (double)p.d_j - dl;
+              gd = (dl / dd) * (S_jj / C - wj + lam * dl / (2.0 * dd) - 1.0 / C + 1.0);
+            }
+          }
+          g = (V)gd;
+        } else {
+          const V w = (len > 0) ? y / ((V)p.delta * (V)len) : V(0);
+          const V sJa = __ldcg(sJ + a);
+          if (p.op > 0) {
+            g = (p.d_j == 0) ? w : ((V)p.delta / (V)(p.d_j + p.delta)) * (w - sJa / Cv);
+          } else {
+            g = (p.d_j == p.delta) ? -w : ((V)p.delta / (V)(p.d_j - p.delta)) * (sJa / Cv - w);
+          }
+        }
+        const V x0 = (a == p.j) ? Cv : V(0);
+        W[a] = V2<V>{x0, g};
+        P[pidx(a, 0, koff)] = (TS)x0;
         P[pidx(a, 1, koff)] = (TS)g;
         pe = (g != V(0));
       }
@@ -504,6 +501,7 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
         mk[t][1] = any_e ? 1ull : 0ull;
       }
     }
+    if (K > 0) alive = prep_barrier(p.bar, ++nb * G, p.limit, &s_ok);
   }
 
   // ---- phase 2: K steps
@@ -514,20 +512,11 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
       PrepItem& it = items[min(u, MAXI)];
       if (u >= MAXI) item_locate(p.in, ioff, nT, blockIdx.x + u * G, p.item, it);
       const int64_t rb = (int64_t)it.T * PT;
-      const auto emit = [&](int r, V a, V b) {
-        const V inv = V(1) / (V)it.len[r];
-        red_add2(Wn + rb + r, Cv * a * inv, b * inv);
-      };
-      if (k == 0)
-        item_gather<V>(it, cc, p.in.col,
-                       [&](int b) {
-                         const V g = gamma_of<V>(p, b, __ldcg(&W[b].x), __ldcg(p.in.len + b),
-                                                 __ldcg(sJ + b), S_II);
-                         return V2<V>{(b == p.j) ? Cv : V(0), g};
-                       },
-                       emit);
-      else
-        item_gather<V>(it, cc, p.in.col, [&](int b) { return ld_v2(Wk + b); }, emit);
+      item_gather<V>(it, cc, p.in.col, [&](int b) { return ld_v2(Wk + b); },
+                     [&](int r, V a, V b) {
+                       const V inv = V(1) / (V)it.len[r];
+                       red_add2(Wn + rb + r, Cv * a * inv, b * inv);
+                     });
       __syncthreads();
     }
     alive = prep_barrier(p.bar, ++nb * G, p.limit, &s_ok);

@@ -29,7 +29,8 @@ namespace {
 constexpr int TM = 128;             // rows of an S tile (M)
 constexpr int TN = 128;             // columns of an S tile (N)
 constexpr int KB = 128;             // bytes of K per stage (one 128-byte swizzle row)
-constexpr int STAGES = 2;
+constexpr int STAGES_STAGED = 2;  // stages when the epilogue stages D in shared memory
+constexpr int STAGES_DIRECT = 3;  // stages when it adds D to S straight from registers
 constexpr int OPB = TM * KB;        // bytes of one operand box: 16 KB
 constexpr int STAGE_BYTES = 4 * OPB;
 constexpr int TC_THREADS = 320;       // 10 warps: TMA, MMA, 8 epilogue
@@ -210,11 +211,17 @@ struct TcManyGraphs {
   }
 };
 
-template <bool F16, typename Src>
+// MIRROR: both triangles of S are kept, so D is also added to S[J, I]; the
+// epilogue stages D in shared memory for the transposed write (2 TMA stages).
+// Otherwise each epilogue thread adds its row's 64 values of D to S straight
+// from the TMEM load, with those 64 S values fetched before the accumulator
+// is ready (3 TMA stages).
+template <bool F16, bool MIRROR, typename Src>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_s_update_tc(const __grid_constant__ CUtensorMap tm_hi,
                   const __grid_constant__ CUtensorMap tm_lo, Src src, int nkb,
                   long long wait_limit, unsigned long long* __restrict__ counters) {
+  constexpr int STAGES = MIRROR ? STAGES_STAGED : STAGES_DIRECT;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES];
   __shared__ __align__(8) uint64_t bar_acc_full[2], bar_acc_empty[2];
@@ -336,10 +343,43 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       float* __restrict__ S = r.S;
       const int64_t ld = r.ld;
       const int I = r.I, J = r.J, n = r.n;
-      const bool mirror = r.mirror;
+      const bool mirror = MIRROR;
       const uint32_t b = tl & 1u;
       const uint32_t tph = (tl >> 1) & 1u;
       ++tl;
+      const int row = quarter * 32 + lane;
+      if (!MIRROR) {
+        // this thread's 64 values of S[I, J] (row `row`, columns chalf ..),
+        // fetched while the tensor cores still work on the tile
+        float* srow = S + (int64_t)(I * TM + row) * ld + (int64_t)J * TN + chalf;
+        float4 sv[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) sv[q] = *reinterpret_cast<const float4*>(srow + 4 * q);
+        const bool got = mbar_wait(smem_u32(&bar_acc_full[b]), tph, wait_limit, &abort_flag);
+        if (!ep_all(got)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float v[32];
+          tmem_ld32(tmem + b * (uint32_t)TN + ((uint32_t)(quarter * 32) << 16) +
+                        (uint32_t)(chalf + 32 * h),
+                    v);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            sv[8 * h + q].x += v[4 * q + 0];
+            sv[8 * h + q].y += v[4 * q + 1];
+            sv[8 * h + q].z += v[4 * q + 2];
+            sv[8 * h + q].w += v[4 * q + 3];
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(smem_u32(&bar_acc_empty[b]));  // the MMA warp may refill this accumulator
+#pragma unroll
+        for (int q = 0; q < 16; ++q) *reinterpret_cast<float4*>(srow + 4 * q) = sv[q];
+      } else {
       const bool got = mbar_wait(smem_u32(&bar_acc_full[b]), tph, wait_limit, &abort_flag);
       if (!ep_all(got)) {
         ok = false;
@@ -347,7 +387,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       // accumulator -> shared tile (row = TMEM lane)
-      const int row = quarter * 32 + lane;
 #pragma unroll 1
       for (int c0 = chalf; c0 < chalf + 64; c0 += 32) {
         float v[32];
@@ -378,7 +417,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           *reinterpret_cast<float4*>(S + (int64_t)(I * TM + r) * ld + (int64_t)J * TN + lane * 4) = v[q];
         }
       }
-      if (I != J && mirror) {
+      if (I != J) {
         // S[J, I] += D^T
         float4 v[NQ];
 #pragma unroll
@@ -397,6 +436,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
       }
       ep_sync();  // the shared tile is free for the next accumulator
+      }
       if (et == 0) {
         const long long vr = max(0, min(TM, n - I * TM)), vc = max(0, min(TN, n - J * TN));
         my_tiles += 1;
@@ -457,27 +497,36 @@ bool make_map(CUtensorMap* m, const void* ptr, int64_t rows, int64_t kd, int eb)
 // A_hi / A_lo: row-major [n_rows][kd], FP32 holding TF32 values (f16 = 0) or
 // FP16 (f16 = 1); kd a multiple of 2 * (128 bytes / element size); the B
 // operand is A with its two column halves swapped.
+template <bool F16, bool MIRROR, typename Src>
+int launch_tc_t(const CUtensorMap& mhi, const CUtensorMap& mlo, const Src& src, int nkb, int grid,
+                long long wait_limit, cudaStream_t st, int64_t* counters) {
+  const size_t smem = (size_t)(MIRROR ? STAGES_STAGED : STAGES_DIRECT) * STAGE_BYTES +
+                      (MIRROR ? (size_t)TM * EP * 4 : 0) + 1024;
+  const void* fn = (const void*)k_s_update_tc<F16, MIRROR, Src>;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return 1;
+  k_s_update_tc<F16, MIRROR, Src><<<grid, TC_THREADS, smem, st>>>(
+      mhi, mlo, src, nkb, wait_limit, (unsigned long long*)counters);
+  return 0;
+}
+
 template <typename Src>
 int launch_tc(const void* Ahi, const void* Alo, int64_t n_rows, int64_t kd, const Src& src,
-              int grid, long long wait_limit, cudaStream_t st, int f16, int64_t* counters) {
+              int grid, long long wait_limit, cudaStream_t st, int f16, int mirror,
+              int64_t* counters) {
   const int eb = f16 ? 2 : 4;
   const int kch = KB / eb;
   if (kd % (2 * kch) != 0 || n_rows % TM != 0) return 1;
   CUtensorMap mhi, mlo;
   if (!make_map(&mhi, Ahi, n_rows, kd, eb)) return 2;
   if (!make_map(&mlo, Alo, n_rows, kd, eb)) return 2;
-  const size_t smem = (size_t)STAGES * STAGE_BYTES + (size_t)TM * EP * 4 + 1024;
-  const void* fn = f16 ? (const void*)k_s_update_tc<true, Src> : (const void*)k_s_update_tc<false, Src>;
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess)
-    return 1;
   const int nkb = (int)(kd / kch);
-  unsigned long long* cnt = (unsigned long long*)counters;
   if (f16)
-    k_s_update_tc<true, Src><<<grid, TC_THREADS, smem, st>>>(mhi, mlo, src, nkb, wait_limit, cnt);
-  else
-    k_s_update_tc<false, Src><<<grid, TC_THREADS, smem, st>>>(mhi, mlo, src, nkb, wait_limit, cnt);
-  return 0;
+    return mirror ? launch_tc_t<true, true>(mhi, mlo, src, nkb, grid, wait_limit, st, counters)
+                  : launch_tc_t<true, false>(mhi, mlo, src, nkb, grid, wait_limit, st, counters);
+  return mirror ? launch_tc_t<false, true>(mhi, mlo, src, nkb, grid, wait_limit, st, counters)
+                : launch_tc_t<false, false>(mhi, mlo, src, nkb, grid, wait_limit, st, counters);
 }
 
 // A_hi / A_lo: row-major [n_rows][kd], FP32 holding TF32 values (f16 = 0) or
@@ -488,15 +537,15 @@ int launch_s_update_tc(float* S, int64_t ld, const void* Ahi, const void* Alo, i
                        const uint64_t* mE, int use_masks, int n, int64_t* counters, int grid,
                        long long wait_limit, cudaStream_t st, int upper, int f16) {
   TcOneGraph src{tiles, nt, mX, mE, use_masks, S, ld, n, upper ? 0 : 1};
-  return launch_tc(Ahi, Alo, n_rows, kd, src, grid, wait_limit, st, f16, counters);
+  return launch_tc(Ahi, Alo, n_rows, kd, src, grid, wait_limit, st, f16, upper ? 0 : 1, counters);
 }
 
 int launch_s_update_tc_multi(const void* Ahi, const void* Alo, int64_t rows, int64_t kd,
                              const MultiGraphDesc* descs, const uint64_t* tiles, const int* ntiles,
                              int64_t* counters, int grid, long long wait_limit, cudaStream_t st,
-                             int f16) {
+                             int f16, int upper) {
   TcManyGraphs src{tiles, ntiles, descs};
-  return launch_tc(Ahi, Alo, rows, kd, src, grid, wait_limit, st, f16, counters);
+  return launch_tc(Ahi, Alo, rows, kd, src, grid, wait_limit, st, f16, upper ? 0 : 1, counters);
 }
 
 }  // namespace sr

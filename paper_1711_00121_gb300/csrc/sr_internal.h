@@ -286,7 +286,7 @@ int launch_s_update_tc(float* S, int64_t ld, const void* Ahi, const void* Alo, i
 int launch_s_update_tc_multi(const void* Ahi, const void* Alo, int64_t rows, int64_t kd,
                              const MultiGraphDesc* descs, const uint64_t* tiles, const int* ntiles,
                              int64_t* counters, int grid, long long wait_limit, cudaStream_t st,
-                             int f16);
+                             int f16, int upper);
 // Tensor-core operands of the graphs of steps[0 .. *count) from their
 // tile-blocked panels (K1 terms, TF32 split, rg columns per half): rows
 // descs[g].row_off + a for a < nT_g * 128.  max_tiles bounds nT_g.
