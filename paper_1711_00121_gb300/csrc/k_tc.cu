@@ -211,17 +211,19 @@ struct TcManyGraphs {
   }
 };
 
-// MIRROR: both triangles of S are kept, so D is also added to S[J, I]; the
-// epilogue stages D in shared memory for the transposed write (2 TMA stages).
-// Otherwise each epilogue thread adds its row's 64 values of D to S straight
-// from the TMEM load, with those 64 S values fetched before the accumulator
-// is ready (3 TMA stages).
-template <bool F16, bool MIRROR, typename Src>
+// STAGED: the epilogue copies D into shared memory and streams S with
+// coalesced 512-byte row segments (2 TMA stages); it also adds D^T to S[J, I]
+// when both triangles are kept (MIRROR).  Otherwise (wide operands: the pass
+// is bound by the tensor cores) each epilogue thread adds its row's 64 values
+// of D to S straight from the TMEM load, with those S values fetched before
+// the accumulator is ready, and the TMA ring has 3 stages.
+template <bool F16, bool STAGED, bool MIRROR, typename Src>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_s_update_tc(const __grid_constant__ CUtensorMap tm_hi,
                   const __grid_constant__ CUtensorMap tm_lo, Src src, int nkb,
                   long long wait_limit, unsigned long long* __restrict__ counters) {
-  constexpr int STAGES = MIRROR ? STAGES_STAGED : STAGES_DIRECT;
+  static_assert(STAGED || !MIRROR, "the transposed write needs the staged epilogue");
+  constexpr int STAGES = STAGED ? STAGES_STAGED : STAGES_DIRECT;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES];
   __shared__ __align__(8) uint64_t bar_acc_full[2], bar_acc_empty[2];
@@ -348,7 +350,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const uint32_t tph = (tl >> 1) & 1u;
       ++tl;
       const int row = quarter * 32 + lane;
-      if (!MIRROR) {
+      if (!STAGED) {
         // this thread's 64 values of S[I, J] (row `row`, columns chalf ..),
         // fetched while the tensor cores still work on the tile
         float* srow = S + (int64_t)(I * TM + row) * ld + (int64_t)J * TN + chalf;
@@ -417,7 +419,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           *reinterpret_cast<float4*>(S + (int64_t)(I * TM + r) * ld + (int64_t)J * TN + lane * 4) = v[q];
         }
       }
-      if (I != J) {
+      if (MIRROR && I != J) {
         // S[J, I] += D^T
         float4 v[NQ];
 #pragma unroll
@@ -497,18 +499,34 @@ bool make_map(CUtensorMap* m, const void* ptr, int64_t rows, int64_t kd, int eb)
 // A_hi / A_lo: row-major [n_rows][kd], FP32 holding TF32 values (f16 = 0) or
 // FP16 (f16 = 1); kd a multiple of 2 * (128 bytes / element size); the B
 // operand is A with its two column halves swapped.
-template <bool F16, bool MIRROR, typename Src>
+template <bool F16, bool STAGED, bool MIRROR, typename Src>
 int launch_tc_t(const CUtensorMap& mhi, const CUtensorMap& mlo, const Src& src, int nkb, int grid,
                 long long wait_limit, cudaStream_t st, int64_t* counters) {
-  const size_t smem = (size_t)(MIRROR ? STAGES_STAGED : STAGES_DIRECT) * STAGE_BYTES +
-                      (MIRROR ? (size_t)TM * EP * 4 : 0) + 1024;
-  const void* fn = (const void*)k_s_update_tc<F16, MIRROR, Src>;
+  const size_t smem = (size_t)(STAGED ? STAGES_STAGED : STAGES_DIRECT) * STAGE_BYTES +
+                      (STAGED ? (size_t)TM * EP * 4 : 0) + 1024;
+  const void* fn = (const void*)k_s_update_tc<F16, STAGED, MIRROR, Src>;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 1;
-  k_s_update_tc<F16, MIRROR, Src><<<grid, TC_THREADS, smem, st>>>(
+  k_s_update_tc<F16, STAGED, MIRROR, Src><<<grid, TC_THREADS, smem, st>>>(
       mhi, mlo, src, nkb, wait_limit, (unsigned long long*)counters);
   return 0;
+}
+
+// Wide operands (at least 1 KB of K per row) make the pass tensor-bound:
+// register epilogue and 3 stages; narrow ones leave it bound by the S stream:
+// staged, coalesced epilogue.
+constexpr int64_t WIDE_K_BYTES = 1024;
+
+template <bool F16, typename Src>
+int launch_tc_f(const CUtensorMap& mhi, const CUtensorMap& mlo, const Src& src, int nkb,
+                int64_t kd_bytes, int grid, long long wait_limit, cudaStream_t st, int mirror,
+                int64_t* counters) {
+  if (mirror)
+    return launch_tc_t<F16, true, true>(mhi, mlo, src, nkb, grid, wait_limit, st, counters);
+  if (kd_bytes >= WIDE_K_BYTES)
+    return launch_tc_t<F16, false, false>(mhi, mlo, src, nkb, grid, wait_limit, st, counters);
+  return launch_tc_t<F16, true, false>(mhi, mlo, src, nkb, grid, wait_limit, st, counters);
 }
 
 template <typename Src>
@@ -523,10 +541,8 @@ int launch_tc(const void* Ahi, const void* Alo, int64_t n_rows, int64_t kd, cons
   if (!make_map(&mlo, Alo, n_rows, kd, eb)) return 2;
   const int nkb = (int)(kd / kch);
   if (f16)
-    return mirror ? launch_tc_t<true, true>(mhi, mlo, src, nkb, grid, wait_limit, st, counters)
-                  : launch_tc_t<true, false>(mhi, mlo, src, nkb, grid, wait_limit, st, counters);
-  return mirror ? launch_tc_t<false, true>(mhi, mlo, src, nkb, grid, wait_limit, st, counters)
-                : launch_tc_t<false, false>(mhi, mlo, src, nkb, grid, wait_limit, st, counters);
+    return launch_tc_f<true>(mhi, mlo, src, nkb, kd * eb, grid, wait_limit, st, mirror, counters);
+  return launch_tc_f<false>(mhi, mlo, src, nkb, kd * eb, grid, wait_limit, st, mirror, counters);
 }
 
 // A_hi / A_lo: row-major [n_rows][kd], FP32 holding TF32 values (f16 = 0) or
