@@ -192,14 +192,17 @@ __global__ void k_pack_tc_tiles(const float* __restrict__ Pp, int GK1, int nterm
 }
 
 // Largest |value| of each pending term: maxes[which][q] over all rows (the
-// bits of a non-negative float order like the float), one warp per term.
+// bits of a non-negative float order like the float).  Block (T, which, z)
+// takes terms z * 32 + [0, 32) of tile T, one warp per term at a time.
+constexpr int TM_TERMS = 32;
 __global__ void k_term_max(const float* __restrict__ Pp, int GK1, int nterms,
                            unsigned int* __restrict__ maxes) {
   const int T = blockIdx.x, which = blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int q = warp; q < nterms; q += blockDim.x >> 5) {
-    const float4 v = reinterpret_cast<const float4*>(
-        Pp + (((int64_t)T * 2 + which) * GK1 + q) * PT)[lane];
+  const int q1 = min(nterms, (int)(blockIdx.z + 1) * TM_TERMS);
+  for (int q = blockIdx.z * TM_TERMS + warp; q < q1; q += blockDim.x >> 5) {
+    const float4 v = __ldcg(reinterpret_cast<const float4*>(
+        Pp + (((int64_t)T * 2 + which) * GK1 + q) * PT) + lane);
     float m = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -213,26 +216,50 @@ __global__ void k_term_max(const float* __restrict__ Pp, int GK1, int nterms,
 // xi_q eta_q^T is unchanged by the scaling (powers of two are exact) and both
 // scaled columns share one magnitude, which keeps them in FP16's normal range.
 // x = hi + lo, hi = fp16(x), lo = fp16(x - hi).
-__global__ void k_pack_f16_tiles(const float* __restrict__ Pp, int GK1, int nterms, int rg,
-                                 int n_rows, const unsigned int* __restrict__ maxes,
-                                 __half* __restrict__ Ahi, __half* __restrict__ Alo, int64_t kd) {
-  const int64_t a = blockIdx.x;
-  const int64_t ba = ((a / PT) * 2) * (int64_t)GK1 * PT + (a % PT);
-  for (int c = threadIdx.x; c < kd; c += blockDim.x) {
-    const int h = c >= rg ? 1 : 0;
-    const int q = c - h * rg;
-    float x = 0.f;
+// Block (T, z) transposes operand columns [64 z, 64 z + 64) of the 128 rows of
+// tile T through shared memory: each panel column is read as one contiguous
+// 512-byte run, each operand row segment written as one 128-byte run.
+constexpr int PK_COLS = 64;
+__global__ void __launch_bounds__(256) k_pack_f16_tiles(
+    const float* __restrict__ Pp, int GK1, int nterms, int rg, const unsigned int* __restrict__ maxes,
+    __half* __restrict__ Ahi, __half* __restrict__ Alo, int64_t kd) {
+  __shared__ float tile[PK_COLS][PT + 1];
+  const int T = blockIdx.x;
+  const int c0 = blockIdx.y * PK_COLS;  // rg is a multiple of PK_COLS: one half per block
+  const int h = c0 >= rg ? 1 : 0;
+  const int q0 = c0 - h * rg;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int cc = warp; cc < PK_COLS; cc += 8) {
+    const int q = q0 + cc;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (q < nterms) {
-      x = Pp[ba + (int64_t)(h * GK1 + q) * PT];
+      v = __ldcs(reinterpret_cast<const float4*>(Pp + (((int64_t)T * 2 + h) * GK1 + q) * PT) +
+                 lane);
       const float mx = __uint_as_float(maxes[q]), me = __uint_as_float(maxes[nterms + q]);
-      if (mx > 0.f && me > 0.f && x != 0.f) {
+      if (mx > 0.f && me > 0.f) {
         const int e = (ilogbf(me) - ilogbf(mx)) / 2;
-        x = ldexpf(x, h ? -e : e);
+        const int sh = h ? -e : e;
+        v.x = ldexpf(v.x, sh);
+        v.y = ldexpf(v.y, sh);
+        v.z = ldexpf(v.z, sh);
+        v.w = ldexpf(v.w, sh);
       }
     }
-    const __half hi = __float2half_rn(x);
-    Ahi[a * kd + c] = hi;
-    Alo[a * kd + c] = __float2half_rn(x - __half2float(hi));
+    tile[cc][4 * lane + 0] = v.x;
+    tile[cc][4 * lane + 1] = v.y;
+    tile[cc][4 * lane + 2] = v.z;
+    tile[cc][4 * lane + 3] = v.w;
+  }
+  __syncthreads();
+  // warp w writes rows w, w + 8, ...: lane l the columns 2l, 2l + 1
+  for (int r = warp; r < PT; r += 8) {
+    const float x0 = tile[2 * lane][r], x1 = tile[2 * lane + 1][r];
+    const __half h0 = __float2half_rn(x0), h1 = __float2half_rn(x1);
+    const __half l0 = __float2half_rn(x0 - __half2float(h0));
+    const __half l1 = __float2half_rn(x1 - __half2float(h1));
+    const int64_t o = ((int64_t)T * PT + r) * kd + c0 + 2 * lane;
+    *reinterpret_cast<__half2*>(Ahi + o) = __halves2half2(h0, h1);
+    *reinterpret_cast<__half2*>(Alo + o) = __halves2half2(l0, l1);
   }
 }
 
@@ -301,9 +328,10 @@ void launch_pack_f16_tiles(const float* Pp, int GK1, int nterms, int rg, int n_r
                            unsigned int* maxes, void* Ahi, void* Alo, int64_t kd, cudaStream_t st) {
   const int nT = n_rows / PT;
   cudaMemsetAsync(maxes, 0, 2 * (size_t)nterms * sizeof(unsigned int), st);
-  k_term_max<<<dim3(nT, 2), 256, 0, st>>>(Pp, GK1, nterms, maxes);
-  k_pack_f16_tiles<<<n_rows, 256, 0, st>>>(Pp, GK1, nterms, rg, n_rows, maxes, (__half*)Ahi,
-                                           (__half*)Alo, kd);
+  k_term_max<<<dim3(nT, 2, (nterms + TM_TERMS - 1) / TM_TERMS), 256, 0, st>>>(Pp, GK1, nterms,
+                                                                             maxes);
+  k_pack_f16_tiles<<<dim3(nT, (unsigned)(kd / PK_COLS)), 256, 0, st>>>(
+      Pp, GK1, nterms, rg, maxes, (__half*)Ahi, (__half*)Alo, kd);
 }
 
 void launch_pack_tc(const double* X, int64_t ldx, int rh, int r, int slot, int rg, int n_rows,

@@ -68,13 +68,16 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
 
 // Grid barrier on a monotonically increasing arrival counter: barrier number
 // b of a launch returns once b * gridDim.x arrivals are visible.  Bounded:
-// false after `limit` polls.
+// false after `limit` polls.  The arrival is a release reduction (it orders
+// the CTA's earlier writes, made visible to thread 0 by the CTA barrier, before
+// it) and the polls are acquire loads, so after the final CTA barrier plain
+// (L1-cached) loads of every thread see every CTA's writes from before the
+// barrier.
 __device__ __forceinline__ bool prep_barrier(unsigned int* count, unsigned int target,
                                              long long limit, int* s_ok) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(count, 1u);
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
     int ok = 1;
     long long it = 0;
     while (ld_acquire(count) < target) {
@@ -84,7 +87,6 @@ __device__ __forceinline__ bool prep_barrier(unsigned int* count, unsigned int t
       }
       __nanosleep(16);
     }
-    __threadfence();
     *s_ok = ok;
   }
   __syncthreads();
@@ -100,12 +102,16 @@ __device__ __forceinline__ void red_add2(V2<double>* p, double x, double y) {
   atomicAdd(&p->x, x);
   atomicAdd(&p->y, y);
 }
+// Gathers of the working vectors go through L1: a column with a large
+// out-degree is read by many rows of the same CTA.  Each W[k] is written (by
+// atomics, in L2) only in the step before the one that reads it, with a grid
+// barrier between, so no L1 line can be stale.
 __device__ __forceinline__ V2<float> ld_v2(const V2<float>* p) {
-  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  const float2 v = *reinterpret_cast<const float2*>(p);
   return V2<float>{v.x, v.y};
 }
 __device__ __forceinline__ V2<double> ld_v2(const V2<double>* p) {
-  const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  const double2 v = *reinterpret_cast<const double2*>(p);
   return V2<double>{v.x, v.y};
 }
 
@@ -180,28 +186,45 @@ __device__ __forceinline__ void seg_emit(int key, V a, V b, Emit emit) {
   if (key >= 0 && (lane == 0 || kprev != key) && (a != V(0) || b != V(0))) emit(key, a, b);
 }
 
-// Sums gather(b) over the nonzeros [e0, e1) of the item's tile, per row, and
-// calls emit(r, a, b) with each row's (partial) sums.  The range is split into
-// one contiguous run per thread; a row wholly inside one run is emitted by
-// that thread, the first and last row of a run go through seg_emit.
-template <typename V, typename Gf, typename Emit>
-__device__ __forceinline__ void item_gather(const PrepItem& it, const int* __restrict__ cc,
-                                            const int32_t* __restrict__ col, Gf gather,
-                                            Emit emit) {
-  const int tid = threadIdx.x;
+// One thread's contiguous run [e0, e1) of an item's nonzeros (flattened order
+// of the tile) and the row r holding e0 (r = -1: empty run).  The same for
+// every step, so the step loop computes it once for the CTA's first item.
+struct Run {
+  int e0, e1, r;
+};
+
+__device__ __forceinline__ Run item_run(const PrepItem& it) {
   const int n_e = it.e1 - it.e0;
   const int per = (n_e + PG - 1) / PG;
-  const int e0 = it.e0 + tid * per;
-  const int e1 = min(it.e1, e0 + per);
-  int r_first = -1, r_last = -1;
-  V fa = V(0), fb = V(0), la = V(0), lb = V(0);
-  if (e0 < e1) {
+  Run u;
+  u.e0 = it.e0 + (int)threadIdx.x * per;
+  u.e1 = min(it.e1, u.e0 + per);
+  u.r = -1;
+  if (u.e0 < u.e1) {
     int lo = 0, hi = PT;
     while (hi - lo > 1) {
       const int mid = (lo + hi) >> 1;
-      if (it.off[mid] <= e0) lo = mid; else hi = mid;
+      if (it.off[mid] <= u.e0) lo = mid; else hi = mid;
     }
-    int r = lo;
+    u.r = lo;
+  }
+  return u;
+}
+
+// Sums gather(b) over the nonzeros of the item's tile, per row, and calls
+// emit(r, a, b) with each row's (partial) sums.  Each thread takes its run; a
+// row wholly inside one run is emitted by that thread, the first and last row
+// of a run go through seg_emit.
+template <typename V, typename Gf, typename Emit>
+__device__ __forceinline__ void item_gather(const PrepItem& it, const Run& run,
+                                            const int* __restrict__ cc,
+                                            const int32_t* __restrict__ col, Gf gather,
+                                            Emit emit) {
+  const int e0 = run.e0, e1 = run.e1;
+  int r_first = -1, r_last = -1;
+  V fa = V(0), fb = V(0), la = V(0), lb = V(0);
+  if (run.r >= 0) {
+    int r = run.r;
     r_first = r;
     V pa = V(0), pb = V(0);
     constexpr int B = 8;
@@ -253,6 +276,112 @@ __device__ __forceinline__ void item_gather(const PrepItem& it, const int* __res
   }
   seg_emit<V>(r_first, fa, fb, emit);
   seg_emit<V>(r_last, la, lb, emit);
+}
+
+// A step over an item of at most 2 * PG nonzeros gives each thread at most two
+// of them, so a thread's part of every step is fixed by the graph: its columns,
+// the rows they fall in (head = row of the first; tail = row of the second
+// when it differs) and the shuffle pattern of the warp that adds up the rows
+// spread over several lanes.  StepPair holds that, set up once per launch.
+template <typename V>
+struct StepPair {
+  int ca, cb;    // columns of the nonzeros (-1: none)
+  int kh, kt;    // head / tail row in the tile (-1: none)
+  V ih, itl;     // 1 / in-degree of the head / tail row
+  int span;      // warp-uniform: the longest run of lanes sharing a head row
+  unsigned fl;   // bits 0-4: take lane + 2^b's head sum; 5: add lane - 1's tail;
+                 // 6: emit the head sum; 7: emit the tail sum
+};
+
+template <typename V>
+__device__ __forceinline__ StepPair<V> pair_setup(const PrepItem& it, const int* __restrict__ cc,
+                                                  const int32_t* __restrict__ col) {
+  const Run run = item_run(it);
+  StepPair<V> q;
+  q.ca = q.cb = q.kh = q.kt = -1;
+  q.ih = q.itl = V(0);
+  auto column = [&](int e, int r) {
+    const int ce = e - it.e0;
+    return (ce < it.clen) ? cc[it.cbase + ce] : __ldcg(col + it.start[r] + (e - it.off[r]));
+  };
+  if (run.r >= 0) {
+    q.kh = run.r;
+    q.ca = column(run.e0, q.kh);
+    q.ih = V(1) / (V)it.len[q.kh];
+    if (run.e1 - run.e0 == 2) {
+      int r2 = q.kh;
+      while (run.e0 + 1 >= it.off[r2 + 1]) ++r2;
+      q.cb = column(run.e0 + 1, r2);
+      if (r2 != q.kh) {
+        q.kt = r2;
+        q.itl = V(1) / (V)it.len[r2];
+      }
+    }
+  }
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  // every lane takes part in the warp-wide intrinsics below
+  const unsigned same = __match_any_sync(full, q.kh);
+  const int seg = (q.kh >= 0) ? __popc(same) : 1;
+  q.span = __reduce_max_sync(full, (unsigned)seg);
+  q.fl = 0;
+#pragma unroll
+  for (int b = 0; b < 5; ++b) {
+    const int k2 = __shfl_down_sync(full, q.kh, 1 << b);
+    if (lane + (1 << b) < 32 && k2 == q.kh && q.kh >= 0) q.fl |= 1u << b;
+  }
+  const int kt_prev = __shfl_up_sync(full, q.kt, 1);
+  const int kh_prev = __shfl_up_sync(full, q.kh, 1);
+  const int kh_next = __shfl_down_sync(full, q.kh, 1);
+  if (lane > 0 && q.kh >= 0 && kt_prev == q.kh) q.fl |= 1u << 5;
+  if (q.kh >= 0 && (lane == 0 || kh_prev != q.kh)) q.fl |= 1u << 6;
+  if (q.kt >= 0 && !(lane < 31 && kh_next == q.kt)) q.fl |= 1u << 7;
+  return q;
+}
+
+// One step of the recurrence for a thread set up by pair_setup: gathers its
+// (xi_k, eta_k) entries, adds the rows up across the warp and emits each row's
+// sum (times C and 1 / in-degree for xi, 1 / in-degree for eta) into W[k + 1].
+template <typename V>
+__device__ __forceinline__ void pair_step(const StepPair<V>& q, const V2<V>* Wk, V2<V>* Wn,
+                                          V Cv) {
+  const unsigned full = 0xffffffffu;
+  V ha = V(0), hb = V(0), ta = V(0), tb = V(0);
+  if (q.ca >= 0) {
+    const V2<V> v = ld_v2(Wk + q.ca);
+    ha = v.x;
+    hb = v.y;
+  }
+  if (q.cb >= 0) {
+    const V2<V> v = ld_v2(Wk + q.cb);
+    if (q.kt >= 0) {
+      ta = v.x;
+      tb = v.y;
+    } else {
+      ha += v.x;
+      hb += v.y;
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < 5; ++b) {
+    if ((1 << b) >= q.span) break;
+    const V xa = __shfl_down_sync(full, ha, 1 << b);
+    const V xb = __shfl_down_sync(full, hb, 1 << b);
+    if (q.fl & (1u << b)) {
+      ha += xa;
+      hb += xb;
+    }
+  }
+  const V pa = __shfl_up_sync(full, ta, 1);
+  const V pb = __shfl_up_sync(full, tb, 1);
+  if (q.fl & (1u << 5)) {
+    ha += pa;
+    hb += pb;
+  }
+  if ((q.fl & (1u << 6)) && (ha != V(0) || hb != V(0)))
+    red_add2(Wn + q.kh, Cv * ha * q.ih, hb * q.ih);
+  if ((q.fl & (1u << 7)) && (ta != V(0) || tb != V(0)))
+    red_add2(Wn + q.kt, Cv * ta * q.itl, tb * q.itl);
 }
 
 __device__ void prep_patch(const PatchOp* __restrict__ ops, int64_t begin, int64_t end,
@@ -419,12 +548,16 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
       item_locate(p.in, ioff, nT, blockIdx.x + u * G, p.item, it);
       if (u < MAXI) {
         const int clen = max(0, min(it.e1 - it.e0, p.cap - cbase));
-        // cache the column indices of [e0, e0 + clen), one warp per row
-        for (int r = warp; r < PT; r += PG / 32) {
-          const int o = it.off[r];
-          const int s0 = max(o, it.e0), s1 = min(o + it.len[r], it.e0 + clen);
-          for (int e = s0 + lane; e < s1; e += 32)
-            cc[cbase + (e - it.e0)] = __ldcg(p.in.col + it.start[r] + (e - o));
+        // cache the column indices of [e0, e0 + clen), one nonzero per thread
+        // (a row of the item may hold all of them)
+#pragma unroll 2
+        for (int e = it.e0 + tid; e < it.e0 + clen; e += PG) {
+          int lo = 0, hi = PT;
+          while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (it.off[mid] <= e) lo = mid; else hi = mid;
+          }
+          cc[cbase + (e - it.e0)] = __ldcg(p.in.col + it.start[lo] + (e - it.off[lo]));
         }
         __syncthreads();
         if (tid == 0) {
@@ -435,7 +568,7 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
         __syncthreads();
       }
       const int64_t rb = (int64_t)it.T * PT;
-      item_gather<V>(it, cc, p.in.col, [&](int b) { return V2<V>{__ldcg(sI + b), V(0)}; },
+      item_gather<V>(it, item_run(it), cc, p.in.col, [&](int b) { return V2<V>{sI[b], V(0)}; },
                      [&](int r, V a, V) { red_add(&W[rb + r].x, a); });
       __syncthreads();
     }
@@ -505,14 +638,27 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
   }
 
   // ---- phase 2: K steps
+  // the CTA's first item takes the fixed per-thread form when it can
+  const bool pair0 = my_items > 0 && items[0].e1 - items[0].e0 <= 2 * PG;
+  StepPair<V> q0;
+  int64_t rb0 = 0;
+  if (pair0) {
+    q0 = pair_setup<V>(items[0], cc, p.in.col);
+    rb0 = (int64_t)items[0].T * PT;
+  }
   for (int k = 0; alive && k < K; ++k) {
     const V2<V>* Wk = W + (int64_t)k * p.n_pad;
     V2<V>* Wn = W + (int64_t)(k + 1) * p.n_pad;
     for (int u = 0; u < my_items; ++u) {
+      if (u == 0 && pair0) {
+        pair_step<V>(q0, Wk, Wn + rb0, Cv);
+        continue;
+      }
       PrepItem& it = items[min(u, MAXI)];
       if (u >= MAXI) item_locate(p.in, ioff, nT, blockIdx.x + u * G, p.item, it);
       const int64_t rb = (int64_t)it.T * PT;
-      item_gather<V>(it, cc, p.in.col, [&](int b) { return ld_v2(Wk + b); },
+      item_gather<V>(it, item_run(it), cc, p.in.col,
+                     [&](int b) { return ld_v2(Wk + b); },
                      [&](int r, V a, V b) {
                        const V inv = V(1) / (V)it.len[r];
                        red_add2(Wn + rb + r, Cv * a * inv, b * inv);
