@@ -67,6 +67,8 @@ struct simrank_ctx {
   uint32_t* d_order = nullptr;   // all tile pairs I <= J in band order (tensor-core S pass)
   int order_nT = -1;
   int order_n = 0;
+  uint64_t* d_jobs = nullptr;    // the same pairs, two per job where they share J
+  int jobs_n = 0;
   void* W = nullptr;             // (xi, eta) working columns of the pre-update kernel
   int* tile_nnz = nullptr;       // per-tile nonzeros (scratch of the pre-update kernel)
   // per-call staging
@@ -438,17 +440,30 @@ simrank_status ensure_order(simrank_ctx* h, int nT) {
   std::vector<uint32_t> v;
   v.reserve((size_t)nT * (nT + 1) / 2);
   constexpr int BAND = 8;
+  std::vector<uint64_t> jb;
+  jb.reserve((size_t)nT * (nT + 1) / 4 + nT);
   for (int b0 = 0; b0 < nT; b0 += BAND)
-    for (int J = b0; J < nT; ++J)
-      for (int I = b0; I < std::min(b0 + BAND, J + 1); ++I)
-        v.push_back(((uint32_t)I << 16) | (uint32_t)J);
+    for (int J = b0; J < nT; ++J) {
+      const int I1 = std::min(b0 + BAND, J + 1);
+      for (int I = b0; I < I1; ++I) v.push_back(((uint32_t)I << 16) | (uint32_t)J);
+      for (int I = b0; I < I1; I += 2)
+        jb.push_back(((uint64_t)I << 32) | ((uint64_t)(I + 1 < I1 ? I + 1 : 0xffff) << 16) |
+                     (uint64_t)J);
+    }
   if (h->d_order) cudaFree(h->d_order);
   h->d_order = nullptr;
+  if (h->d_jobs) cudaFree(h->d_jobs);
+  h->d_jobs = nullptr;
+  h->order_nT = -1;
   CUDA_TRY(h, dev_alloc(&h->d_order, v.size()));
   CUDA_TRY(h, cudaMemcpy(h->d_order, v.data(), v.size() * sizeof(uint32_t),
                          cudaMemcpyHostToDevice));
+  CUDA_TRY(h, dev_alloc(&h->d_jobs, jb.size()));
+  CUDA_TRY(h, cudaMemcpy(h->d_jobs, jb.data(), jb.size() * sizeof(uint64_t),
+                         cudaMemcpyHostToDevice));
   h->order_nT = nT;
   h->order_n = (int)v.size();
+  h->jobs_n = (int)jb.size();
   return SR_OK;
 }
 
@@ -499,7 +514,8 @@ simrank_status flush_pending(simrank_ctx* h) {
     }
     if (ev) CUDA_TRY(h, cudaEventRecord(ev->first, h->st));
     const int rc = launch_s_update_tc((float*)h->S, h->ld, h->ob[12].p, h->ob[13].p, h->n_pad,
-                                      kd, h->d_order, h->order_n, h->pXi, h->pEta,
+                                      kd, h->d_order, h->order_n, h->d_jobs, h->jobs_n,
+                                      h->pXi, h->pEta,
                                       h->cfg.aff ? 1 : 0, h->n_cur, h->counters, h->num_sms,
                                       wait_limit(h), h->st, upper(h), f16 ? 1 : 0);
     if (rc != 0) return fail(h, SR_ERR_CUDA, "tensor-core S update: launch setup failed");
@@ -938,7 +954,8 @@ simrank_status run_one_shot(simrank_ctx* h, const std::map<int32_t, std::vector<
       }
       if (tc) {
         const int rc = launch_s_update_tc((float*)h->S, h->ld, h->ob[8].p, h->ob[9].p, n_pad,
-                                          kd, h->d_order, h->order_n, h->mXi, h->mEta, 0,
+                                          kd, h->d_order, h->order_n, nullptr, 0, h->mXi,
+                                          h->mEta, 0,
                                           h->n_cur, h->counters, h->num_sms, wait_limit, h->st,
                                           upper(h));
         if (rc != 0) return fail(h, SR_ERR_CUDA, "tensor-core S update: launch setup failed");
@@ -1099,7 +1116,7 @@ void free_ctx(simrank_ctx* h) {
                   h->dout.col,  h->d_in_w,   h->d_wsum,    h->S,          h->P64,
                   h->P32,       h->mXi,      h->mEta,      h->tiles,      h->ntiles,
                   h->sI,        h->sJ,       h->scal,      h->counters,   h->diffbits,
-                  h->gbar,      h->W,        h->tile_nnz,  h->d_order,
+                  h->gbar,      h->W,        h->tile_nnz,  h->d_order,    h->d_jobs,
                   h->d_srcs,    h->d_ops,    h->d_cols,     h->d_ext2int};
   for (void* p : ptrs)
     if (p) cudaFree(p);

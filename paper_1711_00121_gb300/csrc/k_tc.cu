@@ -461,6 +461,246 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
 }
 
+// Jobs of two tile pairs that share their column tile J: job = I1 << 32 |
+// I2 << 16 | J (I2 = 0xffff: one pair).  A pair whose AFF mask words show no
+// active cross term is dropped; get() returns the active pairs (0, 1 or 2),
+// the active row tiles first.
+struct TcJobs {
+  const uint64_t* jobs;
+  int nj;
+  const uint64_t* mX;
+  const uint64_t* mE;
+  int use_masks;
+  float* S;
+  int64_t ld;
+  int n;
+  __device__ __forceinline__ int get(int q, int& I1, int& I2, int& J) const {
+    const uint64_t e = jobs[q];
+    I1 = (int)((e >> 32) & 0xffffu);
+    I2 = (int)((e >> 16) & 0xffffu);
+    J = (int)(e & 0xffffu);
+    bool a1 = true, a2 = I2 != 0xffff;
+    if (use_masks) {
+      a1 = ((mX[I1] & mE[J]) | (mE[I1] & mX[J])) != 0ull;
+      if (a2) a2 = ((mX[I2] & mE[J]) | (mE[I2] & mX[J])) != 0ull;
+    }
+    if (!a1) {
+      I1 = I2;
+      a1 = a2;
+      a2 = false;
+    }
+    return a1 ? (a2 ? 2 : 1) : 0;
+  }
+};
+
+constexpr int STAGES_PAIR = 2;
+constexpr int PAIR_STAGE_BYTES = 6 * OPB;  // A1 hi, A1 lo, A2 hi, A2 lo, B hi, B lo
+constexpr uint32_t TMEM_COLS_PAIR = 512;   // two jobs in flight x two 128-column accumulators
+
+// The S pass over jobs of two tile pairs (I1, J), (I2, J) sharing B(J): a
+// stage carries 96 KB of operands for twice the tensor work of a single pair
+// (64 KB), so the same shared memory covers a longer load latency.  Upper
+// tiles only (no transposed write); register epilogue as in k_s_update_tc.
+template <bool F16>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_s_update_tc_pair(const __grid_constant__ CUtensorMap tm_hi,
+                       const __grid_constant__ CUtensorMap tm_lo, TcJobs src, int nkb,
+                       long long wait_limit, unsigned long long* __restrict__ counters) {
+  constexpr int STAGES = STAGES_PAIR;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES];
+  __shared__ __align__(8) uint64_t bar_acc_full[2], bar_acc_empty[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  const int half = nkb / 2;  // B row = A row with its halves swapped
+  const int nj = src.nj;
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&bar_full[s]), 1);
+      mbar_init(smem_u32(&bar_empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&bar_acc_full[b]), 1);
+      mbar_init(smem_u32(&bar_acc_empty[b]), 256);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(TMEM_COLS_PAIR));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  bool ok = true;
+
+  if (warp == 0) {
+    // ---------------- TMA producer
+    if (lane == 0) {
+      uint32_t it = 0;
+      for (int q = blockIdx.x; q < nj && ok; q += gridDim.x) {
+        int I1, I2, J;
+        const int cnt = src.get(q, I1, I2, J);
+        if (cnt == 0) continue;
+        for (int kb = 0; kb < nkb && ok; ++kb, ++it) {
+          const int s = it % STAGES;
+          const uint32_t ph = (it / STAGES) & 1u;
+          if (!mbar_wait(smem_u32(&bar_empty[s]), ph ^ 1u, wait_limit, &abort_flag)) {
+            ok = false;
+            break;
+          }
+          const uint32_t st = base + s * PAIR_STAGE_BYTES;
+          const uint32_t fb = smem_u32(&bar_full[s]);
+          mbar_expect_tx(fb, (uint32_t)(cnt == 2 ? 6 : 4) * OPB);
+          const int kb_b = kb < half ? kb + half : kb - half;
+          constexpr int KCH = F16 ? KB / 2 : KB / 4;  // elements of K per stage
+          tma_load_2d(st + 0 * OPB, &tm_hi, kb * KCH, I1 * TM, fb);
+          tma_load_2d(st + 1 * OPB, &tm_lo, kb * KCH, I1 * TM, fb);
+          if (cnt == 2) {
+            tma_load_2d(st + 2 * OPB, &tm_hi, kb * KCH, I2 * TM, fb);
+            tma_load_2d(st + 3 * OPB, &tm_lo, kb * KCH, I2 * TM, fb);
+          }
+          tma_load_2d(st + 4 * OPB, &tm_hi, kb_b * KCH, J * TN, fb);
+          tma_load_2d(st + 5 * OPB, &tm_lo, kb_b * KCH, J * TN, fb);
+        }
+      }
+      if (!ok) abort_flag = 1;
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer: job jl accumulates in TMEM columns (jl & 1) * 256 + [0, 256)
+    if (lane == 0) {
+      uint32_t it = 0, jl = 0;
+      for (int q = blockIdx.x; q < nj && ok; q += gridDim.x) {
+        int I1, I2, J;
+        const int cnt = src.get(q, I1, I2, J);
+        if (cnt == 0) continue;
+        const uint32_t b = jl & 1u;
+        const uint32_t eph = ((jl >> 1) & 1u) ^ 1u;
+        ++jl;
+        if (!mbar_wait(smem_u32(&bar_acc_empty[b]), eph, wait_limit, &abort_flag)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc = tmem + b * 256u;
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = it % STAGES;
+          const uint32_t ph = (it / STAGES) & 1u;
+          if (!mbar_wait(smem_u32(&bar_full[s]), ph, wait_limit, &abort_flag)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t st = base + s * PAIR_STAGE_BYTES;
+          const uint64_t a1h = smem_desc(st + 0 * OPB), a1l = smem_desc(st + 1 * OPB);
+          const uint64_t a2h = smem_desc(st + 2 * OPB), a2l = smem_desc(st + 3 * OPB);
+          const uint64_t bh = smem_desc(st + 4 * OPB), bl = smem_desc(st + 5 * OPB);
+#pragma unroll
+          for (int kk = 0; kk < KB / 32; ++kk) {
+            const uint64_t adv = (uint64_t)(kk * 32) >> 4;
+            const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
+            mma_k32b<F16>(acc, a1h + adv, bh + adv, first);
+            mma_k32b<F16>(acc, a1h + adv, bl + adv, 1u);
+            mma_k32b<F16>(acc, a1l + adv, bh + adv, 1u);
+            if (cnt == 2) {
+              mma_k32b<F16>(acc + 128u, a2h + adv, bh + adv, first);
+              mma_k32b<F16>(acc + 128u, a2h + adv, bl + adv, 1u);
+              mma_k32b<F16>(acc + 128u, a2l + adv, bh + adv, 1u);
+            }
+          }
+          mma_commit(smem_u32(&bar_empty[s]));  // stage reusable once these MMAs finish
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&bar_acc_full[b]));
+      }
+      if (!ok) abort_flag = 1;
+    }
+  } else {
+    // ---------------- epilogue: warps 2..9 (256 threads); S[I, J] += D per active pair
+    const int et = threadIdx.x - 64;   // 0..255
+    const int ew = et >> 5;            // epilogue warp 0..7
+    const int quarter = warp & 3;      // TMEM lanes this warp may read
+    const int chalf = (ew >> 2) * 64;  // columns [chalf, chalf + 64) of an accumulator
+    const int row = quarter * 32 + lane;
+    float* __restrict__ S = src.S;
+    const int64_t ld = src.ld;
+    const int n = src.n;
+    uint32_t jl = 0;
+    unsigned long long my_tiles = 0, my_bytes = 0;
+    for (int q = blockIdx.x; q < nj; q += gridDim.x) {
+      int I1, I2, J;
+      const int cnt = src.get(q, I1, I2, J);
+      if (cnt == 0) continue;
+      const uint32_t b = jl & 1u;
+      const uint32_t tph = (jl >> 1) & 1u;
+      ++jl;
+      for (int u = 0; u < cnt; ++u) {
+        const int I = u ? I2 : I1;
+        // this thread's 64 values of S[I, J], fetched before the accumulator is read
+        float* srow = S + (int64_t)(I * TM + row) * ld + (int64_t)J * TN + chalf;
+        float4 sv[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) sv[c] = *reinterpret_cast<const float4*>(srow + 4 * c);
+        if (u == 0) {
+          const bool got = mbar_wait(smem_u32(&bar_acc_full[b]), tph, wait_limit, &abort_flag);
+          if (!ep_all(got)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float v[32];
+          tmem_ld32(tmem + b * 256u + (uint32_t)(u * 128) + ((uint32_t)(quarter * 32) << 16) +
+                        (uint32_t)(chalf + 32 * h),
+                    v);
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            sv[8 * h + c].x += v[4 * c + 0];
+            sv[8 * h + c].y += v[4 * c + 1];
+            sv[8 * h + c].z += v[4 * c + 2];
+            sv[8 * h + c].w += v[4 * c + 3];
+          }
+        }
+        if (u == cnt - 1) {
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          mbar_arrive(smem_u32(&bar_acc_empty[b]));  // both accumulators of the job are read
+        }
+#pragma unroll
+        for (int c = 0; c < 16; ++c) *reinterpret_cast<float4*>(srow + 4 * c) = sv[c];
+        if (et == 0) {
+          const long long vr = max(0, min(TM, n - I * TM)), vc = max(0, min(TN, n - J * TN));
+          my_tiles += 1;
+          my_bytes += (unsigned long long)(vr * vc) * 8ull;
+        }
+      }
+      if (!ok) break;
+    }
+    if (!ok) abort_flag = 1;
+    if (et == 0 && my_tiles) {
+      atomicAdd(&counters[CNT_TILES_TOUCHED], my_tiles);
+      atomicAdd(&counters[CNT_S_BYTES], my_bytes);
+    }
+  }
+
+  __syncthreads();
+  if (threadIdx.x == 0 && abort_flag) atomicExch(&counters[CNT_STATUS], (unsigned long long)SR_ERR_TIMEOUT);
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS_PAIR));
+  }
+}
+
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
                               CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
@@ -549,9 +789,33 @@ int launch_tc(const void* Ahi, const void* Alo, int64_t n_rows, int64_t kd, cons
 // FP16 (f16 = 1); kd a multiple of 2 * (128 bytes / element size); the B
 // operand is A with its two column halves swapped.
 int launch_s_update_tc(float* S, int64_t ld, const void* Ahi, const void* Alo, int64_t n_rows,
-                       int64_t kd, const uint32_t* tiles, int nt, const uint64_t* mX,
-                       const uint64_t* mE, int use_masks, int n, int64_t* counters, int grid,
-                       long long wait_limit, cudaStream_t st, int upper, int f16) {
+                       int64_t kd, const uint32_t* tiles, int nt, const uint64_t* jobs, int nj,
+                       const uint64_t* mX, const uint64_t* mE, int use_masks, int n,
+                       int64_t* counters, int grid, long long wait_limit, cudaStream_t st,
+                       int upper, int f16) {
+  const int eb = f16 ? 2 : 4;
+  if (jobs && upper && kd * eb >= WIDE_K_BYTES) {
+    // wide operands, upper tiles: jobs of two tile pairs sharing their column tile
+    const int kch = KB / eb;
+    if (kd % (2 * kch) != 0 || n_rows % TM != 0) return 1;
+    CUtensorMap mhi, mlo;
+    if (!make_map(&mhi, Ahi, n_rows, kd, eb)) return 2;
+    if (!make_map(&mlo, Alo, n_rows, kd, eb)) return 2;
+    const int nkb = (int)(kd / kch);
+    TcJobs src{jobs, nj, mX, mE, use_masks, S, ld, n};
+    const size_t smem = (size_t)STAGES_PAIR * PAIR_STAGE_BYTES + 1024;
+    const void* fn = f16 ? (const void*)k_s_update_tc_pair<true> : (const void*)k_s_update_tc_pair<false>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return 1;
+    if (f16)
+      k_s_update_tc_pair<true><<<grid, TC_THREADS, smem, st>>>(mhi, mlo, src, nkb, wait_limit,
+                                                               (unsigned long long*)counters);
+    else
+      k_s_update_tc_pair<false><<<grid, TC_THREADS, smem, st>>>(mhi, mlo, src, nkb, wait_limit,
+                                                                (unsigned long long*)counters);
+    return 0;
+  }
   TcOneGraph src{tiles, nt, mX, mE, use_masks, S, ld, n, upper ? 0 : 1};
   return launch_tc(Ahi, Alo, n_rows, kd, src, grid, wait_limit, st, f16, upper ? 0 : 1, counters);
 }

@@ -276,10 +276,14 @@ void launch_pack_tc(const double* X, int64_t ldx, int rh, int r, int slot, int r
 // 0 on launch, 1 for a bad shape, 2 if no tensor map could be encoded.
 // tiles[0 .. nt): tile pairs (I << 16 | J) in the order CTAs take them; a
 // pair is skipped when use_masks and (mX[I] & mE[J]) | (mE[I] & mX[J]) == 0.
+// jobs[0 .. nj) (may be null): the same pairs, two per job where they share J
+// (I1 << 32 | I2 << 16 | J, I2 = 0xffff for one), taken instead of tiles when
+// only upper tiles are kept and the operands are at least 1 KB wide.
 int launch_s_update_tc(float* S, int64_t ld, const void* Ahi, const void* Alo, int64_t n_rows,
-                       int64_t kd, const uint32_t* tiles, int nt, const uint64_t* mX,
-                       const uint64_t* mE, int use_masks, int n, int64_t* counters, int grid,
-                       long long wait_limit, cudaStream_t st, int upper = 0, int f16 = 0);
+                       int64_t kd, const uint32_t* tiles, int nt, const uint64_t* jobs, int nj,
+                       const uint64_t* mX, const uint64_t* mE, int use_masks, int n,
+                       int64_t* counters, int grid, long long wait_limit, cudaStream_t st,
+                       int upper = 0, int f16 = 0);
 // The same pass over the tile pairs (g << 32 | I << 16 | J) of many graphs,
 // *ntiles of them; graph g's operand rows start at descs[g].row_off of the
 // shared operands A_hi / A_lo ([rows][kd]).
