@@ -67,7 +67,7 @@ struct simrank_ctx {
   uint32_t* d_order = nullptr;   // all tile pairs I <= J in band order (tensor-core S pass)
   int order_nT = -1;
   int order_n = 0;
-  uint64_t* d_jobs = nullptr;    // the same pairs, two per job where they share J
+  uint64_t* d_jobs = nullptr;    // the same pairs, two per job where they share I
   int jobs_n = 0;
   void* W = nullptr;             // (xi, eta) working columns of the pre-update kernel
   int* tile_nnz = nullptr;       // per-tile nonzeros (scratch of the pre-update kernel)
@@ -442,14 +442,20 @@ simrank_status ensure_order(simrank_ctx* h, int nT) {
   constexpr int BAND = 8;
   std::vector<uint64_t> jb;
   jb.reserve((size_t)nT * (nT + 1) / 4 + nT);
-  for (int b0 = 0; b0 < nT; b0 += BAND)
-    for (int J = b0; J < nT; ++J) {
-      const int I1 = std::min(b0 + BAND, J + 1);
-      for (int I = b0; I < I1; ++I) v.push_back(((uint32_t)I << 16) | (uint32_t)J);
-      for (int I = b0; I < I1; I += 2)
-        jb.push_back(((uint64_t)I << 32) | ((uint64_t)(I + 1 < I1 ? I + 1 : 0xffff) << 16) |
-                     (uint64_t)J);
+  for (int b0 = 0; b0 < nT; b0 += BAND) {
+    for (int J = b0; J < nT; ++J)
+      for (int I = b0; I < std::min(b0 + BAND, J + 1); ++I)
+        v.push_back(((uint32_t)I << 16) | (uint32_t)J);
+    // jobs: column tiles in pairs (J, J + 1), each with the band's row tiles I <= J + 1
+    for (int J = b0; J < nT; J += 2) {
+      const int J2 = J + 1 < nT ? J + 1 : -1;
+      for (int I = b0; I < std::min(b0 + BAND, (J2 >= 0 ? J2 : J) + 1); ++I) {
+        const bool p1 = I <= J, p2 = J2 >= 0 && I <= J2;
+        const int a = p1 ? J : J2, c = (p1 && p2) ? J2 : 0xffff;
+        jb.push_back(((uint64_t)I << 32) | ((uint64_t)a << 16) | (uint64_t)c);
+      }
     }
+  }
   if (h->d_order) cudaFree(h->d_order);
   h->d_order = nullptr;
   if (h->d_jobs) cudaFree(h->d_jobs);

@@ -43,6 +43,11 @@ constexpr uint32_t IDESC_TF32 = (1u << 4) | (2u << 7) | (2u << 10) |
                                 ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 constexpr uint32_t IDESC_F16 = (1u << 4) | (0u << 7) | (0u << 10) |
                                ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+// the same with N = 256 (two column tiles side by side)
+constexpr uint32_t IDESC_TF32_N256 = (1u << 4) | (2u << 7) | (2u << 10) |
+                                     ((uint32_t)(256 >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+constexpr uint32_t IDESC_F16_N256 = (1u << 4) | (0u << 7) | (0u << 10) |
+                                    ((uint32_t)(256 >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -113,6 +118,25 @@ __device__ __forceinline__ void mma_k32b(uint32_t tmem_d, uint64_t adesc, uint64
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
         "l"(adesc), "l"(bdesc), "r"(IDESC_TF32), "r"(accumulate)
+        : "memory");
+  }
+}
+
+// One MMA with a run-time instruction descriptor (N = 128 or 256).
+template <bool F16>
+__device__ __forceinline__ void mma_k32b_d(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                           uint32_t idesc, uint32_t accumulate) {
+  if (F16) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
   }
 }
@@ -461,10 +485,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
 }
 
-// Jobs of two tile pairs that share their column tile J: job = I1 << 32 |
-// I2 << 16 | J (I2 = 0xffff: one pair).  A pair whose AFF mask words show no
-// active cross term is dropped; get() returns the active pairs (0, 1 or 2),
-// the active row tiles first.
+// Jobs of two tile pairs that share their row tile I: job = I << 32 | J1 << 16
+// | J2 (J2 = 0xffff: one pair).  A pair whose AFF mask words show no active
+// cross term is dropped; get() returns the active pairs (0, 1 or 2), the
+// active column tiles first.
 struct TcJobs {
   const uint64_t* jobs;
   int nj;
@@ -474,18 +498,18 @@ struct TcJobs {
   float* S;
   int64_t ld;
   int n;
-  __device__ __forceinline__ int get(int q, int& I1, int& I2, int& J) const {
+  __device__ __forceinline__ int get(int q, int& I, int& J1, int& J2) const {
     const uint64_t e = jobs[q];
-    I1 = (int)((e >> 32) & 0xffffu);
-    I2 = (int)((e >> 16) & 0xffffu);
-    J = (int)(e & 0xffffu);
-    bool a1 = true, a2 = I2 != 0xffff;
+    I = (int)((e >> 32) & 0xffffu);
+    J1 = (int)((e >> 16) & 0xffffu);
+    J2 = (int)(e & 0xffffu);
+    bool a1 = true, a2 = J2 != 0xffff;
     if (use_masks) {
-      a1 = ((mX[I1] & mE[J]) | (mE[I1] & mX[J])) != 0ull;
-      if (a2) a2 = ((mX[I2] & mE[J]) | (mE[I2] & mX[J])) != 0ull;
+      a1 = ((mX[I] & mE[J1]) | (mE[I] & mX[J1])) != 0ull;
+      if (a2) a2 = ((mX[I] & mE[J2]) | (mE[I] & mX[J2])) != 0ull;
     }
     if (!a1) {
-      I1 = I2;
+      J1 = J2;
       a1 = a2;
       a2 = false;
     }
@@ -494,13 +518,14 @@ struct TcJobs {
 };
 
 constexpr int STAGES_PAIR = 2;
-constexpr int PAIR_STAGE_BYTES = 6 * OPB;  // A1 hi, A1 lo, A2 hi, A2 lo, B hi, B lo
-constexpr uint32_t TMEM_COLS_PAIR = 512;   // two jobs in flight x two 128-column accumulators
+constexpr int PAIR_STAGE_BYTES = 6 * OPB;  // A hi, A lo, B1 hi, B2 hi, B1 lo, B2 lo
+constexpr uint32_t TMEM_COLS_PAIR = 512;   // two jobs in flight x 256 accumulator columns
 
-// The S pass over jobs of two tile pairs (I1, J), (I2, J) sharing B(J): a
-// stage carries 96 KB of operands for twice the tensor work of a single pair
-// (64 KB), so the same shared memory covers a longer load latency.  Upper
-// tiles only (no transposed write); register epilogue as in k_s_update_tc.
+// The S pass over jobs of two tile pairs (I, J1), (I, J2) sharing A(I): B(J1)
+// and B(J2) sit side by side in shared memory as one 256-row operand, so a job
+// is one M = 128, N = 256 product per split term (half the shared-memory
+// operand reads per flop of two N = 128 products).  Upper tiles only (no
+// transposed write); register epilogue as in k_s_update_tc.
 template <bool F16>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_s_update_tc_pair(const __grid_constant__ CUtensorMap tm_hi,
@@ -547,8 +572,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (lane == 0) {
       uint32_t it = 0;
       for (int q = blockIdx.x; q < nj && ok; q += gridDim.x) {
-        int I1, I2, J;
-        const int cnt = src.get(q, I1, I2, J);
+        int I, J1, J2;
+        const int cnt = src.get(q, I, J1, J2);
         if (cnt == 0) continue;
         for (int kb = 0; kb < nkb && ok; ++kb, ++it) {
           const int s = it % STAGES;
@@ -562,14 +587,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           mbar_expect_tx(fb, (uint32_t)(cnt == 2 ? 6 : 4) * OPB);
           const int kb_b = kb < half ? kb + half : kb - half;
           constexpr int KCH = F16 ? KB / 2 : KB / 4;  // elements of K per stage
-          tma_load_2d(st + 0 * OPB, &tm_hi, kb * KCH, I1 * TM, fb);
-          tma_load_2d(st + 1 * OPB, &tm_lo, kb * KCH, I1 * TM, fb);
+          tma_load_2d(st + 0 * OPB, &tm_hi, kb * KCH, I * TM, fb);
+          tma_load_2d(st + 1 * OPB, &tm_lo, kb * KCH, I * TM, fb);
+          tma_load_2d(st + 2 * OPB, &tm_hi, kb_b * KCH, J1 * TN, fb);
+          tma_load_2d(st + 4 * OPB, &tm_lo, kb_b * KCH, J1 * TN, fb);
           if (cnt == 2) {
-            tma_load_2d(st + 2 * OPB, &tm_hi, kb * KCH, I2 * TM, fb);
-            tma_load_2d(st + 3 * OPB, &tm_lo, kb * KCH, I2 * TM, fb);
+            tma_load_2d(st + 3 * OPB, &tm_hi, kb_b * KCH, J2 * TN, fb);
+            tma_load_2d(st + 5 * OPB, &tm_lo, kb_b * KCH, J2 * TN, fb);
           }
-          tma_load_2d(st + 4 * OPB, &tm_hi, kb_b * KCH, J * TN, fb);
-          tma_load_2d(st + 5 * OPB, &tm_lo, kb_b * KCH, J * TN, fb);
         }
       }
       if (!ok) abort_flag = 1;
@@ -579,9 +604,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (lane == 0) {
       uint32_t it = 0, jl = 0;
       for (int q = blockIdx.x; q < nj && ok; q += gridDim.x) {
-        int I1, I2, J;
-        const int cnt = src.get(q, I1, I2, J);
+        int I, J1, J2;
+        const int cnt = src.get(q, I, J1, J2);
         if (cnt == 0) continue;
+        const uint32_t idesc = cnt == 2 ? (F16 ? IDESC_F16_N256 : IDESC_TF32_N256)
+                                        : (F16 ? IDESC_F16 : IDESC_TF32);
         const uint32_t b = jl & 1u;
         const uint32_t eph = ((jl >> 1) & 1u) ^ 1u;
         ++jl;
@@ -600,21 +627,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t st = base + s * PAIR_STAGE_BYTES;
-          const uint64_t a1h = smem_desc(st + 0 * OPB), a1l = smem_desc(st + 1 * OPB);
-          const uint64_t a2h = smem_desc(st + 2 * OPB), a2l = smem_desc(st + 3 * OPB);
-          const uint64_t bh = smem_desc(st + 4 * OPB), bl = smem_desc(st + 5 * OPB);
+          // B hi (and B lo): rows of B(J1) then B(J2), one 256-row operand
+          const uint64_t ah = smem_desc(st + 0 * OPB), al = smem_desc(st + 1 * OPB);
+          const uint64_t bh = smem_desc(st + 2 * OPB), bl = smem_desc(st + 4 * OPB);
 #pragma unroll
           for (int kk = 0; kk < KB / 32; ++kk) {
             const uint64_t adv = (uint64_t)(kk * 32) >> 4;
             const uint32_t first = (kb == 0 && kk == 0) ? 0u : 1u;
-            mma_k32b<F16>(acc, a1h + adv, bh + adv, first);
-            mma_k32b<F16>(acc, a1h + adv, bl + adv, 1u);
-            mma_k32b<F16>(acc, a1l + adv, bh + adv, 1u);
-            if (cnt == 2) {
-              mma_k32b<F16>(acc + 128u, a2h + adv, bh + adv, first);
-              mma_k32b<F16>(acc + 128u, a2h + adv, bl + adv, 1u);
-              mma_k32b<F16>(acc + 128u, a2l + adv, bh + adv, 1u);
-            }
+            mma_k32b_d<F16>(acc, ah + adv, bh + adv, idesc, first);
+            mma_k32b_d<F16>(acc, ah + adv, bl + adv, idesc, 1u);
+            mma_k32b_d<F16>(acc, al + adv, bh + adv, idesc, 1u);
           }
           mma_commit(smem_u32(&bar_empty[s]));  // stage reusable once these MMAs finish
         }
@@ -636,14 +658,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint32_t jl = 0;
     unsigned long long my_tiles = 0, my_bytes = 0;
     for (int q = blockIdx.x; q < nj; q += gridDim.x) {
-      int I1, I2, J;
-      const int cnt = src.get(q, I1, I2, J);
+      int I, J1, J2;
+      const int cnt = src.get(q, I, J1, J2);
       if (cnt == 0) continue;
       const uint32_t b = jl & 1u;
       const uint32_t tph = (jl >> 1) & 1u;
       ++jl;
       for (int u = 0; u < cnt; ++u) {
-        const int I = u ? I2 : I1;
+        const int J = u ? J2 : J1;
         // this thread's 64 values of S[I, J], fetched before the accumulator is read
         float* srow = S + (int64_t)(I * TM + row) * ld + (int64_t)J * TN + chalf;
         float4 sv[16];

@@ -276,8 +276,8 @@ void launch_pack_tc(const double* X, int64_t ldx, int rh, int r, int slot, int r
 // 0 on launch, 1 for a bad shape, 2 if no tensor map could be encoded.
 // tiles[0 .. nt): tile pairs (I << 16 | J) in the order CTAs take them; a
 // pair is skipped when use_masks and (mX[I] & mE[J]) | (mE[I] & mX[J]) == 0.
-// jobs[0 .. nj) (may be null): the same pairs, two per job where they share J
-// (I1 << 32 | I2 << 16 | J, I2 = 0xffff for one), taken instead of tiles when
+// jobs[0 .. nj) (may be null): the same pairs, two per job where they share I
+// (I << 32 | J1 << 16 | J2, J2 = 0xffff for one), taken instead of tiles when
 // only upper tiles are kept and the operands are at least 1 KB wide.
 int launch_s_update_tc(float* S, int64_t ld, const void* Ahi, const void* Alo, int64_t n_rows,
                        int64_t kd, const uint32_t* tiles, int nt, const uint64_t* jobs, int nj,
