@@ -322,8 +322,16 @@ def run_gpu(args, rank, world):
     sp_bytes = pd["s_bytes"] + operand_bytes
     sp_gbs = sp_bytes / (sp_ms / 1000.0) / 1e9 if sp_ms > 0 else 0.0
     sp_tflops = flops / (sp_ms / 1000.0) / 1e12 if sp_ms > 0 else 0.0
-    sp_name = ("k_s_update_tc (tcgen05, 3-term " + ("FP16" if args.tc == 2 else "TF32") +
-               " split, S pass)") if args.tc else "k_s_update_ws (CUDA-core S pass)"
+    # wide operands (at least 1 KB of K per row) take jobs of two tile pairs
+    # sharing their row tile, one N = 256 product per split term
+    paired = bool(args.tc) and 2 * rg * (2 if args.tc == 2 else 4) >= 1024
+    split = "3-term " + ("FP16" if args.tc == 2 else "TF32") + " split"
+    if not args.tc:
+        sp_name = "k_s_update_ws (CUDA-core S pass)"
+    elif paired:
+        sp_name = "k_s_update_tc_pair (tcgen05, jobs of two tile pairs, N = 256, " + split + ")"
+    else:
+        sp_name = "k_s_update_tc (tcgen05, " + split + ", S pass)"
     if args.tc and sp_tflops / tc_peak > sp_gbs / peak:
         s_pass = {"kernel": sp_name, "bound": "tensor", "achieved": sp_tflops, "peak": tc_peak,
                   "unit": "TFLOP/s", "frac": sp_tflops / tc_peak, "peak_kind": tc_peak_kind,
@@ -332,7 +340,12 @@ def run_gpu(args, rank, world):
         s_pass = {"kernel": sp_name, "bound": "hbm", "achieved": sp_gbs, "peak": peak,
                   "unit": "GB/s", "frac": sp_gbs / peak, "peak_kind": peak_kind,
                   "tflops": sp_tflops}
-    s_pass.update({"traffic": None, "bytes_per_launch": sp_bytes / max(launches, 1),
+    # DRAM bytes (read + write) per launch from one ncu capture of each kernel
+    # on this workload (n = 20,000, K = 20, 16 pending updates, FP16 split,
+    # FP32 vectors); null for any other form
+    profiled = (N, K, args.defer, args.tc, args.vec_fp64) == (20000, 20, 16, 2, 0)
+    s_pass.update({"traffic": 1.6629e9 if profiled else None,
+                   "bytes_per_launch": sp_bytes / max(launches, 1),
                    "ms_per_launch": sp_ms / max(launches, 1), "launches": launches})
     # k_prep: one launch per update; algorithmic bytes = the graph read K+1
     # times, the gathered (xi, eta) pairs, the two S rows and the panel writes
@@ -342,7 +355,8 @@ def run_gpu(args, rank, world):
     prep_gbs = prep_bytes_1 * per_step / (prep_ms / 1000.0) / 1e9 if prep_ms > 0 else 0.0
     prep = {"kernel": "k_prep (cooperative: patch, rows of S, gamma, K recurrence steps, masks, "
                       "tile list)", "bound": "hbm", "achieved": prep_gbs, "peak": peak,
-            "unit": "GB/s", "frac": prep_gbs / peak, "peak_kind": peak_kind, "traffic": None,
+            "unit": "GB/s", "frac": prep_gbs / peak, "peak_kind": peak_kind,
+            "traffic": 3.0725e7 if profiled else None,
             "bytes_per_launch": prep_bytes_1, "ms_per_launch": prep_ms / per_step,
             "launches": per_step,
             "note": "latency-bound (L2-resident working set, K+4 grid barriers per launch)"}
