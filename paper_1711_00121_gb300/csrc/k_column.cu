@@ -62,6 +62,36 @@ __global__ void k_col_chunk(const RowChunk* __restrict__ chunks, const int32_t* 
   atomicAdd(&Y[(int64_t)ch.row * B + c], rs * acc);
 }
 
+// The same for FP32 blocks with B a multiple of 4: each thread takes four
+// adjacent columns (one 16-byte gather per nonzero, one weight per nonzero
+// for the four) and adds its partial sums with one vector atomic.
+template <bool FORWARD>
+__global__ void k_col_chunk4(const RowChunk* __restrict__ chunks, const int32_t* __restrict__ col,
+                             const float* __restrict__ ew, const int32_t* __restrict__ in_len,
+                             const double* __restrict__ wsum, const float* __restrict__ X,
+                             float* __restrict__ Y, int B4, double scale) {
+  const RowChunk ch = chunks[blockIdx.x];
+  const int c4 = blockIdx.y * blockDim.x + threadIdx.x;
+  if (c4 >= B4) return;
+  const float4* __restrict__ X4 = reinterpret_cast<const float4*>(X);
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 8
+  for (int e = 0; e < ch.len; ++e) {
+    const int a = col[ch.start + e];
+    float w = ew ? ew[ch.start + e] : 1.f;
+    if (FORWARD) w /= wsum ? (float)wsum[a] : (float)in_len[a];
+    const float4 x = X4[(int64_t)a * B4 + c4];
+    acc.x += w * x.x;
+    acc.y += w * x.y;
+    acc.z += w * x.z;
+    acc.w += w * x.w;
+  }
+  const float rs =
+      FORWARD ? 1.f : (float)scale / (wsum ? (float)wsum[ch.row] : (float)in_len[ch.row]);
+  atomicAdd(reinterpret_cast<float4*>(Y) + (int64_t)ch.row * B4 + c4,
+            make_float4(rs * acc.x, rs * acc.y, rs * acc.z, rs * acc.w));
+}
+
 // Y[a][c] += sum_k xi_k[a] eta_k[x_c] + eta_k[a] xi_k[x_c] for one stored
 // update (tile-blocked panels P[T][which][k][128]); the panel values at the
 // block's columns are staged in shared memory.
@@ -223,12 +253,33 @@ static void partial_sim_block_t(const ChunkList& fwd, const ChunkList& hor, cons
   k_col_unit<T><<<(B + 127) / 128, 128, 0, st>>>(cols, B, xs);
   const int ygroups = (B + 127) / 128;
   const int tpb = B >= 128 ? 128 : (B + 31) / 32 * 32;
+  // FP32 blocks of a multiple of 4 columns: four columns per thread
+  const bool vec4 = sizeof(T) == 4 && B % 4 == 0;
+  const int B4 = B / 4;
+  const int tpb4 = B4 >= 256 ? 256 : (B4 + 31) / 32 * 32;
+  const int ygroups4 = (B4 + tpb4 - 1) / tpb4;
+  auto chunk_step = [&](const ChunkList& L, const int32_t* adj, const float* w, bool forward,
+                        const T* X, T* Y, double scale) {
+    if (L.count <= 0) return;
+    if (vec4) {
+      if (forward)
+        k_col_chunk4<true><<<dim3((unsigned)L.count, ygroups4), tpb4, 0, st>>>(
+            L.chunks, adj, w, in_len, wv.wsum, (const float*)X, (float*)Y, B4, scale);
+      else
+        k_col_chunk4<false><<<dim3((unsigned)L.count, ygroups4), tpb4, 0, st>>>(
+            L.chunks, adj, w, in_len, wv.wsum, (const float*)X, (float*)Y, B4, scale);
+    } else if (forward) {
+      k_col_chunk<T, true><<<dim3((unsigned)L.count, ygroups), tpb, 0, st>>>(
+          L.chunks, adj, w, in_len, wv.wsum, X, Y, B, scale);
+    } else {
+      k_col_chunk<T, false><<<dim3((unsigned)L.count, ygroups), tpb, 0, st>>>(
+          L.chunks, adj, w, in_len, wv.wsum, X, Y, B, scale);
+    }
+  };
   for (int t = 1; t <= K; ++t) {
     T* dst = xs + (int64_t)t * blk;
     k_col_fill<T><<<fill_blocks, 256, 0, st>>>(nullptr, 0.0, dst, blk);
-    if (fwd.count > 0)
-      k_col_chunk<T, true><<<dim3((unsigned)fwd.count, ygroups), tpb, 0, st>>>(
-          fwd.chunks, out_col, wv.out_w, in_len, wv.wsum, xs + (int64_t)(t - 1) * blk, dst, B, 1.0);
+    chunk_step(fwd, out_col, wv.out_w, true, xs + (int64_t)(t - 1) * blk, dst, 1.0);
   }
   // Horner: y = x_K; y <- x_{K-t} + C Q y; result (1-C) y (the last step folds the scale)
   const T* y = xs + (int64_t)K * blk;
@@ -241,9 +292,7 @@ static void partial_sim_block_t(const ChunkList& fwd, const ChunkList& hor, cons
     T* dst = (t == K) ? result : bufs[t & 1];
     const double s = (t == K) ? 1.0 - C : 1.0;
     k_col_fill<T><<<fill_blocks, 256, 0, st>>>(xs + (int64_t)(K - t) * blk, s, dst, blk);
-    if (hor.count > 0)
-      k_col_chunk<T, false><<<dim3((unsigned)hor.count, ygroups), tpb, 0, st>>>(
-          hor.chunks, in_col, wv.in_w, in_len, wv.wsum, y, dst, B, s * C);
+    chunk_step(hor, in_col, wv.in_w, false, y, dst, s * C);
     y = dst;
   }
 }
