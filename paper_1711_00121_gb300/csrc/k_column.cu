@@ -92,6 +92,55 @@ __global__ void k_col_chunk4(const RowChunk* __restrict__ chunks, const int32_t*
             make_float4(rs * acc.x, rs * acc.y, rs * acc.z, rs * acc.w));
 }
 
+// Narrow blocks (B = BW <= 4 columns, e.g. the two old columns of one update):
+// one warp per row chunk (a chunk has at most 32 nonzeros), one nonzero per
+// lane, the chunk's sums combined across the warp and added by lane 0.  The
+// forward step reads X already divided by the in-degree (or in-weight) of
+// each row (k_col_prescale), so a nonzero costs one gather and one multiply.
+template <typename T, bool FORWARD, int BW>
+__global__ void k_col_chunk_narrow(const RowChunk* __restrict__ chunks, int64_t count,
+                                   const int32_t* __restrict__ col, const float* __restrict__ ew,
+                                   const int32_t* __restrict__ in_len,
+                                   const double* __restrict__ wsum, const T* __restrict__ X,
+                                   T* __restrict__ Y, double scale) {
+  const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (q >= count) return;  // the whole warp leaves together
+  const RowChunk ch = chunks[q];
+  T acc[BW];
+#pragma unroll
+  for (int c = 0; c < BW; ++c) acc[c] = T(0);
+  if (lane < ch.len) {
+    const int64_t e = ch.start + lane;
+    const int a = col[e];
+    const T w = ew ? (T)ew[e] : T(1);
+#pragma unroll
+    for (int c = 0; c < BW; ++c) acc[c] = w * X[(int64_t)a * BW + c];
+  }
+#pragma unroll
+  for (int c = 0; c < BW; ++c)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+  if (lane == 0) {
+    const T rs = FORWARD ? T(1) : (T)scale / (wsum ? (T)wsum[ch.row] : (T)in_len[ch.row]);
+#pragma unroll
+    for (int c = 0; c < BW; ++c) atomicAdd(&Y[(int64_t)ch.row * BW + c], rs * acc[c]);
+  }
+}
+
+// Z[a][c] = X[a][c] / (in-degree of a, or its in-weight), a < n_rows, c < B
+template <typename T>
+__global__ void k_col_prescale(const T* __restrict__ X, const int32_t* __restrict__ in_len,
+                               const double* __restrict__ wsum, int B, int64_t count,
+                               T* __restrict__ Z) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = e / B;
+    const T d = wsum ? (T)wsum[a] : (T)in_len[a];
+    Z[e] = d != T(0) ? X[e] / d : T(0);
+  }
+}
+
 // Y[a][c] += sum_k xi_k[a] eta_k[x_c] + eta_k[a] xi_k[x_c] for one stored
 // update (tile-blocked panels P[T][which][k][128]); the panel values at the
 // block's columns are staged in shared memory.
@@ -258,10 +307,40 @@ static void partial_sim_block_t(const ChunkList& fwd, const ChunkList& hor, cons
   const int B4 = B / 4;
   const int tpb4 = B4 >= 256 ? 256 : (B4 + 31) / 32 * 32;
   const int ygroups4 = (B4 + tpb4 - 1) / tpb4;
+  // narrow blocks: one warp per chunk; the forward input divided once per row
+  const bool narrow = B <= 4;
+  auto narrow_step = [&](const ChunkList& L, const int32_t* adj, const float* w, bool forward,
+                         const T* X, T* Y, double scale) {
+    const unsigned grid = (unsigned)((L.count + 7) / 8);
+#define SR_NARROW(BW)                                                                          \
+  do {                                                                                         \
+    if (forward)                                                                               \
+      k_col_chunk_narrow<T, true, BW><<<grid, 256, 0, st>>>(L.chunks, L.count, adj, w, in_len,  \
+                                                            wv.wsum, X, Y, scale);             \
+    else                                                                                       \
+      k_col_chunk_narrow<T, false, BW><<<grid, 256, 0, st>>>(L.chunks, L.count, adj, w, in_len, \
+                                                             wv.wsum, X, Y, scale);            \
+  } while (0)
+    switch (B) {
+      case 1: SR_NARROW(1); break;
+      case 2: SR_NARROW(2); break;
+      case 3: SR_NARROW(3); break;
+      default: SR_NARROW(4); break;
+    }
+#undef SR_NARROW
+  };
   auto chunk_step = [&](const ChunkList& L, const int32_t* adj, const float* w, bool forward,
                         const T* X, T* Y, double scale) {
     if (L.count <= 0) return;
-    if (vec4) {
+    if (narrow) {
+      if (forward) {
+        // y0 is free until the Horner steps: it holds X divided by the row degrees
+        k_col_prescale<T><<<fill_blocks, 256, 0, st>>>(X, in_len, wv.wsum, B, blk, y0);
+        narrow_step(L, adj, w, true, y0, Y, scale);
+      } else {
+        narrow_step(L, adj, w, false, X, Y, scale);
+      }
+    } else if (vec4) {
       if (forward)
         k_col_chunk4<true><<<dim3((unsigned)L.count, ygroups4), tpb4, 0, st>>>(
             L.chunks, adj, w, in_len, wv.wsum, (const float*)X, (float*)Y, B4, scale);
