@@ -85,6 +85,12 @@ struct simrank_ctx {
   int32_t* g0_in_len = nullptr;
   ChunkList g0_fwd, g0_hor, cur_fwd, cur_hor;
   int64_t cur_fwd_cap = 0, cur_hor_cap = 0;
+  // column mode: host copies of cur_fwd / cur_hor with the first chunk of
+  // every row, kept current row by row between updates
+  std::vector<RowChunk> hfwd, hhor;
+  std::vector<int64_t> ffwd, fhor;
+  bool col_chunks_ok = false;
+  int col_last_i = -1, col_last_j = -1;
   std::vector<void*> hist;  // per-update panel snapshots (tile-blocked, S precision)
   // one-shot batch scratch (grow-only)
   struct Buf {
@@ -986,12 +992,36 @@ simrank_status run_one_shot(simrank_ctx* h, const std::map<int32_t, std::vector<
   return SR_OK;
 }
 
-// Row chunks (at most kChunk nonzeros each) of the adjacency rows [0, n_rows).
-void build_chunks(const HostAdj& A, int n_rows, std::vector<RowChunk>& out) {
+// Row chunks (at most kChunk nonzeros each) of the adjacency rows [0, n_rows);
+// first (optional) gets the index of each row's first chunk (n_rows + 1).
+void build_chunks(const HostAdj& A, int n_rows, std::vector<RowChunk>& out,
+                  std::vector<int64_t>* first = nullptr) {
   out.clear();
-  for (int a = 0; a < n_rows; ++a)
+  int64_t total = 0;
+  for (int a = 0; a < n_rows; ++a) total += (A.len[a] + kChunk - 1) / kChunk;
+  out.reserve((size_t)total);
+  if (first) first->assign((size_t)n_rows + 1, 0);
+  for (int a = 0; a < n_rows; ++a) {
+    if (first) (*first)[a] = (int64_t)out.size();
     for (int off = 0; off < A.len[a]; off += kChunk)
       out.push_back({a, std::min(kChunk, A.len[a] - off), A.start[a] + off});
+  }
+  if (first) (*first)[n_rows] = (int64_t)out.size();
+}
+
+// Rewrites row a's chunks of a list built by build_chunks (with first) after
+// a change of that row, on the host and on the device; false if the row's
+// number of chunks changed (the list must be rebuilt).
+bool patch_row_chunks(simrank_ctx* h, const HostAdj& A, int a, std::vector<RowChunk>& v,
+                      const std::vector<int64_t>& first, ChunkList& L) {
+  const int64_t c0 = first[a], nc = first[a + 1] - c0;
+  if ((A.len[a] + kChunk - 1) / kChunk != nc) return false;
+  for (int64_t c = 0; c < nc; ++c)
+    v[c0 + c] = {a, std::min(kChunk, A.len[a] - (int)(c * kChunk)), A.start[a] + c * kChunk};
+  if (nc > 0 && cudaMemcpyAsync(L.chunks + c0, v.data() + c0, nc * sizeof(RowChunk),
+                                cudaMemcpyHostToDevice, h->st) != cudaSuccess)
+    return false;
+  return true;
 }
 
 simrank_status upload_chunks(simrank_ctx* h, const std::vector<RowChunk>& v, ChunkList& L,
@@ -1038,7 +1068,7 @@ simrank_status run_column_update(simrank_ctx* h, int i, int j, int op, int d_j, 
   h->launches += 2 * K + 6 + K;
   const size_t pbytes = (size_t)h->nT_cap * 2 * h->K1 * PT * (f32 ? 4 : 8);
   void* snap = nullptr;
-  CUDA_TRY(h, cudaMalloc(&snap, pbytes));
+  CUDA_TRY(h, cudaMallocAsync(&snap, pbytes, h->st));
   h->hist.push_back(snap);
   CUDA_TRY(h, cudaMemcpyAsync(snap, f32 ? (void*)h->P32 : (void*)h->P64, pbytes,
                               cudaMemcpyDeviceToDevice, h->st));
@@ -1135,8 +1165,10 @@ void free_ctx(simrank_ctx* h) {
                      h->g0_hor.chunks, h->cur_fwd.chunks, h->cur_hor.chunks};
   for (void* p : colptrs)
     if (p) cudaFree(p);
+  // the panel snapshots come from the stream-ordered allocator
   for (void* p : h->hist)
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, h->st);
+  if (!h->hist.empty()) cudaStreamSynchronize(h->st);
   for (auto& e : h->events) {
     cudaEventDestroy(e.first);
     cudaEventDestroy(e.second);
@@ -1460,11 +1492,23 @@ simrank_status simrank_apply_updates(simrank_t h, const simrank_update* u, int64
     h->n_cur = n_after;
     for (int64_t t = 0; t < count; ++t) {
       const int32_t i = um[t].src, j = um[t].dst, op = um[t].op;
-      std::vector<RowChunk> ch;
-      build_chunks(h->hout, h->n_pad, ch);
-      if ((s = upload_chunks(h, ch, h->cur_fwd, &h->cur_fwd_cap)) != SR_OK) return s;
-      build_chunks(h->hin, h->n_pad, ch);
-      if ((s = upload_chunks(h, ch, h->cur_hor, &h->cur_hor_cap)) != SR_OK) return s;
+      // chunk lists of the graph before this update: the previous update
+      // changed out-row col_last_i and in-row col_last_j only
+      bool ok_f = h->col_chunks_ok && h->col_last_i >= 0 &&
+                  patch_row_chunks(h, h->hout, h->col_last_i, h->hfwd, h->ffwd, h->cur_fwd);
+      bool ok_h = h->col_chunks_ok && h->col_last_j >= 0 &&
+                  patch_row_chunks(h, h->hin, h->col_last_j, h->hhor, h->fhor, h->cur_hor);
+      if (!ok_f) {
+        build_chunks(h->hout, h->n_pad, h->hfwd, &h->ffwd);
+        if ((s = upload_chunks(h, h->hfwd, h->cur_fwd, &h->cur_fwd_cap)) != SR_OK) return s;
+      }
+      if (!ok_h) {
+        build_chunks(h->hin, h->n_pad, h->hhor, &h->fhor);
+        if ((s = upload_chunks(h, h->hhor, h->cur_hor, &h->cur_hor_cap)) != SR_OK) return s;
+      }
+      h->col_chunks_ok = true;
+      h->col_last_i = i;
+      h->col_last_j = j;
       std::vector<PatchOp> ops1;
       const int d_j = h->hin.len[j];
       if (op > 0) {
@@ -1665,6 +1709,7 @@ simrank_status simrank_grad(simrank_t h, const int32_t* pa, const int32_t* pb, c
   if ((s = upload_chunks(h, ch, h->cur_fwd, &h->cur_fwd_cap)) != SR_OK) return s;
   build_chunks(h->hin, n_pad, ch);
   if ((s = upload_chunks(h, ch, h->cur_hor, &h->cur_hor_cap)) != SR_OK) return s;
+  h->col_chunks_ok = false;
   WeightView wv;
   if (h->weighted) {
     wv.in_w = h->d_in_w;
