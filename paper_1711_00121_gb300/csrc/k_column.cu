@@ -11,6 +11,8 @@
 // is one dense product per block: Y += A G with A = [xi_k, eta_k of every
 // update] (n x 2 U (K+1), straight from the tile-blocked panels) and G the
 // matching values at the block's columns.
+#include <algorithm>
+
 #include "sr_internal.h"
 
 namespace sr {
@@ -92,39 +94,65 @@ __global__ void k_col_chunk4(const RowChunk* __restrict__ chunks, const int32_t*
             make_float4(rs * acc.x, rs * acc.y, rs * acc.z, rs * acc.w));
 }
 
-// Narrow blocks (B = BW <= 4 columns, e.g. the two old columns of one update):
-// one warp per row chunk (a chunk has at most 32 nonzeros), one nonzero per
-// lane, the chunk's sums combined across the warp and added by lane 0.  The
-// forward step reads X already divided by the in-degree (or in-weight) of
-// each row (k_col_prescale), so a nonzero costs one gather and one multiply.
-template <typename T, bool FORWARD, int BW>
-__global__ void k_col_chunk_narrow(const RowChunk* __restrict__ chunks, int64_t count,
-                                   const int32_t* __restrict__ col, const float* __restrict__ ew,
-                                   const int32_t* __restrict__ in_len,
-                                   const double* __restrict__ wsum, const T* __restrict__ X,
-                                   T* __restrict__ Y, double scale) {
-  const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (q >= count) return;  // the whole warp leaves together
-  const RowChunk ch = chunks[q];
-  T acc[BW];
-#pragma unroll
-  for (int c = 0; c < BW; ++c) acc[c] = T(0);
-  if (lane < ch.len) {
-    const int64_t e = ch.start + lane;
-    const int a = col[e];
-    const T w = ew ? (T)ew[e] : T(1);
-#pragma unroll
-    for (int c = 0; c < BW; ++c) acc[c] = w * X[(int64_t)a * BW + c];
+int num_sms_for_narrow() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+      sms = 152;
   }
+  return sms;
+}
+
+// Narrow blocks (B = BW <= 4 columns, e.g. the two old columns of one update):
+// persistent warps, each taking four row chunks at a time (a chunk has at
+// most 32 nonzeros): an 8-lane group per chunk, up to four nonzeros per lane
+// gathered at once, the group's sums combined by shuffles within the group
+// and added by its first lane.  The forward step reads X already divided by
+// the in-degree (or in-weight) of each row (k_col_prescale).
+template <typename T, bool FORWARD, int BW>
+__global__ void __launch_bounds__(256) k_col_chunk_narrow(
+    const RowChunk* __restrict__ chunks, int64_t count, const int32_t* __restrict__ col,
+    const float* __restrict__ ew, const int32_t* __restrict__ in_len,
+    const double* __restrict__ wsum, const T* __restrict__ X, T* __restrict__ Y, double scale) {
+  const int lane = threadIdx.x & 31, g = lane >> 3, gl = lane & 7;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  // the loop bound depends on the warp only: every lane runs every shuffle
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * 4 < count;
+       w += nwarps) {
+    const int64_t q = w * 4 + g;
+    RowChunk ch;
+    ch.row = 0;
+    ch.len = 0;
+    ch.start = 0;
+    if (q < count) ch = chunks[q];
+    int a[4];
+    T wt[4];
 #pragma unroll
-  for (int c = 0; c < BW; ++c)
+    for (int u = 0; u < 4; ++u) {
+      const int e = gl + 8 * u;
+      a[u] = (e < ch.len) ? col[ch.start + e] : -1;
+      wt[u] = (e < ch.len && ew) ? (T)ew[ch.start + e] : T(1);
+    }
+    T acc[BW];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
-  if (lane == 0) {
-    const T rs = FORWARD ? T(1) : (T)scale / (wsum ? (T)wsum[ch.row] : (T)in_len[ch.row]);
+    for (int c = 0; c < BW; ++c) acc[c] = T(0);
 #pragma unroll
-    for (int c = 0; c < BW; ++c) atomicAdd(&Y[(int64_t)ch.row * BW + c], rs * acc[c]);
+    for (int u = 0; u < 4; ++u)
+      if (a[u] >= 0) {
+#pragma unroll
+        for (int c = 0; c < BW; ++c) acc[c] += wt[u] * X[(int64_t)a[u] * BW + c];
+      }
+#pragma unroll
+    for (int c = 0; c < BW; ++c)
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o, 8);
+    if (gl == 0 && ch.len > 0) {
+      const T rs = FORWARD ? T(1) : (T)scale / (wsum ? (T)wsum[ch.row] : (T)in_len[ch.row]);
+#pragma unroll
+      for (int c = 0; c < BW; ++c) atomicAdd(&Y[(int64_t)ch.row * BW + c], rs * acc[c]);
+    }
   }
 }
 
@@ -311,7 +339,9 @@ static void partial_sim_block_t(const ChunkList& fwd, const ChunkList& hor, cons
   const bool narrow = B <= 4;
   auto narrow_step = [&](const ChunkList& L, const int32_t* adj, const float* w, bool forward,
                          const T* X, T* Y, double scale) {
-    const unsigned grid = (unsigned)((L.count + 7) / 8);
+    // persistent: at most 8 CTAs of 8 warps per SM, four chunks per warp at a time
+    const int64_t want = (L.count + 31) / 32;
+    const unsigned grid = (unsigned)std::min<int64_t>(want, (int64_t)num_sms_for_narrow() * 8);
 #define SR_NARROW(BW)                                                                          \
   do {                                                                                         \
     if (forward)                                                                               \
