@@ -143,6 +143,19 @@ def cpu_baseline_sample(s, d, stream, max_updates=1):
     return done / dt, dt, done
 
 
+def max_over_ranks(values, dist=None, device="cpu"):
+    """Element-wise maximum of per-rank timings over all ranks (an all-reduce
+    with MAX; the values unchanged without a process group).  With N
+    independent replicas the whole-job rate is the units of all ranks divided
+    by the slowest rank's time."""
+    import torch
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -286,13 +299,7 @@ def run_gpu(args, rank, world):
             v64 = per_step / (a4.elapsed_time(b4) / 1000.0)
         sr4.close()
     # max over ranks
-    ms_t = torch.tensor([ms], device="cuda")
-    e2e_t = torch.tensor([e2e_s], device="cuda")
-    if dist:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
-    e2e_s = float(e2e_t.item())
+    ms, e2e_s = max_over_ranks([ms, e2e_s], dist, "cuda")
     updates = args.steps * per_step * world
     value = updates / (ms / 1000.0)
     e2e_val = updates / e2e_s
