@@ -74,3 +74,23 @@ def test_column_mode_stream_fp32(P):
     for c, x in enumerate(cols.tolist()[:6]):
         want = O.inc_sr_all_p(n, s, d, base[:, c], x, st.tolist(), C, K)
         assert np.max(np.abs(got[:, c] - want)) < 1e-6, x
+
+
+@pytest.mark.parametrize("width", [1, 3, 4, 5, 8])
+def test_column_mode_fp32_query_widths(P, width):
+    """FP32 queries of every block form: narrow blocks (one warp per four row
+    chunks, B <= 4), four columns per thread (B a multiple of 4) and one column
+    per thread (other widths), after stored updates, against Alg 7."""
+    n, m, C, K = 900, 8000, 0.6, 9
+    s, d = chung_lu_digraph(n, m, 2.1, 2.1, 61)
+    st = update_stream(n, s, d, 6, 62)
+    sr = P.SimRank(n, s, d, C=C, K=K, s_precision=32, mode=P.MODE_COLUMN)
+    sr.apply_updates(st)
+    rng = np.random.default_rng(63 + width)
+    cols = np.sort(rng.choice(n, size=width, replace=False)).astype(np.int32)
+    got = sr.columns(cols)
+    Q0 = O.transition_matrix(n, s, d, sparse=True)
+    base = O.partial_sim_block(Q0, cols, K, C)
+    for c, x in enumerate(cols.tolist()):
+        want = O.inc_sr_all_p(n, s, d, base[:, c], x, st.tolist(), C, K)
+        assert np.max(np.abs(got[:, c] - want)) < 1e-6, (width, x)
