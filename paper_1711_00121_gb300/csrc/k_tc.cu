@@ -1,23 +1,28 @@
-// Tensor-core (tcgen05) symmetric rank-update of S for the one-shot batch form:
+// Tensor-core (tcgen05) symmetric rank-update of S, used by the deferred and
+// per-update S passes and by the one-shot batch form:
 //   S[I,J] += D_IJ,  S[J,I] += D_IJ^T  (I <= J),   D = A B^T,
 // where row a of A is [xi terms | eta terms] and row a of B is the same row
-// with its two halves swapped, so A B^T = Xi H^T + H Xi^T (proof of Thm 2,
-// Eq. 23-28, applied to all sinks of a batch).  FP32 accuracy from a 3-term
-// split x = hi + lo of the operands:
+// with its two halves swapped, so A B^T = Xi H^T + H Xi^T (Alg 1's
+// S + M + M^T for every pending term; the proof of Thm 2, Eq. 23-28, for all
+// sinks of a batch).  FP32 accuracy from a 3-term split x = hi + lo of the
+// operands:
 //   D = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T,  accumulated in FP32 (TMEM),
 // with hi and lo in TF32 (kind::tf32) or, at twice the tensor rate, in FP16
 // (kind::f16) after a power-of-two scaling of each term (exact, see the pack).
 //
-// One CTA per SM, persistent over the tile-pair list.  Warp 0 issues TMA loads
-// (128 rows x 128 bytes boxes, 128-byte swizzle) into a 2-stage ring; warp 1
-// owns two TMEM accumulators (128 lanes x 128 columns each) and issues
-// tcgen05.mma (M = 128, N = 128, K = 32 bytes) for tile t + 1 while warps 2-9
-// drain tile t: they
-// copy the accumulator (tcgen05.ld) into a padded shared tile and stream
-// S[I,J] and S[J,I] from it with coalesced 16-byte accesses.  Every mbarrier
-// wait is bounded and every stop decision of the epilogue warps is taken by
-// all of them: on timeout the kernel records a status word, skips the
-// remaining work and still frees its TMEM.
+// k_s_update_tc: one CTA per SM, persistent over the tile-pair list.  Warp 0
+// issues TMA loads (128 rows x 128 bytes boxes, 128-byte swizzle) into a
+// 2- or 3-stage ring; warp 1 owns two TMEM accumulators (128 lanes x 128
+// columns each) and issues tcgen05.mma (M = 128, N = 128, K = 32 bytes) for
+// tile t + 1 while warps 2-9 drain tile t, either through a padded shared
+// tile with coalesced 16-byte accesses of S[I,J] (and S[J,I] when both
+// triangles are kept) or straight from registers (wide operands).
+// k_s_update_tc_pair (upper tiles, wide operands): jobs of two tile pairs
+// (I, J), (I, J+1) sharing A(I), one M = 128, N = 256 product per split term
+// into a 256-column accumulator.
+// Every mbarrier wait is bounded and every stop decision of the epilogue
+// warps is taken by all of them: on timeout the kernel records a status word,
+// skips the remaining work and still frees its TMEM.
 #include <cuda.h>
 
 #include "sr_internal.h"
