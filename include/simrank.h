@@ -88,7 +88,8 @@ typedef struct simrank_config {
                              pass and, with FP32 S, for the pass of every unit / sink-block update
                              (or of every group of `defer` pending updates); 0 = CUDA cores */
   int32_t init_max_sweeps;/* cap on Jacobi sweeps of Eq. 1 at init / re-anchor */
-  double init_tol;        /* init stops when a sweep changes S by less than this (max-abs) */
+  double init_tol;        /* init stops when a sweep changes S by less than this (max-abs);
+                             <= 0 selects 1e-13 (sweeps stored in FP32 are floored at 3e-7) */
   int32_t profile;        /* 1: time every S-update launch with CUDA events (simrank_get_stats) */
   int32_t relabel;        /* 1: store nodes of in-degree 0 after the others, so that rows that no
                              update can reach (Thm 4) fill whole tiles; ids in the ABI are unchanged */
@@ -122,13 +123,14 @@ typedef struct simrank_config {
                              both triangles.  Default 1. */
   int32_t vec_fp64;       /* chain = 0 with S in FP32: 1 = xi/eta vectors, gamma and the
                              recurrence in FP64; 0 (default) = in FP32.  On GB300 the FP64 form
-                             makes the pre-update launch about 3.5x slower. */
+                             makes the pre-update launch about 3.3x slower. */
   int32_t reserved[3];
 } simrank_config;
 
 /* Fills *cfg with defaults: C = 0.6, K = 15, s_precision = 32, dense, aff = 1,
- * relabel = 1, upper_only = 1, unit apply, fused update, init_tol = 1e-13,
- * 400 init sweeps. */
+ * relabel = 1, upper_only = 1, unit apply, fused update, tc = 0, defer = 0,
+ * vec_fp64 = 0, init_tol = 0 (= 1e-13), 400 init sweeps.  Host only: needs
+ * no GPU. */
 simrank_status simrank_default_config(simrank_config* cfg);
 
 /* Creates a handle for the graph (src[e] -> dst[e]), e < m, on n nodes.

@@ -96,3 +96,37 @@ def test_plan_batch_matches_oracle_partition(seed):
 def test_plan_batch_rejects_bad_net_count():
     with pytest.raises(P.SimrankError):
         P.plan_batch([(0, 1, 1), (0, 1, 1)], 5)
+
+
+def test_default_config_matches_header():
+    """simrank_default_config is host only; its values are the ones the header
+    documents."""
+    from paper_1711_00121_gb300 import _binding as B
+
+    cfg = B.default_config()
+    assert cfg.C == 0.6 and cfg.K == 15 and cfg.s_precision == 32
+    assert cfg.mode == P.MODE_DENSE and cfg.aff == 1 and cfg.relabel == 1
+    assert cfg.upper_only == 1 and cfg.tc == 0 and cfg.defer == 0 and cfg.vec_fp64 == 0
+    assert cfg.init_tol == 0.0 and cfg.init_max_sweeps == 400
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without the built library the binding raises; there is no CPU fallback."""
+    import subprocess
+    import sys
+
+    code = (
+        "import paper_1711_00121_gb300._binding as B\n"
+        f"B.LIB_PATH = {str(tmp_path / 'missing.so')!r}\n"
+        "B._lib = None\n"
+        "try:\n"
+        "    B.lib()\n"
+        "except ImportError as e:\n"
+        "    print('raised', e)\n"
+        "else:\n"
+        "    raise SystemExit('no error')\n"
+    )
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                       timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert "raised" in r.stdout
