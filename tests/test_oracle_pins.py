@@ -514,3 +514,127 @@ def test_sequential_stream_converges_to_final_fixed_point():
     st = update_stream(n, s, d, 6, 98)
     S_seq, edges = O.sequential_unit_updates(n, s, d, S, st.tolist(), C, 150)
     assert np.max(np.abs(S_seq - _dense_new(n, edges, C))) < 1e-12
+
+
+# ------------------------------------------------ finite-K pins (Thm 2, Alg 7, Thm 4)
+
+def _exact(n, s, d, C):
+    return O.simrank_kron_solve(O.transition_matrix(n, s, d), C)
+
+
+def _edge_arrays(edges):
+    return (np.array([a for a, _ in edges], np.int64), np.array([b for _, b in edges], np.int64))
+
+
+@pytest.mark.parametrize("K", [0, 1, 3, 7])
+def test_one_shot_batch_single_block_equals_inc_usr(K):
+    """A batch that is one sink block is a rank-one change of Q, so the proof
+    of Thm 2 (Eqs 23-28) gives T = Q_new S Q_new^T - Q S Q^T = u w^T + w u^T
+    exactly, and the one-shot series equals Alg 1's M_K + M_K^T at the same K
+    (insert with d_j > 0, insert into an isolated node, delete with d_j > 1 and
+    with d_j = 1, a block of two insertions into one sink)."""
+    n = 11
+    s, d = er_graph(n, 28, 300)
+    C = 0.6
+    edges = set(zip(s.tolist(), d.tolist()))
+    deg = O.in_degrees(n, d)
+    S = _exact(n, s, d, C)
+    j = int(np.argmax(deg))
+    absent = [x for x in range(n) if x != j and (x, j) not in edges]
+    iso = int(np.argmin(deg))
+    i_iso = next(x for x in range(n) if x != iso and (x, iso) not in edges)
+    e_many = next(e for e in sorted(edges) if deg[e[1]] > 1)
+    cases = [(j, [absent[0]], O.INSERT), (iso, [i_iso], O.INSERT),
+             (e_many[1], [e_many[0]], O.DELETE), (j, absent[1:3], O.INSERT)]
+    d1 = next((e for e in sorted(edges) if deg[e[1]] == 1), None)
+    if d1 is not None:
+        cases.append((d1[1], [d1[0]], O.DELETE))
+    for sink, srcs, op in cases:
+        new = (edges | {(x, sink) for x in srcs}) if op > 0 else (edges - {(x, sink) for x in srcs})
+        ns, nd = _edge_arrays(new)
+        one = O.one_shot_batch(n, s, d, ns, nd, S, C, K)
+        alg1 = O.inc_usr(n, s, d, S, sink, srcs, op, C, K)
+        assert np.max(np.abs(one - alg1)) < 1e-13, (sink, srcs, op)
+    # K and K + 1 differ, so an off-by-one in the series length fails above
+    sink, srcs, op = cases[0]
+    ns, nd = _edge_arrays(edges | {(srcs[0], sink)})
+    gap = np.max(np.abs(O.one_shot_batch(n, s, d, ns, nd, S, C, K + 1) - O.inc_usr(n, s, d, S, sink, srcs, op, C, K)))
+    assert gap > 1e-9
+
+
+@pytest.mark.parametrize("K", [0, 2, 5])
+def test_inc_sr_all_p_single_update_finite_k(K):
+    """Alg 7 for one update at the same K as Alg 1: with converged old columns
+    (K_old large) column x equals column x of Alg 1 applied to the exact S;
+    with K_old = K (Alg 7 as printed) it equals Alg 1 applied to the truncated
+    S_K of Eq. 17, whose columns are exactly what Procedure 1 returns.  C0
+    insert, C0 delete with d_j > 1 and with d_j = 1; C2 against Alg 4, C1
+    against Alg 3."""
+    n = 10
+    s, d = er_graph(n, 24, 301)
+    C = 0.6
+    edges = set(zip(s.tolist(), d.tolist()))
+    deg = O.in_degrees(n, d)
+    S = _exact(n, s, d, C)
+    S_K = O.simrank_truncated_series(O.transition_matrix(n, s, d), C, K)
+    j = int(np.argmax(deg))
+    i = next(x for x in range(n) if x != j and (x, j) not in edges)
+    e_many = next(e for e in sorted(edges) if deg[e[1]] > 1)
+    ups = [(i, j, O.INSERT), (e_many[0], e_many[1], O.DELETE)]
+    d1 = next((e for e in sorted(edges) if deg[e[1]] == 1), None)
+    if d1 is not None:
+        ups.append((d1[0], d1[1], O.DELETE))
+    for ii, jj, op in ups:
+        conv = O.inc_usr(n, s, d, S, jj, [ii], op, C, K)
+        trunc = O.inc_usr(n, s, d, S_K, jj, [ii], op, C, K)
+        for x in (0, ii, jj, n - 1):
+            col = O.inc_sr_all_p(n, s, d, S[:, x], x, [(ii, jj, op)], C, K, K_old=200)
+            assert np.max(np.abs(col - conv[:, x])) < 1e-13, (ii, jj, op, x)
+            col = O.inc_sr_all_p(n, s, d, S_K[:, x], x, [(ii, jj, op)], C, K)
+            assert np.max(np.abs(col - trunc[:, x])) < 1e-13, (ii, jj, op, x)
+    # C2: a new source into j (Alg 4 at the same K)
+    lit = O.inc_c2(n, s, d, S, j, C, K)
+    for x in (0, j, n - 1, n):
+        col = O.inc_sr_all_p(n, s, d, S[:, x] if x < n else np.zeros(n), x, [(n, j, 1)], C, K, K_old=200)
+        assert np.max(np.abs(col - lit[:, x])) < 1e-13, ("C2", x)
+    # C1: a new sink fed by i (Alg 3; no truncation enters)
+    lit = O.inc_c1(n, s, d, S, i, C)
+    for x in (0, i, n):
+        col = O.inc_sr_all_p(n, s, d, S[:, x] if x < n else np.zeros(n), x, [(i, n, 1)], C, K, K_old=200)
+        assert np.max(np.abs(col - lit[:, x])) < 1e-13, ("C1", x)
+
+
+def _mask(n, nodes):
+    m = np.zeros(n, bool)
+    m[list(nodes)] = True
+    return m
+
+
+def test_thm4_affected_sets_exact_on_hand_built_tree():
+    """Thm 4 (Eqs 39-41) worked by hand on the tree 0->1, 0->2, 1->3, 2->4,
+    3->5, 4->6 (levels {0}, {1,2}, {3,4}, {5,6}; S is non-zero exactly on
+    pairs of one level).
+    Insert (4, 3), d_3 = 1: F1 = O(3) u O(4) = {5, 6}, F2 = {3, 4}, so
+    A_0 x B_0 = {3} x {3,4,5,6}; M_0 = xi_0 eta_0^T has rows {3}, columns
+    {3,4,5,6} -> A_1 x B_1 = O~(3) x O~({3,4,5,6}) = {5} x {3,5,6}; xi_1 is
+    supported on {5} and eta_1 on {3,5,6}, so M_1 has rows {3,5} and columns
+    {3,4,5,6} -> A_2 x B_2 = {5} x {3,5,6}; xi_2 = 0, so every later set is
+    the same.
+    Delete (1, 3), d_3 = 1: F2 is empty, F1 = O(1) u O(2) = {3, 4}:
+    A_0 x B_0 = {3} x {3,4}, A_1 x B_1 = {5} x {5,6}, and from k = 2 on
+    {5} x {5,6}."""
+    n = 7
+    tree = [(0, 1), (0, 2), (1, 3), (2, 4), (3, 5), (4, 6)]
+    s, d = _edge_arrays(tree)
+    C, K = 0.6, 5
+    S = O.simrank_fixed_point(O.transition_matrix(n, s, d), C)
+    for (i, j, op), want in (
+        ((4, 3, O.INSERT), [({3}, {3, 4, 5, 6}), ({5}, {3, 5, 6})] + [({5}, {3, 5, 6})] * (K - 1)),
+        ((1, 3, O.DELETE), [({3}, {3, 4}), ({5}, {5, 6})] + [({5}, {5, 6})] * (K - 1)),
+    ):
+        _, _, terms = O.inc_usr(n, s, d, S, j, [i], op, C, K, return_terms=True)
+        sets = O.affected_sets(n, s, d, S, i, j, op, K, terms)
+        assert len(sets) == K + 1
+        for k, ((A, B), (wa, wb)) in enumerate(zip(sets, want)):
+            assert np.array_equal(A, _mask(n, wa)), (op, k, np.nonzero(A)[0])
+            assert np.array_equal(B, _mask(n, wb)), (op, k, np.nonzero(B)[0])
