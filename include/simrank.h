@@ -123,7 +123,7 @@ typedef struct simrank_config {
                              both triangles.  Default 1. */
   int32_t vec_fp64;       /* chain = 0 with S in FP32: 1 = xi/eta vectors, gamma and the
                              recurrence in FP64; 0 (default) = in FP32.  On GB300 the FP64 form
-                             makes the pre-update launch about 3.3x slower. */
+                             makes the pre-update launch about 2.3x slower. */
   int32_t reserved[3];
 } simrank_config;
 

@@ -31,8 +31,12 @@
 //
 // The vectors and the arithmetic are FP64 (vec64 = 1, or S in FP64) or FP32;
 // the panels the S pass reads have the precision of S, and lambda and row j
-// of gamma are always FP64.  The atomic accumulation makes the last bit of a
-// result depend on the order of the additions.
+// of gamma are always FP64.  The correction of the rows of S by pending
+// panels is summed in the precision of S (those panels are stored in it).
+// GB300 issues FP64 instructions at 1/64 of the FP32 rate, so the FP64 form
+// keeps per-row factors in shared memory, tests for zero on the integer pipe
+// and leaves the additions of the atomics to L2.  The atomic accumulation
+// makes the last bit of a result depend on the order of the additions.
 #include <algorithm>
 
 #include "sr_internal.h"
@@ -93,14 +97,24 @@ __device__ __forceinline__ bool prep_barrier(unsigned int* count, unsigned int t
   return *s_ok != 0;
 }
 
-__device__ __forceinline__ void red_add(float* p, float v) { atomicAdd(p, v); }
-__device__ __forceinline__ void red_add(double* p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void red_add(float* p, float v) {
+  asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_add(double* p, double v) {
+  asm volatile("red.relaxed.gpu.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
 __device__ __forceinline__ void red_add2(V2<float>* p, float x, float y) {
-  atomicAdd(reinterpret_cast<float2*>(p), make_float2(x, y));
+  asm volatile("red.relaxed.gpu.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(x), "f"(y)
+               : "memory");
 }
 __device__ __forceinline__ void red_add2(V2<double>* p, double x, double y) {
-  atomicAdd(&p->x, x);
-  atomicAdd(&p->y, y);
+  red_add(&p->x, x);
+  red_add(&p->y, y);
+}
+// x != 0 on the integer pipe (GB300 issues FP64 compares at the FP64 rate)
+__device__ __forceinline__ bool nz(float x) { return (__float_as_uint(x) << 1) != 0u; }
+__device__ __forceinline__ bool nz(double x) {
+  return ((unsigned long long)__double_as_longlong(x) << 1) != 0ull;
 }
 // Gathers of the working vectors go through L1: a column with a large
 // out-degree is read by many rows of the same CTA.  Each W[k] is written (by
@@ -183,7 +197,7 @@ __device__ __forceinline__ void seg_emit(int key, V a, V b, Emit emit) {
     }
   }
   const int kprev = __shfl_up_sync(0xffffffffu, key, 1);
-  if (key >= 0 && (lane == 0 || kprev != key) && (a != V(0) || b != V(0))) emit(key, a, b);
+  if (key >= 0 && (lane == 0 || kprev != key) && (nz(a) || nz(b))) emit(key, a, b);
 }
 
 // One thread's contiguous run [e0, e1) of an item's nonzeros (flattened order
@@ -227,7 +241,7 @@ __device__ __forceinline__ void item_gather(const PrepItem& it, const Run& run,
     int r = run.r;
     r_first = r;
     V pa = V(0), pb = V(0);
-    constexpr int B = 8;
+    constexpr int B = sizeof(V) == 8 ? 4 : 8;
     for (int e = e0; e < e1; e += B) {
       int rr[B], bb[B];
       int rc = r;
@@ -255,7 +269,7 @@ __device__ __forceinline__ void item_gather(const PrepItem& it, const Run& run,
           if (r == r_first) {
             fa = pa;
             fb = pb;
-          } else if (pa != V(0) || pb != V(0)) {
+          } else if (nz(pa) || nz(pb)) {
             emit(r, pa, pb);  // row wholly inside this run
           }
           pa = pb = V(0);
@@ -287,7 +301,6 @@ template <typename V>
 struct StepPair {
   int ca, cb;    // columns of the nonzeros (-1: none)
   int kh, kt;    // head / tail row in the tile (-1: none)
-  V ih, itl;     // 1 / in-degree of the head / tail row
   int span;      // warp-uniform: the longest run of lanes sharing a head row
   unsigned fl;   // bits 0-4: take lane + 2^b's head sum; 5: add lane - 1's tail;
                  // 6: emit the head sum; 7: emit the tail sum
@@ -299,7 +312,6 @@ __device__ __forceinline__ StepPair<V> pair_setup(const PrepItem& it, const int*
   const Run run = item_run(it);
   StepPair<V> q;
   q.ca = q.cb = q.kh = q.kt = -1;
-  q.ih = q.itl = V(0);
   auto column = [&](int e, int r) {
     const int ce = e - it.e0;
     return (ce < it.clen) ? cc[it.cbase + ce] : __ldcg(col + it.start[r] + (e - it.off[r]));
@@ -307,15 +319,11 @@ __device__ __forceinline__ StepPair<V> pair_setup(const PrepItem& it, const int*
   if (run.r >= 0) {
     q.kh = run.r;
     q.ca = column(run.e0, q.kh);
-    q.ih = V(1) / (V)it.len[q.kh];
     if (run.e1 - run.e0 == 2) {
       int r2 = q.kh;
       while (run.e0 + 1 >= it.off[r2 + 1]) ++r2;
       q.cb = column(run.e0 + 1, r2);
-      if (r2 != q.kh) {
-        q.kt = r2;
-        q.itl = V(1) / (V)it.len[r2];
-      }
+      if (r2 != q.kh) q.kt = r2;
     }
   }
   const unsigned full = 0xffffffffu;
@@ -341,10 +349,11 @@ __device__ __forceinline__ StepPair<V> pair_setup(const PrepItem& it, const int*
 
 // One step of the recurrence for a thread set up by pair_setup: gathers its
 // (xi_k, eta_k) entries, adds the rows up across the warp and emits each row's
-// sum (times C and 1 / in-degree for xi, 1 / in-degree for eta) into W[k + 1].
+// sum (times C / in-degree for xi, 1 / in-degree for eta; rc / ri hold those
+// factors per row of the item's tile) into W[k + 1].
 template <typename V>
 __device__ __forceinline__ void pair_step(const StepPair<V>& q, const V2<V>* Wk, V2<V>* Wn,
-                                          V Cv) {
+                                          const V* rc, const V* ri) {
   const unsigned full = 0xffffffffu;
   V ha = V(0), hb = V(0), ta = V(0), tb = V(0);
   if (q.ca >= 0) {
@@ -378,10 +387,8 @@ __device__ __forceinline__ void pair_step(const StepPair<V>& q, const V2<V>* Wk,
     ha += pa;
     hb += pb;
   }
-  if ((q.fl & (1u << 6)) && (ha != V(0) || hb != V(0)))
-    red_add2(Wn + q.kh, Cv * ha * q.ih, hb * q.ih);
-  if ((q.fl & (1u << 7)) && (ta != V(0) || tb != V(0)))
-    red_add2(Wn + q.kt, Cv * ta * q.itl, tb * q.itl);
+  if ((q.fl & (1u << 6)) && (nz(ha) || nz(hb))) red_add2(Wn + q.kh, ha * rc[q.kh], hb * ri[q.kh]);
+  if ((q.fl & (1u << 7)) && (nz(ta) || nz(tb))) red_add2(Wn + q.kt, ta * rc[q.kt], tb * ri[q.kt]);
 }
 
 __device__ void prep_patch(const PatchOp* __restrict__ ops, int64_t begin, int64_t end,
@@ -414,6 +421,7 @@ template <typename V, typename TS>
 __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ V red[4][2][PT];
+  __shared__ V rrc[PT], rri[PT];  // C / in-degree and 1 / in-degree of the rows of item 0
   __shared__ unsigned long long mk[PREP_MT][2];
   __shared__ int wsum[PG / 32];
   __shared__ int s_ok;
@@ -425,13 +433,13 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
   PrepItem* items = reinterpret_cast<PrepItem*>(dsm);
   int* cc = reinterpret_cast<int*>(items + (MAXI + 1));
   int* ioff = cc + p.cap;  // [nT + 1]
-  V* coef = reinterpret_cast<V*>(ioff + ((p.nT_cap + 1 + 3) & ~3));
+  // the pending correction of the rows of S is summed in the storage precision of S
+  TS* coef = reinterpret_cast<TS*>(ioff + ((p.nT_cap + 1 + 3) & ~3));
   const TS* __restrict__ S = static_cast<const TS*>(p.S);
   TS* P = static_cast<TS*>(p.P);
   V* sI = static_cast<V*>(p.sI);
   V* sJ = static_cast<V*>(p.sJ);
   V2<V>* W = static_cast<V2<V>*>(p.W);
-  const int nrows = nT * PT;
   const int64_t ldk = p.ldk;
   auto pidx = [ldk](int64_t a, int which, int k) -> int64_t {
     return (((a / PT) * 2 + which) * ldk + k) * PT + (a % PT);
@@ -450,23 +458,25 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
     if (tid == 0 && p.tiles) *p.ntiles = 0;
   }
   {
-    const int64_t total = (int64_t)(K + 1) * nrows;
+    // W[0 .. K] over all n_pad rows, 16 bytes per store (n_pad is a multiple of 128)
+    uint4* w16 = reinterpret_cast<uint4*>(W);
+    const int64_t total = (int64_t)(K + 1) * p.n_pad * (int64_t)sizeof(V2<V>) / 16;
     for (int64_t e = (int64_t)blockIdx.x * PG + tid; e < total; e += (int64_t)G * PG)
-      W[(e / nrows) * (int64_t)p.n_pad + (e % nrows)] = V2<V>{V(0), V(0)};
+      w16[e] = make_uint4(0u, 0u, 0u, 0u);
   }
   if (np > 0) {
     // c_x[q] = sum_t xi_q[I_t], c_e[q] = sum_t eta_q[I_t]; the same at j
     for (int q = tid; q < np; q += PG) {
-      V cx = V(0), ce = V(0);
+      TS cx = TS(0), ce = TS(0);
       for (int t = 0; t < p.delta; ++t) {
         const int64_t x = p.I[t];
-        cx += (V)P[pidx(x, 0, q)];
-        ce += (V)P[pidx(x, 1, q)];
+        cx += P[pidx(x, 0, q)];
+        ce += P[pidx(x, 1, q)];
       }
       coef[q] = cx;
       coef[np + q] = ce;
-      coef[2 * np + q] = (V)P[pidx(p.j, 0, q)];
-      coef[3 * np + q] = (V)P[pidx(p.j, 1, q)];
+      coef[2 * np + q] = P[pidx(p.j, 0, q)];
+      coef[3 * np + q] = P[pidx(p.j, 1, q)];
     }
     __syncthreads();
   }
@@ -478,13 +488,18 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
     V vI = V(0), vJ = V(0);
     for (int u = part; u < p.delta; u += 4) vI += (V)s_at(S, p.ld, p.I[u], a, p.upper != 0);
     if (part == 3) vJ = (V)s_at(S, p.ld, p.j, a, p.upper != 0);
-    // S_cur[x, a] = S[x, a] + sum_q xi_q[x] eta_q[a] + eta_q[x] xi_q[a]
+    // S_cur[x, a] = S[x, a] + sum_q xi_q[x] eta_q[a] + eta_q[x] xi_q[a]: the
+    // pending terms are FP32 panels of an FP32 S, so they are added in FP32
+    // (on GB300 an FP64 FMA issues at 1/64 of the FP32 rate)
+    TS cI = TS(0), cJ = TS(0);
     for (int q = part; q < np; q += 4) {
-      const V xa = (V)P[pidx(a, 0, q)];
-      const V ea = (V)P[pidx(a, 1, q)];
-      vI += coef[q] * ea + coef[np + q] * xa;
-      vJ += coef[2 * np + q] * ea + coef[3 * np + q] * xa;
+      const TS xa = P[pidx(a, 0, q)];
+      const TS ea = P[pidx(a, 1, q)];
+      cI += coef[q] * ea + coef[np + q] * xa;
+      cJ += coef[2 * np + q] * ea + coef[3 * np + q] * xa;
     }
+    vI += (V)cI;
+    vJ += (V)cJ;
     red[part][0][r] = vI;
     red[part][1][r] = vJ;
     // nonzeros of the tile after the patch (row j is being patched by CTA 0:
@@ -626,7 +641,7 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
         W[a] = V2<V>{x0, g};
         P[pidx(a, 0, koff)] = (TS)x0;
         P[pidx(a, 1, koff)] = (TS)g;
-        pe = (g != V(0));
+        pe = nz(g);
       }
       const int any_e = __syncthreads_or(pe);
       if (tid == 0) {
@@ -645,13 +660,20 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
   if (pair0) {
     q0 = pair_setup<V>(items[0], cc, p.in.col);
     rb0 = (int64_t)items[0].T * PT;
+    if (tid < PT) {
+      const int len = items[0].len[tid];
+      const V inv = len > 0 ? V(1) / (V)len : V(0);
+      rri[tid] = inv;
+      rrc[tid] = Cv * inv;
+    }
+    __syncthreads();
   }
   for (int k = 0; alive && k < K; ++k) {
     const V2<V>* Wk = W + (int64_t)k * p.n_pad;
     V2<V>* Wn = W + (int64_t)(k + 1) * p.n_pad;
     for (int u = 0; u < my_items; ++u) {
       if (u == 0 && pair0) {
-        pair_step<V>(q0, Wk, Wn + rb0, Cv);
+        pair_step<V>(q0, Wk, Wn + rb0, rrc, rri);
         continue;
       }
       PrepItem& it = items[min(u, MAXI)];
@@ -681,10 +703,13 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
         for (int q = 0; q < PT / 32; ++q) {
           const int64_t a = (int64_t)T * PT + q * 32 + lane;
           const V2<V> v = ld_v2(Wk + a);
-          P[pidx(a, 0, koff + k)] = (TS)v.x;
-          P[pidx(a, 1, koff + k)] = (TS)v.y;
-          nx |= (v.x != V(0));
-          ne |= (v.y != V(0));
+          // the mask bits follow the stored panel values (a value that rounds
+          // to zero in the precision of S adds nothing to S)
+          const TS px = (TS)v.x, pe = (TS)v.y;
+          P[pidx(a, 0, koff + k)] = px;
+          P[pidx(a, 1, koff + k)] = pe;
+          nx |= nz(px);
+          ne |= nz(pe);
         }
         const unsigned bx = __ballot_sync(0xffffffffu, nx), be = __ballot_sync(0xffffffffu, ne);
         const unsigned long long bit = 1ull << (k & 63);
@@ -753,10 +778,10 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
   }
 }
 
-template <typename V>
+template <typename TS>
 size_t prep_smem(int cap, int nT_cap, int npend_max) {
   return (size_t)(MAXI + 1) * sizeof(PrepItem) + (size_t)cap * sizeof(int) +
-         (size_t)((nT_cap + 1 + 3) & ~3) * sizeof(int) + (size_t)4 * npend_max * sizeof(V);
+         (size_t)((nT_cap + 1 + 3) & ~3) * sizeof(int) + (size_t)4 * npend_max * sizeof(TS);
 }
 
 }  // namespace
@@ -765,9 +790,8 @@ int launch_prep(const PrepParams& prm, int s_prec, int vec64, int npend_max, int
                 int max_ctas, int64_t nnz_bound, cudaStream_t st) {
   if (prm.nT <= 0) return 0;
   if (prm.item < 0 || prm.cap < 0 || (prm.cap & 3)) return 1;
-  const bool v64 = (s_prec == 64) || vec64;
-  const size_t smem = v64 ? prep_smem<double>(prm.cap, prm.nT_cap, npend_max)
-                          : prep_smem<float>(prm.cap, prm.nT_cap, npend_max);
+  const size_t smem = (s_prec == 64) ? prep_smem<double>(prm.cap, prm.nT_cap, npend_max)
+                                     : prep_smem<float>(prm.cap, prm.nT_cap, npend_max);
   const void* fn = (s_prec == 64) ? (const void*)k_prep<double, double>
                    : vec64        ? (const void*)k_prep<double, float>
                                   : (const void*)k_prep<float, float>;
