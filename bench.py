@@ -2,19 +2,25 @@
 
 Workload (the power-law update stream): directed Chung-Lu graph, n = 20,000,
 in/out-degree exponent 2.1, mean degree 10 (m = 200,000), C = 0.6, K = 20,
-S in FP32 (1.6 GB, larger than L2; upper tiles kept), xi/eta vectors in FP32,
-affected-area pruning on.  One step applies a batch of 1,000 sequential unit
-updates (80% insertions with degree-biased endpoints, 20% deletions of
-uniform existing edges); each update runs Alg 1 (one cooperative launch for
-its recurrence) and its rank-2(K+1) S change is applied by the tensor-core S
-pass (3-term FP16 split), 16 pending updates per pass by default (--defer /
---tc / --vec-fp64 select the other forms).  Steps continue one valid stream, so every step changes the graph.
+S in FP32 (1.6 GB, larger than L2; upper tiles kept), xi/eta recurrence
+vectors in FP64, affected-area pruning on.  One step applies a batch of 1,000
+sequential unit updates (80% insertions with degree-biased endpoints, 20%
+deletions of uniform existing edges); each update runs Alg 1 (one cooperative
+launch for its recurrence) and its rank-2(K+1) S change is applied by the
+tensor-core S pass (3-term FP16 split), 16 pending updates per pass by
+default (--defer / --tc / --vec-fp64 select the other forms).  Steps
+continue one valid stream, so every step changes the graph.
 
-Prints one JSON line (see the keys below).  ``--impl reference`` times the
-FP64 CPU oracle (Alg 1 as printed, dense) on a bounded sample instead.
-Under torchrun each rank runs an independent replica of the workload (the
-update stream is sequential and has no data-parallel split).
-Other workloads (--workload batched / multi / column) print their own line.
+Prints one JSON line (see the keys below): the device-timed throughput, the
+same through the public call with host buffers (e2e), the two kernels of the
+path against their roofline, the per-edge S pass alone, the other vector
+precision over the same steps, and the max-abs error against the FP64 oracle
+(Alg 1 at the same K on sampled columns, and the drift from the converged
+fixed point after one step).  ``--impl reference`` times the FP64 CPU oracle
+(Alg 1 as printed, dense) on a bounded sample instead.  Under torchrun each
+rank runs an independent replica of the workload (the update stream is
+sequential and has no data-parallel split).  Other workloads (--workload
+batched / multi / column / grad / tree) print their own line.
 """
 from __future__ import annotations
 
@@ -39,9 +45,18 @@ UPDATES_PER_STEP = 1000
 SEED_GRAPH, SEED_STREAM = 2, 3
 METRIC = "edge updates/sec & HBM GB/s: fused rank-2K ΔS vs plain Inc-uSR at 1e-6 error"
 UNIT = "edge updates/s"
-WORKLOAD = ("power-law update stream: directed Chung-Lu n=20000, exponent 2.1, mean degree 10, "
-            "C=0.6, K=20, FP32 S, FP32 vectors, AFF pruning, 1000 sequential unit updates per step "
-            "(80% insert / 20% delete), rank-2(K+1) S changes applied by the tensor-core S pass")
+# DRAM bytes (read + write) per launch from one ncu capture of each kernel on
+# the default stream configuration (profiles/ holds the summaries)
+TRAFFIC_PREP = 3.287e7
+TRAFFIC_S_PASS = 1.661e9
+
+
+def workload_name(args):
+    vec = "FP64" if args.vec_fp64 else "FP32"
+    return ("power-law update stream: directed Chung-Lu n=20000, exponent 2.1, mean degree 10, "
+            f"C=0.6, K=20, FP32 S, {vec} xi/eta vectors, AFF pruning, 1000 sequential unit updates "
+            "per step (80% insert / 20% delete), rank-2(K+1) S changes applied by the tensor-core "
+            "S pass")
 
 
 def read_bf16_peak():
@@ -173,7 +188,7 @@ def run_reference(args, rank):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * statistics.mean(per), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N, "m": M, "C": C, "K": K,
+        "config": {"workload": workload_name(args), "n": N, "m": M, "C": C, "K": K,
                    "l2": "S larger than L2 (1.6 GB FP32)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "one unit update per step at full n (Alg 1, dense FP64), "
@@ -181,6 +196,73 @@ def run_reference(args, rank):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def stream_prep_bytes(n_pad, m, k, pair_bytes, npend_avg, delta=1):
+    """Algorithmic bytes of one pre-update launch (k_prep): each of the K
+    steps reads the column indices (4 B per nonzero) and reads and writes one
+    (xi, eta) pair column (pair_bytes per row each way; the gathered values
+    are re-reads of that column and are not counted again); the panels are
+    written once (2 (K+1) n FP32 values); the rows of S read (delta + 1 rows
+    of FP32) and the pending panels read to correct them (2 n FP32 values per
+    pending term)."""
+    steps = k * (4 * m + 2 * n_pad * pair_bytes)
+    panels = 2 * (k + 1) * n_pad * 4
+    rows = (delta + 1) * n_pad * 4
+    pending = npend_avg * 2 * n_pad * 4
+    return steps + panels + rows + pending
+
+
+def stream_accuracy(P, s, d, stream0, form, cuda_stream, n_updates, seed=7):
+    """max-abs error of the benchmarked form against the FP64 oracle.
+
+    same_k: a fresh handle applies the first ``n_updates`` updates of the
+    stream; sampled columns are compared with Alg 1 applied update by update
+    at the same K in FP64 (oracle.alg1_stream_columns), whose initial S is the
+    converged fixed point (Procedure 1 at K = 80: C^81 / (1 - C) < 1e-17).
+    drift: the same form at K = 60 (truncation below 1e-13) applies the whole
+    first step; sampled columns are compared with the converged fixed point of
+    Eq. 1 on the graph after that step (Procedure 1 at K = 80)."""
+    from oracle import simrank_oracle as O
+
+    K_FP, K_CONV = 80, 60
+    ups = stream0[:n_updates]
+    Q0 = O.transition_matrix(N, s, d, sparse=True)
+    rng = np.random.default_rng(seed)
+    query = sorted(set(rng.choice(N, 12, replace=False).tolist())
+                   | {int(x) for x in ups[-1, :2]} | {int(ups[0, 1])})
+    h = P.SimRank(N, s, d, C=C, K=K, s_precision=32, aff=1, stream=cuda_stream, **form)
+    h.apply_updates(ups)
+    got = h.columns(np.array(query, np.int32))
+    h.close()
+    t0 = time.perf_counter()
+    want = O.alg1_stream_columns(N, s, d, lambda c: O.partial_sim_block(Q0, c, K_FP, C),
+                                 ups.tolist(), C, K, query)
+    oracle_s = time.perf_counter() - t0
+    same_k = float(np.max(np.abs(got - want)))
+    # drift over one full step at a K where truncation has vanished
+    h = P.SimRank(N, s, d, C=C, K=K_CONV, s_precision=32, aff=1, stream=cuda_stream, **form)
+    h.apply_updates(stream0)
+    edges = set(zip(s.tolist(), d.tolist()))
+    for i, j, op in stream0.tolist():
+        if op > 0:
+            edges.add((i, j))
+        else:
+            edges.discard((i, j))
+    fs = np.array([a for a, _ in edges], np.int32)
+    fd = np.array([b for _, b in edges], np.int32)
+    qcols = np.array(sorted(set(rng.choice(N, 12, replace=False).tolist())
+                            | {int(x) for x in stream0[-1, :2]}), np.int32)
+    got = h.columns(qcols)
+    h.close()
+    want = O.partial_sim_block(O.transition_matrix(N, fs, fd, sparse=True), qcols, K_FP, C)
+    drift = float(np.max(np.abs(got - want)))
+    return {"max_abs_same_k": same_k,
+            "same_k": f"first {len(ups)} updates of the stream at K={K} vs FP64 Alg 1 per update "
+                      f"(oracle, {len(query)} sampled columns, {oracle_s:.1f} s on the host)",
+            "max_abs_vs_fixed_point_after_step": drift,
+            "drift": f"the same form at K={K_CONV} after the {len(stream0)} updates of one step vs "
+                     f"the converged fixed point of Eq. 1 on the final graph ({qcols.size} columns)"}
 
 
 def run_gpu(args, rank, world):
@@ -208,42 +290,51 @@ def run_gpu(args, rank, world):
         packed.append((t, arr.size))
     form = dict(defer=args.defer, tc=args.tc, vec_fp64=args.vec_fp64)
 
-    def handle(profile):
+    def handle(profile, **over):
+        kw = dict(form)
+        kw.update(over)
         h = P.SimRank(N, s, d, C=C, K=K, s_precision=32, aff=1, profile=profile,
-                      stream=stream.cuda_stream, **form)
+                      stream=stream.cuda_stream, **kw)
         h.sync()
         return h
 
     def apply(h, t):
         h.apply_updates_ptr(packed[t][0].data_ptr(), packed[t][1])
 
-    # ---- value: device-timed steps (no per-launch profiling on this handle)
-    sr = handle(0)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
-        for t in range(args.warmup):
-            apply(sr, t)
-        sr.sync()
-        st0 = sr.stats()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        with ClockSampler(local) as clk:
+    def timed_steps(h, clocks=False):
+        """W untimed steps, then the K timed steps bracketed by events."""
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            for t in range(args.warmup):
+                apply(h, t)
+            h.sync()
+            st0 = h.stats()
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            clk = ClockSampler(local) if clocks else None
+            if clk:
+                clk.__enter__()
             ev0.record(stream)
             for t in range(args.warmup, total):
-                apply(sr, t)
+                apply(h, t)
             ev1.record(stream)
             torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        ms = ev0.elapsed_time(ev1)
-        st1 = sr.stats()
-        # drift re-anchor (FP64 Jacobi sweeps of Eq. 1 from the current S)
-        ra0 = time.perf_counter()
-        ra_change = sr.reanchor(2)
-        sr.sync()
-        reanchor_ms = (time.perf_counter() - ra0) * 1000.0 / 2
+            if clk:
+                clk.__exit__(None, None, None)
+            if dist:
+                dist.barrier()
+        return ev0.elapsed_time(ev1), st0, h.stats(), clk
+
+    # ---- value: device-timed steps of the headline form (no per-launch profiling)
+    sr = handle(0)
+    ms, st0, st1, clk = timed_steps(sr, clocks=True)
+    # drift re-anchor (FP64 Jacobi sweeps of Eq. 1 from the current S)
+    ra0 = time.perf_counter()
+    ra_change = sr.reanchor(2)
+    sr.sync()
+    reanchor_ms = (time.perf_counter() - ra0) * 1000.0 / 2
     sr.close()
     del sr
     torch.cuda.empty_cache()
@@ -267,8 +358,8 @@ def run_gpu(args, rank, world):
     sr2.close()
     del sr2
     torch.cuda.empty_cache()
-    # ---- per-kernel times: a third replica with CUDA events around every
-    # launch, over the first timed step (kernel times, phase split, roofline)
+    # ---- per-kernel times: a replica with CUDA events around every launch,
+    # over the first timed step (kernel times, phase split, roofline)
     sr3 = handle(1)
     with torch.cuda.stream(stream):
         for t in range(args.warmup):
@@ -281,23 +372,33 @@ def run_gpu(args, rank, world):
     sr3.close()
     del sr3
     torch.cuda.empty_cache()
-    # ---- the same stream with FP64 xi/eta vectors (one step after one warm-up
-    # step), the precision form with FP64 recurrence vectors
-    v64 = None
-    if not args.vec_fp64 and total >= 2:
-        form64 = dict(form, vec_fp64=1)
-        sr4 = P.SimRank(N, s, d, C=C, K=K, s_precision=32, aff=1, stream=stream.cuda_stream,
-                        **form64)
-        with torch.cuda.stream(stream):
-            apply(sr4, 0)
-            sr4.sync()
-            a4, b4 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a4.record(stream)
-            apply(sr4, 1)
-            b4.record(stream)
-            sr4.sync()
-            v64 = per_step / (a4.elapsed_time(b4) / 1000.0)
+    # ---- the per-edge S pass (each update's rank-2(K+1) change applied alone,
+    # an HBM-bound read-modify-write of the affected tiles), profiled replica
+    sr5 = handle(1, defer=0)
+    pe_n = min(args.per_edge_updates, per_step)
+    with torch.cuda.stream(stream):
+        sr5.apply_updates(streams[0][:8])
+        sr5.sync()
+        e0 = sr5.stats()
+        sr5.apply_updates(streams[0][8:8 + pe_n])
+        sr5.sync()
+        e1 = sr5.stats()
+    sr5.close()
+    del sr5
+    torch.cuda.empty_cache()
+    # ---- the other vector precision over the same timed steps
+    other = None
+    if total >= 2:
+        o_fp64 = 0 if args.vec_fp64 else 1
+        sr4 = handle(0, vec_fp64=o_fp64)
+        oms, _, _, oclk = timed_steps(sr4, clocks=True)
         sr4.close()
+        del sr4
+        torch.cuda.empty_cache()
+        other = {"vectors": "f64" if o_fp64 else "f32",
+                 "value": args.steps * per_step / (oms / 1000.0), "unit": UNIT,
+                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": oms / args.steps,
+                 "clocks": oclk.summary()}
     # max over ranks
     ms, e2e_s = max_over_ranks([ms, e2e_s], dist, "cuda")
     updates = args.steps * per_step * world
@@ -319,16 +420,21 @@ def run_gpu(args, rank, world):
     terms = G * (K + 1)
     rg = (terms + 63) // 64 * 64 if args.tc == 2 else (terms + 31) // 32 * 32
     n_pad = (N + 127) // 128 * 128
+    entries = pd["tiles_touched"] * 128 * 128
+    # useful arithmetic of the method: each touched entry of S takes the
+    # 2 G (K+1) rank-one terms of the pass, one FMA (2 flops) each
+    method_flops = entries * 2 * terms * 2
     if args.tc:
         eb = 2 if args.tc == 2 else 4
         operand_bytes = launches * n_pad * (2 * rg) * eb * 2  # hi and lo operands
-        flops = pd["tiles_touched"] * 128 * 128 * (2 * rg) * 2 * 3
+        hw_flops = entries * (2 * rg) * 2 * 3  # three split products, padded inner dim
     else:
         operand_bytes = launches * 2 * terms * n_pad * 4
-        flops = pd["tiles_touched"] * 128 * 128 * 2 * terms * 2
+        hw_flops = method_flops
     sp_bytes = pd["s_bytes"] + operand_bytes
     sp_gbs = sp_bytes / (sp_ms / 1000.0) / 1e9 if sp_ms > 0 else 0.0
-    sp_tflops = flops / (sp_ms / 1000.0) / 1e12 if sp_ms > 0 else 0.0
+    sp_tflops = hw_flops / (sp_ms / 1000.0) / 1e12 if sp_ms > 0 else 0.0
+    sp_method_tflops = method_flops / (sp_ms / 1000.0) / 1e12 if sp_ms > 0 else 0.0
     # wide operands (at least 1 KB of K per row) take jobs of two tile pairs
     # sharing their row tile, one N = 256 product per split term
     paired = bool(args.tc) and 2 * rg * (2 if args.tc == 2 else 4) >= 1024
@@ -347,36 +453,65 @@ def run_gpu(args, rank, world):
         s_pass = {"kernel": sp_name, "bound": "hbm", "achieved": sp_gbs, "peak": peak,
                   "unit": "GB/s", "frac": sp_gbs / peak, "peak_kind": peak_kind,
                   "tflops": sp_tflops}
+    s_pass.update({"method_tflops": sp_method_tflops,
+                   "method_flops_note": "4(K+1) flops per touched entry per update; the hardware "
+                                        "figure counts the 3 split products and the inner "
+                                        f"dimension padded from {2 * terms} to {2 * rg}"})
     # DRAM bytes (read + write) per launch from one ncu capture of each kernel
     # on this workload (n = 20,000, K = 20, 16 pending updates, FP16 split,
-    # FP32 vectors); null for any other form
-    profiled = (N, K, args.defer, args.tc, args.vec_fp64) == (20000, 20, 16, 2, 0)
-    s_pass.update({"traffic": 1.6629e9 if profiled else None,
+    # FP64 vectors); null for any other form
+    profiled = (N, K, args.defer, args.tc, args.vec_fp64) == (20000, 20, 16, 2, 1)
+    s_pass.update({"traffic": TRAFFIC_S_PASS if profiled else None,
                    "bytes_per_launch": sp_bytes / max(launches, 1),
                    "ms_per_launch": sp_ms / max(launches, 1), "launches": launches})
-    # k_prep: one launch per update; algorithmic bytes = the graph read K+1
-    # times, the gathered (xi, eta) pairs, the two S rows and the panel writes
+    # k_prep: one launch per update, latency-bound (L2-resident working set)
     prep_ms = phase[0]
-    prep_bytes_1 = ((K + 1) * (M * 4 + n_pad * 12) + K * M * 16 + 2 * N * 4
-                    + 2 * (K + 1) * n_pad * 4)
-    prep_gbs = prep_bytes_1 * per_step / (prep_ms / 1000.0) / 1e9 if prep_ms > 0 else 0.0
-    prep = {"kernel": "k_prep (cooperative: patch, rows of S, gamma, K recurrence steps, masks, "
-                      "tile list)", "bound": "hbm", "achieved": prep_gbs, "peak": peak,
-            "unit": "GB/s", "frac": prep_gbs / peak, "peak_kind": peak_kind,
-            "traffic": 3.0725e7 if profiled else None,
-            "bytes_per_launch": prep_bytes_1, "ms_per_launch": prep_ms / per_step,
+    pair_bytes = 16 if args.vec_fp64 else 8
+    npend_avg = ((G - 1) / 2.0) * (K + 1) if args.defer > 1 else 0.0
+    prep_bytes_1 = stream_prep_bytes(n_pad, M, K, pair_bytes, npend_avg)
+    prep_us = 1000.0 * prep_ms / per_step
+    prep_gbs = prep_bytes_1 / (prep_us / 1e6) / 1e9 if prep_ms > 0 else 0.0
+    prep = {"kernel": "k_prep<" + ("double" if args.vec_fp64 else "float") + ", float> "
+                      "(cooperative: patch, rows of S, gamma, K recurrence steps, masks)",
+            "bound": "latency", "achieved": prep_gbs, "peak": peak, "unit": "GB/s",
+            "frac": prep_gbs / peak, "peak_kind": peak_kind,
+            "traffic": TRAFFIC_PREP if profiled else None,
+            "bytes_per_launch": prep_bytes_1, "us_per_launch": prep_us,
+            "us_per_step": prep_us / (K + 4), "grid_barriers": K + 3,
             "launches": per_step,
-            "note": "latency-bound (L2-resident working set, K+4 grid barriers per launch)"}
+            "note": "algorithmic bytes as stream_prep_bytes states; L2-resident working set, so "
+                    "the time is set by K + 3 grid barriers and one L2 round trip per step"}
+    # the per-edge S pass (each update alone)
+    pe_launches = e1["s_update_launches"] - e0["s_update_launches"]
+    pe_ms = e1["s_update_ms"] - e0["s_update_ms"]
+    pe_terms = K + 1
+    pe_rg = (pe_terms + 63) // 64 * 64 if args.tc == 2 else (pe_terms + 31) // 32 * 32
+    pe_ops = pe_launches * n_pad * (2 * pe_rg) * (2 if args.tc == 2 else 4) * 2 if args.tc else \
+        pe_launches * 2 * pe_terms * n_pad * 4
+    pe_bytes = (e1["s_bytes"] - e0["s_bytes"]) + pe_ops
+    pe_gbs = pe_bytes / (pe_ms / 1000.0) / 1e9 if pe_ms > 0 else 0.0
+    s_pass_per_edge = {"kernel": ("k_s_update_tc (tcgen05, " + split + ")") if args.tc
+                       else "k_s_update_ws", "bound": "hbm", "achieved": pe_gbs, "peak": peak,
+                       "unit": "GB/s", "frac": pe_gbs / peak, "peak_kind": peak_kind,
+                       "launches": pe_launches, "ms_per_launch": pe_ms / max(pe_launches, 1),
+                       "bytes_per_launch": pe_bytes / max(pe_launches, 1),
+                       "aff_tile_fraction": (e1["tiles_touched"] - e0["tiles_touched"])
+                       / max(e1["tiles_total"] - e0["tiles_total"], 1),
+                       "note": "each update's S change applied alone (--defer 0), S bytes of the "
+                               "touched upper tiles read + written, plus the operands once"}
     dominant = s_pass if sp_ms >= prep_ms else prep
     tiles_touched = st1["tiles_touched"] - st0["tiles_touched"]
     tiles_total = st1["tiles_total"] - st0["tiles_total"]
+    vec = "f64" if args.vec_fp64 else "f32"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N, "m": M, "C": C, "K": K,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": f"{vec} xi/eta vectors, f32 S, 3x{'f16' if args.tc == 2 else 'tf32'} split S pass",
+        "data": "synthetic",
+        "config": {"workload": workload_name(args), "n": N, "m": M, "C": C, "K": K,
                    "updates_per_step": per_step, "defer": args.defer, "tc": args.tc,
-                   "vectors": "f64" if args.vec_fp64 else "f32", "storage": "upper tiles",
+                   "vectors": vec, "storage": "upper tiles",
                    "l2": "inputs larger than L2 (S is 1.6 GB FP32)",
                    "aff_tile_fraction": tiles_touched / max(tiles_total, 1),
                    "s_bytes_gbs_step": (st1["s_bytes"] - st0["s_bytes"]) / (ms / 1000.0) / 1e9,
@@ -386,16 +521,19 @@ def run_gpu(args, rank, world):
                                           "s_pass"], phase)},
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": dominant,
-        "kernels": {"s_pass": s_pass, "prep": prep},
+        "kernels": {"s_pass": s_pass, "prep": prep, "s_pass_per_edge": s_pass_per_edge},
         "reanchor": {"ms_per_sweep": reanchor_ms, "max_change_last_sweep": ra_change,
                      "note": "FP64 Jacobi sweep of Eq. 1 on the n=20000 S after the timed steps"},
-        "fp64_vectors": {"value": v64, "unit": UNIT, "steps": 1,
-                         "note": "same stream, xi/eta vectors and recurrence in FP64"},
+        "other_vectors": other,
         "e2e": {"value": e2e_val, "unit": UNIT,
                 "h2d_bytes_per_step": int(packed[0][1] * 16), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(st1["kernel_launches"] - st0["kernel_launches"]),
         "clocks": clk.summary(),
     }
+    if rank == 0 and args.accuracy_updates > 0:
+        line["accuracy"] = stream_accuracy(P, s, d, streams[0], form, stream.cuda_stream,
+                                           args.accuracy_updates)
+        line["max_abs"] = line["accuracy"]["max_abs_same_k"]
     if rank == 0 and not args.no_cpu_baseline:
         v, dt, n_up = cpu_baseline_sample(s, d, streams[0], 1)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(),
@@ -753,7 +891,12 @@ def main():
                     help="stream workload: rank-one updates kept pending per S pass (0 = apply each)")
     ap.add_argument("--tc", type=int, default=2,
                     help="S passes on the tensor cores: 1 = 3xTF32 split, 2 = 3xFP16 split")
-    ap.add_argument("--vec-fp64", type=int, default=0, help="xi/eta vectors in FP64 (default FP32)")
+    ap.add_argument("--vec-fp64", type=int, default=1,
+                    help="xi/eta recurrence vectors in FP64 (default; 0 = FP32)")
+    ap.add_argument("--per-edge-updates", type=int, default=64,
+                    help="stream workload: updates of the per-edge S-pass replica")
+    ap.add_argument("--accuracy-updates", type=int, default=32,
+                    help="stream workload: updates checked against the same-K FP64 oracle (0 = skip)")
     ap.add_argument("--workload", default="stream",
                     choices=["stream", "batched", "multi", "column", "grad"],
                     help="stream: the benchmarked update stream; batched: one-shot vs per-edge; "

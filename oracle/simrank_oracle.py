@@ -616,6 +616,63 @@ def sequential_unit_updates(n_final, src, dst, S, updates, C, K):
     return S, sorted(edges)
 
 
+def alg1_stream_columns(n, src, dst, S0_block, updates, C, K, query):
+    """Alg 1 applied to each update of a stream in order, returning only the
+    columns ``query`` of the final S (for graphs whose dense S is too large).
+
+    Every update is Alg 1 exactly as in :func:`inc_usr` (w from the old Q and
+    the old column(s) of the sources, lambda and gamma by the d_j branch,
+    xi_{k+1} = C Q xi_k + C (v^T xi_k) u, eta_{k+1} = Q eta_k + (v^T eta_k) u);
+    only the storage of S differs: S_t = S_0 + sum_{u <= t} (M_u + M_u^T) is
+    kept as S_0 plus the factors of each M_u = sum_k xi_k eta_k^T, and a
+    column of the current S is read as S_0[:, x] + sum_u (Xi_u H_u[x, :]^T
+    + H_u Xi_u[x, :]^T).  ``S0_block(cols)`` returns the columns ``cols`` of
+    S_0 (n x len(cols)).  Updates are unit updates between existing nodes.
+    """
+    edges = set(zip(np.asarray(src).tolist(), np.asarray(dst).tolist()))
+    need = sorted({int(x) for u in updates for x in u[:2]} | {int(x) for x in query})
+    base = S0_block(need)
+    pos = {x: c for c, x in enumerate(need)}
+    Xi, H = [], []  # per update: n x (K+1) factor matrices
+
+    def column(x):
+        col = np.array(base[:, pos[x]], np.float64)
+        for A, B in zip(Xi, H):
+            col += A @ B[x, :] + B @ A[x, :]
+        return col
+
+    for i, j, op in updates:
+        i, j, op = int(i), int(j), int(op)
+        if i >= n or j >= n:
+            raise ValueError("alg1_stream_columns handles existing nodes only")
+        s_arr = np.array([a for a, _ in edges], np.int64)
+        d_arr = np.array([b for _, b in edges], np.int64)
+        Q = transition_matrix(n, s_arr, d_arr, sparse=True)
+        d = int(in_degrees(n, d_arr)[j])
+        Si, Sj = column(i), column(j)
+        w = np.asarray(Q @ Si).ravel()
+        u, v = rank_one_factors(Q, d, j, [i], op)
+        gamma, _ = gamma_sink_block(w, Sj, Si[i], Sj[j], d, 1, op, C, j)
+        A = np.zeros((n, K + 1))
+        B = np.zeros((n, K + 1))
+        xi = np.zeros(n)
+        xi[j] = C
+        eta = gamma.copy()
+        A[:, 0], B[:, 0] = xi, eta
+        for k in range(K):
+            xi_next = C * np.asarray(Q @ xi).ravel() + C * float(v @ xi) * u
+            eta_next = np.asarray(Q @ eta).ravel() + float(v @ eta) * u
+            xi, eta = xi_next, eta_next
+            A[:, k + 1], B[:, k + 1] = xi, eta
+        Xi.append(A)
+        H.append(B)
+        if op > 0:
+            edges.add((i, j))
+        else:
+            edges.discard((i, j))
+    return np.stack([column(int(x)) for x in query], axis=1)
+
+
 # ----------------------------------------------------------------------------
 # One-shot batch form (rank-2r Sylvester): the definition written out
 # ----------------------------------------------------------------------------

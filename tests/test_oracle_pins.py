@@ -638,3 +638,18 @@ def test_thm4_affected_sets_exact_on_hand_built_tree():
         for k, ((A, B), (wa, wb)) in enumerate(zip(sets, want)):
             assert np.array_equal(A, _mask(n, wa)), (op, k, np.nonzero(A)[0])
             assert np.array_equal(B, _mask(n, wb)), (op, k, np.nonzero(B)[0])
+
+
+@pytest.mark.parametrize("K", [0, 3, 10])
+def test_alg1_stream_columns_equals_dense_sequential(K):
+    """The column form of a sequential Alg 1 stream equals the dense form
+    (sequential_unit_updates, pinned above) column by column at the same K."""
+    n = 14
+    s, d = er_graph(n, 40, 310)
+    C = 0.6
+    S = _exact(n, s, d, C)
+    st = update_stream(n, s, d, 7, 311)
+    dense, _ = O.sequential_unit_updates(n, s, d, S, st.tolist(), C, K)
+    query = [0, 3, 7, int(st[0, 1]), n - 1]
+    cols = O.alg1_stream_columns(n, s, d, lambda c: S[:, c], st.tolist(), C, K, query)
+    assert np.max(np.abs(cols - dense[:, query])) < 1e-13
