@@ -292,8 +292,9 @@ void simrank_multi_destroy(simrank_multi_t h);
  * n <= 8192 nodes and K <= 31; larger sizes return SR_ERR_ARG.
  *
  * Applies the insertion (op = +1) or deletion (op = -1) of the edge i -> j
- * (0 <= i, j < n, i != j) to S in place, as Alg 1 / Thm 9 at truncation K with
- * the fused, affected-area-pruned S update of simrank_apply_updates.
+ * (0 <= i, j < n, i != j) to S in place: the same change at truncation K that
+ * simrank_apply_updates makes to a dense handle (fused S update, tiles outside
+ * the affected area skipped).
  *  S: device, FP32 or FP64 (s_precision = 32 / 64), row-major with row pitch
  *     ld elements; ld is a multiple of 128 and >= n rounded up to 128, S holds
  *     that many rows, and the padding rows and columns are zero.  On entry S
@@ -302,8 +303,11 @@ void simrank_multi_destroy(simrank_multi_t h);
  *     graph (row a lists every b with an edge b -> a); new_row_ptr / new_col
  *     the same for the graph after the update.  d_j is the old in-degree of j.
  *  cuda_stream: the stream all work is queued on (NULL = default stream).
- * Returns once the work is queued; errors are reported through
- * simrank_last_error(NULL).  All calls share the one scratch array, which
+ * Returns once the work is queued; argument and launch errors are reported
+ * by the status and simrank_last_error(NULL).  The kernels of this entry
+ * point wait on nothing on the device (no grid barrier, no mbarrier), so no
+ * timeout can arise; an error while they run shows at the caller's next
+ * synchronisation of cuda_stream.  All calls share the one scratch array, which
  * keeps the last call's contents (the parts that must start at zero are
  * cleared by each call): calls whose work overlaps on the GPU, from any
  * thread or stream, race and give wrong results.  The first call on each

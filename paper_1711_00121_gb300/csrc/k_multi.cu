@@ -553,14 +553,9 @@ void launch_multi_prep(int s_prec, const MultiGraphDesc* descs, const MultiStep*
                        const int* count, int grid, const int32_t* srcs, const PatchOp* ops,
                        double C, int K, int aff, uint64_t* tiles, int* ntiles, cudaStream_t st) {
   if (grid <= 0) return;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_multi_prep<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         SMEM_BYTES);
-    cudaFuncSetAttribute(k_multi_prep<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         SMEM_BYTES);
-    attr = true;
-  }
+  static std::atomic<unsigned long long> attr64{0}, attr32{0};
+  smem_attr_once((const void*)k_multi_prep<double>, SMEM_BYTES, attr64);
+  smem_attr_once((const void*)k_multi_prep<float>, SMEM_BYTES, attr32);
   if (s_prec == 64)
     k_multi_prep<double><<<grid, MT, SMEM_BYTES, st>>>(descs, steps, count, srcs, ops, C, K, aff,
                                                        tiles, ntiles);

@@ -481,35 +481,24 @@ void launch_s_update(void* S, int s_prec, int64_t ld, const void* P, int K1, con
   const int mirror = upper ? 0 : 1;
   if (s_prec == 64) {
     const size_t smem = (4ull * KC_F64 * PT + (size_t)PT * DP) * sizeof(double);
-    static bool attr64 = false;
-    if (!attr64) {
-      cudaFuncSetAttribute(k_s_update<double, KC_F64, 1, OneGraphTiles<double>>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr64 = true;
-    }
+    static std::atomic<unsigned long long> attr64{0};
+    smem_attr_once((const void*)k_s_update<double, KC_F64, 1, OneGraphTiles<double>>, (int)smem, attr64);
     OneGraphTiles<double> src{(double*)S, ld,        (const double*)P, tiles, mXi,
                               mEta,       use_masks, n,                mirror};
     k_s_update<double, KC_F64, 1><<<grid, 256, smem, st>>>(src, K1, ntiles, k0, k1,
                                                              (unsigned long long*)counters);
   } else if (ws_wait_limit > 0) {
     const size_t smem = (4ull * WS_KC * PT + 2ull * PT * DP) * sizeof(float);
-    static bool attr_ws = false;
-    if (!attr_ws) {
-      cudaFuncSetAttribute(k_s_update_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr_ws = true;
-    }
+    static std::atomic<unsigned long long> attr_ws{0};
+    smem_attr_once((const void*)k_s_update_ws, (int)smem, attr_ws);
     k_s_update_ws<<<grid, WS_THREADS, smem, st>>>((float*)S, ld, (const float*)P, K1, tiles, ntiles,
                                                   mXi, mEta, k0, k1, use_masks, n, mirror,
                                                   ws_wait_limit,
                                                   (unsigned long long*)counters);
   } else {
     const size_t smem = (4ull * KC_F32 * PT + (size_t)PT * DP) * sizeof(float);
-    static bool attr32 = false;
-    if (!attr32) {
-      cudaFuncSetAttribute(k_s_update<float, KC_F32, 2, OneGraphTiles<float>>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr32 = true;
-    }
+    static std::atomic<unsigned long long> attr32{0};
+    smem_attr_once((const void*)k_s_update<float, KC_F32, 2, OneGraphTiles<float>>, (int)smem, attr32);
     OneGraphTiles<float> src{(float*)S, ld, (const float*)P, tiles, mXi, mEta, use_masks, n, mirror};
     k_s_update<float, KC_F32, 2><<<grid, 256, smem, st>>>(src, K1, ntiles, k0, k1,
                                                             (unsigned long long*)counters);
@@ -521,23 +510,15 @@ void launch_s_update_multi(int s_prec, const MultiGraphDesc* descs, const uint64
                            cudaStream_t st) {
   if (s_prec == 64) {
     const size_t smem = (4ull * KC_F64 * PT + (size_t)PT * DP) * sizeof(double);
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_s_update<double, KC_F64, 1, ManyGraphTiles<double>>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    smem_attr_once((const void*)k_s_update<double, KC_F64, 1, ManyGraphTiles<double>>, (int)smem, attr);
     ManyGraphTiles<double> src{descs, tiles};
     k_s_update<double, KC_F64, 1><<<grid, 256, smem, st>>>(src, K1, ntiles, 0, K1,
                                                              (unsigned long long*)counters);
   } else {
     const size_t smem = (4ull * KC_F32 * PT + (size_t)PT * DP) * sizeof(float);
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_s_update<float, KC_F32, 2, ManyGraphTiles<float>>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    smem_attr_once((const void*)k_s_update<float, KC_F32, 2, ManyGraphTiles<float>>, (int)smem, attr);
     ManyGraphTiles<float> src{descs, tiles};
     k_s_update<float, KC_F32, 2><<<grid, 256, smem, st>>>(src, K1, ntiles, 0, K1,
                                                             (unsigned long long*)counters);

@@ -88,6 +88,21 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
   return false;
 }
 
+// Wait with a fixed bound of its own, for draining copies and MMAs in flight
+// after a stop (their completion does not depend on any other thread).
+__device__ __forceinline__ void mbar_drain_wait(uint32_t bar, uint32_t parity) {
+  for (long long it = 0; it < (1ll << 24); ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return;
+  }
+}
+
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
                                             uint32_t bar) {
   asm volatile(
@@ -258,6 +273,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __shared__ __align__(8) uint64_t bar_acc_full[2], bar_acc_empty[2];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
+  __shared__ __align__(8) uint64_t bar_drain;  // MMAs still in flight after a stop
+  uint32_t it_issued = 0;                    // stages the TMA thread has loaded
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
@@ -276,6 +293,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mbar_init(smem_u32(&bar_acc_full[b]), 1);
       mbar_init(smem_u32(&bar_acc_empty[b]), 256);
     }
+    mbar_init(smem_u32(&bar_drain), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -315,6 +333,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           tma_load_2d(st + 3 * OPB, &tm_lo, kb_b * KCH, r.rowJ, fb);
         }
       }
+      it_issued = it;
       if (!ok) abort_flag = 1;
     }
   } else if (warp == 1) {
@@ -482,6 +501,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
 
   __syncthreads();
+  if (abort_flag) {
+    // a stop on timeout can leave TMA loads and MMAs of this CTA in flight:
+    // wait for them (bounded on their own) before shared memory and TMEM go
+    if (warp == 0 && lane == 0) {
+      const uint32_t from = it_issued > (uint32_t)STAGES ? it_issued - (uint32_t)STAGES : 0u;
+      for (uint32_t i = from; i < it_issued; ++i)
+        mbar_drain_wait(smem_u32(&bar_full[i % STAGES]), (i / STAGES) & 1u);
+    }
+    if (warp == 1 && lane == 0) {
+      mma_commit(smem_u32(&bar_drain));
+      mbar_drain_wait(smem_u32(&bar_drain), 0u);
+    }
+  }
   if (threadIdx.x == 0 && abort_flag) atomicExch(&counters[CNT_STATUS], (unsigned long long)SR_ERR_TIMEOUT);
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -542,6 +574,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __shared__ __align__(8) uint64_t bar_acc_full[2], bar_acc_empty[2];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
+  __shared__ __align__(8) uint64_t bar_drain;  // MMAs still in flight after a stop
+  uint32_t it_issued = 0;                    // stages the TMA thread has loaded
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
@@ -558,6 +592,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mbar_init(smem_u32(&bar_acc_full[b]), 1);
       mbar_init(smem_u32(&bar_acc_empty[b]), 256);
     }
+    mbar_init(smem_u32(&bar_drain), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -602,6 +637,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
         }
       }
+      it_issued = it;
       if (!ok) abort_flag = 1;
     }
   } else if (warp == 1) {
@@ -720,6 +756,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
 
   __syncthreads();
+  if (abort_flag) {
+    // a stop on timeout can leave TMA loads and MMAs of this CTA in flight:
+    // wait for them (bounded on their own) before shared memory and TMEM go
+    if (warp == 0 && lane == 0) {
+      const uint32_t from = it_issued > (uint32_t)STAGES ? it_issued - (uint32_t)STAGES : 0u;
+      for (uint32_t i = from; i < it_issued; ++i)
+        mbar_drain_wait(smem_u32(&bar_full[i % STAGES]), (i / STAGES) & 1u);
+    }
+    if (warp == 1 && lane == 0) {
+      mma_commit(smem_u32(&bar_drain));
+      mbar_drain_wait(smem_u32(&bar_drain), 0u);
+    }
+  }
   if (threadIdx.x == 0 && abort_flag) atomicExch(&counters[CNT_STATUS], (unsigned long long)SR_ERR_TIMEOUT);
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <unordered_set>
@@ -219,6 +220,21 @@ void launch_tile_list(const uint64_t* mXi, const uint64_t* mEta, int nT, int aff
 // S[I,J] += sum_{k in [k0,k1)} xi_k[I] eta_k[J]^T + eta_k[I] xi_k[J]^T, and the
 // mirrored tile S[J,I], over the tile list.  n = current node count (for the
 // algorithmic byte counters).
+// Raises a kernel's dynamic shared-memory limit once per device: the attribute
+// belongs to the current device's context, so each device of the process needs
+// its own call (bit d of `done` records device d; devices past 63 set it on
+// every launch).  Two threads may both set it; that is harmless.
+inline cudaError_t smem_attr_once(const void* fn, int bytes, std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+  return e;
+}
+
 // With S in FP32 and ws_wait_limit > 0 the warp-specialised kernel runs (its
 // mbarrier waits are bounded by ws_wait_limit iterations); otherwise the
 // single-role kernel.
