@@ -69,6 +69,13 @@ enum { SR_APPLY_UNIT = 0,        /* each update in order, one rank-one update ea
        SR_APPLY_ONE_SHOT = 2 };  /* whole batch as one rank-2r update (proof of Thm 2, Eq. 23-28) */
 enum { SR_SUPDATE_FUSED = 0,     /* one read-modify-write pass of S per update: S += Xi H^T + H Xi^T */
        SR_SUPDATE_PLAIN = 1 };   /* K+1 passes, one rank-2 term xi_k eta_k^T + eta_k xi_k^T each (Alg 1 as printed) */
+enum { SR_INIT_SWEEPS = 0,       /* S of the initial graph by Jacobi sweeps of Eq. 1 (batch SimRank) */
+       SR_INIT_FOREST = 1,       /* S of a forest of arborescences in closed form (Example 2, §1):
+                                    every node has at most one in-neighbour and no cycle */
+       SR_INIT_COMPONENTS = 2 }; /* S block-diagonal over the weakly connected components of the
+                                    initial graph (Example 1, §1): each group of components (up to
+                                    4096 nodes, or one larger component) gets its own Jacobi sweeps
+                                    of Eq. 1; nodes are stored component by component */
 
 typedef struct simrank_config {
   double C;               /* damping factor, 0 < C < 1 (Eq. 1) */
@@ -124,7 +131,19 @@ typedef struct simrank_config {
   int32_t vec_fp64;       /* chain = 0 with S in FP32: 1 = xi/eta vectors, gamma and the
                              recurrence in FP64; 0 (default) = in FP32.  On GB300 the FP64 form
                              makes the pre-update launch about 2.3x slower. */
-  int32_t reserved[3];
+  int32_t init_form;      /* SR_INIT_SWEEPS (default), SR_INIT_FOREST or SR_INIT_COMPONENTS: how
+                             simrank_init computes S when S0 is NULL (dense mode).  With
+                             SR_INIT_FOREST the initial graph must be a forest of arborescences
+                             (else SR_ERR_ARG).  The edges left out of the initial graph (the
+                             non-tree edges; the edges between blocks) are then applied as
+                             updates: Examples 2 and 1's use of incremental SimRank as a batch
+                             accelerator.  SR_INIT_COMPONENTS sets its own node order (relabel
+                             is ignored). */
+  int32_t reanchor_every; /* dense mode: 0 = off; N > 0 = after every N accepted updates of
+                             apply_updates, run Jacobi sweeps of Eq. 1 from the current S
+                             (the drift correction of simrank_reanchor) until a sweep changes S
+                             by less than init_tol, at most reanchor_sweeps of them */
+  int32_t reanchor_sweeps;/* cap on the sweeps of one automatic re-anchor (0 = 4) */
 } simrank_config;
 
 /* Fills *cfg with defaults: C = 0.6, K = 15, s_precision = 32, dense, aff = 1,
@@ -193,7 +212,11 @@ typedef struct simrank_stats {
                                [2] affected tile list (chain = 1) and deferred S passes,
                                [3] per-update S pass */
   int32_t init_sweeps;
-  int32_t reserved[7];
+  int32_t reanchors;         /* automatic re-anchors run (reanchor_every) */
+  double reanchor_residual;  /* max-abs residual of Eq. 1, max |C Q S Q^T + (1-C) I - S|, at
+                                the last automatic re-anchor, before it (its first sweep's change) */
+  double reanchor_change;    /* max-abs change of that re-anchor's last sweep */
+  int32_t reserved[2];
 } simrank_stats;
 simrank_status simrank_get_stats(simrank_t h, simrank_stats* out);
 

@@ -23,4 +23,7 @@ from ._binding import (  # noqa: F401
     APPLY_ONE_SHOT,
     SUPDATE_FUSED,
     SUPDATE_PLAIN,
+    INIT_SWEEPS,
+    INIT_FOREST,
+    INIT_COMPONENTS,
 )

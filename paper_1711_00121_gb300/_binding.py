@@ -23,6 +23,7 @@ STATUS_NAMES = {
 MODE_DENSE, MODE_COLUMN = 0, 1
 APPLY_UNIT, APPLY_SINK_BLOCKS, APPLY_ONE_SHOT = 0, 1, 2
 SUPDATE_FUSED, SUPDATE_PLAIN = 0, 1
+INIT_SWEEPS, INIT_FOREST, INIT_COMPONENTS = 0, 1, 2
 
 
 class SimrankError(RuntimeError):
@@ -43,7 +44,8 @@ class Config(ctypes.Structure):
         ("prep_ctas", ctypes.c_int32), ("prep_cache", ctypes.c_int32),
         ("multi_launch", ctypes.c_int32), ("prep_item", ctypes.c_int32),
         ("upper_only", ctypes.c_int32), ("vec_fp64", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("init_form", ctypes.c_int32), ("reanchor_every", ctypes.c_int32),
+        ("reanchor_sweeps", ctypes.c_int32),
     ]
 
 
@@ -60,7 +62,9 @@ class Stats(ctypes.Structure):
         ("s_update_launches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
         ("s_update_ms", ctypes.c_double),
         ("init_residual", ctypes.c_double), ("phase_ms", ctypes.c_double * 4),
-        ("init_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7),
+        ("init_sweeps", ctypes.c_int32), ("reanchors", ctypes.c_int32),
+        ("reanchor_residual", ctypes.c_double), ("reanchor_change", ctypes.c_double),
+        ("reserved", ctypes.c_int32 * 2),
     ]
 
 

@@ -35,6 +35,7 @@ struct simrank_ctx {
   int device = 0;
   int num_sms = 0;
   int n_cur = 0, n_cap = 0, n_pad = 0, nT_cap = 0, K1 = 0;
+  int64_t since_anchor = 0;  // updates since the last automatic re-anchor
   int64_t ld = 0;
   bool weighted = false;
   // caller id <-> storage id (identity unless cfg.relabel)
@@ -717,7 +718,8 @@ simrank_status run_rank_one(simrank_ctx* h, int64_t src_off, int delta, int j, i
 // in FP32 storage with FP64 accumulation.  Stops when a sweep changes S by
 // less than `tol` (max-abs) or after max_sweeps; S is symmetrised at the end.
 simrank_status jacobi_sweeps(simrank_ctx* h, int max_sweeps, double tol, double* last_diff,
-                             int* sweeps_done, double* tol_used = nullptr) {
+                             int* sweeps_done, double* tol_used = nullptr,
+                             double* first_diff = nullptr) {
   const int sp = h->cfg.s_precision;
   const size_t elems = (size_t)h->n_pad * h->ld;
   const size_t fp64_budget = (size_t)48 << 30;
@@ -763,6 +765,7 @@ simrank_status jacobi_sweeps(simrank_ctx* h, int max_sweeps, double tol, double*
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     if (e != cudaSuccess) break;
     std::memcpy(&diff, &bits, sizeof(diff));
+    if (it == 1 && first_diff) *first_diff = diff;
     if (diff < tol) break;
   }
   if (e == cudaSuccess) {
@@ -781,6 +784,40 @@ simrank_status jacobi_sweeps(simrank_ctx* h, int max_sweeps, double tol, double*
   *last_diff = diff;
   *sweeps_done = it;
   if (tol_used) *tol_used = tol;
+  return SR_OK;
+}
+
+// Drift correction: Jacobi sweeps of Eq. 1 started from the current S (its
+// lower tiles restored from their mirrors first when only the upper ones are
+// kept), until a sweep changes S by less than tol or after `sweeps` sweeps.
+// The first sweep's change is the residual max |C Q S Q^T + (1-C) I - S| of
+// the S it started from.
+simrank_status reanchor_run(simrank_ctx* h, int sweeps, double tol, double* first, double* last,
+                            int* done) {
+  if (upper(h)) {
+    launch_mirror_lower(h->S, h->cfg.s_precision, h->n_pad, h->ld, h->st);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(h, SR_ERR_CUDA, cudaGetErrorString(e));
+  }
+  return jacobi_sweeps(h, sweeps, tol, last, done, nullptr, first);
+}
+
+// Counts accepted rank-one work towards the automatic re-anchor
+// (cfg.reanchor_every) and runs it when due; pending panels are applied first.
+simrank_status maybe_reanchor(simrank_ctx* h, int64_t updates) {
+  if (h->column || h->cfg.reanchor_every <= 0) return SR_OK;
+  h->since_anchor += updates;
+  if (h->since_anchor < h->cfg.reanchor_every) return SR_OK;
+  h->since_anchor = 0;
+  simrank_status s = flush_pending(h);
+  if (s != SR_OK) return s;
+  double first = 0.0, last = 0.0;
+  int done = 0;
+  if ((s = reanchor_run(h, h->cfg.reanchor_sweeps, h->cfg.init_tol, &first, &last, &done)) != SR_OK)
+    return s;
+  h->stats.reanchors += 1;
+  h->stats.reanchor_residual = first;
+  h->stats.reanchor_change = last;
   return SR_OK;
 }
 
@@ -1240,6 +1277,16 @@ simrank_status simrank_init(const simrank_config* cfg_in, int32_t n, int64_t m, 
     return fail(nullptr, SR_ERR_ARG, "the tensor-core update needs s_precision = 32");
   if (cfg.init_tol <= 0.0) cfg.init_tol = 1e-13;
   if (cfg.init_max_sweeps <= 0) cfg.init_max_sweeps = 400;
+  if (cfg.init_form < SR_INIT_SWEEPS || cfg.init_form > SR_INIT_COMPONENTS)
+    return fail(nullptr, SR_ERR_ARG,
+                "init_form must be SR_INIT_SWEEPS, SR_INIT_FOREST or SR_INIT_COMPONENTS");
+  if (cfg.init_form != SR_INIT_SWEEPS && (cfg.mode != SR_MODE_DENSE || S0))
+    return fail(nullptr, SR_ERR_ARG, "init_form computes the dense S: dense mode, S0 = NULL");
+  if (cfg.init_form == SR_INIT_COMPONENTS && weight)
+    return fail(nullptr, SR_ERR_UNSUPPORTED, "SR_INIT_COMPONENTS on a weighted graph");
+  if (cfg.reanchor_every < 0 || cfg.reanchor_sweeps < 0)
+    return fail(nullptr, SR_ERR_ARG, "reanchor_every and reanchor_sweeps must be >= 0");
+  if (cfg.reanchor_sweeps == 0) cfg.reanchor_sweeps = 4;
 
   simrank_ctx* h = new (std::nothrow) simrank_ctx();
   if (!h) return fail(nullptr, SR_ERR_OOM, "host allocation failed");
@@ -1268,7 +1315,7 @@ simrank_status simrank_init(const simrank_config* cfg_in, int32_t n, int64_t m, 
   h->ext2int.resize(h->n_cap);
   h->int2ext.resize(h->n_cap);
   for (int x = 0; x < h->n_cap; ++x) h->ext2int[x] = h->int2ext[x] = x;
-  if (cfg.relabel && m > 0) {
+  if (cfg.relabel && m > 0 && cfg.init_form != SR_INIT_COMPONENTS) {
     std::vector<char> has_in(n, 0);
     for (int64_t e = 0; e < m; ++e)
       if (dst[e] >= 0 && dst[e] < n) has_in[dst[e]] = 1;
@@ -1276,6 +1323,40 @@ simrank_status simrank_init(const simrank_config* cfg_in, int32_t n, int64_t m, 
     for (int pass = 1; pass >= 0; --pass)
       for (int x = 0; x < n; ++x)
         if (has_in[x] == pass) h->ext2int[x] = next++;
+    for (int x = 0; x < n; ++x) h->int2ext[h->ext2int[x]] = x;
+    h->relabeled = true;
+  }
+  // Example 1: weakly connected components stored one after another, grouped
+  // into bins of at most 4096 nodes (a larger component is a bin of its own);
+  // each bin's diagonal block of S gets its own Jacobi sweeps
+  std::vector<std::pair<int, int>> bins;  // (first storage id, size)
+  if (cfg.init_form == SR_INIT_COMPONENTS) {
+    std::vector<int> root(n);
+    for (int x = 0; x < n; ++x) root[x] = x;
+    auto find = [&](int x) {
+      while (root[x] != x) x = root[x] = root[root[x]];
+      return x;
+    };
+    for (int64_t e = 0; e < m; ++e) {
+      if (src[e] < 0 || dst[e] < 0 || src[e] >= n || dst[e] >= n) continue;  // rejected below
+      const int a = find(src[e]), b = find(dst[e]);
+      if (a != b) root[std::max(a, b)] = std::min(a, b);
+    }
+    std::vector<std::vector<int>> comp(n);
+    for (int x = 0; x < n; ++x) comp[find(x)].push_back(x);
+    int next = 0, bin_start = 0, bin_size = 0;
+    for (int r = 0; r < n; ++r) {
+      if (comp[r].empty()) continue;
+      const int sz = (int)comp[r].size();
+      if (bin_size > 0 && bin_size + sz > 4096) {
+        bins.push_back({bin_start, bin_size});
+        bin_start = next;
+        bin_size = 0;
+      }
+      for (int x : comp[r]) h->ext2int[x] = next++;
+      bin_size += sz;
+    }
+    if (bin_size > 0) bins.push_back({bin_start, bin_size});
     for (int x = 0; x < n; ++x) h->int2ext[h->ext2int[x]] = x;
     h->relabeled = true;
   }
@@ -1319,6 +1400,35 @@ simrank_status simrank_init(const simrank_config* cfg_in, int32_t n, int64_t m, 
   }
   build_adj(h->hin, h->n_pad, in_rows);
   build_adj(h->hout, h->n_pad, out_rows);
+
+  // --- forest form of the initial S (Example 2): each node's parent (its one
+  // in-neighbour) and level; nodes beyond n are isolated roots
+  std::vector<int32_t> f_parent, f_level;
+  int f_top = 0;
+  if (cfg.init_form == SR_INIT_FOREST) {
+    f_parent.assign(h->n_cap, -1);
+    f_level.assign(h->n_cap, -1);
+    for (int x = 0; x < n; ++x) {
+      if (in_rows[x].size() > 1)
+        return bail(fail(h, SR_ERR_ARG, "SR_INIT_FOREST needs every in-degree <= 1 (node " +
+                                            std::to_string(h->int2ext[x]) + ")"));
+      if (!in_rows[x].empty()) f_parent[x] = in_rows[x][0];
+    }
+    std::vector<int32_t> path;
+    for (int x = 0; x < h->n_cap; ++x) {
+      path.clear();
+      int y = x;
+      while (y >= 0 && f_level[y] < 0) {
+        path.push_back(y);
+        if ((int)path.size() > n + 1)
+          return bail(fail(h, SR_ERR_ARG, "SR_INIT_FOREST: the initial graph has a cycle"));
+        y = f_parent[y];
+      }
+      int lv = y < 0 ? -1 : f_level[y];
+      for (auto it = path.rbegin(); it != path.rend(); ++it) f_level[*it] = ++lv;
+      f_top = std::max(f_top, lv);
+    }
+  }
 
   // --- device graph
   auto upload_adj = [&](DevAdj& D, const HostAdj& A) -> simrank_status {
@@ -1419,6 +1529,73 @@ simrank_status simrank_init(const simrank_config* cfg_in, int32_t n, int64_t m, 
     launch_set_diag(h->S, cfg.s_precision, n, h->n_cap, h->ld, 1.0 - cfg.C, h->st);
     if (cudaStreamSynchronize(h->st) != cudaSuccess)
       return bail(fail(h, SR_ERR_CUDA, "init synchronisation failed"));
+  } else if (cfg.init_form == SR_INIT_FOREST) {
+    std::vector<double> powC(f_top + 2, 1.0);
+    for (size_t k = 1; k < powC.size(); ++k) powC[k] = powC[k - 1] * cfg.C;
+    int32_t *d_par = nullptr, *d_lev = nullptr;
+    double* d_pow = nullptr;
+    cudaError_t e = dev_alloc(&d_par, (size_t)h->n_cap);
+    if (e == cudaSuccess) e = dev_alloc(&d_lev, (size_t)h->n_cap);
+    if (e == cudaSuccess) e = dev_alloc(&d_pow, powC.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpy(d_par, f_parent.data(), h->n_cap * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(d_lev, f_level.data(), h->n_cap * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(d_pow, powC.data(), powC.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+      launch_forest_init(h->S, cfg.s_precision, h->ld, d_par, d_lev, d_pow, h->n_cap, h->nT_cap,
+                         upper(h) ? 1 : 0, h->st);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    cudaFree(d_par);
+    cudaFree(d_lev);
+    cudaFree(d_pow);
+    if (e != cudaSuccess)
+      return bail(fail(h, SR_ERR_CUDA, std::string("forest init: ") + cudaGetErrorString(e)));
+    h->stats.init_residual = 0.0;
+    h->stats.init_sweeps = 0;
+  } else if (cfg.init_form == SR_INIT_COMPONENTS) {
+    // every bin's S by the batch algorithm on its own subgraph, copied into
+    // its diagonal block; the blocks between bins stay zero
+    launch_set_diag(h->S, cfg.s_precision, 0, h->n_cap, h->ld, 1.0 - cfg.C, h->st);
+    std::vector<int32_t> bin_of(n);
+    for (size_t b = 0; b < bins.size(); ++b)
+      for (int x = bins[b].first; x < bins[b].first + bins[b].second; ++x) bin_of[x] = (int)b;
+    std::vector<std::vector<int32_t>> bsrc(bins.size()), bdst(bins.size());
+    for (size_t e = 0; e < h->init_src.size(); ++e) {
+      const int b = bin_of[h->init_src[e]];
+      bsrc[b].push_back(h->init_src[e] - bins[b].first);
+      bdst[b].push_back(h->init_dst[e] - bins[b].first);
+    }
+    double worst = 0.0;
+    int most = 0;
+    for (size_t b = 0; b < bins.size(); ++b) {
+      if (bsrc[b].empty()) continue;  // isolated nodes: S_xx = 1 - C is set
+      simrank_config sc = cfg;
+      sc.init_form = SR_INIT_SWEEPS;
+      sc.relabel = 0;
+      sc.upper_only = 0;
+      sc.n_capacity = 0;
+      sc.reanchor_every = 0;
+      simrank_t sub = nullptr;
+      s = simrank_init(&sc, bins[b].second, (int64_t)bsrc[b].size(), bsrc[b].data(),
+                       bdst[b].data(), nullptr, nullptr, &sub);
+      if (s != SR_OK) return bail(fail(h, s, "component init: " + g_init_error));
+      const int64_t r0 = bins[b].first, sz = bins[b].second;
+      cudaError_t e = cudaMemcpy2DAsync((unsigned char*)h->S + (r0 * h->ld + r0) * eb, h->ld * eb,
+                                        sub->S, sub->ld * eb, sz * eb, sz,
+                                        cudaMemcpyDeviceToDevice, h->st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+      worst = std::max(worst, sub->stats.init_residual);
+      most = std::max(most, sub->stats.init_sweeps);
+      simrank_destroy(sub);
+      if (e != cudaSuccess)
+        return bail(fail(h, SR_ERR_CUDA, std::string("component copy: ") + cudaGetErrorString(e)));
+    }
+    h->stats.init_residual = worst;
+    h->stats.init_sweeps = most;
   } else {
     // start from (1 - C) I on the whole capacity
     launch_set_diag(h->S, cfg.s_precision, 0, h->n_cap, h->ld, 1.0 - cfg.C, h->st);
@@ -1558,7 +1735,7 @@ simrank_status simrank_apply_updates(simrank_t h, const simrank_update* u, int64
     if ((s = ensure_dev_capacity(h, 1, (int64_t)ops.size())) != SR_OK) return s;
     if ((s = run_one_shot(h, plus, minus, ops)) != SR_OK) return s;
     h->stats.updates += count;
-    return SR_OK;
+    return maybe_reanchor(h, count);
   }
   if (h->cfg.apply == SR_APPLY_UNIT) {
     for (int64_t t = 0; t < count; ++t) add_r1(um[t].dst, um[t].op, {um[t].src});
@@ -1589,6 +1766,8 @@ simrank_status simrank_apply_updates(simrank_t h, const simrank_update* u, int64
     if ((s = run_rank_one(h, r.src_off, r.delta, r.sink, r.op, r.d_j, r.op_begin, r.op_end)) !=
         SR_OK)
       return s;
+    // every rank-one update (a unit update or a sink block) counts its edges
+    if ((s = maybe_reanchor(h, r.delta)) != SR_OK) return s;
   }
   if ((s = flush_pending(h)) != SR_OK) return s;
   h->stats.updates += count;
@@ -1675,15 +1854,9 @@ simrank_status simrank_reanchor(simrank_t h, int32_t sweeps, double* max_change)
   if (!h) return fail(nullptr, SR_ERR_ARG, "null handle");
   if (h->column) return fail(h, SR_ERR_UNSUPPORTED, "column mode keeps no dense S to re-anchor");
   if (sweeps <= 0) return fail(h, SR_ERR_ARG, "sweeps must be positive");
-  double diff = 0.0;
+  double first = 0.0, diff = 0.0;
   int done = 0;
-  // the sweeps read all of S: restore the lower tiles from their mirrors
-  if (upper(h)) {
-    launch_mirror_lower(h->S, h->cfg.s_precision, h->n_pad, h->ld, h->st);
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return fail(h, SR_ERR_CUDA, cudaGetErrorString(e));
-  }
-  simrank_status s = jacobi_sweeps(h, sweeps, 0.0, &diff, &done);
+  simrank_status s = reanchor_run(h, sweeps, 0.0, &first, &diff, &done);
   if (s != SR_OK) return s;
   h->stats.init_residual = diff;
   h->stats.init_sweeps = done;

@@ -178,6 +178,52 @@ __global__ void k_mirror_lower(T* __restrict__ A, int64_t ld) {
 
 }  // namespace
 
+// Example 2 (§1): on a forest of arborescences (every node has at most one
+// in-neighbour, its parent) Eq. 1 has the closed form
+//   S(a, b) = C^lam (1 - C^(H - lam + 1))
+// when a and b are on the same level H of the same tree, lam being the number
+// of edges from their lowest common ancestor down to a (or b); S(a, b) = 0
+// when they are on different levels or in different trees.  (Row a of Q is
+// e_parent(a), so S(a, b) = C S(p(a), p(b)) for a != b and
+// S(a, a) = C S(p(a), p(a)) + 1 - C, with S(r, x) = (1 - C) [r == x] at a root.)
+// One CTA per 128 x 128 tile (tiles I <= J only when `upper`); thread t owns
+// column t % 128 and every other row.  powC[k] = C^k for k <= max level + 1.
+template <typename T>
+__global__ void __launch_bounds__(256) k_forest_init(T* __restrict__ S, int64_t ld,
+                                                     const int32_t* __restrict__ parent,
+                                                     const int32_t* __restrict__ level,
+                                                     const double* __restrict__ powC, int n,
+                                                     int nT, int upper) {
+  const int I = blockIdx.y, J = blockIdx.x;
+  if (upper && I > J) return;
+  const int c = threadIdx.x & (PT - 1);
+  const int b = J * PT + c;
+  const int lb = b < n ? __ldg(level + b) : -1;
+  for (int r = threadIdx.x >> 7; r < PT; r += 2) {
+    const int a = I * PT + r;
+    T v = T(0);
+    if (a < n && lb >= 0 && __ldg(level + a) == lb) {
+      int x = a, y = b, lam = 0;
+      while (x != y && x >= 0 && lam <= lb) {
+        x = __ldg(parent + x);
+        y = __ldg(parent + y);
+        ++lam;
+      }
+      if (x >= 0 && x == y) v = (T)(powC[lam] * (1.0 - powC[lb - lam + 1]));
+    }
+    S[(int64_t)a * ld + b] = v;
+  }
+}
+
+void launch_forest_init(void* S, int prec, int64_t ld, const int32_t* parent, const int32_t* level,
+                        const double* powC, int n, int nT, int upper, cudaStream_t st) {
+  dim3 grid(nT, nT);
+  if (prec == 64)
+    k_forest_init<double><<<grid, 256, 0, st>>>((double*)S, ld, parent, level, powC, n, nT, upper);
+  else
+    k_forest_init<float><<<grid, 256, 0, st>>>((float*)S, ld, parent, level, powC, n, nT, upper);
+}
+
 void launch_spmm_rows(const DevAdj& in, const float* w, const double* wsum, const void* X,
                       int x_prec, int64_t ldx, void* Y, int y_prec, int64_t ldy, int n_rows,
                       int ncols, double scale, double diag, int n_diag, cudaStream_t st) {

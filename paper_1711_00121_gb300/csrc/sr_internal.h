@@ -261,6 +261,10 @@ void launch_symmetrize(void* A, int prec, int n_pad, int64_t ld, cudaStream_t st
 // B[e] = A[e] for e < count, converting between FP32 and FP64.
 void launch_convert(const void* A, int a_prec, void* B, int b_prec, int64_t count, cudaStream_t st);
 void launch_set_diag(void* A, int prec, int from, int to, int64_t ld, double value, cudaStream_t st);
+// S of a forest of arborescences in closed form (Example 2): parent[x] (-1 at
+// a root) and level[x] for x < n, powC[k] = C^k; S is ld-pitched, nT tiles a side.
+void launch_forest_init(void* S, int prec, int64_t ld, const int32_t* parent, const int32_t* level,
+                        const double* powC, int n, int nT, int upper, cudaStream_t st);
 
 // out[c * n + a] = S[cols[c], perm[a]]  (column c of the symmetric S in caller
 // order; perm maps caller ids to storage ids, nullptr = identity)

@@ -9,6 +9,9 @@ from .graphs import (  # noqa: F401
     er_graph,
     chung_lu_digraph,
     random_arborescence,
+    random_forest,
+    tree_with_extra_edges,
+    block_graph,
     update_stream,
     keyed_update_stream,
     batch_with_new_nodes,

@@ -82,6 +82,73 @@ def random_arborescence(n: int, seed: int):
     return parent, child
 
 
+def random_forest(sizes, seed: int):
+    """Random rooted trees of the given sizes on consecutive ids (the first
+    node of each tree is its root), edges parent -> child."""
+    ps, cs = [], []
+    off = 0
+    for t, sz in enumerate(sizes):
+        p, c = random_arborescence(int(sz), seed * 1000 + t)
+        ps.append(p + off)
+        cs.append(c + off)
+        off += int(sz)
+    return np.concatenate(ps).astype(np.int32), np.concatenate(cs).astype(np.int32)
+
+
+def tree_with_extra_edges(n: int, extra: int, seed: int):
+    """A random rooted tree on n nodes (edges parent -> child) and `extra`
+    further edges that are neither tree edges, duplicates nor self-loops:
+    source uniform, target drawn with probability proportional to
+    (1 + number of extra edges it already has), so some nodes collect many
+    in-neighbours.  Returns (tree_src, tree_dst, extra_src, extra_dst)."""
+    ps, cs = random_arborescence(n, seed)
+    rng = np.random.default_rng(seed + 7)
+    have = set(zip(ps.tolist(), cs.tolist()))
+    w = np.ones(n)
+    es, ed = [], []
+    while len(es) < extra:
+        i = int(rng.integers(0, n))
+        j = _Sampler(w, rng)()
+        if i == j or (i, j) in have:
+            continue
+        have.add((i, j))
+        es.append(i)
+        ed.append(j)
+        w[j] += 1.0
+    return ps, cs, np.array(es, np.int32), np.array(ed, np.int32)
+
+
+def block_graph(sizes, deg: int, cross: int, seed: int):
+    """Directed Chung-Lu blocks (exponent 2.1, mean degree `deg`) on
+    consecutive ids, plus `cross` edges between distinct blocks (uniform
+    endpoints).  Returns (block_src, block_dst, cross_src, cross_dst)."""
+    bs, bd = [], []
+    off = 0
+    starts = []
+    for t, sz in enumerate(sizes):
+        s, d = chung_lu_digraph(int(sz), deg * int(sz), 2.1, 2.1, seed * 1000 + t)
+        bs.append(s + off)
+        bd.append(d + off)
+        starts.append(off)
+        off += int(sz)
+    n = off
+    block_of = np.zeros(n, np.int64)
+    for t, st in enumerate(starts):
+        block_of[st:st + int(sizes[t])] = t
+    rng = np.random.default_rng(seed + 11)
+    have = set()
+    xs, xd = [], []
+    while len(xs) < cross:
+        i, j = int(rng.integers(0, n)), int(rng.integers(0, n))
+        if block_of[i] == block_of[j] or (i, j) in have:
+            continue
+        have.add((i, j))
+        xs.append(i)
+        xd.append(j)
+    return (np.concatenate(bs).astype(np.int32), np.concatenate(bd).astype(np.int32),
+            np.array(xs, np.int32), np.array(xd, np.int32))
+
+
 def edge_weights(m: int, seed: int, low: float = 0.1, high: float = 1.0):
     """Edge weights uniform in (low, high]."""
     rng = np.random.default_rng(seed)
