@@ -799,6 +799,69 @@ def inc_sr_all_p(n, src, dst, S_col_x, x, updates, C, K, K_old=None):
     return col
 
 
+def inc_sr_all_p_blocks(n, n_final, src, dst, S_col_x, x, updates, C, K, K_old=None):
+    """Alg 7 combined with the batch scheme of §8 (the closing remark of §7):
+    column x of S through a batch of updates applied as similar-sink blocks.
+
+    Net update and partition as in Alg 6 (:func:`net_update`,
+    :func:`partition_similar_sink`, :func:`block_case`); new nodes are
+    pre-allocated as isolated nodes (ids n .. n_final - 1, S column (1-C) e_x),
+    so every block is a C0 block of Table 2.  For each block (delta sources I
+    into sink j) the old columns S_{*,i} (i in I) and S_{*,j} come from
+    PartialSim (Procedure 1) at K_old on the current graph, which needs the
+    delta + 1 columns only; w = (1/delta) Q sum_i S_{*,i}, S_II, u, v and gamma
+    follow Table 2, and only the x-th entries of xi_k, eta_k feed the column
+    accumulators.  ``S_col_x`` is column x of the old S on the n old nodes.
+    ``K_old`` defaults to K (Alg 7 as printed).
+    """
+    K_old = K if K_old is None else K_old
+    plus, minus = net_update(updates)
+    dels, ins = partition_similar_sink(plus, minus, lambda y: y < n)
+    order = [(DELETE, j, srcs) for j, srcs in dels]
+    exists = set(range(n))
+    for j, srcs in ins:
+        for _, part in block_case(srcs, j, lambda y: y in exists):
+            order.append((INSERT, j, part))
+            exists.update(part)
+            exists.add(j)
+    col = np.zeros(n_final)
+    if x < n:
+        col[:n] = np.asarray(S_col_x, np.float64)
+    else:
+        col[x] = 1.0 - C
+    edges = set(zip(np.asarray(src).tolist(), np.asarray(dst).tolist()))
+    for op, j, srcs in order:
+        s_arr = np.array([a for a, _ in edges], np.int64)
+        d_arr = np.array([b for _, b in edges], np.int64)
+        Q = transition_matrix(n_final, s_arr, d_arr, sparse=True)
+        d = int(in_degrees(n_final, d_arr)[j])
+        delta = len(srcs)
+        S_cols_I = [partial_sim(Q, i, K_old, C) for i in srcs]
+        sI = np.sum(S_cols_I, axis=0)
+        Sj = partial_sim(Q, j, K_old, C)
+        S_II = float(sum(sI[i] for i in srcs))
+        w = np.asarray(Q @ sI).ravel() / delta
+        u, v = rank_one_factors(Q, d, j, srcs, op)
+        gamma, _ = gamma_sink_block(w, Sj, S_II, Sj[j], d, delta, op, C, j)
+        xi = np.zeros(n_final)
+        xi[j] = C
+        eta = gamma.copy()
+        m_acc = eta[x] * xi
+        n_acc = xi[x] * eta
+        for _ in range(K):
+            xi = C * np.asarray(Q @ xi).ravel() + C * float(v @ xi) * u
+            eta = np.asarray(Q @ eta).ravel() + float(v @ eta) * u
+            m_acc = eta[x] * xi + m_acc
+            n_acc = xi[x] * eta + n_acc
+        col = col + m_acc + n_acc
+        for i in srcs:
+            if op > 0:
+                edges.add((i, j))
+            else:
+                edges.discard((i, j))
+    return col
+
+
 # ----------------------------------------------------------------------------
 # Gradient of a pair loss with respect to edge weights
 # ----------------------------------------------------------------------------

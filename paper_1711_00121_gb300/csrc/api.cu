@@ -91,7 +91,8 @@ struct simrank_ctx {
   std::vector<RowChunk> hfwd, hhor;
   std::vector<int64_t> ffwd, fhor;
   bool col_chunks_ok = false;
-  int col_last_i = -1, col_last_j = -1;
+  std::vector<int32_t> col_last_srcs;  // sources and sink of the last stored update
+  int col_last_j = -1;
   std::vector<void*> hist;  // per-update panel snapshots (tile-blocked, S precision)
   // one-shot batch scratch (grow-only)
   struct Buf {
@@ -1079,30 +1080,62 @@ simrank_status upload_chunks(simrank_ctx* h, const std::vector<RowChunk>& v, Chu
 // One update in column mode (Alg 7 with new nodes as isolated nodes): the
 // old columns S_{*,i}, S_{*,j} by Procedure 1 on the current graph, gamma,
 // the graph patch, the xi/eta recurrence, and a snapshot of the panels.
-simrank_status run_column_update(simrank_ctx* h, int i, int j, int op, int d_j, int64_t op_begin,
-                                 int64_t op_end, int32_t* d_cols2) {
+// One stored update of column mode (Alg 7): a unit update or, with
+// SR_APPLY_SINK_BLOCKS, a sink block of delta sources into j (Table 2, the
+// batch scheme of §8 that the closing remark of §7 combines with Alg 7).  The
+// old columns S_{*,i} (i in I) and S_{*,j} come from Procedure 1 on the
+// current graph; the sources' columns are summed (Table 2 needs their sum and
+// S_II), at most 31 of them per Procedure-1 block, so memory stays
+// O(n (delta + K) + m).  d_cols holds the delta sources then j (device).
+simrank_status run_column_update(simrank_ctx* h, const std::vector<int32_t>& srcs, int j, int op,
+                                 int d_j, int64_t op_begin, int64_t op_end, int32_t* d_cols) {
   const int K = h->cfg.K, n_pad = h->n_pad, nT = (h->n_cur + PT - 1) / PT;
+  const int delta = (int)srcs.size();
   simrank_status s;
-  const int32_t ij[2] = {i, j};
-  CUDA_TRY(h, cudaMemcpyAsync(d_cols2, ij, sizeof(ij), cudaMemcpyHostToDevice, h->st));
-  const size_t blk = (size_t)n_pad * 2 * sizeof(double);
+  std::vector<int32_t> cols(srcs);
+  cols.push_back(j);
+  CUDA_TRY(h, cudaMemcpyAsync(d_cols, cols.data(), cols.size() * sizeof(int32_t),
+                              cudaMemcpyHostToDevice, h->st));
+  constexpr int BMAX = 32;
+  const int bw = std::min<int>(BMAX, delta + 1);
+  const size_t blk = (size_t)n_pad * bw * sizeof(double);
   if ((s = ob_ensure(h, 10, blk * (K + 1))) != SR_OK) return s;
   if ((s = ob_ensure(h, 11, blk * 3)) != SR_OK) return s;
   unsigned char* w = (unsigned char*)h->ob[11].p;
-  launch_partial_sim_block(h->cur_fwd, h->cur_hor, h->dout.col, h->din.col, h->din.len, d_cols2, 2,
-                           n_pad, K, h->cfg.C, 64, h->ob[10].p, w, w + blk, w + 2 * blk, h->st);
-  launch_col_extract(w + 2 * blk, 64, 2, 0, n_pad, h->sI, h->st);
-  launch_col_extract(w + 2 * blk, 64, 2, 1, n_pad, h->sJ, h->st);
-  launch_col_scalars(h->din, h->sI, h->sJ, i, j, h->scal, h->st);
+  if (delta + 1 <= BMAX) {
+    // sources and sink in one block
+    launch_partial_sim_block(h->cur_fwd, h->cur_hor, h->dout.col, h->din.col, h->din.len, d_cols,
+                             delta + 1, n_pad, K, h->cfg.C, 64, h->ob[10].p, w, w + blk,
+                             w + 2 * blk, h->st);
+    launch_col_sum(w + 2 * blk, 64, delta + 1, 0, delta, n_pad, 0, h->sI, h->st);
+    launch_col_extract(w + 2 * blk, 64, delta + 1, delta, n_pad, h->sJ, h->st);
+    h->launches += 2 * K + 4;
+  } else {
+    for (int c0 = 0; c0 < delta; c0 += BMAX - 1) {
+      const int B = std::min(BMAX - 1, delta - c0);
+      launch_partial_sim_block(h->cur_fwd, h->cur_hor, h->dout.col, h->din.col, h->din.len,
+                               d_cols + c0, B, n_pad, K, h->cfg.C, 64, h->ob[10].p, w, w + blk,
+                               w + 2 * blk, h->st);
+      launch_col_sum(w + 2 * blk, 64, B, 0, B, n_pad, c0 > 0 ? 1 : 0, h->sI, h->st);
+      h->launches += 2 * K + 3;
+    }
+    launch_partial_sim_block(h->cur_fwd, h->cur_hor, h->dout.col, h->din.col, h->din.len,
+                             d_cols + delta, 1, n_pad, K, h->cfg.C, 64, h->ob[10].p, w, w + blk,
+                             w + 2 * blk, h->st);
+    launch_col_extract(w + 2 * blk, 64, 1, 0, n_pad, h->sJ, h->st);
+    h->launches += 2 * K + 3;
+  }
+  // S_II and w_j = (1/delta) (Q S_{*,I})_j on the graph before the update
+  launch_scalars_from_rows(h->din, h->sI, h->sJ, d_cols, delta, j, h->scal, h->st);
   const bool f32 = h->cfg.s_precision == 32;
-  launch_gamma(h->din, h->sI, h->sJ, h->scal, j, 1, op, d_j, h->cfg.C, nT, h->K1, h->P64,
+  launch_gamma(h->din, h->sI, h->sJ, h->scal, j, delta, op, d_j, h->cfg.C, nT, h->K1, h->P64,
                f32 ? h->P32 : nullptr, h->mXi, h->mEta, h->st);
   launch_patch(h->d_ops, op_begin, op_end, h->din, h->dout, h->st);
   for (int k = 0; k < K; ++k)
     launch_chain_step(h->din, k, h->cfg.C, nT, h->K1, h->P64, f32 ? h->P32 : nullptr, h->mXi,
                       h->mEta, h->st);
   LAUNCH_CHECK(h);
-  h->launches += 2 * K + 6 + K;
+  h->launches += 3 + K;
   const size_t pbytes = (size_t)h->nT_cap * 2 * h->K1 * PT * (f32 ? 4 : 8);
   void* snap = nullptr;
   CUDA_TRY(h, cudaMallocAsync(&snap, pbytes, h->st));
@@ -1255,8 +1288,9 @@ simrank_status simrank_init(const simrank_config* cfg_in, int32_t n, int64_t m, 
     return fail(nullptr, SR_ERR_ARG, "mode must be SR_MODE_DENSE or SR_MODE_COLUMN");
   if (cfg.mode == SR_MODE_COLUMN) {
     if (S0) return fail(nullptr, SR_ERR_ARG, "column mode keeps no dense S: S0 must be NULL");
-    if (cfg.apply != SR_APPLY_UNIT)
-      return fail(nullptr, SR_ERR_UNSUPPORTED, "column mode applies unit updates (Alg 7)");
+    if (cfg.apply == SR_APPLY_ONE_SHOT)
+      return fail(nullptr, SR_ERR_UNSUPPORTED,
+                  "column mode applies unit updates or sink blocks (Alg 7, §8)");
     cfg.relabel = 0;
   }
   if (n < 1 || m < 0) return fail(nullptr, SR_ERR_ARG, "need n >= 1 and m >= 0");
@@ -1664,15 +1698,25 @@ simrank_status simrank_apply_updates(simrank_t h, const simrank_update* u, int64
     plan.push_back(r);
   };
   if (h->column) {
-    // Alg 7: one update at a time; the old columns come from the graph
-    // before that update, so each update is planned right before it runs
+    // Alg 7: one stored update at a time (a unit update, or with
+    // SR_APPLY_SINK_BLOCKS a similar-sink block of the net batch, §8); the old
+    // columns come from the graph before that update, so each one is planned
+    // right before it runs
+    std::vector<Block> blocks;
+    if (h->cfg.apply == SR_APPLY_SINK_BLOCKS) {
+      std::string msg;
+      if ((s = plan_blocks(um.data(), count, n_old, blocks, msg)) != SR_OK) return fail(h, s, msg);
+    } else {
+      for (int64_t t = 0; t < count; ++t) blocks.push_back(Block{um[t].dst, um[t].op, {um[t].src}});
+    }
     h->n_cur = n_after;
-    for (int64_t t = 0; t < count; ++t) {
-      const int32_t i = um[t].src, j = um[t].dst, op = um[t].op;
-      // chunk lists of the graph before this update: the previous update
-      // changed out-row col_last_i and in-row col_last_j only
-      bool ok_f = h->col_chunks_ok && h->col_last_i >= 0 &&
-                  patch_row_chunks(h, h->hout, h->col_last_i, h->hfwd, h->ffwd, h->cur_fwd);
+    for (const Block& b : blocks) {
+      const int32_t j = b.sink, op = b.op;
+      // chunk lists of the graph before this update: the previous one changed
+      // the out-rows of its sources and the in-row of its sink only
+      bool ok_f = h->col_chunks_ok && !h->col_last_srcs.empty();
+      for (int32_t i : h->col_last_srcs)
+        ok_f = ok_f && patch_row_chunks(h, h->hout, i, h->hfwd, h->ffwd, h->cur_fwd);
       bool ok_h = h->col_chunks_ok && h->col_last_j >= 0 &&
                   patch_row_chunks(h, h->hin, h->col_last_j, h->hhor, h->fhor, h->cur_hor);
       if (!ok_f) {
@@ -1684,25 +1728,29 @@ simrank_status simrank_apply_updates(simrank_t h, const simrank_update* u, int64
         if ((s = upload_chunks(h, h->hhor, h->cur_hor, &h->cur_hor_cap)) != SR_OK) return s;
       }
       h->col_chunks_ok = true;
-      h->col_last_i = i;
+      h->col_last_srcs = b.srcs;
       h->col_last_j = j;
       std::vector<PatchOp> ops1;
       const int d_j = h->hin.len[j];
-      if (op > 0) {
-        adj_append(h->hin, j, i, ops1, true);
-        adj_append(h->hout, i, j, ops1, false);
-        h->edges.insert(ekey(i, j));
-      } else {
-        adj_remove(h->hin, j, i, ops1, true);
-        adj_remove(h->hout, i, j, ops1, false);
-        h->edges.erase(ekey(i, j));
+      for (int32_t i : b.srcs) {
+        if (op > 0) {
+          adj_append(h->hin, j, i, ops1, true);
+          adj_append(h->hout, i, j, ops1, false);
+          h->edges.insert(ekey(i, j));
+        } else {
+          adj_remove(h->hin, j, i, ops1, true);
+          adj_remove(h->hout, i, j, ops1, false);
+          h->edges.erase(ekey(i, j));
+        }
       }
       if ((s = grow_pool(h, h->din, h->hin)) != SR_OK) return s;
       if ((s = grow_pool(h, h->dout, h->hout)) != SR_OK) return s;
-      if ((s = ensure_dev_capacity(h, 2, (int64_t)ops1.size())) != SR_OK) return s;
+      if ((s = ensure_dev_capacity(h, (int64_t)b.srcs.size() + 1, (int64_t)ops1.size())) != SR_OK)
+        return s;
       CUDA_TRY(h, cudaMemcpyAsync(h->d_ops, ops1.data(), ops1.size() * sizeof(PatchOp),
                                   cudaMemcpyHostToDevice, h->st));
-      if ((s = run_column_update(h, i, j, op, d_j, 0, (int64_t)ops1.size(), h->d_srcs)) != SR_OK)
+      if ((s = run_column_update(h, b.srcs, j, op, d_j, 0, (int64_t)ops1.size(), h->d_srcs)) !=
+          SR_OK)
         return s;
     }
     h->stats.updates += count;
@@ -1739,8 +1787,6 @@ simrank_status simrank_apply_updates(simrank_t h, const simrank_update* u, int64
   }
   if (h->cfg.apply == SR_APPLY_UNIT) {
     for (int64_t t = 0; t < count; ++t) add_r1(um[t].dst, um[t].op, {um[t].src});
-  } else if (h->column) {
-    return fail(h, SR_ERR_UNSUPPORTED, "column mode applies unit updates");
   } else {
     // the canonical block order is defined on caller ids
     std::vector<Block> blocks;

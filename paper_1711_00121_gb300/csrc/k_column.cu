@@ -317,6 +317,18 @@ __global__ void k_col_extract(const T* __restrict__ Y, int B, int c, int n, doub
   if (a < n) v[a] = (double)Y[(int64_t)a * B + c];
 }
 
+// v[a] (+)= sum_{c0 <= c < c1} Y[a][c]: the old column S_{*,I} summed over a
+// sink block's sources (Table 2 needs only their sum and S_II)
+template <typename T>
+__global__ void k_col_sum(const T* __restrict__ Y, int B, int c0, int c1, int n, int accumulate,
+                          double* __restrict__ v) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n) return;
+  double s = accumulate ? v[a] : 0.0;
+  for (int c = c0; c < c1; ++c) s += (double)Y[(int64_t)a * B + c];
+  v[a] = s;
+}
+
 }  // namespace
 
 template <typename T>
@@ -493,6 +505,14 @@ void launch_col_out(const void* Y, int prec, int B, int n, void* out, int out_fp
     else
       k_col_out<float, float><<<grid, 256, 0, st>>>((const float*)Y, B, n, (float*)out);
   }
+}
+
+void launch_col_sum(const void* Y, int prec, int B, int c0, int c1, int n, int accumulate, double* v,
+                    cudaStream_t st) {
+  if (prec == 64)
+    k_col_sum<double><<<(n + 255) / 256, 256, 0, st>>>((const double*)Y, B, c0, c1, n, accumulate, v);
+  else
+    k_col_sum<float><<<(n + 255) / 256, 256, 0, st>>>((const float*)Y, B, c0, c1, n, accumulate, v);
 }
 
 void launch_col_extract(const void* Y, int prec, int B, int c, int n, double* v, cudaStream_t st) {

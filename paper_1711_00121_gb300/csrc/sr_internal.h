@@ -372,6 +372,9 @@ void launch_col_scalars(const DevAdj& in, const double* si, const double* sj, in
                         double* scal, cudaStream_t st);
 void launch_col_out(const void* Y, int prec, int B, int n, void* out, int out_fp64, cudaStream_t st);
 void launch_col_extract(const void* Y, int prec, int B, int c, int n, double* v, cudaStream_t st);
+// v[a] = sum_{c0 <= c < c1} Y[a][c] (plus the old v[a] when accumulate != 0)
+void launch_col_sum(const void* Y, int prec, int B, int c0, int c1, int n, int accumulate, double* v,
+                    cudaStream_t st);
 
 // ---- adjoint (k_adjoint.cu)
 // G[e] += scale * sum_{x < B} F[u][x] Y[v][x] for every in-list entry e (row u,

@@ -94,3 +94,38 @@ def test_column_mode_fp32_query_widths(P, width):
     for c, x in enumerate(cols.tolist()):
         want = O.inc_sr_all_p(n, s, d, base[:, c], x, st.tolist(), C, K)
         assert np.max(np.abs(got[:, c] - want)) < 1e-6, (width, x)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_column_mode_sink_blocks(P, prec):
+    """Alg 7 fed by similar-sink blocks (§8; the closing remark of §7): a batch
+    with deletions and new nodes, then a block of 40 insertions into one sink
+    (its source columns summed over two Procedure-1 blocks), against the
+    oracle's column form at the same K (old columns by PartialSim at K)."""
+    from synth import batch_with_new_nodes
+
+    n, m, C, K = 500, 2500, 0.6, 8
+    s, d = er_graph(n, m, 56)
+    ups, n_new = batch_with_new_nodes(n, s, d, 60, 57, frac_new=0.2, reuse_target=0.5)
+    n_final = n + n_new
+    plus, minus = O.net_update(ups.tolist())
+    edges1 = (set(zip(s.tolist(), d.tolist())) | set(plus)) - set(minus)
+    deg1 = np.bincount(np.array([b for _, b in edges1]), minlength=n_final)
+    j0 = int(np.argmax(deg1[:n]))
+    big = [(x, j0, 1) for x in range(n_final) if x != j0 and (x, j0) not in edges1][:40]
+    sr = P.SimRank(n, s, d, C=C, K=K, s_precision=prec, mode=P.MODE_COLUMN, n_capacity=n_final,
+                   apply=P.APPLY_SINK_BLOCKS)
+    sr.apply_updates(ups)
+    sr.apply_updates(big)
+    assert sr.n == n_final
+    rng = np.random.default_rng(58)
+    cols = sorted(set(rng.choice(n_final, 6, replace=False).tolist()) | {j0, big[0][0], n_final - 1})
+    got = sr.columns(np.array(cols, np.int32))
+    Q0 = O.transition_matrix(n, s, d, sparse=True)
+    e1s = np.array([a for a, _ in edges1], np.int64)
+    e1d = np.array([b for _, b in edges1], np.int64)
+    for c, x in enumerate(cols):
+        col0 = O.partial_sim(Q0, x, K, C) if x < n else None
+        mid = O.inc_sr_all_p_blocks(n, n_final, s, d, col0, x, ups.tolist(), C, K)
+        want = O.inc_sr_all_p_blocks(n_final, n_final, e1s, e1d, mid, x, big, C, K)
+        assert np.max(np.abs(got[:, c] - want)) < (1e-10 if prec == 64 else 1e-6), x

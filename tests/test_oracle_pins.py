@@ -653,3 +653,52 @@ def test_alg1_stream_columns_equals_dense_sequential(K):
     query = [0, 3, 7, int(st[0, 1]), n - 1]
     cols = O.alg1_stream_columns(n, s, d, lambda c: S[:, c], st.tolist(), C, K, query)
     assert np.max(np.abs(cols - dense[:, query])) < 1e-13
+
+
+@pytest.mark.parametrize("K", [0, 2, 5])
+def test_inc_sr_all_p_blocks_single_block_finite_k(K):
+    """One sink block through the column form of Alg 7 x §8 at the same K as
+    Alg 1 on the exact S (converged old columns): a two-edge insertion block, a
+    two-edge deletion block, and a block into a new (isolated) sink."""
+    n = 11
+    s, d = er_graph(n, 30, 320)
+    C = 0.6
+    edges = set(zip(s.tolist(), d.tolist()))
+    deg = O.in_degrees(n, d)
+    S = _exact(n, s, d, C)
+    j = int(np.argmax(deg))
+    ins = [x for x in range(n) if x != j and (x, j) not in edges][:2]
+    jd = next(b for b in range(n) if deg[b] >= 3)
+    dels = sorted(a for a, b in edges if b == jd)[:2]
+    for srcs, sink, op in ((ins, j, O.INSERT), (dels, jd, O.DELETE)):
+        want = O.inc_usr(n, s, d, S, sink, srcs, op, C, K)
+        ups = [(i, sink, op) for i in srcs]
+        for x in (0, sink, srcs[0], n - 1):
+            col = O.inc_sr_all_p_blocks(n, n, s, d, S[:, x], x, ups, C, K, K_old=200)
+            assert np.max(np.abs(col - want[:, x])) < 1e-13, (op, x)
+    # two old sources into a new sink n: Alg 1 on the graph padded with the isolated node
+    Sp = np.zeros((n + 1, n + 1))
+    Sp[:n, :n] = S
+    Sp[n, n] = 1 - C
+    want = O.inc_usr(n + 1, s, d, Sp, n, ins, O.INSERT, C, K)
+    for x in (0, ins[0], n):
+        col = O.inc_sr_all_p_blocks(n, n + 1, s, d, S[:, x] if x < n else None, x,
+                                    [(i, n, 1) for i in ins], C, K, K_old=200)
+        assert np.max(np.abs(col - want[:, x])) < 1e-13, ("new sink", x)
+
+
+def test_inc_sr_all_p_blocks_batch_converges():
+    """A batch with insertions, deletions and new nodes at large K equals the
+    brute-force fixed point of the final graph, column by column."""
+    n = 10
+    s, d = er_graph(n, 24, 321)
+    C = 0.6
+    S = _exact(n, s, d, C)
+    ups, n_new = batch_with_new_nodes(n, s, d, 9, 322, frac_new=0.4, reuse_target=0.5)
+    n_final = n + n_new
+    _, edges = O.inc_bsr(n, s, d, S, ups.tolist(), C, 2)
+    S_true = _dense_new(n_final, edges, C)
+    for x in (0, 4, n - 1, n_final - 1):
+        col = O.inc_sr_all_p_blocks(n, n_final, s, d, S[:, x] if x < n else None, x, ups.tolist(),
+                                    C, 150)
+        assert np.max(np.abs(col - S_true[:, x])) < 1e-11, x
