@@ -289,6 +289,13 @@ def run_gpu(args, rank, world):
         t = torch.from_numpy(arr.view(np.uint8)).pin_memory()
         packed.append((t, arr.size))
     form = dict(defer=args.defer, tc=args.tc, vec_fp64=args.vec_fp64)
+    tuned = {}
+    if args.tuned:
+        from paper_1711_00121_gb300 import tune
+
+        tuned = tune.tuned_knobs("stream", N, K, 32, args.vec_fp64)
+        form.update(tuned)
+    args.defer, args.tc = form["defer"], form["tc"]
 
     def handle(profile, **over):
         kw = dict(form)
@@ -511,6 +518,9 @@ def run_gpu(args, rank, world):
         "data": "synthetic",
         "config": {"workload": workload_name(args), "n": N, "m": M, "C": C, "K": K,
                    "updates_per_step": per_step, "defer": args.defer, "tc": args.tc,
+                   "launch": {k: form[k] for k in ("defer", "tc", "prep_item", "prep_ctas")
+                              if k in form},
+                   "launch_from_autotuner": bool(tuned),
                    "vectors": vec, "storage": "upper tiles",
                    "l2": "inputs larger than L2 (S is 1.6 GB FP32)",
                    "aff_tile_fraction": tiles_touched / max(tiles_total, 1),
@@ -696,7 +706,15 @@ def run_multi(args):
         s, d = chung_lu_digraph(n, MDEG * n, 2.1, 2.1, M_SEED * 100000 + g)
         graphs.append((n, s, d))
     res = {}
-    for form, launch in (("batched_cuda_graph", 0), ("per_graph_launches", 1)):
+    from paper_1711_00121_gb300 import tune
+
+    tuned_tc = tune.tuned_knobs("multi", MN_HI, MK, 32, 0).get("tc")
+    forms = [("batched_cuda_graph", 0, args.multi_tc if tuned_tc is None else tuned_tc)]
+    if tuned_tc is not None:
+        # the library default (CUDA-core S pass) next to the tuner's choice
+        forms.append(("batched_untuned", 0, 0))
+    forms.append(("per_graph_launches", 1, forms[0][2]))
+    for form, launch, mtc in forms:
         sets = [ES(n, s, d) for n, s, d in graphs]
 
         def draw(tag):
@@ -707,7 +725,7 @@ def run_multi(args):
         timed = [draw(100 + t) for t in range(args.steps)]
         t0 = time.time()
         mh = P.MultiSimRank(graphs, C=MC, K=MK, s_precision=32, multi_launch=launch,
-                            init_tol=1e-9, tc=args.multi_tc)
+                            init_tol=1e-9, tc=mtc)
         init_s = time.time() - t0
         packed = []
         for ups in warm + timed:
@@ -736,7 +754,7 @@ def run_multi(args):
                      "kernel_launches": st1["kernel_launches"] - st0["kernel_launches"],
                      "s_bytes": st1["s_bytes"] - st0["s_bytes"],
                      "hbm_gbs": (st1["s_bytes"] - st0["s_bytes"]) / host_s / 1e9,
-                     "init_s": init_s, "clocks": clk.summary()}
+                     "init_s": init_s, "tc": mtc, "clocks": clk.summary()}
         if form == "batched_cuda_graph":
             # accuracy: the smallest graph's final S against the FP64 oracle
             from oracle import simrank_oracle as O
@@ -752,12 +770,14 @@ def run_multi(args):
         torch.cuda.empty_cache()
     one = res["batched_cuda_graph"]
     line = {"workload": f"many graphs: {G} directed Chung-Lu graphs (exponent 2.1), n~U[{MN_LO},{MN_HI}], "
-                        f"mean degree {MDEG}, C={MC}, K={MK}, FP32 S, 1-32 unit updates per graph per call, "
-                        f"S pass on " + ("tensor cores (TF32 split)" if args.multi_tc else "CUDA cores"),
+                        f"mean degree {MDEG}, C={MC}, K={MK}, FP32 S, 1-32 unit updates per graph per call",
             "sum_S_gb": float(sum(int(((n + 127) // 128 * 128)) ** 2 * 4 for n in sizes) / 1e9),
             "updates_per_call": int(counts.sum()), "steps": args.steps, "warmup": args.warmup,
             "forms": res,
-            "speedup_batched_vs_per_graph": one["updates_per_s"] / res["per_graph_launches"]["updates_per_s"]}
+            "speedup_batched_vs_per_graph": one["updates_per_s"] / res["per_graph_launches"]["updates_per_s"],
+            "autotuner": {"tc": tuned_tc, "cache": tune.cache_path()},
+            "speedup_tuned_vs_untuned": (one["updates_per_s"] / res["batched_untuned"]["updates_per_s"]
+                                         if "batched_untuned" in res else None)}
     print(json.dumps(line), flush=True)
 
 
@@ -811,14 +831,60 @@ def run_column(args):
                 sr.sync()
                 times.append(a.elapsed_time(b))
     ms = sum(times) / len(times)
+    sr.close()
     line = {"workload": f"column block: directed Chung-Lu n={n} m={m} exponent 2.1, C={CC}, K={CK}, "
                         f"{CU} stored unit updates, blocks of {CB} columns, FP32",
             "metric": "columns/s", "value": CB / (ms / 1000.0), "unit": "columns/s",
             "ms_per_block": ms, "steps": args.steps, "init_s": init_s,
             "apply_ms_per_update": apply_ms / CU,
             "s_per_column_per_update": (ms / 1000.0) / CB / CU, "clocks": clk.summary()}
+    if args.column_blocks:
+        line["sink_blocks"] = column_sink_blocks(P, torch, n, s, d, stream)
     print(json.dumps(line), flush=True)
-    sr.close()
+
+
+def column_sink_blocks(P, torch, n, s, d, stream, sinks=8, per=8):
+    """Alg 7 with similar-sink blocks (§8) at the column-workload size: the
+    same sinks x per insertions (per sources into each of `sinks` nodes of
+    large in-degree) stored as unit updates or as one block per sink, then
+    one query of CB columns; times by CUDA events."""
+    rng = np.random.default_rng(13)
+    indeg = np.bincount(d, minlength=n)
+    top = np.argsort(-indeg)[:64]
+    sink_ids = rng.choice(top, size=sinks, replace=False)
+    ups = []
+    for j in sink_ids.tolist():
+        have = set(s[d == j].tolist())
+        srcs = set()
+        while len(srcs) < per:
+            i = int(rng.integers(0, n))
+            if i != j and i not in have:
+                srcs.add(i)
+        ups.extend((i, j, 1) for i in sorted(srcs))
+    ups = np.array(ups, np.int32)
+    cols = np.sort(rng.choice(n, size=CB, replace=False)).astype(np.int32)
+    out = torch.empty((CB, n), dtype=torch.float32, device="cuda")
+    res = {}
+    for form, apply in (("unit_updates", P.APPLY_UNIT), ("sink_blocks", P.APPLY_SINK_BLOCKS)):
+        sr = P.SimRank(n, s, d, C=CC, K=CK, s_precision=32, mode=P.MODE_COLUMN, apply=apply,
+                       stream=stream.cuda_stream)
+        with torch.cuda.stream(stream):
+            a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            a.record(stream)
+            sr.apply_updates(ups)
+            b.record(stream)
+            sr.columns_device(cols, out)
+            c.record(stream)
+            sr.sync()
+        st = sr.stats()
+        res[form] = {"stored_updates": st["rank_one_updates"], "store_ms": a.elapsed_time(b),
+                     "query_ms": b.elapsed_time(c), "columns_per_s": CB / (b.elapsed_time(c) / 1000.0)}
+        sr.close()
+        torch.cuda.empty_cache()
+    return {"batch": f"{sinks * per} insertions: {per} sources into each of {sinks} sinks of large "
+                     f"in-degree", "query_columns": CB, "forms": res,
+            "store_speedup": res["unit_updates"]["store_ms"] / res["sink_blocks"]["store_ms"],
+            "query_speedup": res["unit_updates"]["query_ms"] / res["sink_blocks"]["query_ms"]}
 
 
 # --------------------------------------------------------------------------
@@ -956,6 +1022,39 @@ def run_accelerate(args):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------
+# Autotuner run: times the launch knobs on the stream workload's graph (both
+# vector precisions) and the S-pass form on 64 of the many-graph workload's
+# graphs, and writes the cache (SIMRANK_TUNE_CACHE, else the package's
+# tuned.json) that the other workloads read with --tuned.
+# --------------------------------------------------------------------------
+def run_tune(args):
+    import torch
+
+    from paper_1711_00121_gb300 import tune
+
+    torch.cuda.set_device(0)
+    s, d = chung_lu_digraph(N, M, GAMMA, GAMMA, SEED_GRAPH)
+    out = {"cache": tune.cache_path(), "gpu": tune.gpu_name(), "stream": {}}
+    for v in (1, 0):
+        r = tune.tune_stream(N, s, d, C=C, K=K, s_precision=32, vec_fp64=v, updates=192, warmup=64)
+        out["stream"][f"vec_fp64={v}"] = {"knobs": r["knobs"], "us_per_update": r["us_per_update"],
+                                          "candidates": len(r["measured"])}
+    rng = np.random.default_rng(M_SEED)
+    sizes = rng.integers(MN_LO, MN_HI + 1, size=args.graphs)[:64]
+    graphs = [(int(n), *chung_lu_digraph(int(n), MDEG * int(n), 2.1, 2.1, M_SEED * 100000 + g))
+              for g, n in enumerate(sizes)]
+    graphs = [(n, s_, d_) for n, s_, d_ in graphs]
+    r = tune.tune_multi(graphs, C=MC, K=MK, s_precision=32, updates=8)
+    # the many-graph key is the workload's largest n
+    entries = tune.load()
+    kk = tune.key("multi", tune.gpu_name(), max(int(g[0]) for g in graphs), MK, 32, 0)
+    entries[tune.key("multi", tune.gpu_name(), MN_HI, MK, 32, 0)] = entries[kk]
+    tune.save(entries)
+    out["multi"] = {"knobs": r["knobs"], "measured": r["measured"]}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -971,16 +1070,20 @@ def main():
                     help="S passes on the tensor cores: 1 = 3xTF32 split, 2 = 3xFP16 split")
     ap.add_argument("--vec-fp64", type=int, default=1,
                     help="xi/eta recurrence vectors in FP64 (default; 0 = FP32)")
+    ap.add_argument("--tuned", type=int, default=1,
+                    help="use the launch knobs the autotuner cached for this GPU (--workload tune)")
     ap.add_argument("--per-edge-updates", type=int, default=64,
                     help="stream workload: updates of the per-edge S-pass replica")
     ap.add_argument("--accuracy-updates", type=int, default=32,
                     help="stream workload: updates checked against the same-K FP64 oracle (0 = skip)")
     ap.add_argument("--workload", default="stream",
-                    choices=["stream", "batched", "multi", "column", "grad", "accelerate"],
+                    choices=["stream", "batched", "multi", "column", "grad", "accelerate", "tune"],
                     help="stream: the benchmarked update stream; batched: one-shot vs per-edge; "
                          "multi: many graphs batched vs per-graph launches; column: column-block "
                          "mode queries")
     ap.add_argument("--column-n", type=int, default=CN, help="column workload: node count")
+    ap.add_argument("--column-blocks", type=int, default=1,
+                    help="column workload: also store a sink-concentrated batch as blocks vs units")
     ap.add_argument("--fd-edges", type=int, default=3, help="grad workload: edges checked by FD")
     ap.add_argument("--graphs", type=int, default=MG, help="multi workload: number of graphs")
     ap.add_argument("--multi-tc", type=int, default=1,
@@ -1005,6 +1108,9 @@ def main():
         return
     if args.workload == "accelerate":
         run_accelerate(args)
+        return
+    if args.workload == "tune":
+        run_tune(args)
         return
     if args.impl == "reference":
         run_reference(args, rank)

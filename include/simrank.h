@@ -220,7 +220,17 @@ typedef struct simrank_stats {
 } simrank_stats;
 simrank_status simrank_get_stats(simrank_t h, simrank_stats* out);
 
-/* Re-anchors S to the fixed point of Eq. 1 on the current graph by up to
+/* Changes the launch shape of a handle's later updates without touching its
+ * state: defer, tc, prep_ctas, prep_cache, prep_item and s_kernel are taken
+ * from *knobs (validated as by simrank_init; every other field is ignored).
+ * Pending updates are applied first (synchronises).  The results of the
+ * method do not depend on these fields beyond rounding (the tensor-core and
+ * CUDA-core S passes and the FP16 / TF32 splits round differently).  This is
+ * the call the autotuner (paper_1711_00121_gb300.tune) times its candidates
+ * through; the paper has no counterpart. */
+simrank_status simrank_set_launch(simrank_t h, const simrank_config* knobs);
+
+/* Re-anchors S to the fixed point of Eq. 1 on the current graph by up to/* Re-anchors S to the fixed point of Eq. 1 on the current graph by up to
  * `sweeps` Jacobi sweeps started from the current S (drift correction after
  * long FP32 update streams).  *max_change (nullable) receives the max-abs
  * change of the last sweep.  Synchronises. */

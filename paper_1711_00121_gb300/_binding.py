@@ -86,6 +86,7 @@ SIGNATURES = {
     "simrank_destroy": (None, [_P]),
     "simrank_get_stats": (_I32, [_P, ctypes.POINTER(Stats)]),
     "simrank_reanchor": (_I32, [_P, _I32, ctypes.POINTER(ctypes.c_double)]),
+    "simrank_set_launch": (_I32, [_P, ctypes.POINTER(Config)]),
     "simrank_plan_batch": (_I32, [_P, _I64, _I32, _I32, ctypes.POINTER(_I32), _P, _P, _P, _P]),
     "simrank_grad": (_I32, [_P, _P, _P, _P, _I64, ctypes.POINTER(ctypes.c_double), _P]),
     "simrank_update_noalloc": (_I32, [_I32, _I64, _P, _I32, _P, _P, _P, _P, _I32, _I32, _I32, _I32,
@@ -157,8 +158,18 @@ def updates_array(upd) -> np.ndarray:
 class SimRank:
     """Handle on a graph and its SimRank matrix in GPU memory."""
 
-    def __init__(self, n, src, dst, weight=None, S0=None, stream=None, **cfg_kw):
+    def __init__(self, n, src, dst, weight=None, S0=None, stream=None, tuned=False, **cfg_kw):
+        """cfg_kw: simrank_config fields.  tuned=True takes the launch knobs the
+        autotuner cached for this GPU and shape (paper_1711_00121_gb300.tune)
+        for every knob not given explicitly."""
         self._h = None
+        if tuned:
+            from .tune import tuned_knobs
+
+            probe = default_config(**cfg_kw)
+            for k, v in tuned_knobs("stream", n, probe.K, probe.s_precision, probe.vec_fp64).items():
+                cfg_kw.setdefault(k, v)
+        self.tuned_config = dict(cfg_kw)
         cfg = default_config(**cfg_kw)
         if stream is not None:
             cfg.cuda_stream = stream
@@ -239,6 +250,17 @@ class SimRank:
                                   _ptr(g)), self._h)
         return L.value, g
 
+    def set_launch(self, **knobs):
+        """Changes the launch shape of later updates (defer, tc, prep_ctas,
+        prep_cache, prep_item, s_kernel); other config fields keep their values."""
+        cfg = Config()
+        ctypes.memmove(ctypes.byref(cfg), ctypes.byref(self.config), ctypes.sizeof(Config))
+        for k, v in knobs.items():
+            setattr(cfg, k, v)
+        _check(lib().simrank_set_launch(self._h, ctypes.byref(cfg)), self._h)
+        for k, v in knobs.items():
+            setattr(self.config, k, v)
+
     def reanchor(self, sweeps):
         d = ctypes.c_double()
         _check(lib().simrank_reanchor(self._h, int(sweeps), ctypes.byref(d)), self._h)
@@ -257,7 +279,17 @@ class MultiSimRank:
     ``graphs`` is a list of (n, src, dst) or (n, src, dst, n_capacity).
     """
 
-    def __init__(self, graphs, stream=None, **cfg_kw):
+    def __init__(self, graphs, stream=None, tuned=False, **cfg_kw):
+        """graphs as above; cfg_kw: simrank_config fields; tuned=True takes the
+        S-pass form the autotuner cached for this GPU (unless tc is given)."""
+        if tuned:
+            from .tune import tuned_knobs
+
+            probe = default_config(**cfg_kw)
+            nmax = max(int(gr[0]) for gr in graphs)
+            for k, v in tuned_knobs("multi", nmax, probe.K, probe.s_precision, 0).items():
+                cfg_kw.setdefault(k, v)
+        self.tuned_config = dict(cfg_kw)
         cfg = default_config(**cfg_kw)
         if stream is not None:
             cfg.cuda_stream = stream

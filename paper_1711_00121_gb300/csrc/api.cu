@@ -1084,9 +1084,10 @@ simrank_status upload_chunks(simrank_ctx* h, const std::vector<RowChunk>& v, Chu
 // SR_APPLY_SINK_BLOCKS, a sink block of delta sources into j (Table 2, the
 // batch scheme of §8 that the closing remark of §7 combines with Alg 7).  The
 // old columns S_{*,i} (i in I) and S_{*,j} come from Procedure 1 on the
-// current graph; the sources' columns are summed (Table 2 needs their sum and
-// S_II), at most 31 of them per Procedure-1 block, so memory stays
-// O(n (delta + K) + m).  d_cols holds the delta sources then j (device).
+// current graph; Table 2 needs only the sum of the sources' columns and S_II,
+// and Procedure 1 started from the indicator of the sources gives that sum as
+// one column, so memory stays O(Kn + m) for any delta.  d_cols holds the
+// delta sources then j (device).
 simrank_status run_column_update(simrank_ctx* h, const std::vector<int32_t>& srcs, int j, int op,
                                  int d_j, int64_t op_begin, int64_t op_end, int32_t* d_cols) {
   const int K = h->cfg.K, n_pad = h->n_pad, nT = (h->n_cur + PT - 1) / PT;
@@ -1096,35 +1097,19 @@ simrank_status run_column_update(simrank_ctx* h, const std::vector<int32_t>& src
   cols.push_back(j);
   CUDA_TRY(h, cudaMemcpyAsync(d_cols, cols.data(), cols.size() * sizeof(int32_t),
                               cudaMemcpyHostToDevice, h->st));
-  constexpr int BMAX = 32;
-  const int bw = std::min<int>(BMAX, delta + 1);
-  const size_t blk = (size_t)n_pad * bw * sizeof(double);
+  // one Procedure-1 block of two columns: column 0 starts from the
+  // indicator of the sources (Procedure 1 is linear, so it yields
+  // sum_i S_{*,i} directly), column 1 from e_j
+  const size_t blk = (size_t)n_pad * 2 * sizeof(double);
   if ((s = ob_ensure(h, 10, blk * (K + 1))) != SR_OK) return s;
   if ((s = ob_ensure(h, 11, blk * 3)) != SR_OK) return s;
   unsigned char* w = (unsigned char*)h->ob[11].p;
-  if (delta + 1 <= BMAX) {
-    // sources and sink in one block
-    launch_partial_sim_block(h->cur_fwd, h->cur_hor, h->dout.col, h->din.col, h->din.len, d_cols,
-                             delta + 1, n_pad, K, h->cfg.C, 64, h->ob[10].p, w, w + blk,
-                             w + 2 * blk, h->st);
-    launch_col_sum(w + 2 * blk, 64, delta + 1, 0, delta, n_pad, 0, h->sI, h->st);
-    launch_col_extract(w + 2 * blk, 64, delta + 1, delta, n_pad, h->sJ, h->st);
-    h->launches += 2 * K + 4;
-  } else {
-    for (int c0 = 0; c0 < delta; c0 += BMAX - 1) {
-      const int B = std::min(BMAX - 1, delta - c0);
-      launch_partial_sim_block(h->cur_fwd, h->cur_hor, h->dout.col, h->din.col, h->din.len,
-                               d_cols + c0, B, n_pad, K, h->cfg.C, 64, h->ob[10].p, w, w + blk,
-                               w + 2 * blk, h->st);
-      launch_col_sum(w + 2 * blk, 64, B, 0, B, n_pad, c0 > 0 ? 1 : 0, h->sI, h->st);
-      h->launches += 2 * K + 3;
-    }
-    launch_partial_sim_block(h->cur_fwd, h->cur_hor, h->dout.col, h->din.col, h->din.len,
-                             d_cols + delta, 1, n_pad, K, h->cfg.C, 64, h->ob[10].p, w, w + blk,
-                             w + 2 * blk, h->st);
-    launch_col_extract(w + 2 * blk, 64, 1, 0, n_pad, h->sJ, h->st);
-    h->launches += 2 * K + 3;
-  }
+  launch_partial_sim_block(h->cur_fwd, h->cur_hor, h->dout.col, h->din.col, h->din.len, d_cols, 2,
+                           n_pad, K, h->cfg.C, 64, h->ob[10].p, w, w + blk, w + 2 * blk, h->st,
+                           WeightView(), delta);
+  launch_col_extract(w + 2 * blk, 64, 2, 0, n_pad, h->sI, h->st);
+  launch_col_extract(w + 2 * blk, 64, 2, 1, n_pad, h->sJ, h->st);
+  h->launches += 2 * K + 5;
   // S_II and w_j = (1/delta) (Q S_{*,I})_j on the graph before the update
   launch_scalars_from_rows(h->din, h->sI, h->sJ, d_cols, delta, j, h->scal, h->st);
   const bool f32 = h->cfg.s_precision == 32;
@@ -1893,6 +1878,38 @@ simrank_status simrank_get_stats(simrank_t h, simrank_stats* out) {
   r.s_update_ms = h->prof_ms;
   for (int q = 0; q < 4; ++q) r.phase_ms[q] = h->phase_ms[q];
   *out = r;
+  return SR_OK;
+}
+
+simrank_status simrank_set_launch(simrank_t h, const simrank_config* knobs) {
+  if (!h || !knobs) return fail(h, SR_ERR_ARG, "null argument");
+  const simrank_config& k = *knobs;
+  if (k.prep_ctas < 0 || k.prep_cache < 0 || k.prep_cache > 16384 || k.prep_cache % 4 ||
+      k.prep_item < 0)
+    return fail(h, SR_ERR_ARG, "prep_ctas, prep_item >= 0; prep_cache a multiple of 4 in [0, 16384]");
+  if (k.defer < 0 || (k.defer > 1 && (int64_t)k.defer * h->K1 > 4096))
+    return fail(h, SR_ERR_ARG, "defer * (K + 1) must be at most 4096");
+  if (k.tc < 0 || k.tc > 2) return fail(h, SR_ERR_ARG, "tc must be 0, 1 or 2");
+  if (k.tc && h->cfg.s_precision != 32)
+    return fail(h, SR_ERR_ARG, "the tensor-core update needs s_precision = 32");
+  if (k.s_kernel < 0 || k.s_kernel > 1) return fail(h, SR_ERR_ARG, "s_kernel must be 0 or 1");
+  // pending updates are applied under the old group size, whose buffers go
+  simrank_status s = flush_pending(h);
+  if (s != SR_OK) return s;
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  if (h->Pp && std::max(1, (int)k.defer) != group(h)) {
+    cudaFree(h->Pp);
+    cudaFree(h->pXi);
+    cudaFree(h->pEta);
+    h->Pp = nullptr;
+    h->pXi = h->pEta = nullptr;
+  }
+  h->cfg.defer = k.defer;
+  h->cfg.tc = k.tc;
+  h->cfg.prep_ctas = k.prep_ctas;
+  h->cfg.prep_cache = k.prep_cache;
+  h->cfg.prep_item = k.prep_item;
+  h->cfg.s_kernel = k.s_kernel;
   return SR_OK;
 }
 

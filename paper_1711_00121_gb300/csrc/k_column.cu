@@ -26,6 +26,17 @@ __global__ void k_col_unit(const int32_t* __restrict__ cols, int B, T* __restric
   if (c < B) X0[(int64_t)cols[c] * B + c] = (T)1;
 }
 
+// Column 0 of X0 = the indicator of the distinct ids cols[0 .. g0), column c
+// (1 <= c < B) = e_{cols[g0 + c - 1]}: Procedure 1 is linear in its start
+// vector, so column 0 of its result is the sum of the g0 columns.
+template <typename T>
+__global__ void k_col_unit_grouped(const int32_t* __restrict__ cols, int g0, int B,
+                                   T* __restrict__ X0) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < g0) X0[(int64_t)cols[q] * B] = (T)1;
+  else if (q < g0 + B - 1) X0[(int64_t)cols[q] * B + (q - g0 + 1)] = (T)1;
+}
+
 // Y[a][c] = s * X[a][c] (X may be null: Y = 0), a < n_rows, c < B
 template <typename T>
 __global__ void k_col_fill(const T* __restrict__ X, double s, T* __restrict__ Y, int64_t count) {
@@ -317,29 +328,20 @@ __global__ void k_col_extract(const T* __restrict__ Y, int B, int c, int n, doub
   if (a < n) v[a] = (double)Y[(int64_t)a * B + c];
 }
 
-// v[a] (+)= sum_{c0 <= c < c1} Y[a][c]: the old column S_{*,I} summed over a
-// sink block's sources (Table 2 needs only their sum and S_II)
-template <typename T>
-__global__ void k_col_sum(const T* __restrict__ Y, int B, int c0, int c1, int n, int accumulate,
-                          double* __restrict__ v) {
-  const int a = blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= n) return;
-  double s = accumulate ? v[a] : 0.0;
-  for (int c = c0; c < c1; ++c) s += (double)Y[(int64_t)a * B + c];
-  v[a] = s;
-}
-
 }  // namespace
 
 template <typename T>
 static void partial_sim_block_t(const ChunkList& fwd, const ChunkList& hor, const int32_t* out_col,
                                 const int32_t* in_col, const WeightView& wv, const int32_t* in_len,
                                 const int32_t* cols, int B, int n_rows, int K, double C, T* xs, T* y0,
-                                T* y1, T* result, cudaStream_t st) {
+                                T* y1, T* result, cudaStream_t st, int group0) {
   const int64_t blk = (int64_t)n_rows * B;
   const int fill_blocks = 4096;
   k_col_fill<T><<<fill_blocks, 256, 0, st>>>(nullptr, 0.0, xs, blk);
-  k_col_unit<T><<<(B + 127) / 128, 128, 0, st>>>(cols, B, xs);
+  if (group0 > 1)
+    k_col_unit_grouped<T><<<(group0 + B + 126) / 128, 128, 0, st>>>(cols, group0, B, xs);
+  else
+    k_col_unit<T><<<(B + 127) / 128, 128, 0, st>>>(cols, B, xs);
   const int ygroups = (B + 127) / 128;
   const int tpb = B >= 128 ? 128 : (B + 31) / 32 * 32;
   // FP32 blocks of a multiple of 4 columns: four columns per thread
@@ -421,13 +423,14 @@ static void partial_sim_block_t(const ChunkList& fwd, const ChunkList& hor, cons
 void launch_partial_sim_block(const ChunkList& fwd, const ChunkList& hor, const int32_t* out_col,
                               const int32_t* in_col, const int32_t* in_len, const int32_t* cols,
                               int B, int n_rows, int K, double C, int prec, void* xs, void* y0,
-                              void* y1, void* result, cudaStream_t st, const WeightView& wv) {
+                              void* y1, void* result, cudaStream_t st, const WeightView& wv,
+                              int group0) {
   if (prec == 64)
     partial_sim_block_t<double>(fwd, hor, out_col, in_col, wv, in_len, cols, B, n_rows, K, C,
-                                (double*)xs, (double*)y0, (double*)y1, (double*)result, st);
+                                (double*)xs, (double*)y0, (double*)y1, (double*)result, st, group0);
   else
     partial_sim_block_t<float>(fwd, hor, out_col, in_col, wv, in_len, cols, B, n_rows, K, C,
-                               (float*)xs, (float*)y0, (float*)y1, (float*)result, st);
+                               (float*)xs, (float*)y0, (float*)y1, (float*)result, st, group0);
 }
 
 // Y = Q^T X (FP64 blocks [n_rows][B])
@@ -505,14 +508,6 @@ void launch_col_out(const void* Y, int prec, int B, int n, void* out, int out_fp
     else
       k_col_out<float, float><<<grid, 256, 0, st>>>((const float*)Y, B, n, (float*)out);
   }
-}
-
-void launch_col_sum(const void* Y, int prec, int B, int c0, int c1, int n, int accumulate, double* v,
-                    cudaStream_t st) {
-  if (prec == 64)
-    k_col_sum<double><<<(n + 255) / 256, 256, 0, st>>>((const double*)Y, B, c0, c1, n, accumulate, v);
-  else
-    k_col_sum<float><<<(n + 255) / 256, 256, 0, st>>>((const float*)Y, B, c0, c1, n, accumulate, v);
 }
 
 void launch_col_extract(const void* Y, int prec, int B, int c, int n, double* v, cudaStream_t st) {

@@ -350,7 +350,7 @@ void launch_partial_sim_block(const ChunkList& fwd, const ChunkList& hor, const 
                               const int32_t* in_col, const int32_t* in_len, const int32_t* cols,
                               int B, int n_rows, int K, double C, int prec, void* xs, void* y0,
                               void* y1, void* result, cudaStream_t st,
-                              const WeightView& wv = WeightView());
+                              const WeightView& wv = WeightView(), int group0 = 1);
 void launch_col_forward64(const ChunkList& fwd, const int32_t* out_col, const WeightView& wv,
                           const int32_t* in_len, const double* X, double* Y, int B, int n_rows,
                           cudaStream_t st);
@@ -372,9 +372,6 @@ void launch_col_scalars(const DevAdj& in, const double* si, const double* sj, in
                         double* scal, cudaStream_t st);
 void launch_col_out(const void* Y, int prec, int B, int n, void* out, int out_fp64, cudaStream_t st);
 void launch_col_extract(const void* Y, int prec, int B, int c, int n, double* v, cudaStream_t st);
-// v[a] = sum_{c0 <= c < c1} Y[a][c] (plus the old v[a] when accumulate != 0)
-void launch_col_sum(const void* Y, int prec, int B, int c0, int c1, int n, int accumulate, double* v,
-                    cudaStream_t st);
 
 // ---- adjoint (k_adjoint.cu)
 // G[e] += scale * sum_{x < B} F[u][x] Y[v][x] for every in-list entry e (row u,

@@ -100,7 +100,7 @@ def test_column_mode_fp32_query_widths(P, width):
 def test_column_mode_sink_blocks(P, prec):
     """Alg 7 fed by similar-sink blocks (§8; the closing remark of §7): a batch
     with deletions and new nodes, then a block of 40 insertions into one sink
-    (its source columns summed over two Procedure-1 blocks), against the
+    (one Procedure-1 column started from the indicator of its 40 sources), against the
     oracle's column form at the same K (old columns by PartialSim at K)."""
     from synth import batch_with_new_nodes
 
