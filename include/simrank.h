@@ -122,8 +122,11 @@ typedef struct simrank_config {
                              graphs before their S passes and one S pass over all their tiles,
                              replayed from a CUDA graph; 1 = the same kernels launched graph by
                              graph (the per-graph-launch baseline) */
-  int32_t prep_item;      /* chain = 0: nonzeros per work item of the fused launch's gathers
-                             (0 = 1024); a tile with more nonzeros is split over several CTAs */
+  int32_t prep_item;      /* chain = 0: 0 (default) = the nonzeros of all rows split evenly over
+                             the CTAs of the fused launch, two per thread (work items of 1024
+                             when that does not fit); > 0 = work items of at most this many
+                             nonzeros inside one 128-row tile, a tile with more split over
+                             several CTAs */
   int32_t upper_only;     /* dense mode: 1 = keep only the 128 x 128 tiles of S on or above the
                              block diagonal current (S is symmetric; updates then read and write
                              half the bytes, and reads of a lower tile take its mirror); 0 = keep

@@ -70,7 +70,9 @@ struct simrank_ctx {
   int order_n = 0;
   uint64_t* d_jobs = nullptr;    // the same pairs, two per job where they share I
   int jobs_n = 0;
-  void* W = nullptr;             // (xi, eta) working columns of the pre-update kernel
+  void* W = nullptr;              // (xi, eta) working columns of the pre-update kernel
+  void* rinv = nullptr;           // its per-row (C / in-degree, 1 / in-degree)
+  int32_t* loff = nullptr;        // its per-row offsets inside the tile
   int* tile_nnz = nullptr;       // per-tile nonzeros (scratch of the pre-update kernel)
   // per-call staging
   int32_t* d_srcs = nullptr;
@@ -632,9 +634,14 @@ simrank_status run_rank_one(simrank_ctx* h, int64_t src_off, int delta, int j, i
     pp.nT_cap = h->nT_cap;
     if (!h->W) {
       CUDA_TRY(h, cudaMalloc(&h->W, (size_t)h->K1 * h->n_pad * 2 * sizeof(double)));
+      CUDA_TRY(h, cudaMalloc(&h->rinv, (size_t)h->n_pad * 2 * sizeof(double)));
+      CUDA_TRY(h, dev_alloc(&h->loff, (size_t)h->n_pad));
       CUDA_TRY(h, dev_alloc(&h->tile_nnz, (size_t)h->nT_cap));
     }
     pp.W = h->W;
+    pp.rinv = h->rinv;
+    pp.loff = h->loff;
+    pp.flat = h->cfg.prep_item == 0 ? 1 : 0;
     pp.tile_nnz = h->tile_nnz;
     pp.bar = h->gbar + 2;
     pp.limit = wait_limit(h);
@@ -1207,7 +1214,7 @@ void free_ctx(simrank_ctx* h) {
                   h->dout.col,  h->d_in_w,   h->d_wsum,    h->S,          h->P64,
                   h->P32,       h->mXi,      h->mEta,      h->tiles,      h->ntiles,
                   h->sI,        h->sJ,       h->scal,      h->counters,   h->diffbits,
-                  h->gbar,      h->W,        h->tile_nnz,  h->d_order,    h->d_jobs,
+                  h->gbar,      h->W,        h->rinv,       h->loff,     h->tile_nnz,  h->d_order,    h->d_jobs,
                   h->d_srcs,    h->d_ops,    h->d_cols,     h->d_ext2int};
   for (void* p : ptrs)
     if (p) cudaFree(p);

@@ -14,12 +14,17 @@
 // Phases and steps are separated by a bounded grid barrier.
 //
 // Work split.  A gather of one scattered vector element per nonzero is bound
-// by the L1 throughput of the SM that issues it, so the nonzeros, not the
-// rows, are spread evenly: every 128-row tile is cut into items of at most
-// `item` flattened nonzeros, and items go round-robin to the CTAs (a hub row
-// with thousands of in-neighbours spreads over many SMs).  Each CTA keeps the
-// row extents and column indices of its first items in shared memory for all
-// K steps.  Partial row sums are combined within a warp and added to the next
+// by the L1 throughput of the SM that issues it, and on GB300 the FP64 form
+// by the FP64 issue rate of the SM, so the nonzeros, not the rows, are spread
+// evenly.  Flat split (default): the in-lists of all rows, flattened in row
+// order, are cut into equal contiguous ranges, one per CTA, two nonzeros per
+// thread, located once per launch from the tile offsets and the in-tile row
+// offsets that phase 0 writes.  Item split (a set `item`, or too many
+// nonzeros for two per thread): every 128-row tile is cut into items of at
+// most `item` flattened nonzeros, and items go round-robin to the CTAs (a hub
+// row with thousands of in-neighbours spreads over many SMs); each CTA keeps
+// the row extents and column indices of its first items in shared memory for
+// all K steps.  Partial row sums are combined within a warp and added to the next
 // column with global atomics.  xi_k and eta_k are kept interleaved in the
 // working buffer W[k][a] (one 8- or 16-byte load per nonzero).  Row-wise work
 // (gamma; after the last step, the copy of the columns into the tile-blocked
@@ -126,6 +131,15 @@ __device__ __forceinline__ V2<float> ld_v2(const V2<float>* p) {
 }
 __device__ __forceinline__ V2<double> ld_v2(const V2<double>* p) {
   const double2 v = *reinterpret_cast<const double2*>(p);
+  return V2<double>{v.x, v.y};
+}
+
+__device__ __forceinline__ V2<float> ld_v2cg(const V2<float>* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return V2<float>{v.x, v.y};
+}
+__device__ __forceinline__ V2<double> ld_v2cg(const V2<double>* p) {
+  const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
   return V2<double>{v.x, v.y};
 }
 
@@ -307,6 +321,9 @@ struct StepPair {
 };
 
 template <typename V>
+__device__ __forceinline__ void pair_pattern(StepPair<V>& q);
+
+template <typename V>
 __device__ __forceinline__ StepPair<V> pair_setup(const PrepItem& it, const int* __restrict__ cc,
                                                   const int32_t* __restrict__ col) {
   const Run run = item_run(it);
@@ -326,17 +343,31 @@ __device__ __forceinline__ StepPair<V> pair_setup(const PrepItem& it, const int*
       if (r2 != q.kh) q.kt = r2;
     }
   }
+  pair_pattern(q);
+  return q;
+}
+
+// The warp-wide pattern of a step for threads whose (ca, cb, kh, kt) are set:
+// row keys must not decrease with the lane.
+template <typename V>
+__device__ __forceinline__ void pair_pattern(StepPair<V>& q) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   // every lane takes part in the warp-wide intrinsics below
   const unsigned same = __match_any_sync(full, q.kh);
   const int seg = (q.kh >= 0) ? __popc(same) : 1;
   q.span = __reduce_max_sync(full, (unsigned)seg);
+  // a segment's lanes are consecutive (row keys do not decrease with the lane):
+  // a tree over the segment that leaves the total in its first lane only adds,
+  // in round b, the partial of lane + 2^b into the lanes at positions 0 mod
+  // 2^(b+1), so a segment of s lanes costs s - 1 additions
+  const int pos = lane - (__ffs(same) - 1);
   q.fl = 0;
 #pragma unroll
   for (int b = 0; b < 5; ++b) {
     const int k2 = __shfl_down_sync(full, q.kh, 1 << b);
-    if (lane + (1 << b) < 32 && k2 == q.kh && q.kh >= 0) q.fl |= 1u << b;
+    if (lane + (1 << b) < 32 && k2 == q.kh && q.kh >= 0 && (pos & ((2 << b) - 1)) == 0)
+      q.fl |= 1u << b;
   }
   const int kt_prev = __shfl_up_sync(full, q.kt, 1);
   const int kh_prev = __shfl_up_sync(full, q.kh, 1);
@@ -344,25 +375,23 @@ __device__ __forceinline__ StepPair<V> pair_setup(const PrepItem& it, const int*
   if (lane > 0 && q.kh >= 0 && kt_prev == q.kh) q.fl |= 1u << 5;
   if (q.kh >= 0 && (lane == 0 || kh_prev != q.kh)) q.fl |= 1u << 6;
   if (q.kt >= 0 && !(lane < 31 && kh_next == q.kt)) q.fl |= 1u << 7;
-  return q;
 }
 
 // One step of the recurrence for a thread set up by pair_setup: gathers its
 // (xi_k, eta_k) entries, adds the rows up across the warp and emits each row's
 // sum (times C / in-degree for xi, 1 / in-degree for eta; rc / ri hold those
 // factors per row of the item's tile) into W[k + 1].
-template <typename V>
-__device__ __forceinline__ void pair_step(const StepPair<V>& q, const V2<V>* Wk, V2<V>* Wn,
-                                          const V* rc, const V* ri) {
+template <typename V, typename Gf, typename Emit>
+__device__ __forceinline__ void pair_step(const StepPair<V>& q, Gf gather, Emit emit) {
   const unsigned full = 0xffffffffu;
   V ha = V(0), hb = V(0), ta = V(0), tb = V(0);
   if (q.ca >= 0) {
-    const V2<V> v = ld_v2(Wk + q.ca);
+    const V2<V> v = gather(q.ca);
     ha = v.x;
     hb = v.y;
   }
   if (q.cb >= 0) {
-    const V2<V> v = ld_v2(Wk + q.cb);
+    const V2<V> v = gather(q.cb);
     if (q.kt >= 0) {
       ta = v.x;
       tb = v.y;
@@ -387,8 +416,49 @@ __device__ __forceinline__ void pair_step(const StepPair<V>& q, const V2<V>* Wk,
     ha += pa;
     hb += pb;
   }
-  if ((q.fl & (1u << 6)) && (nz(ha) || nz(hb))) red_add2(Wn + q.kh, ha * rc[q.kh], hb * ri[q.kh]);
-  if ((q.fl & (1u << 7)) && (nz(ta) || nz(tb))) red_add2(Wn + q.kt, ta * rc[q.kt], tb * ri[q.kt]);
+  if ((q.fl & (1u << 6)) && (nz(ha) || nz(hb))) emit(q.kh, ha, hb);
+  if ((q.fl & (1u << 7)) && (nz(ta) || nz(tb))) emit(q.kt, ta, tb);
+}
+
+// The flat split: CTA c takes the nonzeros [c E, (c + 1) E) of the in-lists of
+// all rows flattened in row order, E = ceil(nnz / CTAs), two per thread, so
+// every CTA gets the same number whatever the tiles hold.  Nonzero e is found
+// by its tile (tile offsets toff, shared) and its row in the tile (in-tile row
+// offsets loff, global); rows are keyed by their global index.
+__device__ __forceinline__ void flat_locate(const int* toff, int nT, const int* __restrict__ loff,
+                                            const DevAdj& in, int e, int& row, int& col) {
+  int lo = 0, hi = nT;  // the last tile T with toff[T] <= e
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (toff[mid] <= e) lo = mid; else hi = mid;
+  }
+  const int l = e - toff[lo];
+  const int* lt = loff + (int64_t)lo * PT;
+  int a = 0, b = PT;  // the last row of the tile with loff <= l
+  while (b - a > 1) {
+    const int mid = (a + b) >> 1;
+    if (__ldcg(lt + mid) <= l) a = mid; else b = mid;
+  }
+  row = lo * PT + a;
+  col = __ldcg(in.col + __ldcg(in.start + row) + (l - __ldcg(lt + a)));
+}
+
+template <typename V>
+__device__ __forceinline__ StepPair<V> flat_setup(const int* toff, int nT, const int* loff,
+                                                  const DevAdj& in, int e0, int e1) {
+  StepPair<V> q;
+  q.ca = q.cb = q.kh = q.kt = -1;
+  const int e = e0 + 2 * (int)threadIdx.x;
+  if (e < e1) {
+    flat_locate(toff, nT, loff, in, e, q.kh, q.ca);
+    if (e + 1 < e1) {
+      int r2;
+      flat_locate(toff, nT, loff, in, e + 1, r2, q.cb);
+      if (r2 != q.kh) q.kt = r2;
+    }
+  }
+  pair_pattern(q);
+  return q;
 }
 
 __device__ void prep_patch(const PatchOp* __restrict__ ops, int64_t begin, int64_t end,
@@ -422,6 +492,7 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ V red[4][2][PT];
   __shared__ V rrc[PT], rri[PT];  // C / in-degree and 1 / in-degree of the rows of item 0
+  __shared__ V2<V> fsh[PG][2];      // flat split: the same for each thread's head / tail row
   __shared__ unsigned long long mk[PREP_MT][2];
   __shared__ int wsum[PG / 32];
   __shared__ int s_ok;
@@ -440,6 +511,7 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
   V* sI = static_cast<V*>(p.sI);
   V* sJ = static_cast<V*>(p.sJ);
   V2<V>* W = static_cast<V2<V>*>(p.W);
+  V2<V>* rinv = static_cast<V2<V>*>(p.rinv);  // (C / in-degree, 1 / in-degree) per row
   const int64_t ldk = p.ldk;
   auto pidx = [ldk](int64_t a, int which, int k) -> int64_t {
     return (((a / PT) * 2 + which) * ldk + k) * PT + (a % PT);
@@ -506,28 +578,41 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
     // it counts with its new length; no other row's length changes)
     int L = 0;
     if (part == 0) L = (a == p.j) ? new_len_j : p.in.len[a];
+    // inclusive scan of the row lengths over the tile (warps 0..3 hold its rows)
+    int incl = L;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) L += __shfl_xor_sync(0xffffffffu, L, o);
-    if (lane == 0) wsum[warp] = L;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
     __syncthreads();
     if (tid < PT) {
       sI[a] = (red[0][0][r] + red[1][0][r]) + (red[2][0][r] + red[3][0][r]);
       sJ[a] = (red[0][1][r] + red[1][1][r]) + (red[2][1][r] + red[3][1][r]);
+      int base = 0;
+      for (int w = 0; w < warp; ++w) base += wsum[w];
+      p.loff[a] = base + incl - L;  // nonzeros of the tile before row a
     }
     if (tid == 0) p.tile_nnz[T] = (wsum[0] + wsum[1]) + (wsum[2] + wsum[3]);
     __syncthreads();
   }
   alive = prep_barrier(p.bar, ++nb * G, p.limit, &s_ok);
 
-  // ---- phase 1: item table; w = Q sI summed by atomics into W[0].x
+  // ---- phase 1: the split of the nonzeros over the CTAs; w = Q sI summed by
+  // atomics into W[0].x
   int my_items = 0;
+  bool flat = false;
+  StepPair<V> q0;
   if (alive) {
-    {
-      // ioff[T] = items of tiles before T (tile T has ceil(nnz_T / item) items)
+    // ioff[T] = the units of the tiles before T: their nonzeros (flat split,
+    // tried first when allowed) or their items of at most `item` nonzeros
+    for (int pass = p.flat ? 0 : 1; pass < 2; ++pass) {
+      const int div = pass == 0 ? 1 : p.item;
       const int per = (nT + PG - 1) / PG;
       const int t0 = min(nT, tid * per), t1 = min(nT, t0 + per);
       int s = 0;
-      for (int T = t0; T < t1; ++T) s += (__ldcg(p.tile_nnz + T) + p.item - 1) / p.item;
+      for (int T = t0; T < t1; ++T) s += (__ldcg(p.tile_nnz + T) + div - 1) / div;
       int incl = s;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -551,10 +636,28 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
       int run = wsum[warp] + incl - s;
       for (int T = t0; T < t1; ++T) {
         ioff[T] = run;
-        run += (__ldcg(p.tile_nnz + T) + p.item - 1) / p.item;
+        run += (__ldcg(p.tile_nnz + T) + div - 1) / div;
       }
       __syncthreads();
+      if (pass == 0) {
+        // every CTA computes the same nnz, so the choice is uniform over the grid
+        const int nnz = ioff[nT];
+        const int per_cta = (nnz + G - 1) / G;
+        if (per_cta <= 2 * PG) {
+          flat = true;
+          const int e0 = min(nnz, (int)blockIdx.x * per_cta), e1 = min(nnz, e0 + per_cta);
+          q0 = flat_setup<V>(ioff, nT, p.loff, p.in, e0, e1);
+          break;
+        }
+        __syncthreads();  // ioff is rewritten by the item pass
+      }
     }
+  }
+  if (alive && flat) {
+    pair_step<V>(q0, [&](int b) { return V2<V>{sI[b], V(0)}; },
+                 [&](int r, V a, V) { red_add(&W[r].x, a); });
+    alive = prep_barrier(p.bar, ++nb * G, p.limit, &s_ok);
+  } else if (alive) {
     const int n_items = ioff[nT];
     my_items = (n_items > (int)blockIdx.x) ? (n_items - (int)blockIdx.x + G - 1) / G : 0;
     int cbase = 0;
@@ -599,6 +702,8 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
       if (tid < PT) {
         const int64_t a = (int64_t)T * PT + tid;
         const int len = __ldcg(p.in.len + a);
+        // the factors of row a of Q on the new graph, for every step below
+        const V inv = len > 0 ? V(1) / (V)len : V(0);
         const V y = __ldcg(&W[a].x);
         const double dl = (double)p.delta;
         V g;
@@ -639,6 +744,7 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
         }
         const V x0 = (a == p.j) ? Cv : V(0);
         W[a] = V2<V>{x0, g};
+        rinv[a] = V2<V>{Cv * inv, inv};
         P[pidx(a, 0, koff)] = (TS)x0;
         P[pidx(a, 1, koff)] = (TS)g;
         pe = nz(g);
@@ -654,26 +760,35 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
 
   // ---- phase 2: K steps
   // the CTA's first item takes the fixed per-thread form when it can
-  const bool pair0 = my_items > 0 && items[0].e1 - items[0].e0 <= 2 * PG;
-  StepPair<V> q0;
+  const bool pair0 = !flat && my_items > 0 && items[0].e1 - items[0].e0 <= 2 * PG;
   int64_t rb0 = 0;
+  if (flat) {
+    // flat split: the factors of each thread's head and tail rows
+    fsh[tid][0] = q0.kh >= 0 ? ld_v2cg(rinv + q0.kh) : V2<V>{V(0), V(0)};
+    fsh[tid][1] = q0.kt >= 0 ? ld_v2cg(rinv + q0.kt) : V2<V>{V(0), V(0)};
+  }
   if (pair0) {
     q0 = pair_setup<V>(items[0], cc, p.in.col);
     rb0 = (int64_t)items[0].T * PT;
     if (tid < PT) {
-      const int len = items[0].len[tid];
-      const V inv = len > 0 ? V(1) / (V)len : V(0);
-      rri[tid] = inv;
-      rrc[tid] = Cv * inv;
+      const V2<V> f = ld_v2cg(rinv + rb0 + tid);
+      rrc[tid] = f.x;
+      rri[tid] = f.y;
     }
     __syncthreads();
   }
   for (int k = 0; alive && k < K; ++k) {
     const V2<V>* Wk = W + (int64_t)k * p.n_pad;
     V2<V>* Wn = W + (int64_t)(k + 1) * p.n_pad;
+    if (flat)
+      pair_step<V>(q0, [&](int b) { return ld_v2(Wk + b); }, [&](int r, V a, V b) {
+        const V2<V> f = fsh[tid][r == q0.kh ? 0 : 1];
+        red_add2(Wn + r, a * f.x, b * f.y);
+      });
     for (int u = 0; u < my_items; ++u) {
       if (u == 0 && pair0) {
-        pair_step<V>(q0, Wk, Wn + rb0, rrc, rri);
+        pair_step<V>(q0, [&](int b) { return ld_v2(Wk + b); },
+                     [&](int r, V a, V b) { red_add2(Wn + rb0 + r, a * rrc[r], b * rri[r]); });
         continue;
       }
       PrepItem& it = items[min(u, MAXI)];
@@ -682,8 +797,8 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
       item_gather<V>(it, item_run(it), cc, p.in.col,
                      [&](int b) { return ld_v2(Wk + b); },
                      [&](int r, V a, V b) {
-                       const V inv = V(1) / (V)it.len[r];
-                       red_add2(Wn + rb + r, Cv * a * inv, b * inv);
+                       const V2<V> f = ld_v2cg(rinv + rb + r);
+                       red_add2(Wn + rb + r, a * f.x, b * f.y);
                      });
       __syncthreads();
     }

@@ -168,6 +168,9 @@ struct PrepParams {
   int item;
   int n_pad, nT_cap;
   void* W;
+  void* rinv;  // per row: (C / in-degree, 1 / in-degree) in the vector precision, n_pad pairs
+  int* loff;   // per row: nonzeros of its tile before it (n_pad)
+  int flat;    // 1: split the nonzeros evenly over the CTAs when two per thread suffice
   int* tile_nnz;
   unsigned int* bar;
   long long limit;

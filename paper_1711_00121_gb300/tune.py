@@ -6,7 +6,8 @@ computes (beyond rounding):
 - ``defer``: how many updates' S changes one S pass applies together (the
   pass then is one rank-2G(K+1) product);
 - ``tc``: the tensor-core split of that pass (1 = 3xTF32, 2 = 3xFP16);
-- ``prep_item``: nonzeros per work item of the pre-update kernel's gathers;
+- ``prep_item``: nonzeros per work item of the pre-update kernel's gathers
+  (0: an even split of all nonzeros over the CTAs);
 - ``prep_ctas``: the CTA cap of that kernel (0 = every co-resident CTA);
 - for many graphs (``MultiSimRank``): ``tc`` (tensor-core or CUDA-core pass).
 
@@ -125,7 +126,7 @@ def timing_updates(n: int, src, dst, count: int, seed: int = 0) -> np.ndarray:
 
 def stream_space(K: int, num_sms: int) -> dict:
     defer = [g for g in (16, 8, 24, 32) if g * (K + 1) <= 4096]
-    return {"defer": defer, "tc": [2, 1], "prep_item": [1024, 512, 2048], "prep_ctas": [0, num_sms]}
+    return {"defer": defer, "tc": [2, 1], "prep_item": [0, 1024, 512, 2048], "prep_ctas": [0, num_sms]}
 
 
 def tune_stream(n, src, dst, C: float = 0.6, K: int = 15, s_precision: int = 32, vec_fp64: int = 1,
