@@ -96,7 +96,8 @@ typedef struct simrank_config {
                              (or of every group of `defer` pending updates); 0 = CUDA cores */
   int32_t init_max_sweeps;/* cap on Jacobi sweeps of Eq. 1 at init / re-anchor */
   double init_tol;        /* init stops when a sweep changes S by less than this (max-abs);
-                             <= 0 selects 1e-13 (sweeps stored in FP32 are floored at 3e-7) */
+                             <= 0 selects 1e-13 (sweeps stored in FP32 stop at 1e-7 or at
+                             their rounding noise, below 3e-7) */
   int32_t profile;        /* 1: time every S-update launch with CUDA events (simrank_get_stats) */
   int32_t relabel;        /* 1: store nodes of in-degree 0 after the others, so that rows that no
                              update can reach (Thm 4) fill whole tiles; ids in the ABI are unchanged */
