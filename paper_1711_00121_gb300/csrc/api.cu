@@ -733,9 +733,13 @@ simrank_status jacobi_sweeps(simrank_ctx* h, int max_sweeps, double tol, double*
   const size_t fp64_budget = (size_t)48 << 30;
   const int wp = (sp == 64 || 3 * elems * 8 <= fp64_budget) ? 64 : 32;
   const size_t bytes = elems * (wp == 64 ? 8 : 4);
-  // sweeps stored in FP32 cannot change S by less than its rounding (about
-  // 6e-8 relative), so their stopping test is floored at 3e-7
-  if (wp == 32) tol = std::max(tol, 3e-7);
+  // sweeps stored in FP32 cannot change S by much less than its rounding
+  // (about 6e-8 relative): their stopping test is floored at 1e-7, and below
+  // 3e-7 they also stop once three sweeps in a row changed S no less than the
+  // sweep before (the change has reached the rounding noise)
+  if (wp == 32) tol = std::max(tol, 1e-7);
+  int flat_sweeps = 0;
+  double prev = INFINITY;
   void* bufs[3] = {nullptr, nullptr, nullptr};
   const bool alias = (wp == sp);
   for (int b = (alias ? 1 : 0); b < 3; ++b) {
@@ -775,6 +779,14 @@ simrank_status jacobi_sweeps(simrank_ctx* h, int max_sweeps, double tol, double*
     std::memcpy(&diff, &bits, sizeof(diff));
     if (it == 1 && first_diff) *first_diff = diff;
     if (diff < tol) break;
+    if (wp == 32) {
+      flat_sweeps = diff >= prev ? flat_sweeps + 1 : 0;
+      prev = diff;
+      if (diff < 3e-7 && flat_sweeps >= 3) {
+        tol = diff * 1.0000001;  // converged to the rounding noise of FP32 storage
+        break;
+      }
+    }
   }
   if (e == cudaSuccess) {
     launch_symmetrize(A, wp, h->n_pad, h->ld, h->st);
