@@ -1091,7 +1091,7 @@ def main():
                     help="multi workload: S passes on the tensor cores (TF32 split)")
     ap.add_argument("--batch", type=int, default=64, help="batched workload: edges per batch")
     ap.add_argument("--batch-k", type=int, default=BK,
-                    help="batched workload: K (25 as configured; 72 puts the truncation below 1e-8)")
+                    help="batched workload: K (25 as configured)")
     ap.add_argument("--per-edge-sample", type=int, default=256,
                     help="batched workload: per-edge updates timed per batch")
     args = ap.parse_args()

@@ -101,6 +101,13 @@ struct simrank_ctx {
     void* p = nullptr;
     size_t bytes = 0;
   } ob[24];
+  // column mode: per-tile nonzeros of the in-lists (host), the work-item table
+  // of the chain steps and its partial-sum accumulators (device)
+  std::vector<int64_t> col_tnnz;
+  int32_t* col_items = nullptr;  // item_tile | item_sub | tile_items
+  int64_t col_items_cap = 0;
+  double* col_gacc = nullptr;    // 2 x 128 doubles per tile, kept at zero between steps
+  unsigned int* col_tcount = nullptr;
   // deferred S updates: pending panels [T][which][G*K1][128] (FP32), count, tile masks
   float* Pp = nullptr;
   int np = 0;
@@ -1135,9 +1142,50 @@ simrank_status run_column_update(simrank_ctx* h, const std::vector<int32_t>& src
   launch_gamma(h->din, h->sI, h->sJ, h->scal, j, delta, op, d_j, h->cfg.C, nT, h->K1, h->P64,
                f32 ? h->P32 : nullptr, h->mXi, h->mEta, h->st);
   launch_patch(h->d_ops, op_begin, op_end, h->din, h->dout, h->st);
+  // the K steps on the new graph, tiles cut into work items of at most
+  // chain_item_size() nonzeros (the host mirror already holds the new graph)
+  if (h->col_tnnz.empty()) {
+    h->col_tnnz.assign(h->nT_cap, 0);
+    for (int a = 0; a < h->n_pad; ++a) h->col_tnnz[a / PT] += h->hin.len[a];
+  } else {
+    int64_t s_j = 0;
+    for (int a = (j / PT) * PT; a < (j / PT + 1) * PT; ++a) s_j += h->hin.len[a];
+    h->col_tnnz[j / PT] = s_j;
+  }
+  const int64_t item = chain_item_size();
+  std::vector<int32_t> it_tile, it_sub, t_items(nT);
+  for (int T = 0; T < nT; ++T) {
+    const int parts = (int)std::max<int64_t>(1, (h->col_tnnz[T] + item - 1) / item);
+    t_items[T] = parts;
+    for (int q = 0; q < parts; ++q) {
+      it_tile.push_back(T);
+      it_sub.push_back(q);
+    }
+  }
+  const int64_t n_items = (int64_t)it_tile.size();
+  const int64_t need = 2 * n_items + h->nT_cap;
+  if (need > h->col_items_cap) {
+    if (h->col_items) cudaFree(h->col_items);
+    h->col_items = nullptr;
+    CUDA_TRY(h, dev_alloc(&h->col_items, (size_t)need));
+    h->col_items_cap = need;
+  }
+  if (!h->col_gacc) {
+    CUDA_TRY(h, dev_alloc(&h->col_gacc, (size_t)h->nT_cap * 2 * PT));
+    CUDA_TRY(h, dev_alloc(&h->col_tcount, (size_t)h->nT_cap));
+    CUDA_TRY(h, cudaMemsetAsync(h->col_gacc, 0, (size_t)h->nT_cap * 2 * PT * sizeof(double), h->st));
+    CUDA_TRY(h, cudaMemsetAsync(h->col_tcount, 0, (size_t)h->nT_cap * sizeof(unsigned int), h->st));
+  }
+  int32_t* d_tile = h->col_items;
+  int32_t* d_sub = d_tile + n_items;
+  int32_t* d_titems = d_sub + n_items;
+  CUDA_TRY(h, cudaMemcpyAsync(d_tile, it_tile.data(), n_items * 4, cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(d_sub, it_sub.data(), n_items * 4, cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(d_titems, t_items.data(), nT * 4, cudaMemcpyHostToDevice, h->st));
   for (int k = 0; k < K; ++k)
-    launch_chain_step(h->din, k, h->cfg.C, nT, h->K1, h->P64, f32 ? h->P32 : nullptr, h->mXi,
-                      h->mEta, h->st);
+    launch_chain_step_items(h->din, d_tile, d_sub, d_titems, (int)n_items, k, h->cfg.C, h->K1,
+                            h->P64, f32 ? h->P32 : nullptr, h->mXi, h->mEta, h->col_gacc,
+                            h->col_tcount, h->st);
   LAUNCH_CHECK(h);
   h->launches += 3 + K;
   const size_t pbytes = (size_t)h->nT_cap * 2 * h->K1 * PT * (f32 ? 4 : 8);
@@ -1227,7 +1275,8 @@ void free_ctx(simrank_ctx* h) {
                   h->P32,       h->mXi,      h->mEta,      h->tiles,      h->ntiles,
                   h->sI,        h->sJ,       h->scal,      h->counters,   h->diffbits,
                   h->gbar,      h->W,        h->rinv,       h->loff,     h->tile_nnz,  h->d_order,    h->d_jobs,
-                  h->d_srcs,    h->d_ops,    h->d_cols,     h->d_ext2int};
+                  h->d_srcs,    h->d_ops,    h->d_cols,     h->d_ext2int, h->col_items,
+                  h->col_gacc,  h->col_tcount};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& b : h->ob)

@@ -179,6 +179,7 @@ __global__ void k_or_any(const uint64_t* __restrict__ mXi, const uint64_t* __res
 // sums its run in registers and flushes one partial sum per row it touches
 // into shared accumulators.  NV = number of gathered vectors (1 or 2).
 constexpr int GT = 512;  // threads of a gather CTA
+constexpr int CHAIN_ITEM = 16 * GT;  // nonzeros per work item of k_chain_step_items
 
 struct TileRows {
   int64_t start[PT];
@@ -224,8 +225,13 @@ __device__ __forceinline__ void tile_rows_load(const DevAdj& in, int T, TileRows
 template <int NV>
 __device__ __forceinline__ void warp_segment_flush(int key, double (&val)[NV], double (*acc)[PT]) {
   const int lane = threadIdx.x & 31;
+  // only as many rounds as the longest run of equal keys needs (GB300 issues
+  // each FP64 addition at 1/64 of the FP32 rate, predicated lanes included)
+  const unsigned same = __match_any_sync(0xffffffffu, key);
+  const int span = (int)__reduce_max_sync(0xffffffffu, key >= 0 ? (unsigned)__popc(same) : 1u);
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
+    if (o >= span) break;
     const int k2 = __shfl_down_sync(0xffffffffu, key, o);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -246,17 +252,20 @@ __device__ __forceinline__ void warp_segment_flush(int key, double (&val)[NV], d
 // rows that start and end inside its run are stored directly (no other
 // thread touches them); its first and last row may be shared with the
 // neighbouring runs and are combined by warp_segment_flush.
+// With g1 >= 0 only the flattened nonzeros [g0, g1) of the tile are gathered
+// (one work item of a tile split over several CTAs): acc then holds this
+// item's partial sums of the rows it touches.
 template <int NV, typename G>
 __device__ __forceinline__ void tile_gather(const DevAdj& in, const TileRows& tr, G gather,
-                                            double (*acc)[PT]) {
+                                            double (*acc)[PT], int g0 = 0, int g1 = -1) {
   const int tid = threadIdx.x;
   for (int r = tid; r < PT; r += GT)
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v][r] = 0.0;
   __syncthreads();
-  const int total = tr.off[PT];
-  const int per = (total + GT - 1) / GT;
-  const int e0 = tid * per;
+  const int total = g1 >= 0 ? g1 : tr.off[PT];
+  const int per = (total - g0 + GT - 1) / GT;
+  const int e0 = g0 + tid * per;
   const int e1 = min(total, e0 + per);
   int r_first = -1, r_last = -1;
   double pf[NV], pl[NV];
@@ -462,6 +471,84 @@ __global__ void __launch_bounds__(GT) k_chain_step(DevAdj in, int k, double C, i
   }
 }
 
+// The same step with the tiles cut into work items of at most CHAIN_ITEM
+// nonzeros (item q: tile item_tile[q], nonzeros [item_sub[q] * CHAIN_ITEM,
+// ...) of its flattened in-lists): a hub tile no longer holds one CTA for the
+// whole step.  The items of a tile with several add their partial row sums
+// into gacc[T]; the item that arrives last (counter tile_count[T]) finishes
+// the tile and clears gacc[T] and its counter for the next step.
+__global__ void __launch_bounds__(GT) k_chain_step_items(
+    DevAdj in, const int* __restrict__ item_tile, const int* __restrict__ item_sub,
+    const int* __restrict__ tile_items, int k, double C, int K1, double* __restrict__ P64,
+    float* __restrict__ P32, uint64_t* __restrict__ mXi, uint64_t* __restrict__ mEta,
+    double* __restrict__ gacc, unsigned int* __restrict__ tile_count) {
+  __shared__ TileRows tr;
+  __shared__ double acc[2][PT];
+  __shared__ int any_x, any_e, last;
+  const int tid = threadIdx.x;
+  const int q = blockIdx.x;
+  const int T = item_tile[q];
+  const int parts = tile_items[T];
+  if (tid == 0) {
+    any_x = 0;
+    any_e = 0;
+    last = 1;
+  }
+  tile_rows_load(in, T, tr);
+  const int g0 = item_sub[q] * CHAIN_ITEM;
+  const int g1 = min(tr.off[PT], g0 + CHAIN_ITEM);
+  const double* __restrict__ src = P64;
+  tile_gather<2>(in, tr,
+                 [&](int v, int b) {
+                   return src[(((int64_t)(b / PT) * 2 + v) * K1 + k) * PT + (b % PT)];
+                 },
+                 acc, g0, g1);
+  double* ga = gacc + (int64_t)T * 2 * PT;
+  if (parts > 1) {
+    if (tid < PT) {
+      if (acc[0][tid] != 0.0) atomicAdd(&ga[tid], acc[0][tid]);
+      if (acc[1][tid] != 0.0) atomicAdd(&ga[PT + tid], acc[1][tid]);
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = (atomicAdd(&tile_count[T], 1u) == (unsigned int)(parts - 1)) ? 1 : 0;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (tid < PT) {
+      acc[0][tid] = __ldcg(&ga[tid]);
+      acc[1][tid] = __ldcg(&ga[PT + tid]);
+      ga[tid] = 0.0;
+      ga[PT + tid] = 0.0;
+    }
+    if (tid == 0) tile_count[T] = 0u;
+    __syncthreads();
+  }
+  if (tid < PT) {
+    const int r = tid;
+    const int len = tr.len[r];
+    const double inv = (len > 0) ? 1.0 / (double)len : 0.0;
+    const double x = C * acc[0][r] * inv;
+    const double y = acc[1][r] * inv;
+    const int64_t bx = ((int64_t)T * 2 + 0) * K1 * PT + (int64_t)(k + 1) * PT + r;
+    const int64_t be = bx + (int64_t)K1 * PT;
+    P64[bx] = x;
+    P64[be] = y;
+    if (P32) {
+      P32[bx] = (float)x;
+      P32[be] = (float)y;
+    }
+    if (x != 0.0) any_x = 1;
+    if (y != 0.0) any_e = 1;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const unsigned long long bit = 1ull << ((k + 1) & 63);
+    if (any_x) atomicOr((unsigned long long*)&mXi[T], bit);
+    if (any_e) atomicOr((unsigned long long*)&mEta[T], bit);
+  }
+}
+
 __global__ void k_tile_list(const uint64_t* __restrict__ mXi, const uint64_t* __restrict__ mEta,
                             int nT, int aff, uint32_t* __restrict__ tiles,
                             int* __restrict__ ntiles) {
@@ -542,6 +629,16 @@ void launch_chain_step(const DevAdj& in, int k, double C, int nT, int K1, double
                        uint64_t* mXi, uint64_t* mEta, cudaStream_t st) {
   k_chain_step<<<nT, GT, 0, st>>>(in, k, C, K1, P64, P32, mXi, mEta);
 }
+
+void launch_chain_step_items(const DevAdj& in, const int* item_tile, const int* item_sub,
+                             const int* tile_items, int n_items, int k, double C, int K1,
+                             double* P64, float* P32, uint64_t* mXi, uint64_t* mEta, double* gacc,
+                             unsigned int* tile_count, cudaStream_t st) {
+  k_chain_step_items<<<n_items, GT, 0, st>>>(in, item_tile, item_sub, tile_items, k, C, K1, P64,
+                                             P32, mXi, mEta, gacc, tile_count);
+}
+
+int chain_item_size() { return CHAIN_ITEM; }
 
 void launch_tile_list(const uint64_t* mXi, const uint64_t* mEta, int nT, int aff, uint32_t* tiles,
                       int* ntiles, cudaStream_t st) {

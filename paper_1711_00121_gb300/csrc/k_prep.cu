@@ -200,8 +200,12 @@ __device__ __forceinline__ void item_locate(const DevAdj& in, const int* ioff, i
 template <typename V, typename Emit>
 __device__ __forceinline__ void seg_emit(int key, V a, V b, Emit emit) {
   const int lane = threadIdx.x & 31;
+  // only as many rounds as the longest run of equal keys needs
+  const unsigned same = __match_any_sync(0xffffffffu, key);
+  const int span = (int)__reduce_max_sync(0xffffffffu, key >= 0 ? (unsigned)__popc(same) : 1u);
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
+    if (o >= span) break;
     const int k2 = __shfl_down_sync(0xffffffffu, key, o);
     const V xa = __shfl_down_sync(0xffffffffu, a, o);
     const V xb = __shfl_down_sync(0xffffffffu, b, o);

@@ -217,6 +217,15 @@ void launch_s_update_multi(int s_prec, const MultiGraphDesc* descs, const uint64
                            cudaStream_t st);
 
 // Affected tile pairs (I <= J) of Thm 4 at tile granularity.
+// The chain step with tiles cut into items of at most chain_item_size()
+// nonzeros (item_tile / item_sub per item, tile_items per tile); gacc (2 * 128
+// doubles per tile) and tile_count (per tile) must start at zero and are left
+// at zero.
+void launch_chain_step_items(const DevAdj& in, const int* item_tile, const int* item_sub,
+                             const int* tile_items, int n_items, int k, double C, int K1,
+                             double* P64, float* P32, uint64_t* mXi, uint64_t* mEta, double* gacc,
+                             unsigned int* tile_count, cudaStream_t st);
+int chain_item_size();
 void launch_tile_list(const uint64_t* mXi, const uint64_t* mEta, int nT, int aff, uint32_t* tiles,
                       int* ntiles, cudaStream_t st);
 
