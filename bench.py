@@ -47,8 +47,8 @@ METRIC = "edge updates/sec & HBM GB/s: fused rank-2K ΔS vs plain Inc-uSR at 1e-
 UNIT = "edge updates/s"
 # DRAM bytes (read + write) per launch from one ncu capture of each kernel on
 # the default stream configuration (profiles/ holds the summaries)
-TRAFFIC_PREP = 3.287e7
-TRAFFIC_S_PASS = 1.661e9
+TRAFFIC_PREP = 6.141e7
+TRAFFIC_S_PASS = 1.828e9
 
 
 def workload_name(args):
@@ -465,9 +465,10 @@ def run_gpu(args, rank, world):
                                         "figure counts the 3 split products and the inner "
                                         f"dimension padded from {2 * terms} to {2 * rg}"})
     # DRAM bytes (read + write) per launch from one ncu capture of each kernel
-    # on this workload (n = 20,000, K = 20, 16 pending updates, FP16 split,
-    # FP64 vectors); null for any other form
-    profiled = (N, K, args.defer, args.tc, args.vec_fp64) == (20000, 20, 16, 2, 1)
+    # on this workload (n = 20,000, K = 20, 24 pending updates, FP16 split,
+    # FP64 vectors, flat split); null for any other form
+    profiled = ((N, K, args.defer, args.tc, args.vec_fp64) == (20000, 20, 24, 2, 1)
+                and form.get("prep_item", 0) == 0)
     s_pass.update({"traffic": TRAFFIC_S_PASS if profiled else None,
                    "bytes_per_launch": sp_bytes / max(launches, 1),
                    "ms_per_launch": sp_ms / max(launches, 1), "launches": launches})
