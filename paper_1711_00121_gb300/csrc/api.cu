@@ -100,7 +100,7 @@ struct simrank_ctx {
   struct Buf {
     void* p = nullptr;
     size_t bytes = 0;
-  } ob[24];
+  } ob[26];
   // column mode: per-tile nonzeros of the in-lists (host), the work-item table
   // of the chain steps and its partial-sum accumulators (device)
   std::vector<int64_t> col_tnnz;
@@ -519,17 +519,28 @@ simrank_status flush_pending(simrank_ctx* h) {
     if (!ev) return fail(h, SR_ERR_CUDA, "cudaEventCreate failed");
   }
   if (h->cfg.tc) {
-    // tc = 2: FP16 operands (terms rounded up to 64), else TF32 (rounded up to 32)
+    // tc = 2: FP16 operands, terms rounded up to 64 (B read from A by
+    // swapping 128-byte boxes), or to 32 with B stored on its own when that
+    // saves a k-block of a narrow pass; tc = 1: TF32, terms rounded up to 32
     const bool f16 = h->cfg.tc == 2;
-    const int rg = f16 ? (nterms + 63) / 64 * 64 : (nterms + 31) / 32 * 32;
+    int rg = f16 ? (nterms + 63) / 64 * 64 : (nterms + 31) / 32 * 32;
+    const int rg32 = (nterms + 31) / 32 * 32;
+    const bool own_b = f16 && rg32 != rg && 2 * (int64_t)rg32 * 2 < TC_WIDE_K_BYTES;
+    if (own_b) rg = rg32;
     const int64_t kd = 2 * (int64_t)rg;
     const size_t eb = f16 ? 2 : 4;
     if ((s = ob_ensure(h, 12, (size_t)h->n_pad * kd * eb)) != SR_OK) return s;
     if ((s = ob_ensure(h, 13, (size_t)h->n_pad * kd * eb)) != SR_OK) return s;
+    if (own_b) {
+      if ((s = ob_ensure(h, 24, (size_t)h->n_pad * kd * eb)) != SR_OK) return s;
+      if ((s = ob_ensure(h, 25, (size_t)h->n_pad * kd * eb)) != SR_OK) return s;
+    }
+    void* bhi = own_b ? h->ob[24].p : nullptr;
+    void* blo = own_b ? h->ob[25].p : nullptr;
     if (f16) {
       if ((s = ob_ensure(h, 19, 2 * (size_t)nterms * sizeof(unsigned int))) != SR_OK) return s;
       launch_pack_f16_tiles(h->Pp, GK1, nterms, rg, nT * PT, (unsigned int*)h->ob[19].p,
-                            h->ob[12].p, h->ob[13].p, kd, h->st);
+                            h->ob[12].p, h->ob[13].p, bhi, blo, kd, h->st);
       h->launches += 2;
     } else {
       launch_pack_tc_tiles(h->Pp, GK1, nterms, rg, nT * PT, (float*)h->ob[12].p,
@@ -540,7 +551,7 @@ simrank_status flush_pending(simrank_ctx* h) {
                                       kd, h->d_order, h->order_n, h->d_jobs, h->jobs_n,
                                       h->pXi, h->pEta,
                                       h->cfg.aff ? 1 : 0, h->n_cur, h->counters, h->num_sms,
-                                      wait_limit(h), h->st, upper(h), f16 ? 1 : 0);
+                                      wait_limit(h), h->st, upper(h), f16 ? 1 : 0, bhi, blo);
     if (rc != 0) return fail(h, SR_ERR_CUDA, "tensor-core S update: launch setup failed");
     h->launches += 2;
   } else {

@@ -216,21 +216,23 @@ __global__ void k_term_max(const float* __restrict__ Pp, int GK1, int nterms,
 // xi_q eta_q^T is unchanged by the scaling (powers of two are exact) and both
 // scaled columns share one magnitude, which keeps them in FP16's normal range.
 // x = hi + lo, hi = fp16(x), lo = fp16(x - hi).
+// Bhi / Blo (optional): the same rows with their two halves swapped, for a
+// pass whose operand rows are too narrow to swap the halves by TMA box.
 // Block (T, z) transposes operand columns [64 z, 64 z + 64) of the 128 rows of
 // tile T through shared memory: each panel column is read as one contiguous
 // 512-byte run, each operand row segment written as one 128-byte run.
 constexpr int PK_COLS = 64;
 __global__ void __launch_bounds__(256) k_pack_f16_tiles(
     const float* __restrict__ Pp, int GK1, int nterms, int rg, const unsigned int* __restrict__ maxes,
-    __half* __restrict__ Ahi, __half* __restrict__ Alo, int64_t kd) {
+    __half* __restrict__ Ahi, __half* __restrict__ Alo, __half* __restrict__ Bhi,
+    __half* __restrict__ Blo, int64_t kd) {
   __shared__ float tile[PK_COLS][PT + 1];
   const int T = blockIdx.x;
-  const int c0 = blockIdx.y * PK_COLS;  // rg is a multiple of PK_COLS: one half per block
-  const int h = c0 >= rg ? 1 : 0;
-  const int q0 = c0 - h * rg;
+  const int c0 = blockIdx.y * PK_COLS;  // rg is a multiple of 32
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int cc = warp; cc < PK_COLS; cc += 8) {
-    const int q = q0 + cc;
+    const int h = c0 + cc >= rg ? 1 : 0;
+    const int q = c0 + cc - h * rg;
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (q < nterms) {
       v = __ldcs(reinterpret_cast<const float4*>(Pp + (((int64_t)T * 2 + h) * GK1 + q) * PT) +
@@ -257,9 +259,15 @@ __global__ void __launch_bounds__(256) k_pack_f16_tiles(
     const __half h0 = __float2half_rn(x0), h1 = __float2half_rn(x1);
     const __half l0 = __float2half_rn(x0 - __half2float(h0));
     const __half l1 = __float2half_rn(x1 - __half2float(h1));
-    const int64_t o = ((int64_t)T * PT + r) * kd + c0 + 2 * lane;
-    *reinterpret_cast<__half2*>(Ahi + o) = __halves2half2(h0, h1);
-    *reinterpret_cast<__half2*>(Alo + o) = __halves2half2(l0, l1);
+    const int c = c0 + 2 * lane;
+    const int64_t o = ((int64_t)T * PT + r) * kd;
+    *reinterpret_cast<__half2*>(Ahi + o + c) = __halves2half2(h0, h1);
+    *reinterpret_cast<__half2*>(Alo + o + c) = __halves2half2(l0, l1);
+    if (Bhi) {
+      const int cb = c < rg ? c + rg : c - rg;  // rg is even: the pair stays in one half
+      *reinterpret_cast<__half2*>(Bhi + o + cb) = __halves2half2(h0, h1);
+      *reinterpret_cast<__half2*>(Blo + o + cb) = __halves2half2(l0, l1);
+    }
   }
 }
 
@@ -325,13 +333,14 @@ void launch_pack_tc_tiles(const float* Pp, int GK1, int nterms, int rg, int n_ro
 }
 
 void launch_pack_f16_tiles(const float* Pp, int GK1, int nterms, int rg, int n_rows,
-                           unsigned int* maxes, void* Ahi, void* Alo, int64_t kd, cudaStream_t st) {
+                           unsigned int* maxes, void* Ahi, void* Alo, void* Bhi, void* Blo,
+                           int64_t kd, cudaStream_t st) {
   const int nT = n_rows / PT;
   cudaMemsetAsync(maxes, 0, 2 * (size_t)nterms * sizeof(unsigned int), st);
   k_term_max<<<dim3(nT, 2, (nterms + TM_TERMS - 1) / TM_TERMS), 256, 0, st>>>(Pp, GK1, nterms,
                                                                              maxes);
   k_pack_f16_tiles<<<dim3(nT, (unsigned)(kd / PK_COLS)), 256, 0, st>>>(
-      Pp, GK1, nterms, rg, maxes, (__half*)Ahi, (__half*)Alo, kd);
+      Pp, GK1, nterms, rg, maxes, (__half*)Ahi, (__half*)Alo, (__half*)Bhi, (__half*)Blo, kd);
 }
 
 void launch_pack_tc(const double* X, int64_t ldx, int rh, int r, int slot, int rg, int n_rows,

@@ -14,9 +14,9 @@
 // issues TMA loads (128 rows x 128 bytes boxes, 128-byte swizzle) into a
 // 2- or 3-stage ring; warp 1 owns two TMEM accumulators (128 lanes x 128
 // columns each) and issues tcgen05.mma (M = 128, N = 128, K = 32 bytes) for
-// tile t + 1 while warps 2-9 drain tile t, either through a padded shared
-// tile with coalesced 16-byte accesses of S[I,J] (and S[J,I] when both
-// triangles are kept) or straight from registers (wide operands).
+// tile t + 1 while warps 2-9 drain tile t, either through a shared copy of
+// the accumulator with coalesced 16-byte accesses of S[I,J] (and S[J,I] when
+// both triangles are kept) or straight from registers (wide operands).
 // k_s_update_tc_pair (upper tiles, wide operands): jobs of two tile pairs
 // (I, J), (I, J+1) sharing A(I), one M = 128, N = 256 product per split term
 // into a 256-column accumulator.
@@ -257,16 +257,23 @@ struct TcManyGraphs {
 
 // STAGED: the epilogue copies D into shared memory and streams S with
 // coalesced 512-byte row segments (2 TMA stages); it also adds D^T to S[J, I]
-// when both triangles are kept (MIRROR).  Otherwise (wide operands: the pass
-// is bound by the tensor cores) each epilogue thread adds its row's 64 values
-// of D to S straight from the TMEM load, with those S values fetched before
-// the accumulator is ready, and the TMA ring has 3 stages.
-template <bool F16, bool STAGED, bool MIRROR, typename Src>
+// when both triangles are kept (MIRROR).  SW (staged, upper tiles only): D is
+// staged as four 128 x 32 boxes in the 128-byte swizzle, so that both the
+// TMEM-row writes and the row-segment reads are free of bank conflicts, and
+// each warp's 16 rows of S[I, J] are fetched before the accumulator wait.
+// Otherwise (wide operands: the pass is bound by the tensor cores) each
+// epilogue thread adds its row's 64 values of D to S straight from the TMEM
+// load, with those S values fetched before the accumulator is ready, and the
+// TMA ring has 3 stages.
+template <bool F16, bool STAGED, bool MIRROR, bool SW, typename Src>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_s_update_tc(const __grid_constant__ CUtensorMap tm_hi,
-                  const __grid_constant__ CUtensorMap tm_lo, Src src, int nkb,
+                  const __grid_constant__ CUtensorMap tm_lo,
+                  const __grid_constant__ CUtensorMap tm_bhi,
+                  const __grid_constant__ CUtensorMap tm_blo, Src src, int nkb, int bswap,
                   long long wait_limit, unsigned long long* __restrict__ counters) {
   static_assert(STAGED || !MIRROR, "the transposed write needs the staged epilogue");
+  static_assert(!SW || (STAGED && !MIRROR), "the swizzled epilogue keeps upper tiles only");
   constexpr int STAGES = STAGED ? STAGES_STAGED : STAGES_DIRECT;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES];
@@ -280,7 +287,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
   float* sD = reinterpret_cast<float*>(smem_raw + (base - smem_u32(smem_raw)) +
                                        (size_t)STAGES * STAGE_BYTES);
-  const int half = nkb / 2;  // B row = A row with its halves swapped
+  const int half = nkb / 2;  // bswap: B row = A row with its halves swapped
   const int nt = src.count();
 
   if (threadIdx.x == 0) {
@@ -325,12 +332,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const uint32_t st = base + s * STAGE_BYTES;
           const uint32_t fb = smem_u32(&bar_full[s]);
           mbar_expect_tx(fb, STAGE_BYTES);
-          const int kb_b = kb < half ? kb + half : kb - half;
+          const int kb_b = !bswap ? kb : kb < half ? kb + half : kb - half;
           constexpr int KCH = F16 ? KB / 2 : KB / 4;  // elements of K per stage
           tma_load_2d(st + 0 * OPB, &tm_hi, kb * KCH, r.rowI, fb);
           tma_load_2d(st + 1 * OPB, &tm_lo, kb * KCH, r.rowI, fb);
-          tma_load_2d(st + 2 * OPB, &tm_hi, kb_b * KCH, r.rowJ, fb);
-          tma_load_2d(st + 3 * OPB, &tm_lo, kb_b * KCH, r.rowJ, fb);
+          tma_load_2d(st + 2 * OPB, &tm_bhi, kb_b * KCH, r.rowJ, fb);
+          tma_load_2d(st + 3 * OPB, &tm_blo, kb_b * KCH, r.rowJ, fb);
         }
       }
       it_issued = it;
@@ -430,6 +437,55 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
         for (int q = 0; q < 16; ++q) *reinterpret_cast<float4*>(srow + 4 * q) = sv[q];
       } else {
+      if (SW) {
+        constexpr int NQ = TM / 8;  // rows ew + 8 q of the tile; lane l: columns 4 l .. 4 l + 3
+        // this warp's rows of S[I, J], in flight while the tile is multiplied
+        float4 sv[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+          sv[q] = *reinterpret_cast<const float4*>(S + (int64_t)(I * TM + ew + 8 * q) * ld +
+                                                   (int64_t)J * TN + lane * 4);
+        const bool got = mbar_wait(smem_u32(&bar_acc_full[b]), tph, wait_limit, &abort_flag);
+        if (!ep_all(got)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        ep_sync();  // every thread is done with the previous tile's shared copy
+        // accumulator -> shared tile, one 32-column box at a time: box c / 32
+        // holds columns [c, c + 32); row `row` is 128 bytes at row * 128, its
+        // 16-byte chunk k stored at chunk k ^ (row & 7)
+        const uint32_t ta =
+            tmem + b * (uint32_t)TN + ((uint32_t)(quarter * 32) << 16) + (uint32_t)chalf;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+          float v[32];
+          tmem_ld32(ta + 32u * h, v);
+          float* box = sD + (chalf / 32 + h) * (TM * 32) + row * 32;
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            *reinterpret_cast<float4*>(box + (k ^ (row & 7)) * 4) =
+                make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(smem_u32(&bar_acc_empty[b]));  // the MMA warp may refill this accumulator
+        ep_sync();
+        // a warp covers one 512-byte row segment per access: lane l takes
+        // chunk l & 7 of box l >> 3
+        const float* bsrc = sD + (lane >> 3) * (TM * 32);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const int r = ew + 8 * q;
+          const float4 d =
+              *reinterpret_cast<const float4*>(bsrc + r * 32 + (((lane & 7) ^ (r & 7)) * 4));
+          sv[q].x += d.x;
+          sv[q].y += d.y;
+          sv[q].z += d.z;
+          sv[q].w += d.w;
+          *reinterpret_cast<float4*>(S + (int64_t)(I * TM + r) * ld + (int64_t)J * TN +
+                                     lane * 4) = sv[q];
+        }
+      } else {
       const bool got = mbar_wait(smem_u32(&bar_acc_full[b]), tph, wait_limit, &abort_flag);
       if (!ep_all(got)) {
         ok = false;
@@ -486,6 +542,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
       }
       ep_sync();  // the shared tile is free for the next accumulator
+      }
       }
       if (et == 0) {
         const long long vr = max(0, min(TM, n - I * TM)), vc = max(0, min(TN, n - J * TN));
@@ -812,65 +869,80 @@ bool make_map(CUtensorMap* m, const void* ptr, int64_t rows, int64_t kd, int eb)
 
 }  // namespace
 
-// A_hi / A_lo: row-major [n_rows][kd], FP32 holding TF32 values (f16 = 0) or
-// FP16 (f16 = 1); kd a multiple of 2 * (128 bytes / element size); the B
-// operand is A with its two column halves swapped.
-template <bool F16, bool STAGED, bool MIRROR, typename Src>
-int launch_tc_t(const CUtensorMap& mhi, const CUtensorMap& mlo, const Src& src, int nkb, int grid,
-                long long wait_limit, cudaStream_t st, int64_t* counters) {
+// Tensor maps of the operands: A (hi, lo) and B (hi, lo); bswap: B is A
+// with its halves swapped, read by box.
+struct TcMaps {
+  CUtensorMap hi, lo, bhi, blo;
+  int bswap;
+};
+
+template <bool F16, bool STAGED, bool MIRROR, bool SW, typename Src>
+int launch_tc_t(const TcMaps& m, const Src& src, int nkb, int grid, long long wait_limit,
+                cudaStream_t st, int64_t* counters) {
+  const size_t tile = SW ? (size_t)TM * TN * 4 : (size_t)TM * EP * 4;
   const size_t smem = (size_t)(STAGED ? STAGES_STAGED : STAGES_DIRECT) * STAGE_BYTES +
-                      (STAGED ? (size_t)TM * EP * 4 : 0) + 1024;
-  const void* fn = (const void*)k_s_update_tc<F16, STAGED, MIRROR, Src>;
+                      (STAGED ? tile : 0) + 1024;
+  const void* fn = (const void*)k_s_update_tc<F16, STAGED, MIRROR, SW, Src>;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 1;
-  k_s_update_tc<F16, STAGED, MIRROR, Src><<<grid, TC_THREADS, smem, st>>>(
-      mhi, mlo, src, nkb, wait_limit, (unsigned long long*)counters);
+  k_s_update_tc<F16, STAGED, MIRROR, SW, Src><<<grid, TC_THREADS, smem, st>>>(
+      m.hi, m.lo, m.bhi, m.blo, src, nkb, m.bswap, wait_limit, (unsigned long long*)counters);
   return 0;
 }
 
 // Wide operands (at least 1 KB of K per row) make the pass tensor-bound:
 // register epilogue and 3 stages; narrow ones leave it bound by the S stream:
-// staged, coalesced epilogue.
-constexpr int64_t WIDE_K_BYTES = 1024;
+// staged, coalesced epilogue (swizzled, with S fetched early, for upper tiles).
+constexpr int64_t WIDE_K_BYTES = TC_WIDE_K_BYTES;
 
 template <bool F16, typename Src>
-int launch_tc_f(const CUtensorMap& mhi, const CUtensorMap& mlo, const Src& src, int nkb,
-                int64_t kd_bytes, int grid, long long wait_limit, cudaStream_t st, int mirror,
-                int64_t* counters) {
+int launch_tc_f(const TcMaps& m, const Src& src, int nkb, int64_t kd_bytes, int grid,
+                long long wait_limit, cudaStream_t st, int mirror, int64_t* counters) {
   if (mirror)
-    return launch_tc_t<F16, true, true>(mhi, mlo, src, nkb, grid, wait_limit, st, counters);
+    return launch_tc_t<F16, true, true, false>(m, src, nkb, grid, wait_limit, st, counters);
   if (kd_bytes >= WIDE_K_BYTES)
-    return launch_tc_t<F16, false, false>(mhi, mlo, src, nkb, grid, wait_limit, st, counters);
-  return launch_tc_t<F16, true, false>(mhi, mlo, src, nkb, grid, wait_limit, st, counters);
+    return launch_tc_t<F16, false, false, false>(m, src, nkb, grid, wait_limit, st, counters);
+  return launch_tc_t<F16, true, false, true>(m, src, nkb, grid, wait_limit, st, counters);
 }
 
+// Bhi / Blo: B on its own, or null (B = A with its halves swapped).
 template <typename Src>
 int launch_tc(const void* Ahi, const void* Alo, int64_t n_rows, int64_t kd, const Src& src,
               int grid, long long wait_limit, cudaStream_t st, int f16, int mirror,
-              int64_t* counters) {
+              int64_t* counters, const void* Bhi = nullptr, const void* Blo = nullptr) {
   const int eb = f16 ? 2 : 4;
   const int kch = KB / eb;
-  if (kd % (2 * kch) != 0 || n_rows % TM != 0) return 1;
-  CUtensorMap mhi, mlo;
-  if (!make_map(&mhi, Ahi, n_rows, kd, eb)) return 2;
-  if (!make_map(&mlo, Alo, n_rows, kd, eb)) return 2;
+  const bool bswap = Bhi == nullptr;
+  if (kd % ((bswap ? 2 : 1) * kch) != 0 || n_rows % TM != 0 || bswap != (Blo == nullptr))
+    return 1;
+  TcMaps m;
+  m.bswap = bswap ? 1 : 0;
+  if (!make_map(&m.hi, Ahi, n_rows, kd, eb)) return 2;
+  if (!make_map(&m.lo, Alo, n_rows, kd, eb)) return 2;
+  if (bswap) {
+    m.bhi = m.hi;
+    m.blo = m.lo;
+  } else {
+    if (!make_map(&m.bhi, Bhi, n_rows, kd, eb)) return 2;
+    if (!make_map(&m.blo, Blo, n_rows, kd, eb)) return 2;
+  }
   const int nkb = (int)(kd / kch);
-  if (f16)
-    return launch_tc_f<true>(mhi, mlo, src, nkb, kd * eb, grid, wait_limit, st, mirror, counters);
-  return launch_tc_f<false>(mhi, mlo, src, nkb, kd * eb, grid, wait_limit, st, mirror, counters);
+  if (f16) return launch_tc_f<true>(m, src, nkb, kd * eb, grid, wait_limit, st, mirror, counters);
+  return launch_tc_f<false>(m, src, nkb, kd * eb, grid, wait_limit, st, mirror, counters);
 }
 
 // A_hi / A_lo: row-major [n_rows][kd], FP32 holding TF32 values (f16 = 0) or
-// FP16 (f16 = 1); kd a multiple of 2 * (128 bytes / element size); the B
-// operand is A with its two column halves swapped.
+// FP16 (f16 = 1); the B operand is A with its two column halves swapped, read
+// from A by box (kd a multiple of 2 * (128 bytes / element size)) or from
+// B_hi / B_lo when given (kd a multiple of 128 bytes / element size).
 int launch_s_update_tc(float* S, int64_t ld, const void* Ahi, const void* Alo, int64_t n_rows,
                        int64_t kd, const uint32_t* tiles, int nt, const uint64_t* jobs, int nj,
                        const uint64_t* mX, const uint64_t* mE, int use_masks, int n,
                        int64_t* counters, int grid, long long wait_limit, cudaStream_t st,
-                       int upper, int f16) {
+                       int upper, int f16, const void* Bhi, const void* Blo) {
   const int eb = f16 ? 2 : 4;
-  if (jobs && upper && kd * eb >= WIDE_K_BYTES) {
+  if (jobs && upper && kd * eb >= WIDE_K_BYTES && !Bhi) {
     // wide operands, upper tiles: jobs of two tile pairs sharing their column tile
     const int kch = KB / eb;
     if (kd % (2 * kch) != 0 || n_rows % TM != 0) return 1;
@@ -893,7 +965,8 @@ int launch_s_update_tc(float* S, int64_t ld, const void* Ahi, const void* Alo, i
     return 0;
   }
   TcOneGraph src{tiles, nt, mX, mE, use_masks, S, ld, n, upper ? 0 : 1};
-  return launch_tc(Ahi, Alo, n_rows, kd, src, grid, wait_limit, st, f16, upper ? 0 : 1, counters);
+  return launch_tc(Ahi, Alo, n_rows, kd, src, grid, wait_limit, st, f16, upper ? 0 : 1, counters,
+                   Bhi, Blo);
 }
 
 int launch_s_update_tc_multi(const void* Ahi, const void* Alo, int64_t rows, int64_t kd,

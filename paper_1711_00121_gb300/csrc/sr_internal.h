@@ -304,8 +304,14 @@ void launch_pack_ffma(const double* X, int64_t ldx, int rh, int r, int slot, int
                       void* Pn, int p_prec, uint64_t* mXi, uint64_t* mEta, cudaStream_t st);
 void launch_pack_tc(const double* X, int64_t ldx, int rh, int r, int slot, int rg, int n_rows,
                     float* Ahi, float* Alo, int64_t kd, cudaStream_t st);
-// tcgen05 symmetric update S += A B^T (B = A with halves swapped), 3xTF32; returns
-// 0 on launch, 1 for a bad shape, 2 if no tensor map could be encoded.
+// Operand rows at least this wide (bytes) make the tensor-core S pass bound by
+// the tensor cores rather than by the S stream.
+constexpr int64_t TC_WIDE_K_BYTES = 1024;
+// tcgen05 symmetric update S += A B^T (B = A with halves swapped), 3-term
+// split (TF32, or FP16 when f16); returns 0 on launch, 1 for a bad shape, 2 if
+// no tensor map could be encoded.  Bhi / Blo: B stored on its own (kd a
+// multiple of 128 bytes), else B is read from A by swapping the two halves'
+// TMA boxes (kd a multiple of 256 bytes).
 // tiles[0 .. nt): tile pairs (I << 16 | J) in the order CTAs take them; a
 // pair is skipped when use_masks and (mX[I] & mE[J]) | (mE[I] & mX[J]) == 0.
 // jobs[0 .. nj) (may be null): the same pairs, two per job where they share I
@@ -315,7 +321,8 @@ int launch_s_update_tc(float* S, int64_t ld, const void* Ahi, const void* Alo, i
                        int64_t kd, const uint32_t* tiles, int nt, const uint64_t* jobs, int nj,
                        const uint64_t* mX, const uint64_t* mE, int use_masks, int n,
                        int64_t* counters, int grid, long long wait_limit, cudaStream_t st,
-                       int upper = 0, int f16 = 0);
+                       int upper = 0, int f16 = 0, const void* Bhi = nullptr,
+                       const void* Blo = nullptr);
 // The same pass over the tile pairs (g << 32 | I << 16 | J) of many graphs,
 // *ntiles of them; graph g's operand rows start at descs[g].row_off of the
 // shared operands A_hi / A_lo ([rows][kd]).
@@ -332,7 +339,8 @@ void launch_multi_pack_tc(const MultiGraphDesc* descs, const MultiStep* steps, c
 // FP16 operands (row-major [n_rows][kd] hi/lo) from tile-blocked FP32 pending
 // panels, each term scaled by 2^(+-e_q) (exact); maxes: 2 * nterms scratch uints.
 void launch_pack_f16_tiles(const float* Pp, int GK1, int nterms, int rg, int n_rows,
-                           unsigned int* maxes, void* Ahi, void* Alo, int64_t kd, cudaStream_t st);
+                           unsigned int* maxes, void* Ahi, void* Alo, void* Bhi, void* Blo,
+                           int64_t kd, cudaStream_t st);
 
 // ---- column mode (§7), k_column.cu
 // A piece of one adjacency row: row id, count (<= kChunk) and pool offset.
