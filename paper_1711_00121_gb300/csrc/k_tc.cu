@@ -278,6 +278,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar_full[STAGES], bar_empty[STAGES];
   __shared__ __align__(8) uint64_t bar_acc_full[2], bar_acc_empty[2];
+  // the MMA warp hands each active pair (I < 0: no more) to the epilogue with
+  // its accumulator slot, so that the epilogue's S loads wait on no list or
+  // mask reads of its own
+  __shared__ TcRef ep_ref[2];
+  __shared__ __align__(8) uint64_t bar_ref[2];
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   __shared__ __align__(8) uint64_t bar_drain;  // MMAs still in flight after a stop
@@ -299,6 +304,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&bar_acc_full[b]), 1);
       mbar_init(smem_u32(&bar_acc_empty[b]), 256);
+      mbar_init(smem_u32(&bar_ref[b]), 1);
     }
     mbar_init(smem_u32(&bar_drain), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -358,6 +364,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        ep_ref[b] = r;
+        mbar_arrive(smem_u32(&bar_ref[b]));
         const uint32_t acc = tmem + b * (uint32_t)TN;
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int s = it % STAGES;
@@ -384,6 +392,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (!ok) break;
         mma_commit(smem_u32(&bar_acc_full[b]));
       }
+      if (ok) {
+        // end of the list, in the next slot once the epilogue has left it
+        const uint32_t b = tl & 1u;
+        if (!mbar_wait(smem_u32(&bar_acc_empty[b]), ((tl >> 1) & 1u) ^ 1u, wait_limit,
+                       &abort_flag)) {
+          ok = false;
+        } else {
+          ep_ref[b].I = -1;
+          mbar_arrive(smem_u32(&bar_ref[b]));
+        }
+      }
       if (!ok) abort_flag = 1;
     }
   } else {
@@ -394,29 +413,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int chalf = (ew >> 2) * 64;    // columns [chalf, chalf + 64) of the accumulator
     uint32_t tl = 0;
     unsigned long long my_tiles = 0, my_bytes = 0;
-    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
-      TcRef r;
-      if (!src.get(t, r)) continue;
+    for (;;) {
+      const uint32_t b = tl & 1u;
+      const uint32_t tph = (tl >> 1) & 1u;
+      // each warp reads the posted pair on its own and fetches its S rows;
+      // one barrier per pair (tile_go) then agrees on going on, on the end of
+      // the list, or on a stop
+      const bool posted =
+          __all_sync(0xffffffffu, mbar_wait(smem_u32(&bar_ref[b]), tph, wait_limit, &abort_flag));
+      TcRef r = {};
+      if (posted) r = ep_ref[b];
+      const bool go = posted && r.I >= 0;
+      const bool at_end = posted && r.I < 0;
+      auto tile_go = [&]() -> bool {
+        const bool got =
+            go ? mbar_wait(smem_u32(&bar_acc_full[b]), tph, wait_limit, &abort_flag) : at_end;
+        if (ep_all(go && got)) return true;
+        if (!ep_all(at_end)) ok = false;
+        return false;
+      };
+      ++tl;
       float* __restrict__ S = r.S;
       const int64_t ld = r.ld;
       const int I = r.I, J = r.J, n = r.n;
       const bool mirror = MIRROR;
-      const uint32_t b = tl & 1u;
-      const uint32_t tph = (tl >> 1) & 1u;
-      ++tl;
       const int row = quarter * 32 + lane;
       if (!STAGED) {
         // this thread's 64 values of S[I, J] (row `row`, columns chalf ..),
         // fetched while the tensor cores still work on the tile
         float* srow = S + (int64_t)(I * TM + row) * ld + (int64_t)J * TN + chalf;
         float4 sv[16];
+        if (go) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) sv[q] = *reinterpret_cast<const float4*>(srow + 4 * q);
-        const bool got = mbar_wait(smem_u32(&bar_acc_full[b]), tph, wait_limit, &abort_flag);
-        if (!ep_all(got)) {
-          ok = false;
-          break;
+          for (int q = 0; q < 16; ++q) sv[q] = *reinterpret_cast<const float4*>(srow + 4 * q);
         }
+        if (!tile_go()) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -441,15 +472,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         constexpr int NQ = TM / 8;  // rows ew + 8 q of the tile; lane l: columns 4 l .. 4 l + 3
         // this warp's rows of S[I, J], in flight while the tile is multiplied
         float4 sv[NQ];
+        if (go) {
 #pragma unroll
-        for (int q = 0; q < NQ; ++q)
-          sv[q] = *reinterpret_cast<const float4*>(S + (int64_t)(I * TM + ew + 8 * q) * ld +
-                                                   (int64_t)J * TN + lane * 4);
-        const bool got = mbar_wait(smem_u32(&bar_acc_full[b]), tph, wait_limit, &abort_flag);
-        if (!ep_all(got)) {
-          ok = false;
-          break;
+          for (int q = 0; q < NQ; ++q)
+            sv[q] = *reinterpret_cast<const float4*>(S + (int64_t)(I * TM + ew + 8 * q) * ld +
+                                                     (int64_t)J * TN + lane * 4);
         }
+        if (!tile_go()) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         ep_sync();  // every thread is done with the previous tile's shared copy
         // accumulator -> shared tile, one 32-column box at a time: box c / 32
@@ -486,11 +515,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                      lane * 4) = sv[q];
         }
       } else {
-      const bool got = mbar_wait(smem_u32(&bar_acc_full[b]), tph, wait_limit, &abort_flag);
-      if (!ep_all(got)) {
-        ok = false;
-        break;
-      }
+      if (!tile_go()) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       // accumulator -> shared tile (row = TMEM lane)
 #pragma unroll 1
