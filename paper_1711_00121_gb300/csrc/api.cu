@@ -66,6 +66,7 @@ struct simrank_ctx {
   unsigned long long* diffbits = nullptr;
   unsigned int* gbar = nullptr;  // grid barrier state of the cooperative pre-update kernel
   uint32_t* d_order = nullptr;   // all tile pairs I <= J in band order (tensor-core S pass)
+  uint32_t* d_order_row = nullptr;  // the same pairs in row-major order (narrow operands)
   int order_nT = -1;
   int order_n = 0;
   uint64_t* d_jobs = nullptr;    // the same pairs, two per job where they share I
@@ -448,14 +449,20 @@ bool deferring(const simrank_ctx* h) {
 // Updates per pending group (1 when tensor cores apply each update at once).
 int group(const simrank_ctx* h) { return std::max(1, (int)h->cfg.defer); }
 
-// All tile pairs (I <= J) of nT tiles, in the order the tensor-core S pass
-// takes them: bands of 8 tile rows; within a band, J ascending and, for each
-// J, the band's rows I <= J.  Concurrent CTAs then work on a few row bands
-// and a few column tiles, so their operand rows are shared through L2.
+// All tile pairs (I <= J) of nT tiles, in the orders the tensor-core S passes
+// take them.  Band order: bands of 8 tile rows; within a band, J ascending
+// and, for each J, the band's rows I <= J.  Concurrent CTAs then work on a few
+// row bands and a few column tiles, so their operand rows are shared through
+// L2 (what counts for wide operands).  Row-major order: concurrent CTAs
+// stream adjacent 512-byte segments of the same S rows (what counts when the
+// operands are narrow and stay in L2 anyway).
 simrank_status ensure_order(simrank_ctx* h, int nT) {
   if (h->order_nT == nT) return SR_OK;
-  std::vector<uint32_t> v;
+  std::vector<uint32_t> v, vr;
   v.reserve((size_t)nT * (nT + 1) / 2);
+  vr.reserve((size_t)nT * (nT + 1) / 2);
+  for (int I = 0; I < nT; ++I)
+    for (int J = I; J < nT; ++J) vr.push_back(((uint32_t)I << 16) | (uint32_t)J);
   constexpr int BAND = 8;
   std::vector<uint64_t> jb;
   jb.reserve((size_t)nT * (nT + 1) / 4 + nT);
@@ -475,11 +482,16 @@ simrank_status ensure_order(simrank_ctx* h, int nT) {
   }
   if (h->d_order) cudaFree(h->d_order);
   h->d_order = nullptr;
+  if (h->d_order_row) cudaFree(h->d_order_row);
+  h->d_order_row = nullptr;
   if (h->d_jobs) cudaFree(h->d_jobs);
   h->d_jobs = nullptr;
   h->order_nT = -1;
   CUDA_TRY(h, dev_alloc(&h->d_order, v.size()));
   CUDA_TRY(h, cudaMemcpy(h->d_order, v.data(), v.size() * sizeof(uint32_t),
+                         cudaMemcpyHostToDevice));
+  CUDA_TRY(h, dev_alloc(&h->d_order_row, vr.size()));
+  CUDA_TRY(h, cudaMemcpy(h->d_order_row, vr.data(), vr.size() * sizeof(uint32_t),
                          cudaMemcpyHostToDevice));
   CUDA_TRY(h, dev_alloc(&h->d_jobs, jb.size()));
   CUDA_TRY(h, cudaMemcpy(h->d_jobs, jb.data(), jb.size() * sizeof(uint64_t),
@@ -488,6 +500,11 @@ simrank_status ensure_order(simrank_ctx* h, int nT) {
   h->order_n = (int)v.size();
   h->jobs_n = (int)jb.size();
   return SR_OK;
+}
+
+// The tile order for operand rows of kd_bytes (ensure_order has run).
+const uint32_t* tile_order(const simrank_ctx* h, int64_t kd_bytes) {
+  return kd_bytes < TC_WIDE_K_BYTES ? h->d_order_row : h->d_order;
 }
 
 // Applies the pending updates' panels to S in one pass (rank 2 * np * K1).
@@ -548,7 +565,8 @@ simrank_status flush_pending(simrank_ctx* h) {
     }
     if (ev) CUDA_TRY(h, cudaEventRecord(ev->first, h->st));
     const int rc = launch_s_update_tc((float*)h->S, h->ld, h->ob[12].p, h->ob[13].p, h->n_pad,
-                                      kd, h->d_order, h->order_n, h->d_jobs, h->jobs_n,
+                                      kd, tile_order(h, kd * (int64_t)eb), h->order_n,
+                                      h->d_jobs, h->jobs_n,
                                       h->pXi, h->pEta,
                                       h->cfg.aff ? 1 : 0, h->n_cur, h->counters, h->num_sms,
                                       wait_limit(h), h->st, upper(h), f16 ? 1 : 0, bhi, blo);
@@ -1041,7 +1059,8 @@ simrank_status run_one_shot(simrank_ctx* h, const std::map<int32_t, std::vector<
       }
       if (tc) {
         const int rc = launch_s_update_tc((float*)h->S, h->ld, h->ob[8].p, h->ob[9].p, n_pad,
-                                          kd, h->d_order, h->order_n, nullptr, 0, h->mXi,
+                                          kd, tile_order(h, kd * 4), h->order_n, nullptr, 0,
+                                          h->mXi,
                                           h->mEta, 0,
                                           h->n_cur, h->counters, h->num_sms, wait_limit, h->st,
                                           upper(h));
@@ -1285,7 +1304,7 @@ void free_ctx(simrank_ctx* h) {
                   h->dout.col,  h->d_in_w,   h->d_wsum,    h->S,          h->P64,
                   h->P32,       h->mXi,      h->mEta,      h->tiles,      h->ntiles,
                   h->sI,        h->sJ,       h->scal,      h->counters,   h->diffbits,
-                  h->gbar,      h->W,        h->rinv,       h->loff,     h->tile_nnz,  h->d_order,    h->d_jobs,
+                  h->gbar,      h->W,        h->rinv,       h->loff,     h->tile_nnz,  h->d_order,    h->d_order_row, h->d_jobs,
                   h->d_srcs,    h->d_ops,    h->d_cols,     h->d_ext2int, h->col_items,
                   h->col_gacc,  h->col_tcount};
   for (void* p : ptrs)
