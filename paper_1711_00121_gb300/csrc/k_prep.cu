@@ -321,7 +321,8 @@ struct StepPair {
   int kh, kt;    // head / tail row in the tile (-1: none)
   int span;      // warp-uniform: the longest run of lanes sharing a head row
   unsigned fl;   // bits 0-4: take lane + 2^b's head sum; 5: add lane - 1's tail;
-                 // 6: emit the head sum; 7: emit the tail sum
+                 // 6: emit the head sum; 7: emit the tail sum; 8-12: the first lane
+                 // of the head row's run of lanes
 };
 
 template <typename V>
@@ -366,7 +367,7 @@ __device__ __forceinline__ void pair_pattern(StepPair<V>& q) {
   // in round b, the partial of lane + 2^b into the lanes at positions 0 mod
   // 2^(b+1), so a segment of s lanes costs s - 1 additions
   const int pos = lane - (__ffs(same) - 1);
-  q.fl = 0;
+  q.fl = (unsigned)(__ffs(same) - 1) << 8;
 #pragma unroll
   for (int b = 0; b < 5; ++b) {
     const int k2 = __shfl_down_sync(full, q.kh, 1 << b);
@@ -385,8 +386,15 @@ __device__ __forceinline__ void pair_pattern(StepPair<V>& q) {
 // (xi_k, eta_k) entries, adds the rows up across the warp and emits each row's
 // sum (times C / in-degree for xi, 1 / in-degree for eta; rc / ri hold those
 // factors per row of the item's tile) into W[k + 1].
+template <typename Gf, typename Emit>
+__device__ __forceinline__ void pair_step_fx(const StepPair<double>& q, Gf gather, Emit emit);
+
 template <typename V, typename Gf, typename Emit>
 __device__ __forceinline__ void pair_step(const StepPair<V>& q, Gf gather, Emit emit) {
+  if constexpr (sizeof(V) == 8) {
+    pair_step_fx(q, gather, emit);
+    return;
+  }
   const unsigned full = 0xffffffffu;
   V ha = V(0), hb = V(0), ta = V(0), tb = V(0);
   if (q.ca >= 0) {
@@ -422,6 +430,97 @@ __device__ __forceinline__ void pair_step(const StepPair<V>& q, Gf gather, Emit 
   }
   if ((q.fl & (1u << 6)) && (nz(ha) || nz(hb))) emit(q.kh, ha, hb);
   if ((q.fl & (1u << 7)) && (nz(ta) || nz(tb))) emit(q.kt, ta, tb);
+}
+
+// Exact row sums of FP64 values on the integer pipe (GB300 issues FP64 at
+// 1/64 of the FP32 rate, and a warp pays for an FP64 instruction whichever of
+// its lanes use it).  The values of one row's run of lanes are turned into
+// 64-bit fixed-point numbers with 55 fraction bits below the run's largest
+// binary exponent em (truncated there, an error below 2^(em - 1078) each), the
+// fixed-point numbers (at most 65: two per lane and an incoming tail, so
+// below 2^63 in total) are added exactly, and the total is rounded to FP64
+// once.  The error stays below 65 ulp of the largest value at 2^-55 each,
+// where FP64 additions in any order can lose (n - 1) 2^-53 of the sum of the
+// magnitudes.  Subnormal values count as zero.
+__device__ __forceinline__ int fx_exp(double v) {  // biased exponent (0: zero, subnormal)
+  return (__double2hiint(v) >> 20) & 0x7ff;
+}
+__device__ __forceinline__ long long fx_of(double v, int em) {
+  const long long b = __double_as_longlong(v);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex == 0) return 0;
+  const long long m = (b & 0xfffffffffffffLL) | 0x10000000000000LL;  // 53-bit significand
+  const int sh = ex - em + 3;  // v * 2^(1078 - em) = m * 2^sh, sh <= 3
+  const long long f = sh >= 0 ? (m << sh) : (sh > -54 ? (m >> -sh) : 0);
+  return b < 0 ? -f : f;
+}
+// t * 2^(em - 1078), rounded once
+__device__ __forceinline__ double fx_value(long long t, int em) {
+  if (t == 0) return 0.0;
+  const double d = (double)t;  // |t| < 2^63: one rounding
+  if (em >= 56 && em < 1960) {
+    // the power of two is exact: add it to the exponent field (the result stays normal)
+    return __longlong_as_double(__double_as_longlong(d) + ((long long)(em - 1078) << 52));
+  }
+  return ldexp(d, em - 1078);
+}
+
+// pair_step for FP64 vectors with the row sums formed exactly as above: the
+// run's largest exponent goes through the same shuffle tree (integer max) and
+// back to every lane of the run from its first lane, then the fixed-point
+// values through the tree (integer adds).  A tail that ends its row in this
+// lane is one value and is emitted as it is.
+template <typename Gf, typename Emit>
+__device__ __forceinline__ void pair_step_fx(const StepPair<double>& q, Gf gather, Emit emit) {
+  const unsigned full = 0xffffffffu;
+  double h1x = 0.0, h1y = 0.0, h2x = 0.0, h2y = 0.0, tx = 0.0, ty = 0.0;
+  if (q.ca >= 0) {
+    const V2<double> v = gather(q.ca);
+    h1x = v.x;
+    h1y = v.y;
+  }
+  if (q.cb >= 0) {
+    const V2<double> v = gather(q.cb);
+    if (q.kt >= 0) {
+      tx = v.x;
+      ty = v.y;
+    } else {
+      h2x = v.x;
+      h2y = v.y;
+    }
+  }
+  // lane - 1's tail, added into this lane's head row (bit 5)
+  double px = __shfl_up_sync(full, tx, 1), py = __shfl_up_sync(full, ty, 1);
+  if (!(q.fl & (1u << 5))) px = py = 0.0;
+  int ex = max(max(fx_exp(h1x), fx_exp(h2x)), fx_exp(px));
+  int ey = max(max(fx_exp(h1y), fx_exp(h2y)), fx_exp(py));
+#pragma unroll
+  for (int b = 0; b < 5; ++b) {
+    if ((1 << b) >= q.span) break;
+    const int xe = __shfl_down_sync(full, ex, 1 << b);
+    const int ye = __shfl_down_sync(full, ey, 1 << b);
+    if (q.fl & (1u << b)) {
+      ex = max(ex, xe);
+      ey = max(ey, ye);
+    }
+  }
+  const int first = (int)((q.fl >> 8) & 31u);
+  ex = __shfl_sync(full, ex, first);
+  ey = __shfl_sync(full, ey, first);
+  long long fx = fx_of(h1x, ex) + fx_of(h2x, ex) + fx_of(px, ex);
+  long long fy = fx_of(h1y, ey) + fx_of(h2y, ey) + fx_of(py, ey);
+#pragma unroll
+  for (int b = 0; b < 5; ++b) {
+    if ((1 << b) >= q.span) break;
+    const long long xa = __shfl_down_sync(full, fx, 1 << b);
+    const long long xb = __shfl_down_sync(full, fy, 1 << b);
+    if (q.fl & (1u << b)) {
+      fx += xa;
+      fy += xb;
+    }
+  }
+  if ((q.fl & (1u << 6)) && (fx != 0 || fy != 0)) emit(q.kh, fx_value(fx, ex), fx_value(fy, ey));
+  if ((q.fl & (1u << 7)) && (nz(tx) || nz(ty))) emit(q.kt, tx, ty);
 }
 
 // The flat split: CTA c takes the nonzeros [c E, (c + 1) E) of the in-lists of
