@@ -44,6 +44,7 @@
 // makes the last bit of a result depend on the order of the additions.
 #include <algorithm>
 
+#include "fx64.h"
 #include "sr_internal.h"
 
 namespace sr {
@@ -432,39 +433,13 @@ __device__ __forceinline__ void pair_step(const StepPair<V>& q, Gf gather, Emit 
   if ((q.fl & (1u << 7)) && (nz(ta) || nz(tb))) emit(q.kt, ta, tb);
 }
 
-// Exact row sums of FP64 values on the integer pipe (GB300 issues FP64 at
-// 1/64 of the FP32 rate, and a warp pays for an FP64 instruction whichever of
-// its lanes use it).  The values of one row's run of lanes are turned into
-// 64-bit fixed-point numbers with 55 fraction bits below the run's largest
-// binary exponent em (truncated there, an error below 2^(em - 1078) each), the
-// fixed-point numbers (at most 65: two per lane and an incoming tail, so
-// below 2^63 in total) are added exactly, and the total is rounded to FP64
-// once.  The error stays below 65 ulp of the largest value at 2^-55 each,
-// where FP64 additions in any order can lose (n - 1) 2^-53 of the sum of the
-// magnitudes.  Subnormal values count as zero.
-__device__ __forceinline__ int fx_exp(double v) {  // biased exponent (0: zero, subnormal)
-  return (__double2hiint(v) >> 20) & 0x7ff;
-}
-__device__ __forceinline__ long long fx_of(double v, int em) {
-  const long long b = __double_as_longlong(v);
-  const int ex = (int)((b >> 52) & 0x7ff);
-  if (ex == 0) return 0;
-  const long long m = (b & 0xfffffffffffffLL) | 0x10000000000000LL;  // 53-bit significand
-  const int sh = ex - em + 3;  // v * 2^(1078 - em) = m * 2^sh, sh <= 3
-  const long long f = sh >= 0 ? (m << sh) : (sh > -54 ? (m >> -sh) : 0);
-  return b < 0 ? -f : f;
-}
-// t * 2^(em - 1078), rounded once
-__device__ __forceinline__ double fx_value(long long t, int em) {
-  if (t == 0) return 0.0;
-  const double d = (double)t;  // |t| < 2^63: one rounding
-  if (em >= 56 && em < 1960) {
-    // the power of two is exact: add it to the exponent field (the result stays normal)
-    return __longlong_as_double(__double_as_longlong(d) + ((long long)(em - 1078) << 52));
-  }
-  return ldexp(d, em - 1078);
-}
-
+// Exact row sums of FP64 values on the integer pipe (fx64.h): the values of
+// one row's run of lanes (at most 65: two per lane and an incoming tail, so
+// below 2^63 in total) are turned into 64-bit fixed-point numbers with 55
+// fraction bits below the run's largest binary exponent, added exactly, and
+// the total is rounded to FP64 once.  The error stays below 65 * 2^-55 of the
+// largest value, where FP64 additions in any order can lose (n - 1) 2^-53 of
+// the sum of the magnitudes.
 // pair_step for FP64 vectors with the row sums formed exactly as above: the
 // run's largest exponent goes through the same shuffle tree (integer max) and
 // back to every lane of the run from its first lane, then the fixed-point
