@@ -643,6 +643,9 @@ simrank_status run_rank_one(simrank_ctx* h, int64_t src_off, int delta, int j, i
     pp.op = op;
     pp.d_j = d_j;
     pp.C = C;
+    pp.inv_C = 1.0 / C;
+    pp.inv_delta = 1.0 / (double)delta;
+    pp.gq = (d_j + op * delta) != 0 ? (double)delta / (double)(d_j + op * delta) : 0.0;
     pp.K = h->cfg.K;
     pp.nT = nT;
     if (defer) {

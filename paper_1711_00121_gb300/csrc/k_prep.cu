@@ -573,11 +573,11 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
   __shared__ V2<V> fsh[PG][2];      // flat split: the same for each thread's head / tail row
   __shared__ unsigned long long mk[PREP_MT][2];
   __shared__ int wsum[PG / 32];
-  __shared__ int s_ok;
+  __shared__ int s_ok, s_div;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int G = gridDim.x;
   const int nT = p.nT;
-  const int mt = (nT + G - 1) / G;
+  const int mt = p.mt;
   // dynamic shared memory: item slots, column cache, item offsets, pending coefficients
   PrepItem* items = reinterpret_cast<PrepItem*>(dsm);
   int* cc = reinterpret_cast<int*>(items + (MAXI + 1));
@@ -690,7 +690,10 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
       const int per = (nT + PG - 1) / PG;
       const int t0 = min(nT, tid * per), t1 = min(nT, t0 + per);
       int s = 0;
-      for (int T = t0; T < t1; ++T) s += (__ldcg(p.tile_nnz + T) + div - 1) / div;
+      for (int T = t0; T < t1; ++T) {
+        const int c = __ldcg(p.tile_nnz + T);
+        s += div == 1 ? c : (c + div - 1) / div;
+      }
       int incl = s;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -708,13 +711,20 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
           if (lane >= o) w += y;
         }
         if (lane < PG / 32) wsum[lane] = w - v;
-        if (lane == PG / 32 - 1) ioff[nT] = w;
+        if (lane == PG / 32 - 1) {
+          ioff[nT] = w;
+          // the CTA's share, by one thread (a division would be issued by
+          // every thread): nonzeros per CTA (flat pass) or this CTA's items
+          const int b = (int)blockIdx.x;
+          s_div = pass == 0 ? (w + G - 1) / G : (w > b ? (w - b + G - 1) / G : 0);
+        }
       }
       __syncthreads();
       int run = wsum[warp] + incl - s;
       for (int T = t0; T < t1; ++T) {
         ioff[T] = run;
-        run += (__ldcg(p.tile_nnz + T) + div - 1) / div;
+        const int c = __ldcg(p.tile_nnz + T);
+        run += div == 1 ? c : (c + div - 1) / div;
       }
       __syncthreads();
       if (pass == 0) {
@@ -736,8 +746,7 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
                  [&](int r, V a, V) { red_add(&W[r].x, a); });
     alive = prep_barrier(p.bar, ++nb * G, p.limit, &s_ok);
   } else if (alive) {
-    const int n_items = ioff[nT];
-    my_items = (n_items > (int)blockIdx.x) ? (n_items - (int)blockIdx.x + G - 1) / G : 0;
+    my_items = s_div;
     int cbase = 0;
     for (int u = 0; u < my_items; ++u) {
       PrepItem& it = items[min(u, MAXI)];
@@ -812,12 +821,13 @@ __global__ void __launch_bounds__(PG, 2) k_prep(PrepParams p) {
           }
           g = (V)gd;
         } else {
-          const V w = (len > 0) ? y / ((V)p.delta * (V)len) : V(0);
+          const V w = y * inv * (V)p.inv_delta;
           const V sJa = __ldcg(sJ + a);
+          const V sc = sJa * (V)p.inv_C;
           if (p.op > 0) {
-            g = (p.d_j == 0) ? w : ((V)p.delta / (V)(p.d_j + p.delta)) * (w - sJa / Cv);
+            g = (p.d_j == 0) ? w : (V)p.gq * (w - sc);
           } else {
-            g = (p.d_j == p.delta) ? -w : ((V)p.delta / (V)(p.d_j - p.delta)) * (sJa / Cv - w);
+            g = (p.d_j == p.delta) ? -w : (V)p.gq * (sc - w);
           }
         }
         const V x0 = (a == p.j) ? Cv : V(0);
@@ -1007,6 +1017,7 @@ int launch_prep(const PrepParams& prm, int s_prec, int vec64, int npend_max, int
   if (prm.npend > npend_max) return 1;
   PrepParams a = prm;
   if (a.item == 0) a.item = 1024;
+  a.mt = (prm.nT + grid - 1) / grid;
   void* args[] = {&a};
   if (cudaLaunchCooperativeKernel(fn, grid, PG, args, smem, st) != cudaSuccess) return 1;
   return 0;

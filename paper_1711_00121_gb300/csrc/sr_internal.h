@@ -153,6 +153,11 @@ struct PrepParams {
   const int32_t* I;
   int delta, j, op, d_j;
   double C;
+  // quotients that are the same for every row, computed once on the host (a
+  // division in the kernel would be issued by every thread): 1 / C, 1 / delta
+  // and delta / (d_j + op delta) (0 when that sum is 0)
+  double inv_C, inv_delta, gq;
+  int mt;  // tiles per CTA, ceil(nT / grid) (set by launch_prep)
   int K;
   int nT;
   void* P;
