@@ -47,8 +47,10 @@ METRIC = "edge updates/sec & HBM GB/s: fused rank-2K ΔS vs plain Inc-uSR at 1e-
 UNIT = "edge updates/s"
 # DRAM bytes (read + write) per launch from one ncu capture of each kernel on
 # the default stream configuration (profiles/ holds the summaries)
-TRAFFIC_PREP = 6.141e7
+TRAFFIC_PREP = 6.137e7
 TRAFFIC_S_PASS = 1.828e9
+# the per-update S pass (--defer 0 replica, FP16 split): a typical launch
+TRAFFIC_S_PASS_EDGE = 1.417e9
 
 
 def workload_name(args):
@@ -505,6 +507,8 @@ def run_gpu(args, rank, world):
                        "bytes_per_launch": pe_bytes / max(pe_launches, 1),
                        "aff_tile_fraction": (e1["tiles_touched"] - e0["tiles_touched"])
                        / max(e1["tiles_total"] - e0["tiles_total"], 1),
+                       "traffic": (TRAFFIC_S_PASS_EDGE if (N, K, args.tc) == (20000, 20, 2)
+                                   else None),
                        "note": "each update's S change applied alone (--defer 0), S bytes of the "
                                "touched upper tiles read + written, plus the operands once"}
     dominant = s_pass if sp_ms >= prep_ms else prep
