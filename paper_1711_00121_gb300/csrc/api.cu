@@ -101,7 +101,7 @@ struct simrank_ctx {
   struct Buf {
     void* p = nullptr;
     size_t bytes = 0;
-  } ob[26];
+  } ob[27];
   // column mode: per-tile nonzeros of the in-lists (host), the work-item table
   // of the chain steps and its partial-sum accumulators (device)
   std::vector<int64_t> col_tnnz;
@@ -891,6 +891,9 @@ simrank_status ob_ensure(simrank_ctx* h, int slot, size_t bytes) {
   return SR_OK;
 }
 
+void build_chunks(const HostAdj& A, int n_rows, std::vector<RowChunk>& out,
+                  std::vector<int64_t>* first);
+
 // The whole batch as one rank-2r update (proof of Thm 2 with dQ = U V^T over
 // the r distinct sinks).  `plus` / `minus` hold the net insertions and
 // deletions per sink (storage ids); `ops` turn the old graph into the new one.
@@ -1001,6 +1004,15 @@ simrank_status run_one_shot(simrank_ctx* h, const std::map<int32_t, std::vector<
   launch_transpose_rect(Wc, n_pad, X + rp, ldx, r, n_pad, h->st);
   LAUNCH_CHECK(h);
   h->launches += 3;
+  // the steps below gather by row chunks of the new graph (the host mirror
+  // holds it), so that a hub row spreads over many warps
+  std::vector<RowChunk> chv;
+  build_chunks(h->hin, n_pad, chv, nullptr);
+  if ((s = ob_ensure(h, 26, std::max<size_t>(1, chv.size()) * sizeof(RowChunk))) != SR_OK) return s;
+  const RowChunk* d_chunks = (const RowChunk*)h->ob[26].p;
+  if (!chv.empty())
+    CUDA_TRY(h, cudaMemcpyAsync(h->ob[26].p, chv.data(), chv.size() * sizeof(RowChunk),
+                                cudaMemcpyHostToDevice, h->st));
 
   // k-groups: as many terms per S pass as fit an operand budget
   const bool tc = h->cfg.tc != 0 && sp == 32;
@@ -1023,9 +1035,12 @@ simrank_status run_one_shot(simrank_ctx* h, const std::map<int32_t, std::vector<
   int slot = 0;
   for (int k = 0; k <= h->cfg.K; ++k) {
     if (k > 0) {
-      launch_spmm_rows(h->din, nullptr, nullptr, X, 64, ldx, Xn, 64, ldx, n_pad, rp, C, 0.0, 0, h->st);
-      launch_spmm_rows(h->din, nullptr, nullptr, X + rp, 64, ldx, Xn + rp, 64, ldx, n_pad, rp, 1.0,
-                       0.0, 0, h->st);
+      CUDA_TRY(h, cudaMemsetAsync(Xn, 0, (size_t)nr * 2 * 8, h->st));
+      if (launch_spmm_chunks64(d_chunks, (int64_t)chv.size(), h->din.col, h->din.len, X, ldx, Xn,
+                               ldx, rp, C, h->st) != 0 ||
+          launch_spmm_chunks64(d_chunks, (int64_t)chv.size(), h->din.col, h->din.len, X + rp,
+                               ldx, Xn + rp, ldx, rp, 1.0, h->st) != 0)
+        return fail(h, SR_ERR_CUDA, "chunked SpMM: bad shape");
       std::swap(X, Xn);
       h->launches += 2;
     }

@@ -350,3 +350,81 @@ void launch_pack_tc(const double* X, int64_t ldx, int rh, int r, int slot, int r
 }
 
 }  // namespace sr
+
+namespace sr {
+namespace {
+
+// Y[row][c] += scale / len(row) * sum_{e in chunk} X[col_e][c] (Q times a
+// block of columns, in FP64), for the column quads c = 4 q < ncols; Y zeroed by
+// the caller.  A group of LPC lanes takes one row chunk (at most kChunk
+// nonzeros), lane l of the group the quad blockIdx.y * LPC + l, so a long row
+// is spread over many groups and meets in atomics.
+template <int LPC>
+__global__ void __launch_bounds__(256) k_spmm_chunks64(const RowChunk* __restrict__ chunks,
+                                                       int64_t count,
+                                                       const int32_t* __restrict__ col,
+                                                       const int32_t* __restrict__ len,
+                                                       const double* __restrict__ X, int64_t ldx,
+                                                       double* __restrict__ Y, int64_t ldy,
+                                                       int ncols, double scale) {
+  const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LPC;
+  const int c0 = 4 * ((int)blockIdx.y * LPC + (int)(threadIdx.x % LPC));
+  if (q >= count || c0 >= ncols) return;
+  const RowChunk ch = chunks[q];
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int e = 0;
+  for (; e + 2 <= ch.len; e += 2) {
+    const int b0 = __ldg(col + ch.start + e), b1 = __ldg(col + ch.start + e + 1);
+    const double2* p0 = reinterpret_cast<const double2*>(X + (int64_t)b0 * ldx + c0);
+    const double2* p1 = reinterpret_cast<const double2*>(X + (int64_t)b1 * ldx + c0);
+    const double2 u0 = p0[0], v0 = p0[1], u1 = p1[0], v1 = p1[1];
+    a0 += u0.x + u1.x;
+    a1 += u0.y + u1.y;
+    a2 += v0.x + v1.x;
+    a3 += v0.y + v1.y;
+  }
+  if (e < ch.len) {
+    const int b0 = __ldg(col + ch.start + e);
+    const double2* p0 = reinterpret_cast<const double2*>(X + (int64_t)b0 * ldx + c0);
+    const double2 u0 = p0[0], v0 = p0[1];
+    a0 += u0.x;
+    a1 += u0.y;
+    a2 += v0.x;
+    a3 += v0.y;
+  }
+  const double rs = scale / (double)len[ch.row];
+  double* y = Y + (int64_t)ch.row * ldy + c0;
+  atomicAdd(y + 0, rs * a0);
+  atomicAdd(y + 1, rs * a1);
+  atomicAdd(y + 2, rs * a2);
+  atomicAdd(y + 3, rs * a3);
+}
+
+template <int LPC>
+void spmm_chunks64_t(const RowChunk* chunks, int64_t count, const int32_t* col,
+                     const int32_t* len, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                     int ncols, double scale, cudaStream_t st) {
+  const int quads = ncols / 4;
+  const dim3 grid((unsigned)((count * LPC + 255) / 256), (unsigned)((quads + LPC - 1) / LPC));
+  k_spmm_chunks64<LPC><<<grid, 256, 0, st>>>(chunks, count, col, len, X, ldx, Y, ldy, ncols,
+                                              scale);
+}
+
+}  // namespace
+
+int launch_spmm_chunks64(const RowChunk* chunks, int64_t count, const int32_t* col,
+                         const int32_t* len, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                         int ncols, double scale, cudaStream_t st) {
+  if (ncols % 4 || ldx % 2 || ldy % 2 || ((uintptr_t)X & 15)) return 1;
+  if (count <= 0 || ncols <= 0) return 0;
+  const int quads = ncols / 4;
+  if (quads <= 8)
+    spmm_chunks64_t<8>(chunks, count, col, len, X, ldx, Y, ldy, ncols, scale, st);
+  else if (quads <= 16)
+    spmm_chunks64_t<16>(chunks, count, col, len, X, ldx, Y, ldy, ncols, scale, st);
+  else
+    spmm_chunks64_t<32>(chunks, count, col, len, X, ldx, Y, ldy, ncols, scale, st);
+  return 0;
+}
+
+}  // namespace sr

@@ -359,6 +359,12 @@ struct ChunkList {
   RowChunk* chunks = nullptr;  // device
   int64_t count = 0;
 };
+// Y[a][c] += scale / len(a) * sum over a's in-list of X[b][c], columns c <
+// ncols (a multiple of 4), by row chunks (FP64 atomics into Y, which the
+// caller zeroes); X 16-byte aligned with even ldx.  Returns 1 for a bad shape.
+int launch_spmm_chunks64(const RowChunk* chunks, int64_t count, const int32_t* col,
+                         const int32_t* len, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                         int ncols, double scale, cudaStream_t st);
 // Edge weights of a weighted Q (all null: Q[a][b] = 1 / in-degree(a)):
 // out_w / in_w give the weight of each out-list / in-list entry by pool
 // position, wsum[a] the total in-weight of a.

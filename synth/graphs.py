@@ -298,7 +298,9 @@ def batch_with_new_nodes(n: int, src, dst, b: int, seed: int, frac_new: float = 
     target already created in this batch, so some new sinks receive several
     edges.  New node ids are n_cur, n_cur+1, ... in order of first use.  The
     remaining edges are updates between existing nodes (``frac_insert``
-    insertions, the rest deletions), drawn as in :func:`update_stream`.
+    insertions, the rest deletions of edges that existed before the batch),
+    drawn as in :func:`update_stream`; the batch is returned in a random
+    order, so a deletion never targets an edge the batch inserts.
     Returns (updates int32 (b,3), number of new nodes).
     """
     rng = np.random.default_rng(seed)
@@ -311,6 +313,7 @@ def batch_with_new_nodes(n: int, src, dst, b: int, seed: int, frac_new: float = 
     draw_dst = _Sampler(g.in_deg[:n_old] + 1.0, rng)
     ups = []
     new_targets = []
+    fresh = set()  # edges this batch inserts
     for kind in kinds:
         if kind == 0:  # source new, target old
             i = g.add_node()
@@ -333,6 +336,7 @@ def batch_with_new_nodes(n: int, src, dst, b: int, seed: int, frac_new: float = 
                 j = g.add_node()
                 new_targets.append(j)
         g.insert(i, j)
+        fresh.add((i, j))
         ups.append((i, j, UPDATE_INSERT))
     for _ in range(b - n_new_edges):
         if rng.random() < frac_insert or not g.edges:
@@ -342,11 +346,12 @@ def batch_with_new_nodes(n: int, src, dst, b: int, seed: int, frac_new: float = 
                 if i != j and not g.has(i, j):
                     break
             g.insert(i, j)
+            fresh.add((i, j))
             ups.append((i, j, UPDATE_INSERT))
         else:
             while True:
                 i, j = g.edges[int(rng.integers(0, len(g.edges)))]
-                if i < n_old and j < n_old:
+                if i < n_old and j < n_old and (i, j) not in fresh:
                     break
             g.delete(i, j)
             ups.append((i, j, UPDATE_DELETE))
