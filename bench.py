@@ -1047,7 +1047,7 @@ def run_tune(args):
         out["stream"][f"vec_fp64={v}"] = {"knobs": r["knobs"], "us_per_update": r["us_per_update"],
                                           "candidates": len(r["measured"])}
     rng = np.random.default_rng(M_SEED)
-    sizes = rng.integers(MN_LO, MN_HI + 1, size=args.graphs)[:64]
+    sizes = rng.integers(MN_LO, MN_HI + 1, size=args.graphs)[:128]
     graphs = [(int(n), *chung_lu_digraph(int(n), MDEG * int(n), 2.1, 2.1, M_SEED * 100000 + g))
               for g, n in enumerate(sizes)]
     graphs = [(n, s_, d_) for n, s_, d_ in graphs]
