@@ -101,7 +101,7 @@ struct simrank_ctx {
   struct Buf {
     void* p = nullptr;
     size_t bytes = 0;
-  } ob[27];
+  } ob[28];
   // column mode: per-tile nonzeros of the in-lists (host), the work-item table
   // of the chain steps and its partial-sum accumulators (device)
   std::vector<int64_t> col_tnnz;
@@ -1015,17 +1015,23 @@ simrank_status run_one_shot(simrank_ctx* h, const std::map<int32_t, std::vector<
                                 cudaMemcpyHostToDevice, h->st));
 
   // k-groups: as many terms per S pass as fit an operand budget
+  // tc = 2: FP16 split, terms balanced by powers of two (rg a multiple of 64);
+  // tc = 1: TF32 split (rg a multiple of 32)
   const bool tc = h->cfg.tc != 0 && sp == 32;
+  const bool f16 = tc && h->cfg.tc == 2;
+  const int ra = f16 ? 64 : 32;
+  const size_t eb = f16 ? 2 : 4;
   const int nT = (h->n_cur + PT - 1) / PT;
   const size_t budget = (size_t)8 << 30;
-  const size_t per_k = tc ? (size_t)n_pad * 2 * (size_t)((r + 31) / 32 * 32) * 4 * 2
+  const size_t per_k = tc ? (size_t)n_pad * 2 * (size_t)((r + ra - 1) / ra * ra) * eb * 2
                           : (size_t)n_pad * 2 * (size_t)r * (sp == 64 ? 8 : 4);
   const int g = (int)std::max<size_t>(1, std::min<size_t>((size_t)h->K1, budget / per_k));
-  const int rg = tc ? ((g * r + 31) / 32) * 32 : g * r;
+  const int rg = tc ? ((g * r + ra - 1) / ra) * ra : g * r;
   const int64_t kd = 2 * (int64_t)rg;
   if (tc) {
-    if ((s = ob_ensure(h, 8, (size_t)n_pad * kd * 4)) != SR_OK) return s;
-    if ((s = ob_ensure(h, 9, (size_t)n_pad * kd * 4)) != SR_OK) return s;
+    if ((s = ob_ensure(h, 8, (size_t)n_pad * kd * eb)) != SR_OK) return s;
+    if ((s = ob_ensure(h, 9, (size_t)n_pad * kd * eb)) != SR_OK) return s;
+    if (f16 && (s = ob_ensure(h, 27, 2 * (size_t)r * sizeof(unsigned int))) != SR_OK) return s;
   } else {
     if ((s = ob_ensure(h, 8, (size_t)h->nT_cap * 2 * (size_t)(g * r) * PT * (sp == 64 ? 8 : 4))) !=
         SR_OK)
@@ -1046,14 +1052,17 @@ simrank_status run_one_shot(simrank_ctx* h, const std::map<int32_t, std::vector<
     }
     if (slot == 0) {
       if (tc) {
-        CUDA_TRY(h, cudaMemsetAsync(h->ob[8].p, 0, (size_t)n_pad * kd * 4, h->st));
-        CUDA_TRY(h, cudaMemsetAsync(h->ob[9].p, 0, (size_t)n_pad * kd * 4, h->st));
+        CUDA_TRY(h, cudaMemsetAsync(h->ob[8].p, 0, (size_t)n_pad * kd * eb, h->st));
+        CUDA_TRY(h, cudaMemsetAsync(h->ob[9].p, 0, (size_t)n_pad * kd * eb, h->st));
       } else {
         CUDA_TRY(h, cudaMemsetAsync(h->mXi, 0, h->nT_cap * sizeof(uint64_t), h->st));
         CUDA_TRY(h, cudaMemsetAsync(h->mEta, 0, h->nT_cap * sizeof(uint64_t), h->st));
       }
     }
-    if (tc)
+    if (f16)
+      launch_pack_f16_oneshot(X, ldx, rp, r, slot, rg, n_pad, (unsigned int*)h->ob[27].p,
+                              h->ob[8].p, h->ob[9].p, kd, h->st);
+    else if (tc)
       launch_pack_tc(X, ldx, rp, r, slot, rg, n_pad, (float*)h->ob[8].p, (float*)h->ob[9].p, kd,
                      h->st);
     else
@@ -1077,11 +1086,9 @@ simrank_status run_one_shot(simrank_ctx* h, const std::map<int32_t, std::vector<
       }
       if (tc) {
         const int rc = launch_s_update_tc((float*)h->S, h->ld, h->ob[8].p, h->ob[9].p, n_pad,
-                                          kd, tile_order(h, kd * 4), h->order_n, nullptr, 0,
-                                          h->mXi,
-                                          h->mEta, 0,
-                                          h->n_cur, h->counters, h->num_sms, wait_limit, h->st,
-                                          upper(h));
+                                          kd, tile_order(h, kd * (int64_t)eb), h->order_n,
+                                          nullptr, 0, h->mXi, h->mEta, 0, h->n_cur, h->counters,
+                                          h->num_sms, wait_limit, h->st, upper(h), f16 ? 1 : 0);
         if (rc != 0) return fail(h, SR_ERR_CUDA, "tensor-core S update: launch setup failed");
       } else {
         const bool ws = sp == 32 && h->cfg.s_kernel == 0;

@@ -400,6 +400,57 @@ __global__ void __launch_bounds__(256) k_spmm_chunks64(const RowChunk* __restric
   atomicAdd(y + 3, rs * a3);
 }
 
+// Largest |value| of every term column of the one-shot block X (FP64
+// [n_rows][ldx]): maxes[c] for xi column c < r, maxes[r + c] for the W column
+// rh + c, as the bits of an FP32 magnitude (non-negative floats order like
+// their bits).  Block (32, 8): a lane per column, 8 row phases.
+__global__ void __launch_bounds__(256) k_oneshot_max(const double* __restrict__ X, int64_t ldx,
+                                                     int rh, int r, int n_rows,
+                                                     unsigned int* __restrict__ maxes) {
+  __shared__ float red[8][32];
+  const int c2 = blockIdx.x * 32 + threadIdx.x;
+  float m = 0.f;
+  if (c2 < 2 * r) {
+    const int which = c2 >= r ? 1 : 0;
+    const int64_t col = (int64_t)which * rh + (c2 - which * r);
+    for (int64_t a = (int64_t)blockIdx.y * 8 + threadIdx.y; a < n_rows; a += (int64_t)gridDim.y * 8)
+      m = fmaxf(m, (float)fabs(X[a * ldx + col]));
+  }
+  red[threadIdx.y][threadIdx.x] = m;
+  __syncthreads();
+  if (threadIdx.y == 0 && c2 < 2 * r) {
+#pragma unroll
+    for (int y = 1; y < 8; ++y) m = fmaxf(m, red[y][threadIdx.x]);
+    if (m > 0.f) atomicMax(&maxes[c2], __float_as_uint(m));
+  }
+}
+
+// FP16 tensor-core operands of the one-shot update from X_k: term t of the
+// slot (xi column t, W column rh + t) goes to columns slot * r + t and
+// rg + slot * r + t of A_hi / A_lo, after scaling the xi column by 2^e and the
+// W column by 2^-e, e = (exponent of max |W_t| - exponent of max |xi_t|) / 2:
+// their product is unchanged (powers of two are exact) and both share one
+// magnitude inside FP16's range.  x = hi + lo, hi = fp16(x), lo = fp16(x - hi).
+__global__ void k_pack_f16_oneshot(const double* __restrict__ X, int64_t ldx, int rh, int r,
+                                   int slot, int rg, int n_rows,
+                                   const unsigned int* __restrict__ maxes,
+                                   __half* __restrict__ Ahi, __half* __restrict__ Alo, int64_t kd) {
+  const int64_t a = blockIdx.x;
+  const int t = blockIdx.y * blockDim.x + threadIdx.x;
+  if (t >= r || a >= n_rows) return;
+  const float mx = __uint_as_float(maxes[t]), me = __uint_as_float(maxes[r + t]);
+  const int e = (mx > 0.f && me > 0.f) ? (ilogbf(me) - ilogbf(mx)) / 2 : 0;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const double x = ldexp(X[a * ldx + (int64_t)h * rh + t], h ? -e : e);
+    const __half hi = __double2half(x);
+    const __half lo = __double2half(x - (double)__half2float(hi));
+    const int64_t c = (int64_t)h * rg + (int64_t)slot * r + t;
+    Ahi[a * kd + c] = hi;
+    Alo[a * kd + c] = lo;
+  }
+}
+
 template <int LPC>
 void spmm_chunks64_t(const RowChunk* chunks, int64_t count, const int32_t* col,
                      const int32_t* len, const double* X, int64_t ldx, double* Y, int64_t ldy,
@@ -411,6 +462,17 @@ void spmm_chunks64_t(const RowChunk* chunks, int64_t count, const int32_t* col,
 }
 
 }  // namespace
+
+void launch_pack_f16_oneshot(const double* X, int64_t ldx, int rh, int r, int slot, int rg,
+                             int n_rows, unsigned int* maxes, void* Ahi, void* Alo, int64_t kd,
+                             cudaStream_t st) {
+  cudaMemsetAsync(maxes, 0, 2 * (size_t)r * sizeof(unsigned int), st);
+  const dim3 mg((unsigned)((2 * r + 31) / 32), 64), mb(32, 8);
+  k_oneshot_max<<<mg, mb, 0, st>>>(X, ldx, rh, r, n_rows, maxes);
+  const dim3 grid((unsigned)n_rows, (unsigned)((r + 127) / 128));
+  k_pack_f16_oneshot<<<grid, 128, 0, st>>>(X, ldx, rh, r, slot, rg, n_rows, maxes, (__half*)Ahi,
+                                           (__half*)Alo, kd);
+}
 
 int launch_spmm_chunks64(const RowChunk* chunks, int64_t count, const int32_t* col,
                          const int32_t* len, const double* X, int64_t ldx, double* Y, int64_t ldy,

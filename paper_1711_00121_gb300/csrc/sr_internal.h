@@ -309,6 +309,11 @@ void launch_pack_ffma(const double* X, int64_t ldx, int rh, int r, int slot, int
                       void* Pn, int p_prec, uint64_t* mXi, uint64_t* mEta, cudaStream_t st);
 void launch_pack_tc(const double* X, int64_t ldx, int rh, int r, int slot, int rg, int n_rows,
                     float* Ahi, float* Alo, int64_t kd, cudaStream_t st);
+// The same operands in FP16 with each term balanced by a power of two
+// (maxes: 2 r unsigned ints of scratch).
+void launch_pack_f16_oneshot(const double* X, int64_t ldx, int rh, int r, int slot, int rg,
+                             int n_rows, unsigned int* maxes, void* Ahi, void* Alo, int64_t kd,
+                             cudaStream_t st);
 // Operand rows at least this wide (bytes) make the tensor-core S pass bound by
 // the tensor cores rather than by the S stream.
 constexpr int64_t TC_WIDE_K_BYTES = 1024;

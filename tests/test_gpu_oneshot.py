@@ -56,7 +56,7 @@ def test_one_shot_fp64_vs_definition(P):
     assert maxabs(sr.dense(), want) < TOL64
 
 
-@pytest.mark.parametrize("tc", [0, 1])
+@pytest.mark.parametrize("tc", [0, 1, 2])
 def test_one_shot_fp32_vs_definition(P, tc):
     n, m, C, K = 1100, 8800, 0.8, 12
     s, d, S, ups, n_final, Sp, ns, nd = setup(n, m, 32, 96, 0.1, C, powerlaw=True)
@@ -89,12 +89,13 @@ def test_one_shot_tc_matches_ffma_many_chunks(P):
             have.add((i, j))
             ups.append((i, j, 1))
     res = []
-    for tc in (0, 1):
+    for tc in (0, 1, 2):
         sr = P.SimRank(n, s, d, C=C, K=K, s_precision=32, apply=P.APPLY_ONE_SHOT, tc=tc)
         sr.apply_updates(ups)
         sr.sync()
         res.append(sr.dense())
     assert maxabs(res[0], res[1]) < TOL32
+    assert maxabs(res[0], res[2]) < TOL32
     S = O.simrank_fixed_point(O.transition_matrix(n, s, d, sparse=True), C, tol=1e-15)
     plus, minus = O.net_update(ups)
     new = (set(edges) | set(plus)) - set(minus)
@@ -102,6 +103,7 @@ def test_one_shot_tc_matches_ffma_many_chunks(P):
     nd = np.array([bb for _, bb in new], np.int64)
     want = O.one_shot_batch(n, s, d, ns, nd, S, C, K)
     assert maxabs(res[1], want) < TOL32
+    assert maxabs(res[2], want) < TOL32
 
 
 def test_one_shot_converges_to_batch_recompute(P):
