@@ -90,10 +90,10 @@ typedef struct simrank_config {
   int32_t apply;          /* SR_APPLY_* */
   int32_t s_update;       /* SR_SUPDATE_* */
   int32_t tc;             /* S passes on the tensor cores: 1 = 3xTF32 split, 2 = 3xFP16 split with
-                             an exact power-of-two balancing of each term (twice the tensor rate;
-                             the one-shot form keeps TF32); used for the one-shot batch form's
-                             pass and, with FP32 S, for the pass of every unit / sink-block update
-                             (or of every group of `defer` pending updates); 0 = CUDA cores */
+                             an exact power-of-two balancing of each term (twice the tensor rate);
+                             used, with FP32 S, for the one-shot batch form's pass and for the
+                             pass of every unit / sink-block update (or of every group of `defer`
+                             pending updates); 0 = CUDA cores */
   int32_t init_max_sweeps;/* cap on Jacobi sweeps of Eq. 1 at init / re-anchor */
   double init_tol;        /* init stops when a sweep changes S by less than this (max-abs);
                              <= 0 selects 1e-13 (sweeps stored in FP32 stop at 1e-7 or at
