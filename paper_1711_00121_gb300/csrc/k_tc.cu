@@ -506,14 +506,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const float* bsrc = sD + (lane >> 3) * (TM * 32);
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-          const int r = ew + 8 * q;
+          const int tr = ew + 8 * q;
           const float4 d =
-              *reinterpret_cast<const float4*>(bsrc + r * 32 + (((lane & 7) ^ (r & 7)) * 4));
+              *reinterpret_cast<const float4*>(bsrc + tr * 32 + (((lane & 7) ^ (tr & 7)) * 4));
           sv[q].x += d.x;
           sv[q].y += d.y;
           sv[q].z += d.z;
           sv[q].w += d.w;
-          *reinterpret_cast<float4*>(S + (int64_t)(I * TM + r) * ld + (int64_t)J * TN +
+          *reinterpret_cast<float4*>(S + (int64_t)(I * TM + tr) * ld + (int64_t)J * TN +
                                      lane * 4) = sv[q];
         }
       } else {
@@ -536,18 +536,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         float4 v[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-          const int r = ew + 8 * q;
-          v[q] = *reinterpret_cast<const float4*>(S + (int64_t)(I * TM + r) * ld + (int64_t)J * TN + lane * 4);
+          const int tr = ew + 8 * q;
+          v[q] = *reinterpret_cast<const float4*>(S + (int64_t)(I * TM + tr) * ld + (int64_t)J * TN + lane * 4);
         }
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-          const int r = ew + 8 * q;
-          const float* d = sD + r * EP + lane * 4;
+          const int tr = ew + 8 * q;
+          const float* d = sD + tr * EP + lane * 4;
           v[q].x += d[0];
           v[q].y += d[1];
           v[q].z += d[2];
           v[q].w += d[3];
-          *reinterpret_cast<float4*>(S + (int64_t)(I * TM + r) * ld + (int64_t)J * TN + lane * 4) = v[q];
+          *reinterpret_cast<float4*>(S + (int64_t)(I * TM + tr) * ld + (int64_t)J * TN + lane * 4) = v[q];
         }
       }
       if (MIRROR && I != J) {
